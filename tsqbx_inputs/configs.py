@@ -1,0 +1,139 @@
+"""The synthetic workloads (seeded).  Base seed 20191114; config i uses seed+i.
+
+  sphere      -- Laplace SLP p=5: icosphere (3 subdivisions, 1280 flat triangles),
+                 6 nodes per triangle, one center per node (alternating sides),
+                 radius lists of 4h.
+  torus       -- Laplace SLP+DLP p=9: torus R=1, r=0.35, 256 x 96 quads
+                 (49,152 triangles, 294,912 sources), 2 centers per node,
+                 GIGAQBX octree lists with n_max=64, t_f=0.9, n_mpole=40.
+  torus_helm  -- Helmholtz SLP k=10 p=12: 444 x 166 quads (147,408 triangles,
+                 884,448 sources), octree lists as above, plane-wave density.
+  ellipsoids  -- 64 ellipsoids (semi-axes U(0.5,2)), log-uniform sizes, nearest
+                 lists of log-uniform length 50..800, p in {5,7,9}.
+Scaled-down variants (same recipe, fewer quads) serve the parity tests.
+"""
+import numpy as np
+
+from . import density as dens
+from . import lists as L
+from . import mesh
+from .geometry import Geometry
+
+BASE_SEED = 20191114
+
+
+def _surface_nodes(V, F, order_sources=True):
+    xyz, w, nrm, h, wex = mesh.nodes_on_triangles(V, F)
+    if order_sources:
+        perm = mesh.morton_order(xyz)
+        xyz, w, nrm, h, wex = xyz[perm], w[perm], nrm[perm], h[perm], wex[perm]
+    return xyz, w, nrm, h
+
+
+def _geometry_radius(xyz, w, nrm, h, signs, radius_factor):
+    C, Rr, T, Tn, node = mesh.centers_and_targets(xyz, nrm, h, signs)
+    grs, rb, re = L.radius_lists(xyz, C, radius_factor * h[node])
+    n = len(C)
+    return Geometry(np.ascontiguousarray(xyz.T), w, np.ascontiguousarray(nrm.T),
+                    np.ascontiguousarray(C.T), Rr, np.ascontiguousarray(T.T),
+                    np.arange(n, dtype=np.int32), np.ascontiguousarray(Tn.T),
+                    np.arange(n, dtype=np.int32), grs, rb, re)
+
+
+def _geometry_octree(xyz, w, nrm, h, signs, n_max=64, t_f=0.9, n_mpole=40):
+    C, Rr, T, Tn, node = mesh.centers_and_targets(xyz, nrm, h, signs)
+    tree, sperm, corder, cgroup, grs, rb, re = L.octree_lists(xyz, C, Rr, n_max, t_f, n_mpole)
+    xyz, w, nrm = xyz[sperm], w[sperm], nrm[sperm]
+    C, Rr, T, Tn = C[corder], Rr[corder], T[corder], Tn[corder]
+    n = len(C)
+    g = Geometry(np.ascontiguousarray(xyz.T), w, np.ascontiguousarray(nrm.T),
+                 np.ascontiguousarray(C.T), Rr, np.ascontiguousarray(T.T),
+                 np.arange(n, dtype=np.int32), np.ascontiguousarray(Tn.T),
+                 cgroup, grs, rb, re)
+    g.meta.update(n_boxes=int(tree.n_boxes), n_leaves=int(tree.is_leaf.sum()),
+                  max_level=int(tree.level.max()), n_max=n_max, t_f=t_f, n_mpole=n_mpole)
+    return g, tree
+
+
+def sphere(seed_offset=0, subdiv=3):
+    """Laplace SLP workload on the icosphere (radius lists of 4h)."""
+    rng = np.random.default_rng(BASE_SEED + 0 + seed_offset)
+    V, F = mesh.icosphere(subdiv)
+    F = mesh.orient_outward(V, F, lambda c: np.zeros_like(c))
+    xyz, w, nrm, h = _surface_nodes(V, F)
+    sign = np.where(np.arange(len(xyz)) % 2 == 0, 1.0, -1.0)
+    g = _geometry_radius(xyz, w, nrm, h, [sign], 4.0)
+    g.meta.update(name=f"sphere-ico{subdiv}", kernel="laplace", p=5)
+    return g, dens.sphere_density(xyz, rng)
+
+
+def torus(nu=256, nv=96, seed_offset=0, n_max=64):
+    """Laplace SLP+DLP workload on the torus with octree lists."""
+    rng = np.random.default_rng(BASE_SEED + 1 + seed_offset)
+    V, F = mesh.torus(nu, nv, 1.0, 0.35)
+    F = mesh.orient_outward(V, F, _torus_core)
+    xyz, w, nrm, h = _surface_nodes(V, F)
+    one = np.ones(len(xyz))
+    g, tree = _geometry_octree(xyz, w, nrm, h, [one, -one], n_max=n_max)
+    g.meta.update(name=f"torus-{nu}x{nv}", kernel="laplace", p=9)
+    src = g.src_xyz.T
+    return g, dens.harmonic_density(src, rng), tree
+
+
+def torus_helmholtz(nu=444, nv=166, k=10.0, seed_offset=0, n_max=64):
+    """Helmholtz SLP workload on the refined torus with octree lists."""
+    rng = np.random.default_rng(BASE_SEED + 2 + seed_offset)
+    V, F = mesh.torus(nu, nv, 1.0, 0.35)
+    F = mesh.orient_outward(V, F, _torus_core)
+    xyz, w, nrm, h = _surface_nodes(V, F)
+    one = np.ones(len(xyz))
+    g, tree = _geometry_octree(xyz, w, nrm, h, [one, -one], n_max=n_max)
+    g.meta.update(name=f"torus-{nu}x{nv}", kernel="helmholtz", p=12, k=k)
+    return g, dens.plane_wave_density(g.src_xyz.T, k, rng), tree
+
+
+def _torus_core(c, R=1.0):
+    """Nearest point of the torus core circle (radius R in the xy-plane)."""
+    rho = np.linalg.norm(c[:, :2], axis=1, keepdims=True)
+    core = np.zeros_like(c)
+    core[:, :2] = R * c[:, :2] / np.maximum(rho, 1e-300)
+    return core
+
+
+def ellipsoid(freq, axes, list_len_range=(50, 800), rng=None, seed_offset=0):
+    """One ellipsoid of the batched workload: geodesic sphere of frequency freq
+    scaled by axes, one center per node (alternating sides), nearest lists with
+    log-uniform lengths."""
+    rng = rng if rng is not None else np.random.default_rng(BASE_SEED + 3 + seed_offset)
+    V, F = mesh.geodesic_sphere(freq)
+    V = V * np.asarray(axes)[None, :]
+    F = mesh.orient_outward(V, F, lambda c: np.zeros_like(c))
+    xyz, w, nrm, h = _surface_nodes(V, F)
+    sign = np.where(np.arange(len(xyz)) % 2 == 0, 1.0, -1.0)
+    C, Rr, T, Tn, node = mesh.centers_and_targets(xyz, nrm, h, [sign])
+    lo, hi = np.log(list_len_range[0]), np.log(list_len_range[1])
+    counts = np.minimum(np.exp(rng.uniform(lo, hi, len(C))).astype(np.int64), len(xyz))
+    grs, rb, re = L.nearest_lists(xyz, C, counts)
+    n = len(C)
+    g = Geometry(np.ascontiguousarray(xyz.T), w, np.ascontiguousarray(nrm.T),
+                 np.ascontiguousarray(C.T), Rr, np.ascontiguousarray(T.T),
+                 np.arange(n, dtype=np.int32), np.ascontiguousarray(Tn.T),
+                 np.arange(n, dtype=np.int32), grs, rb, re)
+    g.meta.update(name=f"ellipsoid-f{freq}", kernel="laplace")
+    return g, dens.sphere_density(xyz, rng)
+
+
+def ellipsoid_batch(n_surfaces=64, min_src=1000, max_src=200000, seed_offset=0):
+    """The batched workload: n_surfaces seeded ellipsoids with log-uniform sizes
+    (120 f^2 sources for frequency f) and p uniform in {5, 7, 9}."""
+    rng = np.random.default_rng(BASE_SEED + 3 + seed_offset)
+    out = []
+    for _ in range(n_surfaces):
+        axes = rng.uniform(0.5, 2.0, 3)
+        target = np.exp(rng.uniform(np.log(min_src), np.log(max_src)))
+        freq = int(max(3, min(40, round(np.sqrt(target / 120.0)))))
+        p = int(rng.choice([5, 7, 9]))
+        g, mu = ellipsoid(freq, axes, rng=rng)
+        g.meta["p"] = p
+        out.append((g, mu))
+    return out
