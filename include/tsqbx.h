@@ -1,0 +1,209 @@
+/*
+ * tsqbx.h -- C ABI of libtsqbx: the near-field target-specific QBX (TSQBX)
+ * step of GIGAQBX (Wala & Kloeckner, arXiv:1811.01110), on one GB300 GPU.
+ *
+ * What one evaluation computes (Alg. 1 Stages 3, 5(a), 6(a); Sec. 2.6
+ * eq. tsqbx; Appendix A).  For every target t with QBX center c = center(t),
+ * and every source s listed in the pair list of c's group (List 1, List 3
+ * close and List 4 close of c's owning box, given as half-open index ranges,
+ * Sec. 3.2), the library adds w_s mu_s K^(p)(t, s) to the target's output,
+ * where K^(p) is the p-th order target-specific expansion about c:
+ *
+ *   Laplace single layer   G^(p)   = 1/(4 pi) sum_{n<=p} |t-c|^n / |s-c|^{n+1} P_n(cos g)
+ *   Laplace double layer   n_s . grad_s G^(p)                         (Appendix A)
+ *   Helmholtz single layer G_k^(p) = ik/(4 pi) sum_{n<=p} (2n+1) j_n(k|t-c|)
+ *                                     h_n(k|s-c|) P_n(cos g)         (Appendix A)
+ *
+ * g is the angle between s-c and t-c, j_n / h_n the spherical Bessel and
+ * Hankel functions of the first kind.  The result is the near part
+ * L^{qbx,near}_c(t) of the QBX local expansion at each target (Sec. 3.3); the
+ * far part is the caller's.  Pair lists are summed exactly as given:
+ * duplicated ranges count twice.
+ *
+ * Conventions for every entry point:
+ *  - Status: 0 (TSQBX_OK) on success, TSQBX_PENDING (1) from tsqbx_poll while
+ *    work is in flight, a negative TSQBX_E_* code on error.  No C++ exception
+ *    crosses the ABI; tsqbx_strerror() names every code.
+ *  - Arrays are structure-of-arrays: an "xyz [3][n]" array holds the n x
+ *    coordinates, then the n y, then the n z coordinates (doubles).
+ *  - Geometry pointers are HOST pointers, read only during tsqbx_plan_create
+ *    and owned by the caller; the plan keeps its own device copies.
+ *  - Density / output pointers may be host or device memory where stated.
+ *  - Every entry point is thread-safe with respect to different plans; calls
+ *    on one plan must not run concurrently from several host threads, except
+ *    tsqbx_poll.
+ */
+#ifndef TSQBX_H
+#define TSQBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TSQBX_API __attribute__((visibility("default")))
+#else
+#define TSQBX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Highest expansion order accepted (the paper's experiments use p <= 9 for
+ * Laplace and p = 4 for Helmholtz, Sec. 5). */
+#define TSQBX_P_MAX 20
+
+/* ---------------------------------------------------------------- status */
+enum {
+    TSQBX_OK = 0,
+    TSQBX_PENDING = 1,         /* tsqbx_poll: still running                        */
+    TSQBX_E_INVAL = -1,        /* bad sizes, null pointers, index out of range, p   */
+    TSQBX_E_DIVERGENT = -2,    /* a listed pair has |t-c| >= |s-c| or s == c        */
+    TSQBX_E_NOMEM = -3,        /* device or pinned-host allocation failed           */
+    TSQBX_E_CUDA = -4,         /* a CUDA runtime call failed                        */
+    TSQBX_E_TIMEOUT = -5,      /* tsqbx_poll: not done within the timeout           */
+    TSQBX_E_BUSY = -6,         /* tsqbx_submit: every slot of the plan is in flight */
+    TSQBX_E_NOTFOUND = -7,     /* unknown or already collected ticket               */
+    TSQBX_E_KERNEL = -8,       /* a kernel flagged an out-of-range index            */
+    TSQBX_E_UNSUPPORTED = -9   /* kernel/layer/precision combination not provided   */
+};
+
+/* ------------------------------------------------------------- options */
+typedef enum { TSQBX_LAPLACE = 0, TSQBX_HELMHOLTZ = 1 } tsqbx_kernel;
+
+/* layer mask: single layer, double layer (source-normal derivative) */
+enum { TSQBX_SLP = 1u, TSQBX_DLP = 2u };
+
+/* FP64: every step in double precision (results within 1e-12 relative of an
+ *       FP64 reference).
+ * MIXED (Laplace only): coordinates differenced in float-float, the
+ *       recurrence and geometry ratios in FP32, per-lane sums Kahan-
+ *       compensated in FP32 and per-target reduction in FP64 (results within
+ *       1e-6 relative of an FP64 reference). */
+typedef enum { TSQBX_FP64 = 0, TSQBX_MIXED = 1 } tsqbx_precision;
+
+enum {
+    TSQBX_FLAG_ALLOW_DIVERGENT = 1u,  /* accept pairs with |t-c| >= |s-c| (report only) */
+    TSQBX_FLAG_SKIP_CHECK = 2u        /* do not run the per-pair convergence check      */
+};
+
+typedef struct {
+    tsqbx_kernel kernel;
+    uint32_t layers;            /* TSQBX_SLP | TSQBX_DLP (Helmholtz: TSQBX_SLP)       */
+    int p;                      /* expansion order, 0 <= p <= TSQBX_P_MAX             */
+    double k;                   /* Helmholtz wavenumber (> 0); ignored for Laplace    */
+    tsqbx_precision precision;
+    int device;                 /* CUDA device ordinal                                */
+    uint32_t flags;             /* TSQBX_FLAG_*                                       */
+    int lanes_per_target;       /* 0 = chosen per group; 1..32 forces a value         */
+    int n_slots;                /* concurrent submits per plan; 0 = 2                 */
+} tsqbx_options;
+
+/* ------------------------------------------------------------ geometry */
+/* The problem statement of Sec. 3.3: quadrature sources with weights (and
+ * normals for the double layer), QBX centers with radii, targets mapped to
+ * centers, and per center group the pair list as a CSR of source ranges.
+ * Centers of one group (e.g. the centers owned by one octree box) share the
+ * list.  All pointers are host pointers, caller-owned, read during
+ * tsqbx_plan_create only. */
+typedef struct {
+    int64_t n_src;
+    const double *src_xyz;          /* [3][n_src]                                  */
+    const double *src_weight;       /* [n_src] quadrature weight incl. Jacobian    */
+    const double *src_normal;       /* [3][n_src] unit normals; NULL without DLP    */
+    int64_t n_ctr;
+    const double *ctr_xyz;          /* [3][n_ctr]                                  */
+    const double *ctr_radius;       /* [n_ctr] ball radius (reported, may be NULL) */
+    int64_t n_tgt;
+    const double *tgt_xyz;          /* [3][n_tgt]                                  */
+    const int32_t *tgt_center;      /* [n_tgt] center of each target              */
+    int64_t n_group;
+    const int32_t *ctr_group;       /* [n_ctr] group of each center                */
+    const int64_t *group_range_start; /* [n_group+1] CSR offsets, [0] == 0         */
+    const int32_t *range_begin;     /* [nnz] first source of each range            */
+    const int32_t *range_end;       /* [nnz] one past the last source              */
+} tsqbx_geometry;
+
+typedef struct tsqbx_plan_s *tsqbx_plan;
+
+/* Counts describing a plan. */
+typedef struct {
+    int64_t n_src, n_ctr, n_tgt, n_group;
+    int64_t n_pairs;           /* (target, source) pairs, duplicates counted        */
+    int64_t n_pair_terms;      /* n_pairs * (p + 1): the throughput unit            */
+    int64_t n_items;           /* warp work items                                   */
+    int64_t n_divergent;       /* pairs with |t-c| >= |s-c| (0 if the check was off) */
+    int64_t n_coincident;      /* pairs with s == c                                  */
+    int64_t list_entries;      /* sum over groups of listed sources                  */
+    double lane_utilisation;   /* active lanes / 32 averaged over items (by cost)    */
+    size_t device_bytes;       /* device memory held by the plan                     */
+} tsqbx_plan_stats;
+
+/* Create a plan: validates the geometry and options, counts divergent pairs
+ * on the device (unless TSQBX_FLAG_SKIP_CHECK), builds the work items and
+ * uploads everything.  On success *out owns device memory until
+ * tsqbx_plan_destroy.  Errors: TSQBX_E_INVAL, TSQBX_E_DIVERGENT (plan not
+ * created; the counts are lost), TSQBX_E_NOMEM, TSQBX_E_CUDA,
+ * TSQBX_E_UNSUPPORTED. */
+TSQBX_API int tsqbx_plan_create(const tsqbx_geometry *geometry, const tsqbx_options *options,
+                      tsqbx_plan *out);
+
+/* Release a plan (waits for its in-flight work).  NULL is ignored. */
+TSQBX_API void tsqbx_plan_destroy(tsqbx_plan plan);
+
+/* Fill *stats.  Errors: TSQBX_E_INVAL. */
+TSQBX_API int tsqbx_plan_info(tsqbx_plan plan, tsqbx_plan_stats *stats);
+
+/* Device bytes held by the plan (geometry, lists, work items, slot buffers):
+ * the admission unit of a serving loop.  Errors: TSQBX_E_INVAL. */
+TSQBX_API int tsqbx_plan_footprint(tsqbx_plan plan, size_t *bytes);
+
+/* Blocking evaluation.  density: n_src doubles (Laplace) or n_src complex
+ * doubles as interleaved (re, im) pairs (Helmholtz).  out_slp / out_dlp:
+ * n_tgt doubles (Laplace) or n_tgt interleaved complex values (Helmholtz),
+ * indexed by target; NULL for a layer not in the plan's mask.  Each pointer
+ * may be host (pageable or pinned) or device memory.  Returns after the
+ * outputs are written.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA, TSQBX_E_KERNEL. */
+TSQBX_API int tsqbx_eval(tsqbx_plan plan, const void *density, void *out_slp, void *out_dlp);
+
+/* Asynchronous evaluation on DEVICE pointers only (same layouts as
+ * tsqbx_eval), enqueued on `stream` (a cudaStream_t; NULL = the plan's own
+ * stream).  Returns once the work is enqueued; the caller orders later work
+ * on that stream.  Uses slot 0's scratch: concurrent calls on one plan must
+ * be ordered on one stream.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_eval_async(tsqbx_plan plan, const void *d_density, void *d_out_slp, void *d_out_dlp,
+                     void *stream);
+
+/* Submit an evaluation and return at once with a ticket.  Pointers as for
+ * tsqbx_eval; host density is copied before return, host outputs are written
+ * by the tsqbx_poll call that reports completion, so they must stay valid
+ * until then.  Errors: TSQBX_E_INVAL, TSQBX_E_BUSY (every slot in flight:
+ * poll first), TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_submit(tsqbx_plan plan, const void *density, void *out_slp, void *out_dlp,
+                 uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (0: just test, < 0: wait indefinitely)
+ * for a ticket.  Returns TSQBX_OK once (the ticket is then retired),
+ * TSQBX_PENDING if timeout_us == 0 and work is in flight, TSQBX_E_TIMEOUT if
+ * a positive timeout expired, TSQBX_E_NOTFOUND for an unknown ticket,
+ * TSQBX_E_KERNEL / TSQBX_E_CUDA on failure (ticket retired). */
+TSQBX_API int tsqbx_poll(uint64_t ticket, int timeout_us);
+
+/* Duration in milliseconds of the expansion kernel of the most recent
+ * tsqbx_eval / tsqbx_eval_async on this plan, measured with CUDA events
+ * recorded on the launching stream immediately before and after that kernel
+ * (the per-evaluation w*mu preparation kernel is outside the interval).
+ * Waits for that kernel to finish.  Errors: TSQBX_E_INVAL (no evaluation
+ * yet), TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
+
+/* Static description of a status code. */
+TSQBX_API const char *tsqbx_strerror(int status);
+
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+TSQBX_API int tsqbx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSQBX_H */

@@ -1,0 +1,191 @@
+"""paper_1811_01110_gb300 -- the near-field TSQBX step of GIGAQBX on GB300.
+
+Thin Python binding over the C ABI of ``libtsqbx`` (include/tsqbx.h).  All
+arithmetic runs in the library's CUDA kernels; this module only marshals
+arguments (numpy arrays for host memory, torch CUDA tensors for device
+memory) and raises on error codes.
+
+    plan = Plan(geometry, kernel="laplace", layers=("slp", "dlp"), p=9,
+                precision="fp64")
+    u = plan.eval(density)             # {'slp': ndarray, 'dlp': ndarray}
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import TsqbxError, check, lib, strerror  # noqa: F401
+
+_KERNELS = {"laplace": _lib.TSQBX_LAPLACE, "helmholtz": _lib.TSQBX_HELMHOLTZ}
+_PRECISIONS = {"fp64": _lib.TSQBX_FP64, "mixed": _lib.TSQBX_MIXED}
+_LAYERS = {"slp": _lib.TSQBX_SLP, "dlp": _lib.TSQBX_DLP}
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _is_torch(x):
+    return hasattr(x, "data_ptr") and hasattr(x, "is_cuda")
+
+
+def _addr(x, nbytes, what):
+    """Raw address of a numpy array or torch tensor holding at least nbytes."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+        if x.numel() * x.element_size() < nbytes:
+            raise ValueError(f"{what} is too small")
+        return ctypes.c_void_p(x.data_ptr())
+    if not isinstance(x, np.ndarray) or not x.flags.c_contiguous:
+        raise ValueError(f"{what} must be a C-contiguous numpy array or torch tensor")
+    if x.nbytes < nbytes:
+        raise ValueError(f"{what} is too small")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+class Plan:
+    """A device-resident TSQBX evaluation plan (tsqbx_plan_create)."""
+
+    def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
+                 precision="fp64", device=0, allow_divergent=False, skip_check=False,
+                 lanes_per_target=0, n_slots=2):
+        g = geometry
+        self.kernel = kernel
+        self.layers = tuple(layers)
+        self.p = int(p)
+        self.complex = kernel == "helmholtz"
+        f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+        i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+        keep = dict(src_xyz=f64(g.src_xyz), src_weight=f64(g.src_weight),
+                    src_normal=f64(g.src_normal) if "dlp" in self.layers else None,
+                    ctr_xyz=f64(g.ctr_xyz), ctr_radius=f64(getattr(g, "ctr_radius", None)),
+                    tgt_xyz=f64(g.tgt_xyz), tgt_center=i32(g.tgt_center),
+                    ctr_group=i32(g.ctr_group),
+                    group_range_start=np.ascontiguousarray(g.group_range_start, dtype=np.int64),
+                    range_begin=i32(g.range_begin), range_end=i32(g.range_end))
+        self.n_src = int(keep["src_weight"].shape[0])
+        self.n_tgt = int(keep["tgt_xyz"].shape[1]) if keep["tgt_xyz"].ndim == 2 else 0
+        geo = _lib.tsqbx_geometry(
+            self.n_src, _ptr(keep["src_xyz"], ctypes.c_double), _ptr(keep["src_weight"], ctypes.c_double),
+            _ptr(keep["src_normal"], ctypes.c_double),
+            int(keep["ctr_xyz"].shape[1]), _ptr(keep["ctr_xyz"], ctypes.c_double),
+            _ptr(keep["ctr_radius"], ctypes.c_double),
+            self.n_tgt, _ptr(keep["tgt_xyz"], ctypes.c_double), _ptr(keep["tgt_center"], ctypes.c_int32),
+            int(keep["group_range_start"].shape[0] - 1), _ptr(keep["ctr_group"], ctypes.c_int32),
+            _ptr(keep["group_range_start"], ctypes.c_int64),
+            _ptr(keep["range_begin"], ctypes.c_int32), _ptr(keep["range_end"], ctypes.c_int32))
+        mask = 0
+        for name in self.layers:
+            mask |= _LAYERS[name]
+        flags = (_lib.TSQBX_FLAG_ALLOW_DIVERGENT if allow_divergent else 0) | \
+                (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0)
+        opt = _lib.tsqbx_options(_KERNELS[kernel], mask, self.p, float(k), _PRECISIONS[precision],
+                                 int(device), flags, int(lanes_per_target), int(n_slots))
+        h = ctypes.c_void_p()
+        check(lib().tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)),
+              "tsqbx_plan_create")
+        self._h = h
+        self.width = 2 if self.complex else 1
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tsqbx_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- queries
+    def info(self):
+        st = _lib.tsqbx_plan_stats()
+        check(lib().tsqbx_plan_info(self._h, ctypes.byref(st)), "tsqbx_plan_info")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def footprint(self):
+        b = ctypes.c_size_t()
+        check(lib().tsqbx_plan_footprint(self._h, ctypes.byref(b)), "tsqbx_plan_footprint")
+        return int(b.value)
+
+    def kernel_ms(self):
+        """Event-timed duration of the last expansion kernel (tsqbx_plan_kernel_ms)."""
+        ms = ctypes.c_float()
+        check(lib().tsqbx_plan_kernel_ms(self._h, ctypes.byref(ms)), "tsqbx_plan_kernel_ms")
+        return float(ms.value)
+
+    # -- evaluation
+    def _density_addr(self, density):
+        if _is_torch(density):
+            return _addr(density, self.n_src * 8 * self.width, "density")
+        dt = np.complex128 if self.complex else np.float64
+        d = np.ascontiguousarray(density, dtype=dt)
+        self._keep_density = d
+        return _addr(d, self.n_src * 8 * self.width, "density")
+
+    def _alloc_out(self, like_torch):
+        outs = {}
+        for name in self.layers:
+            if like_torch is not None:
+                import torch
+                dt = torch.complex128 if self.complex else torch.float64
+                outs[name] = torch.empty(self.n_tgt, dtype=dt, device=like_torch.device)
+            else:
+                outs[name] = np.empty(self.n_tgt, dtype=np.complex128 if self.complex else np.float64)
+        return outs
+
+    def _out_addrs(self, outs):
+        nb = self.n_tgt * 8 * self.width
+        return (_addr(outs.get("slp"), nb, "out_slp"), _addr(outs.get("dlp"), nb, "out_dlp"))
+
+    def eval(self, density, out=None):
+        """Blocking evaluation (tsqbx_eval).  density: numpy (host) or torch
+        CUDA tensor; returns a dict of outputs of the same kind."""
+        like = density if _is_torch(density) and density.is_cuda else None
+        outs = out if out is not None else self._alloc_out(like)
+        a_slp, a_dlp = self._out_addrs(outs)
+        check(lib().tsqbx_eval(self._h, self._density_addr(density), a_slp, a_dlp), "tsqbx_eval")
+        return outs
+
+    def eval_async(self, density, out, stream=None):
+        """Enqueue on a CUDA stream (tsqbx_eval_async); device tensors only.
+        stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        handle = None
+        if stream is not None:
+            handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        a_slp, a_dlp = self._out_addrs(out)
+        check(lib().tsqbx_eval_async(self._h, self._density_addr(density), a_slp, a_dlp, handle),
+              "tsqbx_eval_async")
+        return out
+
+    def submit(self, density, out=None):
+        """tsqbx_submit: returns (ticket, outs); outs are valid once poll() returns True."""
+        like = density if _is_torch(density) and density.is_cuda else None
+        outs = out if out is not None else self._alloc_out(like)
+        a_slp, a_dlp = self._out_addrs(outs)
+        t = ctypes.c_uint64()
+        check(lib().tsqbx_submit(self._h, self._density_addr(density), a_slp, a_dlp, ctypes.byref(t)),
+              "tsqbx_submit")
+        self._inflight = getattr(self, "_inflight", {})
+        self._inflight[t.value] = (outs, getattr(self, "_keep_density", None))
+        return t.value, outs
+
+
+def poll(ticket, timeout_us=0):
+    """tsqbx_poll: True when done, False while pending (timeout_us == 0)."""
+    rc = lib().tsqbx_poll(ctypes.c_uint64(ticket), int(timeout_us))
+    if rc == _lib.TSQBX_PENDING:
+        return False
+    check(rc, "tsqbx_poll")
+    return True

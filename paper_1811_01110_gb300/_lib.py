@@ -1,0 +1,108 @@
+"""ctypes binding of libtsqbx (include/tsqbx.h): argument marshalling only.
+
+Every name mirrors the C ABI.  The shared library is the in-tree
+``paper_1811_01110_gb300/libtsqbx.so`` produced by ``build.py``; importing
+this module never builds or falls back to anything -- a missing library is an
+error.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtsqbx.so")
+
+TSQBX_P_MAX = 20
+TSQBX_OK, TSQBX_PENDING = 0, 1
+TSQBX_E_INVAL, TSQBX_E_DIVERGENT, TSQBX_E_NOMEM, TSQBX_E_CUDA = -1, -2, -3, -4
+TSQBX_E_TIMEOUT, TSQBX_E_BUSY, TSQBX_E_NOTFOUND, TSQBX_E_KERNEL = -5, -6, -7, -8
+TSQBX_E_UNSUPPORTED = -9
+TSQBX_LAPLACE, TSQBX_HELMHOLTZ = 0, 1
+TSQBX_SLP, TSQBX_DLP = 1, 2
+TSQBX_FP64, TSQBX_MIXED = 0, 1
+TSQBX_FLAG_ALLOW_DIVERGENT, TSQBX_FLAG_SKIP_CHECK = 1, 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class tsqbx_geometry(ctypes.Structure):
+    _fields_ = [
+        ("n_src", ctypes.c_int64), ("src_xyz", _dp), ("src_weight", _dp), ("src_normal", _dp),
+        ("n_ctr", ctypes.c_int64), ("ctr_xyz", _dp), ("ctr_radius", _dp),
+        ("n_tgt", ctypes.c_int64), ("tgt_xyz", _dp), ("tgt_center", _i32p),
+        ("n_group", ctypes.c_int64), ("ctr_group", _i32p), ("group_range_start", _i64p),
+        ("range_begin", _i32p), ("range_end", _i32p),
+    ]
+
+
+class tsqbx_options(ctypes.Structure):
+    _fields_ = [
+        ("kernel", ctypes.c_int), ("layers", ctypes.c_uint32), ("p", ctypes.c_int),
+        ("k", ctypes.c_double), ("precision", ctypes.c_int), ("device", ctypes.c_int),
+        ("flags", ctypes.c_uint32), ("lanes_per_target", ctypes.c_int), ("n_slots", ctypes.c_int),
+    ]
+
+
+class tsqbx_plan_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_src", ctypes.c_int64), ("n_ctr", ctypes.c_int64), ("n_tgt", ctypes.c_int64),
+        ("n_group", ctypes.c_int64), ("n_pairs", ctypes.c_int64), ("n_pair_terms", ctypes.c_int64),
+        ("n_items", ctypes.c_int64), ("n_divergent", ctypes.c_int64),
+        ("n_coincident", ctypes.c_int64), ("list_entries", ctypes.c_int64),
+        ("lane_utilisation", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+# (name, restype, argtypes) for every entry point declared in include/tsqbx.h
+_SIGNATURES = [
+    ("tsqbx_plan_create", ctypes.c_int,
+     [ctypes.POINTER(tsqbx_geometry), ctypes.POINTER(tsqbx_options), ctypes.POINTER(ctypes.c_void_p)]),
+    ("tsqbx_plan_destroy", None, [ctypes.c_void_p]),
+    ("tsqbx_plan_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_plan_stats)]),
+    ("tsqbx_plan_footprint", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    ("tsqbx_eval", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("tsqbx_eval_async", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("tsqbx_submit", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.POINTER(ctypes.c_uint64)]),
+    ("tsqbx_poll", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    ("tsqbx_plan_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("tsqbx_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("tsqbx_version", ctypes.c_int, []),
+]
+
+_lib = None
+
+
+def lib():
+    """The loaded libtsqbx (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().tsqbx_strerror(int(code)).decode()
+
+
+class TsqbxError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+def check(code, where):
+    if code < 0:
+        raise TsqbxError(code, where)
+    return code

@@ -1,0 +1,76 @@
+// internal.cuh -- device-side layout shared by the libtsqbx kernels and the
+// host plan code.  Not part of the public ABI (include/tsqbx.h is).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsqbx {
+
+// Warp work item: the targets [slot_begin, slot_begin + n_tgt) of one group
+// (all sharing that group's source list), L lanes per target.
+//   x = group, y = slot_begin, z = n_tgt (<= 32 / L), w = L (1..32)
+using Item = int4;
+
+constexpr int kWarpsPerBlock = 4;   // independent warps per CTA
+constexpr int kTile = 64;           // sources staged per warp per tile
+constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;  // 1/(4 pi)
+
+// Everything a kernel needs about a plan's geometry (device pointers).
+struct DevGeom {
+    int64_t n_src = 0, n_tgt = 0, n_items = 0;
+    const Item *items = nullptr;
+    const int64_t *grp_off = nullptr;   // [n_group+1] offsets into grp_src
+    const int32_t *grp_src = nullptr;   // flattened source indices of each group
+    // FP64 source records
+    const double4_32a *src_pw = nullptr;    // {x, y, z, w}
+    const double4_32a *src_n = nullptr;     // {nx, ny, nz, 0}
+    // mixed-precision source records: coordinates as float-float pairs
+    const float4 *src_hi = nullptr;     // {xh, yh, zh, 0}
+    const float4 *src_lo = nullptr;     // {xl, yl, zl, 0}
+    const float4 *src_nf = nullptr;     // {nx, ny, nz, 0}
+    // target slots, in item order
+    const int32_t *slot_tgt = nullptr;  // output index of the slot's target
+    const double4_32a *slot_c = nullptr;    // {cx, cy, cz, 0}
+    const double4_32a *slot_e = nullptr;    // {ex, ey, ez, rho^2},  e = t - c
+    const float4 *slot_chi = nullptr;   // float-float center
+    const float4 *slot_clo = nullptr;
+    const float4 *slot_ef = nullptr;    // {ex, ey, ez, rho^2} rounded to FP32
+};
+
+// Per-evaluation buffers (device pointers).
+struct DevEval {
+    const double *wmu = nullptr;        // Laplace FP64: w_s mu_s
+    const float *wmu_f = nullptr;       // Laplace mixed: (float)(w_s mu_s)
+    const double2 *wmu_c = nullptr;     // Helmholtz: w_s mu_s (complex)
+    double *out_slp = nullptr;          // indexed by target (real or interleaved complex)
+    double *out_dlp = nullptr;
+    int *status = nullptr;              // bit 0: out-of-range source index seen
+    double k = 0.0;                     // Helmholtz wavenumber
+};
+
+// Launchers (one per translation unit).  Return a cudaError_t as int.
+int launch_laplace_fp64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e,
+                        cudaStream_t s);
+int launch_laplace_mixed(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e,
+                         cudaStream_t s);
+int launch_helmholtz_fp64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e,
+                          cudaStream_t s);
+
+// Legendre three-term recurrence in the scaled form used by every kernel:
+//   Q_n = (rho/R)^n P_n(x) = kappa_n T_n,
+//   T_{n+1} = qx T_n - beta_n q2 T_{n-1},  qx = (rho/R) x,  q2 = (rho/R)^2,
+// from Bonnet's (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1} with
+// kappa_{n+1} = kappa_n (2n+1)/(n+1) and beta_n = n^2 / ((2n+1)(2n-1)).
+__host__ __device__ constexpr double rec_kappa(int n)
+{
+    double k = 1.0;
+    for (int m = 0; m < n; ++m) k *= (2.0 * m + 1.0) / (m + 1.0);
+    return k;
+}
+__host__ __device__ constexpr double rec_beta(int n)
+{
+    return (1.0 * n * n) / ((2.0 * n + 1.0) * (2.0 * n - 1.0));
+}
+
+}  // namespace tsqbx

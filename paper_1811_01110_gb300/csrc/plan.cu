@@ -1,0 +1,752 @@
+// plan.cu -- host side of libtsqbx: plan construction (validation, grouping of
+// targets into warp work items, packing of source/target records, upload,
+// convergence check), evaluation, and the submit/poll ticket machinery.
+//
+// The C ABI is declared in include/tsqbx.h; every entry point below traps C++
+// exceptions and converts CUDA failures into TSQBX_E_* codes.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+#include "tsqbx.h"
+
+using namespace tsqbx;
+
+namespace {
+
+// ------------------------------------------------------------- prep kernels
+
+// Per-evaluation source weights times density: w_s mu_s in the form each
+// kernel family stages.
+__global__ void prep_wmu_fp64(const double4_32a *src_pw, const double *mu, int64_t n, double *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src_pw[i].w * mu[i];
+}
+
+__global__ void prep_wmu_f32(const double4_32a *src_pw, const double *mu, int64_t n, float *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)(src_pw[i].w * mu[i]);
+}
+
+__global__ void prep_wmu_c128(const double4_32a *src_pw, const double2 *mu, int64_t n, double2 *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double w = src_pw[i].w;
+        const double2 m = mu[i];
+        out[i] = make_double2(w * m.x, w * m.y);
+    }
+}
+
+// Convergence check over every listed pair (same item walk as the kernels):
+// counts |t-c|^2 >= |s-c|^2 (outside the expansion's region of convergence,
+// Appendix A) and s == c.
+__global__ void check_pairs_kernel(const DevGeom g, unsigned long long *n_div,
+                                   unsigned long long *n_zero)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (item >= g.n_items) return;
+    const Item it = g.items[item];
+    const int64_t s0 = g.grp_off[it.x];
+    const int ns = (int)(g.grp_off[it.x + 1] - s0);
+    unsigned long long nd = 0, nz = 0;
+    for (int j = 0; j < it.z; ++j) {
+        const double4_32a c = g.slot_c[it.y + j];
+        const double rho2 = g.slot_e[it.y + j].w;
+        for (int k = lane; k < ns; k += 32) {
+            const int s = g.grp_src[s0 + k];
+            if ((unsigned)s >= (unsigned)g.n_src) continue;
+            const double4_32a p = g.src_pw[s];
+            const double dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+            const double R2 = dx * dx + dy * dy + dz * dz;
+            if (R2 == 0.0) ++nz;
+            else if (rho2 >= R2) ++nd;
+        }
+    }
+    if (nd) atomicAdd(n_div, nd);
+    if (nz) atomicAdd(n_zero, nz);
+}
+
+// ------------------------------------------------------------------ helpers
+
+struct CudaFail {
+    cudaError_t err;
+};
+
+inline void ck(cudaError_t e)
+{
+    if (e != cudaSuccess) throw CudaFail{e};
+}
+
+int status_of(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) return TSQBX_E_NOMEM;
+    return TSQBX_E_CUDA;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) ck(cudaSetDevice(dev));
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline bool finite3(const double *xyz, int64_t n, int64_t i)
+{
+    return std::isfinite(xyz[i]) && std::isfinite(xyz[n + i]) && std::isfinite(xyz[2 * n + i]);
+}
+
+void split_ff(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- plan
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void *d_density = nullptr;     // device copy of a host density
+    void *d_wmu = nullptr;         // w mu scratch (f64, f32 or c128)
+    double *d_out[2] = {nullptr, nullptr};
+    int *d_status = nullptr;
+    void *h_density = nullptr;     // pinned staging
+    void *h_out[2] = {nullptr, nullptr};
+    int *h_status = nullptr;
+    bool busy = false;
+    uint64_t ticket = 0;
+    void *user_out[2] = {nullptr, nullptr};
+    bool copy_out[2] = {false, false};
+};
+
+struct tsqbx_plan_s {
+    tsqbx_options opt{};
+    DevGeom g;
+    std::vector<void *> dev_allocs;
+    std::vector<void *> host_allocs;
+    size_t device_bytes = 0;
+    tsqbx_plan_stats stats{};
+    std::vector<Slot> slots;
+    std::mutex mu;
+    cudaEvent_t k_begin = nullptr, k_end = nullptr;   // brackets the expansion kernel (slot 0)
+    bool k_timed = false;
+    size_t density_bytes = 0, out_bytes = 0, wmu_bytes = 0;
+
+    template <class T>
+    T *dalloc(size_t count)
+    {
+        if (count == 0) count = 1;
+        void *p = nullptr;
+        ck(cudaMalloc(&p, count * sizeof(T)));
+        dev_allocs.push_back(p);
+        device_bytes += count * sizeof(T);
+        return static_cast<T *>(p);
+    }
+    template <class T>
+    T *upload(const std::vector<T> &v)
+    {
+        T *p = dalloc<T>(v.size());
+        if (!v.empty()) ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return p;
+    }
+    void *halloc(size_t bytes)
+    {
+        void *p = nullptr;
+        ck(cudaMallocHost(&p, bytes ? bytes : 1));
+        host_allocs.push_back(p);
+        return p;
+    }
+    ~tsqbx_plan_s()
+    {
+        for (auto &s : slots) {
+            if (s.stream) cudaStreamSynchronize(s.stream);
+            if (s.done) cudaEventDestroy(s.done);
+            if (s.stream) cudaStreamDestroy(s.stream);
+        }
+        if (k_begin) cudaEventDestroy(k_begin);
+        if (k_end) cudaEventDestroy(k_end);
+        for (void *p : dev_allocs) cudaFree(p);
+        for (void *p : host_allocs) cudaFreeHost(p);
+    }
+};
+
+namespace {
+
+std::mutex g_ticket_mu;
+std::unordered_map<uint64_t, std::pair<tsqbx_plan, int>> g_tickets;
+std::atomic<uint64_t> g_next_ticket{1};
+
+int validate(const tsqbx_geometry *G, const tsqbx_options *o)
+{
+    if (!G || !o) return TSQBX_E_INVAL;
+    if (o->kernel != TSQBX_LAPLACE && o->kernel != TSQBX_HELMHOLTZ) return TSQBX_E_INVAL;
+    if (o->layers == 0 || (o->layers & ~(uint32_t)(TSQBX_SLP | TSQBX_DLP))) return TSQBX_E_INVAL;
+    if (o->p < 0 || o->p > TSQBX_P_MAX) return TSQBX_E_INVAL;
+    if (o->precision != TSQBX_FP64 && o->precision != TSQBX_MIXED) return TSQBX_E_INVAL;
+    if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64)
+        return TSQBX_E_INVAL;
+    if (o->kernel == TSQBX_HELMHOLTZ) {
+        if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
+        if (o->precision != TSQBX_FP64) return TSQBX_E_UNSUPPORTED;
+        if (o->layers != TSQBX_SLP) return TSQBX_E_UNSUPPORTED;
+    }
+    if (G->n_src < 0 || G->n_ctr < 0 || G->n_tgt < 0 || G->n_group < 0) return TSQBX_E_INVAL;
+    if (G->n_src > INT32_MAX || G->n_ctr > INT32_MAX || G->n_tgt > INT32_MAX || G->n_group > INT32_MAX)
+        return TSQBX_E_INVAL;
+    if ((G->n_src && (!G->src_xyz || !G->src_weight)) || (G->n_ctr && !G->ctr_xyz) ||
+        (G->n_tgt && (!G->tgt_xyz || !G->tgt_center)) || (G->n_ctr && !G->ctr_group) ||
+        !G->group_range_start)
+        return TSQBX_E_INVAL;
+    if ((o->layers & TSQBX_DLP) && G->n_src && !G->src_normal) return TSQBX_E_INVAL;
+    if (G->group_range_start[0] != 0) return TSQBX_E_INVAL;
+    for (int64_t q = 0; q < G->n_group; ++q)
+        if (G->group_range_start[q + 1] < G->group_range_start[q]) return TSQBX_E_INVAL;
+    const int64_t nnz = G->group_range_start[G->n_group];
+    if (nnz > 0 && (!G->range_begin || !G->range_end)) return TSQBX_E_INVAL;
+    for (int64_t i = 0; i < nnz; ++i)
+        if (G->range_begin[i] < 0 || G->range_end[i] < G->range_begin[i] ||
+            G->range_end[i] > G->n_src)
+            return TSQBX_E_INVAL;
+    for (int64_t t = 0; t < G->n_tgt; ++t)
+        if (G->tgt_center[t] < 0 || G->tgt_center[t] >= G->n_ctr || !finite3(G->tgt_xyz, G->n_tgt, t))
+            return TSQBX_E_INVAL;
+    for (int64_t c = 0; c < G->n_ctr; ++c)
+        if (G->ctr_group[c] < 0 || G->ctr_group[c] >= G->n_group || !finite3(G->ctr_xyz, G->n_ctr, c))
+            return TSQBX_E_INVAL;
+    for (int64_t s = 0; s < G->n_src; ++s) {
+        if (!finite3(G->src_xyz, G->n_src, s) || !std::isfinite(G->src_weight[s])) return TSQBX_E_INVAL;
+        if ((o->layers & TSQBX_DLP) && !finite3(G->src_normal, G->n_src, s)) return TSQBX_E_INVAL;
+    }
+    return TSQBX_OK;
+}
+
+// Lanes per target for a group of nt targets sharing ns sources: minimise the
+// warp-time estimate  items(L) * (ceil(ns / L) + staging + setup).
+int choose_lanes(int64_t nt, int64_t ns)
+{
+    int best = 1;
+    double best_cost = 1e300;
+    for (int L = 1; L <= 32; ++L) {
+        const int64_t tpw = 32 / L;
+        const int64_t items = (nt + tpw - 1) / tpw;
+        const double cost = (double)items * ((double)((ns + L - 1) / L) + 0.25 * (double)ns / 32.0 + 4.0);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = L; }
+    }
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsqbx_version(void) { return 10000; }
+
+const char *tsqbx_strerror(int status)
+{
+    switch (status) {
+    case TSQBX_OK: return "ok";
+    case TSQBX_PENDING: return "pending: work still in flight";
+    case TSQBX_E_INVAL: return "invalid argument (size, pointer, index range or order)";
+    case TSQBX_E_DIVERGENT: return "a listed pair has |t-c| >= |s-c| or s == c";
+    case TSQBX_E_NOMEM: return "out of device or pinned host memory";
+    case TSQBX_E_CUDA: return "CUDA runtime error";
+    case TSQBX_E_TIMEOUT: return "timed out";
+    case TSQBX_E_BUSY: return "every slot of the plan is in flight";
+    case TSQBX_E_NOTFOUND: return "unknown or already collected ticket";
+    case TSQBX_E_KERNEL: return "a kernel found an out-of-range source index";
+    case TSQBX_E_UNSUPPORTED: return "kernel/layer/precision combination not provided";
+    default: return "unknown status";
+    }
+}
+
+int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_plan *out)
+{
+    if (!out) return TSQBX_E_INVAL;
+    *out = nullptr;
+    int rc = validate(G, o);
+    if (rc) return rc;
+    tsqbx_plan P = nullptr;
+    try {
+        DeviceGuard dg(o->device);
+        P = new tsqbx_plan_s;
+        P->opt = *o;
+        if (P->opt.n_slots == 0) P->opt.n_slots = 2;
+        const bool dlp = (o->layers & TSQBX_DLP) != 0;
+        const bool mixed = o->precision == TSQBX_MIXED;
+        const int64_t n_src = G->n_src, n_tgt = G->n_tgt, n_group = G->n_group;
+
+        // targets grouped by their center's group (stable counting sort)
+        std::vector<int64_t> tcount(n_group + 1, 0);
+        for (int64_t t = 0; t < n_tgt; ++t) ++tcount[G->ctr_group[G->tgt_center[t]] + 1];
+        for (int64_t q = 0; q < n_group; ++q) tcount[q + 1] += tcount[q];
+        std::vector<int32_t> slot_tgt(n_tgt);
+        {
+            std::vector<int64_t> pos(tcount.begin(), tcount.end() - 1);
+            for (int64_t t = 0; t < n_tgt; ++t) slot_tgt[pos[G->ctr_group[G->tgt_center[t]]]++] = (int32_t)t;
+        }
+        // flattened source list per group
+        std::vector<int64_t> grp_off(n_group + 1, 0);
+        for (int64_t q = 0; q < n_group; ++q) {
+            int64_t ns = 0;
+            for (int64_t r = G->group_range_start[q]; r < G->group_range_start[q + 1]; ++r)
+                ns += G->range_end[r] - G->range_begin[r];
+            if (ns > INT32_MAX) { delete P; return TSQBX_E_INVAL; }
+            grp_off[q + 1] = grp_off[q] + ns;
+        }
+        std::vector<int32_t> grp_src((size_t)grp_off[n_group]);
+        for (int64_t q = 0; q < n_group; ++q) {
+            int64_t w = grp_off[q];
+            for (int64_t r = G->group_range_start[q]; r < G->group_range_start[q + 1]; ++r)
+                for (int32_t s = G->range_begin[r]; s < G->range_end[r]; ++s) grp_src[w++] = s;
+        }
+        // work items, heaviest first
+        struct ItemC { Item it; double cost; };
+        std::vector<ItemC> items;
+        double used = 0.0, offered = 0.0;
+        int64_t n_pairs = 0;
+        for (int64_t q = 0; q < n_group; ++q) {
+            const int64_t nt = tcount[q + 1] - tcount[q];
+            if (nt == 0) continue;
+            const int64_t ns = grp_off[q + 1] - grp_off[q];
+            n_pairs += nt * ns;
+            const int L = o->lanes_per_target ? o->lanes_per_target : choose_lanes(nt, ns);
+            const int64_t tpw = 32 / L;
+            for (int64_t b = 0; b < nt; b += tpw) {
+                const int64_t m = std::min(tpw, nt - b);
+                const double cost = (double)((ns + L - 1) / L) + 0.25 * (double)ns / 32.0 + 4.0;
+                items.push_back({make_int4((int)q, (int)(tcount[q] + b), (int)m, L), cost});
+                used += cost * (double)(m * L);
+                offered += cost * 32.0;
+            }
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const ItemC &a, const ItemC &b) { return a.cost > b.cost; });
+        std::vector<Item> item_v(items.size());
+        for (size_t i = 0; i < items.size(); ++i) item_v[i] = items[i].it;
+
+        // target slot records
+        std::vector<double4_32a> slot_c(n_tgt), slot_e(n_tgt);
+        std::vector<float4> slot_chi, slot_clo, slot_ef;
+        if (mixed) { slot_chi.resize(n_tgt); slot_clo.resize(n_tgt); slot_ef.resize(n_tgt); }
+        const int64_t nc = G->n_ctr;
+        for (int64_t i = 0; i < n_tgt; ++i) {
+            const int64_t t = slot_tgt[i];
+            const int64_t c = G->tgt_center[t];
+            double cc[3], e[3];
+            for (int a = 0; a < 3; ++a) {
+                cc[a] = G->ctr_xyz[a * nc + c];
+                e[a] = G->tgt_xyz[a * n_tgt + t] - cc[a];
+            }
+            const double rho2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+            slot_c[i] = make_double4_32a(cc[0], cc[1], cc[2], 0.0);
+            slot_e[i] = make_double4_32a(e[0], e[1], e[2], rho2);
+            if (mixed) {
+                float h[3], l[3];
+                for (int a = 0; a < 3; ++a) split_ff(cc[a], h[a], l[a]);
+                slot_chi[i] = make_float4(h[0], h[1], h[2], 0.f);
+                slot_clo[i] = make_float4(l[0], l[1], l[2], 0.f);
+                slot_ef[i] = make_float4((float)e[0], (float)e[1], (float)e[2], (float)rho2);
+            }
+        }
+        // source records
+        std::vector<double4_32a> src_pw(n_src), src_n;
+        std::vector<float4> src_hi, src_lo, src_nf;
+        if (dlp) src_n.resize(n_src);
+        if (mixed) { src_hi.resize(n_src); src_lo.resize(n_src); if (dlp) src_nf.resize(n_src); }
+        for (int64_t s = 0; s < n_src; ++s) {
+            const double x = G->src_xyz[s], y = G->src_xyz[n_src + s], z = G->src_xyz[2 * n_src + s];
+            src_pw[s] = make_double4_32a(x, y, z, G->src_weight[s]);
+            if (dlp) {
+                const double nx = G->src_normal[s], ny = G->src_normal[n_src + s],
+                             nz = G->src_normal[2 * n_src + s];
+                src_n[s] = make_double4_32a(nx, ny, nz, 0.0);
+                if (mixed) src_nf[s] = make_float4((float)nx, (float)ny, (float)nz, 0.f);
+            }
+            if (mixed) {
+                float h[3], l[3];
+                split_ff(x, h[0], l[0]); split_ff(y, h[1], l[1]); split_ff(z, h[2], l[2]);
+                src_hi[s] = make_float4(h[0], h[1], h[2], 0.f);
+                src_lo[s] = make_float4(l[0], l[1], l[2], 0.f);
+            }
+        }
+        // upload
+        DevGeom &g = P->g;
+        g.n_src = n_src;
+        g.n_tgt = n_tgt;
+        g.n_items = (int64_t)item_v.size();
+        g.items = P->upload(item_v);
+        g.grp_off = P->upload(grp_off);
+        g.grp_src = P->upload(grp_src);
+        g.src_pw = P->upload(src_pw);
+        if (dlp) g.src_n = P->upload(src_n);
+        if (mixed) {
+            g.src_hi = P->upload(src_hi);
+            g.src_lo = P->upload(src_lo);
+            if (dlp) g.src_nf = P->upload(src_nf);
+            g.slot_chi = P->upload(slot_chi);
+            g.slot_clo = P->upload(slot_clo);
+            g.slot_ef = P->upload(slot_ef);
+        }
+        g.slot_tgt = P->upload(slot_tgt);
+        g.slot_c = P->upload(slot_c);
+        g.slot_e = P->upload(slot_e);
+
+        // convergence check on the device
+        int64_t n_div = 0, n_zero = 0;
+        if (!(o->flags & TSQBX_FLAG_SKIP_CHECK) && g.n_items > 0) {
+            unsigned long long *cnt = nullptr;
+            ck(cudaMalloc(&cnt, 2 * sizeof(unsigned long long)));
+            ck(cudaMemset(cnt, 0, 2 * sizeof(unsigned long long)));
+            const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+            check_pairs_kernel<<<(unsigned)blocks, kWarpsPerBlock * 32>>>(g, cnt, cnt + 1);
+            unsigned long long h[2] = {0, 0};
+            cudaError_t e1 = cudaGetLastError();
+            cudaError_t e2 = cudaMemcpy(h, cnt, sizeof(h), cudaMemcpyDeviceToHost);
+            cudaFree(cnt);
+            ck(e1);
+            ck(e2);
+            n_div = (int64_t)h[0];
+            n_zero = (int64_t)h[1];
+            if (n_zero > 0 || (n_div > 0 && !(o->flags & TSQBX_FLAG_ALLOW_DIVERGENT))) {
+                delete P;
+                return TSQBX_E_DIVERGENT;
+            }
+        }
+
+        // evaluation slots
+        const bool helm = o->kernel == TSQBX_HELMHOLTZ;
+        P->density_bytes = (size_t)n_src * (helm ? 2 : 1) * sizeof(double);
+        P->out_bytes = (size_t)n_tgt * (helm ? 2 : 1) * sizeof(double);
+        P->wmu_bytes = (size_t)n_src * (helm ? sizeof(double2) : mixed ? sizeof(float) : sizeof(double));
+        P->slots.resize(P->opt.n_slots + 1);   // slot 0 serves tsqbx_eval / tsqbx_eval_async
+        for (auto &s : P->slots) {
+            ck(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+            ck(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+            s.d_density = P->dalloc<char>(P->density_bytes);
+            s.d_wmu = P->dalloc<char>(P->wmu_bytes);
+            if (o->layers & TSQBX_SLP) s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            s.d_status = P->dalloc<int>(1);
+            s.h_density = P->halloc(P->density_bytes);
+            s.h_out[0] = P->halloc(P->out_bytes);
+            s.h_out[1] = P->halloc(P->out_bytes);
+            s.h_status = static_cast<int *>(P->halloc(sizeof(int)));
+        }
+
+        ck(cudaEventCreate(&P->k_begin));
+        ck(cudaEventCreate(&P->k_end));
+
+        tsqbx_plan_stats &st = P->stats;
+        st.n_src = n_src;
+        st.n_ctr = G->n_ctr;
+        st.n_tgt = n_tgt;
+        st.n_group = n_group;
+        st.n_pairs = n_pairs;
+        st.n_pair_terms = n_pairs * (int64_t)(o->p + 1);
+        st.n_items = g.n_items;
+        st.n_divergent = n_div;
+        st.n_coincident = n_zero;
+        st.list_entries = grp_off[n_group];
+        st.lane_utilisation = offered > 0 ? used / offered : 1.0;
+        st.device_bytes = P->device_bytes;
+        *out = P;
+        return TSQBX_OK;
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        delete P;
+        return status_of(f.err);
+    } catch (const std::bad_alloc &) {
+        delete P;
+        return TSQBX_E_NOMEM;
+    } catch (...) {
+        delete P;
+        return TSQBX_E_CUDA;
+    }
+}
+
+void tsqbx_plan_destroy(tsqbx_plan P)
+{
+    if (!P) return;
+    {
+        std::lock_guard<std::mutex> lk(g_ticket_mu);
+        for (auto it = g_tickets.begin(); it != g_tickets.end();)
+            it = (it->second.first == P) ? g_tickets.erase(it) : std::next(it);
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(P->opt.device);
+    delete P;
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
+int tsqbx_plan_info(tsqbx_plan P, tsqbx_plan_stats *st)
+{
+    if (!P || !st) return TSQBX_E_INVAL;
+    *st = P->stats;
+    return TSQBX_OK;
+}
+
+int tsqbx_plan_kernel_ms(tsqbx_plan P, float *ms)
+{
+    if (!P || !ms || !P->k_timed) return TSQBX_E_INVAL;
+    DeviceGuard dg(P->opt.device);
+    cudaError_t e = cudaEventSynchronize(P->k_end);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, P->k_begin, P->k_end);
+    if (e != cudaSuccess) { cudaGetLastError(); return status_of(e); }
+    return TSQBX_OK;
+}
+
+int tsqbx_plan_footprint(tsqbx_plan P, size_t *bytes)
+{
+    if (!P || !bytes) return TSQBX_E_INVAL;
+    *bytes = P->device_bytes;
+    return TSQBX_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Enqueue prep + kernel for one evaluation on stream s using slot scratch.
+int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
+            cudaStream_t s)
+{
+    const tsqbx_options &o = P->opt;
+    const int64_t n = P->g.n_src;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
+    DevEval ev;
+    ev.status = slot.d_status;
+    ev.out_slp = (o.layers & TSQBX_SLP) ? d_slp : nullptr;
+    ev.out_dlp = (o.layers & TSQBX_DLP) ? d_dlp : nullptr;
+    ev.k = o.k;
+    if (n > 0) {
+        if (o.kernel == TSQBX_HELMHOLTZ) {
+            prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double2 *>(d_density), n,
+                                                     static_cast<double2 *>(slot.d_wmu));
+        } else if (o.precision == TSQBX_MIXED) {
+            prep_wmu_f32<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double *>(d_density), n,
+                                                    static_cast<float *>(slot.d_wmu));
+        } else {
+            prep_wmu_fp64<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double *>(d_density), n,
+                                                     static_cast<double *>(slot.d_wmu));
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return status_of(e);
+    }
+    ev.wmu = static_cast<const double *>(slot.d_wmu);
+    ev.wmu_f = static_cast<const float *>(slot.d_wmu);
+    ev.wmu_c = static_cast<const double2 *>(slot.d_wmu);
+    const bool slp = (o.layers & TSQBX_SLP) != 0, dlp = (o.layers & TSQBX_DLP) != 0;
+    const bool timed = &slot == &P->slots[0];
+    if (timed) ck(cudaEventRecord(P->k_begin, s));
+    int rc;
+    if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(o.p, slp, dlp, P->g, ev, s);
+    else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(o.p, slp, dlp, P->g, ev, s);
+    else rc = launch_laplace_fp64(o.p, slp, dlp, P->g, ev, s);
+    if (rc != 0) return status_of((cudaError_t)rc);
+    if (timed) {
+        ck(cudaEventRecord(P->k_end, s));
+        P->k_timed = true;
+    }
+    return TSQBX_OK;
+}
+
+bool layer_args_ok(tsqbx_plan P, const void *out_slp, const void *out_dlp)
+{
+    if ((P->opt.layers & TSQBX_SLP) && !out_slp && P->g.n_tgt) return false;
+    if ((P->opt.layers & TSQBX_DLP) && !out_dlp && P->g.n_tgt) return false;
+    return true;
+}
+
+// Stage inputs, enqueue, and (for host outputs) copy back into pinned
+// staging; records slot.done.  Host outputs are delivered by finish().
+int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *out_dlp)
+{
+    const void *d_density = density;
+    if (P->g.n_src && !is_device_ptr(density)) {
+        std::memcpy(slot.h_density, density, P->density_bytes);
+        ck(cudaMemcpyAsync(slot.d_density, slot.h_density, P->density_bytes, cudaMemcpyHostToDevice,
+                           slot.stream));
+        d_density = slot.d_density;
+    }
+    void *outs[2] = {out_slp, out_dlp};
+    double *d_outs[2] = {nullptr, nullptr};
+    for (int l = 0; l < 2; ++l) {
+        slot.user_out[l] = outs[l];
+        slot.copy_out[l] = false;
+        if (!outs[l] || !slot.d_out[l]) continue;
+        if (is_device_ptr(outs[l])) d_outs[l] = static_cast<double *>(outs[l]);
+        else { d_outs[l] = slot.d_out[l]; slot.copy_out[l] = true; }
+    }
+    ck(cudaMemsetAsync(slot.d_status, 0, sizeof(int), slot.stream));
+    int rc = enqueue(P, slot, d_density, d_outs[0], d_outs[1], slot.stream);
+    if (rc) return rc;
+    for (int l = 0; l < 2; ++l)
+        if (slot.copy_out[l] && P->out_bytes)
+            ck(cudaMemcpyAsync(slot.h_out[l], slot.d_out[l], P->out_bytes, cudaMemcpyDeviceToHost,
+                               slot.stream));
+    ck(cudaMemcpyAsync(slot.h_status, slot.d_status, sizeof(int), cudaMemcpyDeviceToHost, slot.stream));
+    ck(cudaEventRecord(slot.done, slot.stream));
+    return TSQBX_OK;
+}
+
+int finish(tsqbx_plan P, Slot &slot)
+{
+    for (int l = 0; l < 2; ++l)
+        if (slot.copy_out[l]) std::memcpy(slot.user_out[l], slot.h_out[l], P->out_bytes);
+    return *slot.h_status ? TSQBX_E_KERNEL : TSQBX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsqbx_eval(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp)
+{
+    if (!P || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp)) return TSQBX_E_INVAL;
+    try {
+        DeviceGuard dg(P->opt.device);
+        std::lock_guard<std::mutex> lk(P->mu);
+        Slot &slot = P->slots[0];
+        int rc = start(P, slot, density, out_slp, out_dlp);
+        if (rc) return rc;
+        ck(cudaEventSynchronize(slot.done));
+        return finish(P, slot);
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    } catch (...) {
+        return TSQBX_E_CUDA;
+    }
+}
+
+int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void *d_out_dlp, void *stream)
+{
+    if (!P || (P->g.n_src && !d_density) || !layer_args_ok(P, d_out_slp, d_out_dlp)) return TSQBX_E_INVAL;
+    try {
+        DeviceGuard dg(P->opt.device);
+        Slot &slot = P->slots[0];
+        cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : slot.stream;
+        return enqueue(P, slot, d_density, static_cast<double *>(d_out_slp), static_cast<double *>(d_out_dlp), s);
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    } catch (...) {
+        return TSQBX_E_CUDA;
+    }
+}
+
+int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp, uint64_t *ticket)
+{
+    if (!P || !ticket || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp))
+        return TSQBX_E_INVAL;
+    try {
+        DeviceGuard dg(P->opt.device);
+        std::lock_guard<std::mutex> lk(P->mu);
+        int idx = -1;
+        for (size_t i = 1; i < P->slots.size(); ++i)
+            if (!P->slots[i].busy) { idx = (int)i; break; }
+        if (idx < 0) return TSQBX_E_BUSY;
+        Slot &slot = P->slots[idx];
+        int rc = start(P, slot, density, out_slp, out_dlp);
+        if (rc) return rc;
+        slot.busy = true;
+        slot.ticket = g_next_ticket.fetch_add(1);
+        {
+            std::lock_guard<std::mutex> tl(g_ticket_mu);
+            g_tickets[slot.ticket] = {P, idx};
+        }
+        *ticket = slot.ticket;
+        return TSQBX_OK;
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    } catch (...) {
+        return TSQBX_E_CUDA;
+    }
+}
+
+int tsqbx_poll(uint64_t ticket, int timeout_us)
+{
+    tsqbx_plan P = nullptr;
+    int idx = -1;
+    {
+        std::lock_guard<std::mutex> tl(g_ticket_mu);
+        auto it = g_tickets.find(ticket);
+        if (it == g_tickets.end()) return TSQBX_E_NOTFOUND;
+        P = it->second.first;
+        idx = it->second.second;
+    }
+    try {
+        DeviceGuard dg(P->opt.device);
+        Slot &slot = P->slots[idx];
+        cudaError_t q = cudaEventQuery(slot.done);
+        if (q == cudaErrorNotReady) {
+            if (timeout_us == 0) return TSQBX_PENDING;
+            if (timeout_us < 0) {
+                q = cudaEventSynchronize(slot.done);
+            } else {
+                const auto t_end = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+                while ((q = cudaEventQuery(slot.done)) == cudaErrorNotReady) {
+                    if (std::chrono::steady_clock::now() >= t_end) return TSQBX_E_TIMEOUT;
+                    std::this_thread::sleep_for(std::chrono::microseconds(20));
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lk(P->mu);
+        {
+            std::lock_guard<std::mutex> tl(g_ticket_mu);
+            if (!g_tickets.erase(ticket)) return TSQBX_E_NOTFOUND;
+        }
+        int rc;
+        if (q != cudaSuccess) {
+            cudaGetLastError();
+            rc = status_of(q);
+        } else {
+            rc = finish(P, slot);
+        }
+        slot.busy = false;
+        return rc;
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    } catch (...) {
+        return TSQBX_E_CUDA;
+    }
+}
+
+}  // extern "C"

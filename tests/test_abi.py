@@ -1,0 +1,90 @@
+"""The C ABI library without a GPU: it loads, exports every entry point that
+include/tsqbx.h declares, and rejects invalid input on the host before any
+CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tsqbx.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1811_01110_gb300 import build
+    build.build()
+    import paper_1811_01110_gb300 as pkg
+    return pkg.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return re.findall(r"TSQBX_API\s+[\w\s\*]+?\b(tsqbx_\w+)\s*\(", text)
+
+
+def test_header_declares_the_entry_points():
+    names = set(declared_functions())
+    assert {"tsqbx_plan_create", "tsqbx_eval", "tsqbx_submit", "tsqbx_poll",
+            "tsqbx_plan_destroy", "tsqbx_strerror"} <= names
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    binding = {n for n, _, _ in __import__("paper_1811_01110_gb300._lib", fromlist=["x"])._SIGNATURES}
+    assert binding == set(declared_functions())
+
+
+def test_strerror_and_version(L):
+    import paper_1811_01110_gb300 as pkg
+    assert L.tsqbx_version() >= 10000
+    for code in range(-9, 2):
+        assert pkg.strerror(code) != "unknown status"
+    assert pkg.strerror(-100) == "unknown status"
+
+
+def test_poll_unknown_ticket(L):
+    assert L.tsqbx_poll(ctypes.c_uint64(123456789), 0) == -7
+
+
+def _tiny(rng=np.random.default_rng(0)):
+    from helpers import cloud_geometry
+    return cloud_geometry(rng, n_ctr=3, n_src=10)
+
+
+def _create(g, **kw):
+    import paper_1811_01110_gb300 as pkg
+    try:
+        pkg.Plan(g, **kw)
+    except pkg.TsqbxError as e:
+        return e.code
+    return 0
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda g: setattr(g, "tgt_center", np.full_like(g.tgt_center, 99)), -1),
+    (lambda g: setattr(g, "range_end", g.range_end + 1000), -1),
+    (lambda g: setattr(g, "range_begin", g.range_end + 1), -1),
+    (lambda g: setattr(g, "group_range_start", g.group_range_start[::-1].copy()), -1),
+    (lambda g: setattr(g, "ctr_group", np.full_like(g.ctr_group, -1)), -1),
+    (lambda g: g.src_xyz.__setitem__((0, 0), np.nan), -1),
+])
+def test_invalid_geometry_rejected_on_host(L, mutate, code):
+    g = _tiny()
+    mutate(g)
+    assert _create(g) == code
+
+
+def test_invalid_options_rejected_on_host(L):
+    g = _tiny()
+    assert _create(g, p=-1) == -1
+    assert _create(g, p=21) == -1
+    assert _create(g, kernel="helmholtz", k=0.0) == -1
+    assert _create(g, kernel="helmholtz", k=1.0, precision="mixed") == -9
+    assert _create(g, kernel="helmholtz", k=1.0, layers=("dlp",)) == -9
+    assert _create(g, lanes_per_target=33) == -1
+    g.src_normal = None
+    assert _create(g, layers=("slp", "dlp")) == -1

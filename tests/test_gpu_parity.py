@@ -1,0 +1,205 @@
+"""GPU parity: libtsqbx (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (max-norm relative: max_t |u_gpu - u_oracle| / max_t |u_oracle|,
+per output layer):  FP64 mode 1e-12,  mixed mode 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import cloud_geometry
+from tsqbx_inputs import configs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_01110_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def check_laplace(pkg, g, mu, p, precision, layers=("slp", "dlp"), **kw):
+    ref = oracle.tsqbx_laplace(g, p, mu, slp="slp" in layers, dlp="dlp" in layers)
+    with pkg.Plan(g, "laplace", layers, p=p, precision=precision, **kw) as plan:
+        out = plan.eval(mu)
+    for layer in layers:
+        e = relerr(out[layer], ref[layer])
+        assert e <= TOL[precision], (layer, precision, p, e)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("p", list(range(0, 21)))
+def test_laplace_every_order(pkg, precision, p):
+    rng = np.random.default_rng(100 + p)
+    g = cloud_geometry(rng, n_ctr=12, n_src=150, q_max=0.6, tgt_per_ctr=3, list_frac=0.7)
+    mu = rng.standard_normal(g.n_src)
+    check_laplace(pkg, g, mu, p, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("lanes", [1, 2, 3, 5, 8, 16, 32])
+def test_laplace_forced_lane_counts(pkg, precision, lanes):
+    """Every lanes-per-target value, groups of 1..40 targets (ragged items)."""
+    rng = np.random.default_rng(7)
+    g = cloud_geometry(rng, n_ctr=6, n_src=300, q_max=0.5, tgt_per_ctr=40, list_frac=0.9)
+    mu = rng.standard_normal(g.n_src)
+    check_laplace(pkg, g, mu, 9, precision, lanes_per_target=lanes)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_laplace_sphere_workload(pkg, precision):
+    g, mu = configs.sphere()
+    out = check_laplace(pkg, g, mu, 5, precision, layers=("slp",))
+    assert np.all(np.isfinite(out["slp"]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_laplace_small_torus_octree_lists(pkg, precision):
+    g, mu, _ = configs.torus(48, 18)
+    check_laplace(pkg, g, mu, 9, precision)
+
+
+def test_laplace_full_torus_sampled_targets(pkg):
+    """The benchmark configuration (torus 256 x 96, octree lists, p = 9), in the
+    launch configuration the benchmark times; 600 sampled targets checked
+    against the oracle one by one, both precisions."""
+    g, mu, _ = configs.torus()
+    rng = np.random.default_rng(3)
+    idx = np.sort(rng.choice(g.n_tgt, 600, replace=False))
+    ref = oracle.tsqbx_laplace(g, 9, mu, subset=idx, slp=True, dlp=True)
+    for precision in ("fp64", "mixed"):
+        with pkg.Plan(g, "laplace", ("slp", "dlp"), p=9, precision=precision) as plan:
+            out = plan.eval(mu)
+            info = plan.info()
+        assert info["n_pairs"] == g.n_pairs() == oracle.count_pairs(g)
+        for layer in ("slp", "dlp"):
+            e = relerr(out[layer][idx], ref[layer])
+            assert e <= TOL[precision], (precision, layer, e)
+
+
+def test_edge_cases(pkg):
+    rng = np.random.default_rng(11)
+    # duplicated ranges are summed twice; one center with an empty list
+    g = cloud_geometry(rng, n_ctr=4, n_src=60, dup=True, tgt_per_ctr=5, rho_zero=True)
+    g.group_range_start = g.group_range_start.copy()
+    g.range_begin, g.range_end = g.range_begin.copy(), g.range_end.copy()
+    # empty list for group 0: drop its ranges
+    a, b = g.group_range_start[0], g.group_range_start[1]
+    keep = np.ones(len(g.range_begin), bool)
+    keep[a:b] = False
+    g.range_begin, g.range_end = g.range_begin[keep], g.range_end[keep]
+    g.group_range_start = np.concatenate([[0, 0], g.group_range_start[2:] - (b - a)])
+    mu = rng.standard_normal(g.n_src)
+    out = check_laplace(pkg, g, mu, 7, "fp64")
+    assert np.all(out["slp"][g.ctr_group[g.tgt_center] == 0] == 0.0)
+    check_laplace(pkg, g, mu, 7, "mixed")
+
+
+def test_no_targets_and_no_sources(pkg):
+    rng = np.random.default_rng(5)
+    g = cloud_geometry(rng, n_ctr=2, n_src=10)
+    g.tgt_xyz = np.zeros((3, 0))
+    g.tgt_center = np.zeros(0, np.int32)
+    with pkg.Plan(g, "laplace", ("slp",), p=3) as plan:
+        out = plan.eval(np.ones(g.n_src))
+    assert out["slp"].shape == (0,)
+
+
+def test_divergent_pairs(pkg):
+    rng = np.random.default_rng(9)
+    g = cloud_geometry(rng, n_ctr=2, n_src=20)
+    g.tgt_xyz = g.tgt_xyz.copy()
+    c = g.tgt_center[0]
+    g.tgt_xyz[:, 0] = g.ctr_xyz[:, c] + 10.0        # far outside every |s-c|
+    with pytest.raises(pkg.TsqbxError) as ei:
+        pkg.Plan(g, "laplace", ("slp",), p=4)
+    assert ei.value.code == -2
+    nd, nz = oracle.count_divergent(g)
+    with pkg.Plan(g, "laplace", ("slp",), p=4, allow_divergent=True) as plan:
+        assert plan.info()["n_divergent"] == nd > 0
+        out = plan.eval(np.ones(g.n_src))
+    ref = oracle.tsqbx_laplace(g, 4, np.ones(g.n_src))["slp"]
+    assert relerr(out["slp"], ref) <= 1e-12
+    # a source on a center is always rejected
+    h = cloud_geometry(rng, n_ctr=2, n_src=20)
+    h.src_xyz = h.src_xyz.copy()
+    h.src_xyz[:, h.range_begin[0]] = h.ctr_xyz[:, 0]
+    with pytest.raises(pkg.TsqbxError) as ei:
+        pkg.Plan(h, "laplace", ("slp",), p=4, allow_divergent=True)
+    assert ei.value.code == -2
+
+
+@pytest.mark.parametrize("p,k", [(0, 1.0), (4, 5.0), (12, 10.0), (12, 1.0), (20, 3.0)])
+def test_helmholtz_slp(pkg, p, k):
+    rng = np.random.default_rng(p + 17)
+    g = cloud_geometry(rng, n_ctr=10, n_src=120, q_max=0.6, tgt_per_ctr=3, rho_zero=True)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    ref = oracle.tsqbx_helmholtz(g, p, k, mu)["slp"]
+    with pkg.Plan(g, "helmholtz", ("slp",), p=p, k=k) as plan:
+        out = plan.eval(mu)["slp"]
+    assert relerr(out, ref) <= 1e-12
+
+
+def test_helmholtz_small_torus(pkg):
+    g, mu, _ = configs.torus_helmholtz(40, 16, k=10.0)
+    ref = oracle.tsqbx_helmholtz(g, 12, 10.0, mu)["slp"]
+    with pkg.Plan(g, "helmholtz", ("slp",), p=12, k=10.0) as plan:
+        out = plan.eval(mu)["slp"]
+    assert relerr(out, ref) <= 1e-12
+
+
+def test_paths_agree_and_are_deterministic(pkg):
+    """Host pointers, device tensors, eval_async and submit/poll give
+    bit-identical results; repeated evaluations are bit-identical."""
+    import torch
+    rng = np.random.default_rng(21)
+    g = cloud_geometry(rng, n_ctr=20, n_src=200, tgt_per_ctr=4)
+    mu = rng.standard_normal(g.n_src)
+    for precision in ("fp64", "mixed"):
+        with pkg.Plan(g, "laplace", ("slp", "dlp"), p=8, precision=precision) as plan:
+            a = plan.eval(mu)
+            b = plan.eval(mu)
+            dmu = torch.from_numpy(mu).cuda()
+            c = plan.eval(dmu)
+            outs = {k: torch.empty(g.n_tgt, dtype=torch.float64, device="cuda") for k in ("slp", "dlp")}
+            s = torch.cuda.Stream()
+            plan.eval_async(dmu, outs, stream=s)
+            s.synchronize()
+            t, d = plan.submit(mu)
+            assert pkg.poll(t, timeout_us=-1)
+            for layer in ("slp", "dlp"):
+                assert np.array_equal(a[layer], b[layer])
+                assert np.array_equal(a[layer], c[layer].cpu().numpy())
+                assert np.array_equal(a[layer], outs[layer].cpu().numpy())
+                assert np.array_equal(a[layer], d[layer])
+
+
+def test_submit_slots_and_busy(pkg):
+    rng = np.random.default_rng(23)
+    g = cloud_geometry(rng, n_ctr=8, n_src=100, tgt_per_ctr=2)
+    mus = [rng.standard_normal(g.n_src) for _ in range(3)]
+    with pkg.Plan(g, "laplace", ("slp",), p=5, n_slots=2) as plan:
+        t1, o1 = plan.submit(mus[0])
+        t2, o2 = plan.submit(mus[1])
+        with pytest.raises(pkg.TsqbxError) as ei:
+            plan.submit(mus[2])
+        assert ei.value.code == -6
+        assert pkg.poll(t1, -1) and pkg.poll(t2, -1)
+        with pytest.raises(pkg.TsqbxError) as ei:
+            pkg.poll(t1, 0)
+        assert ei.value.code == -7
+        for mu, o in zip(mus[:2], (o1, o2)):
+            ref = oracle.tsqbx_laplace(g, 5, mu)["slp"]
+            assert relerr(o["slp"], ref) <= 1e-12
