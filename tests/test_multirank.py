@@ -1,0 +1,65 @@
+"""World-size-2 CPU (gloo) test of the sharded evaluation: each rank evaluates
+its shard of targets, the outputs are all-gathered and reassembled, and the
+result equals the single-rank evaluation exactly."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1811_01110_gb300.sharding import gather_outputs, shard_targets
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, result_path):
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    import torch.distributed as dist
+    import oracle
+    from tsqbx_inputs import configs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g, mu, _ = configs.torus(24, 10)
+    shards = shard_targets(g, world)
+    mine = oracle.tsqbx_laplace(g, 7, mu, subset=shards[rank], slp=True, dlp=True)
+    parts = [None] * world
+    dist.all_gather_object(parts, {k: v.tolist() for k, v in mine.items()})
+    if rank == 0:
+        full = {k: gather_outputs([np.array(p[k]) for p in parts], shards, g.n_tgt)
+                for k in ("slp", "dlp")}
+        ref = oracle.tsqbx_laplace(g, 7, mu, slp=True, dlp=True)
+        ok = all(np.array_equal(full[k], ref[k]) for k in ("slp", "dlp"))
+        counts = [int(g.group_source_counts()[g.ctr_group[g.tgt_center[s]]].sum()) for s in shards]
+        with open(result_path, "w") as f:
+            f.write(f"{int(ok)} {counts[0]} {counts[1]}")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shards_cover_targets_once():
+    from tsqbx_inputs import configs
+    g, mu, _ = configs.torus(24, 10)
+    for world in (1, 2, 3, 8):
+        shards = shard_targets(g, world)
+        allidx = np.sort(np.concatenate(shards))
+        assert np.array_equal(allidx, np.arange(g.n_tgt))
+        pairs = [g.group_source_counts()[g.ctr_group[g.tgt_center[s]]].sum() for s in shards]
+        assert max(pairs) <= 1.25 * (sum(pairs) / world) + 2000
+
+
+def test_gloo_world2_sharded_equals_full(tmp_path):
+    mp = pytest.importorskip("torch.multiprocessing")
+    port = _free_port()
+    res = tmp_path / "res.txt"
+    mp.start_processes(_worker, args=(2, port, str(res)), nprocs=2, join=True, start_method="spawn")
+    ok, c0, c1 = map(int, res.read_text().split())
+    assert ok == 1
+    assert abs(c0 - c1) <= 0.1 * (c0 + c1)
