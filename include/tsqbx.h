@@ -65,7 +65,8 @@ enum {
     TSQBX_E_BUSY = -6,         /* tsqbx_submit: every slot of the plan is in flight */
     TSQBX_E_NOTFOUND = -7,     /* unknown or already collected ticket               */
     TSQBX_E_KERNEL = -8,       /* a kernel flagged an out-of-range index            */
-    TSQBX_E_UNSUPPORTED = -9   /* kernel/layer/precision combination not provided   */
+    TSQBX_E_UNSUPPORTED = -9,  /* kernel/layer/precision combination not provided   */
+    TSQBX_E_TOO_LARGE = -10    /* tsqbx_eval_noalloc: more sources than its scratch */
 };
 
 /* ------------------------------------------------------------- options */
@@ -196,6 +197,40 @@ TSQBX_API int tsqbx_poll(uint64_t ticket, int timeout_us);
  * Waits for that kernel to finish.  Errors: TSQBX_E_INVAL (no evaluation
  * yet), TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
+
+/* ------------------------------------------------ no-allocation evaluation
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc -- e.g. a program whose device memory is owned by its own
+ * pool or arena, or a latency-critical loop that cannot accept cudaMalloc's
+ * implicit synchronisation.  Such callers cannot create a plan (that
+ * allocates), so everything is passed as DEVICE arrays and nothing is
+ * allocated: the scratch it needs (w_s mu_s per source and a status word)
+ * lives in one fixed __device__ array of 8 MiB inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *
+ * Computes the Laplace single and/or double layer (FP64) exactly as
+ * tsqbx_eval does for a plan with the same geometry, p and layers.
+ *  d_geometry: a HOST struct whose counts are sizes and whose pointer fields
+ *              are all DEVICE pointers in the tsqbx_geometry layout;
+ *              group_range_start must hold n_group + 1 entries; ctr_radius is
+ *              ignored; src_normal is required for TSQBX_DLP.
+ *  d_density:  n_src doubles (device).  d_out_slp / d_out_dlp: n_tgt doubles
+ *              (device) for the requested layers.
+ *  stream:     cudaStream_t (NULL = legacy default stream); the call blocks
+ *              until the work on that stream is done.
+ * Limits and sharing: n_src <= TSQBX_NOALLOC_MAX_SRC (else TSQBX_E_TOO_LARGE).
+ * Every call on a device shares the one scratch array, which keeps the last
+ * call's contents (the status word is cleared and w mu rewritten by each
+ * call): calls that overlap on the GPU race and must be serialised.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Index ranges are checked on the device: an
+ * out-of-range index is skipped and reported as TSQBX_E_KERNEL.  Errors:
+ * TSQBX_E_INVAL, TSQBX_E_TOO_LARGE, TSQBX_E_KERNEL, TSQBX_E_CUDA. */
+#define TSQBX_NOALLOC_MAX_SRC 1048544
+TSQBX_API int tsqbx_eval_noalloc(const tsqbx_geometry *d_geometry, int p, uint32_t layers,
+                                 const double *d_density, double *d_out_slp, double *d_out_dlp,
+                                 void *stream);
 
 /* Static description of a status code. */
 TSQBX_API const char *tsqbx_strerror(int status);

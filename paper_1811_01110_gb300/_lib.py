@@ -16,6 +16,8 @@ TSQBX_OK, TSQBX_PENDING = 0, 1
 TSQBX_E_INVAL, TSQBX_E_DIVERGENT, TSQBX_E_NOMEM, TSQBX_E_CUDA = -1, -2, -3, -4
 TSQBX_E_TIMEOUT, TSQBX_E_BUSY, TSQBX_E_NOTFOUND, TSQBX_E_KERNEL = -5, -6, -7, -8
 TSQBX_E_UNSUPPORTED = -9
+TSQBX_E_TOO_LARGE = -10
+TSQBX_NOALLOC_MAX_SRC = 1048544
 TSQBX_LAPLACE, TSQBX_HELMHOLTZ = 0, 1
 TSQBX_SLP, TSQBX_DLP = 1, 2
 TSQBX_FP64, TSQBX_MIXED = 0, 1
@@ -69,6 +71,9 @@ _SIGNATURES = [
       ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_poll", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
     ("tsqbx_plan_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("tsqbx_eval_noalloc", ctypes.c_int,
+     [ctypes.POINTER(tsqbx_geometry), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("tsqbx_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("tsqbx_version", ctypes.c_int, []),
 ]

@@ -288,6 +288,7 @@ const char *tsqbx_strerror(int status)
     case TSQBX_E_NOTFOUND: return "unknown or already collected ticket";
     case TSQBX_E_KERNEL: return "a kernel found an out-of-range source index";
     case TSQBX_E_UNSUPPORTED: return "kernel/layer/precision combination not provided";
+    case TSQBX_E_TOO_LARGE: return "more sources than the fixed no-allocation scratch holds";
     default: return "unknown status";
     }
 }

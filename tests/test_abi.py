@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(L):
 def test_strerror_and_version(L):
     import paper_1811_01110_gb300 as pkg
     assert L.tsqbx_version() >= 10000
-    for code in range(-9, 2):
+    for code in range(-10, 2):
         assert pkg.strerror(code) != "unknown status"
     assert pkg.strerror(-100) == "unknown status"
 
