@@ -98,6 +98,10 @@ typedef struct {
     uint32_t flags;             /* TSQBX_FLAG_*                                       */
     int lanes_per_target;       /* 0 = chosen per group; 1..32 forces a value         */
     int n_slots;                /* concurrent submits per plan; 0 = 2                 */
+    int max_item_iters;         /* cap on per-lane pair iterations of one warp item;
+                                   longer lists are cut into source slices whose
+                                   partial sums are added in slice order; 0 = automatic
+                                   (32..512, scaled to the problem and the SM count) */
 } tsqbx_options;
 
 /* ------------------------------------------------------------ geometry */

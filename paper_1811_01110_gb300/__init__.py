@@ -51,7 +51,7 @@ class Plan:
 
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
-                 lanes_per_target=0, n_slots=2):
+                 lanes_per_target=0, n_slots=2, max_item_iters=0):
         g = geometry
         self.kernel = kernel
         self.layers = tuple(layers)
@@ -83,7 +83,8 @@ class Plan:
         flags = (_lib.TSQBX_FLAG_ALLOW_DIVERGENT if allow_divergent else 0) | \
                 (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0)
         opt = _lib.tsqbx_options(_KERNELS[kernel], mask, self.p, float(k), _PRECISIONS[precision],
-                                 int(device), flags, int(lanes_per_target), int(n_slots))
+                                 int(device), flags, int(lanes_per_target), int(n_slots),
+                                 int(max_item_iters))
         h = ctypes.c_void_p()
         check(lib().tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)),
               "tsqbx_plan_create")

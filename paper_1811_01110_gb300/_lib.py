@@ -43,6 +43,7 @@ class tsqbx_options(ctypes.Structure):
         ("kernel", ctypes.c_int), ("layers", ctypes.c_uint32), ("p", ctypes.c_int),
         ("k", ctypes.c_double), ("precision", ctypes.c_int), ("device", ctypes.c_int),
         ("flags", ctypes.c_uint32), ("lanes_per_target", ctypes.c_int), ("n_slots", ctypes.c_int),
+        ("max_item_iters", ctypes.c_int),
     ]
 
 

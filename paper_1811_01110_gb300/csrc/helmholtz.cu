@@ -27,17 +27,17 @@ helmholtz_slp_kernel(const DevGeom g, const DevEval ev)
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
     const Item it = g.items[item];
-    const int L = it.w;
+    const int L = it.L;
     const int j = lane / L, sub = lane - j * L;
-    const bool active = j < it.z;
+    const bool active = j < it.n_tgt;
     const double k = ev.k, kinv = 1.0 / ev.k;
     double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rhoinv = 0;
     double cj[P + 1];                  // (2n+1) kappa_n j_n(k rho)
 #pragma unroll
     for (int n = 0; n <= P; ++n) cj[n] = 0.0;
     if (active) {
-        const double4_32a c = g.slot_c[it.y + j];
-        const double4_32a e = g.slot_e[it.y + j];
+        const double4_32a c = g.slot_c[it.slot_begin + j];
+        const double4_32a e = g.slot_e[it.slot_begin + j];
         cx = c.x; cy = c.y; cz = c.z;
         ex = e.x; ey = e.y; ez = e.z;
         const double rho = sqrt(e.w);
@@ -81,13 +81,13 @@ helmholtz_slp_kernel(const DevGeom g, const DevEval ev)
 #pragma unroll
         for (int n = 0; n <= P; ++n) cj[n] = (2.0 * n + 1.0) * rec_kappa(n) * jn[n];
     }
-    const int64_t s0 = g.grp_off[it.x];
-    const int ns = (int)(g.grp_off[it.x + 1] - s0);
+    const int64_t s0 = g.grp_off[it.group];
+    const int src_hi = it.src_hi;
     double (*T)[kTile] = tile[warp];
     double acc_re = 0.0, acc_im = 0.0;
 
-    for (int base = 0; base < ns; base += kTile) {
-        const int cnt = min(kTile, ns - base);
+    for (int base = it.src_lo; base < src_hi; base += kTile) {
+        const int cnt = min(kTile, src_hi - base);
         for (int kk = lane; kk < cnt; kk += 32) {
             int s = g.grp_src[s0 + base + kk];
             double2 wm = make_double2(0.0, 0.0);
@@ -145,10 +145,15 @@ helmholtz_slp_kernel(const DevGeom g, const DevEval ev)
         if (sub + off < L) { acc_re += vr; acc_im += vi; }
     }
     if (active && sub == 0) {
-        const int t = g.slot_tgt[it.y + j];
-        if (ev.out_slp) {
-            ev.out_slp[2 * (int64_t)t] = acc_re * kInv4Pi;
-            ev.out_slp[2 * (int64_t)t + 1] = acc_im * kInv4Pi;
+        double *dst = nullptr;
+        if (it.part < 0) {
+            if (ev.out_slp) dst = ev.out_slp + 2 * (int64_t)g.slot_tgt[it.slot_begin + j];
+        } else {
+            dst = ev.part_slp + 2 * ((int64_t)it.part + j);
+        }
+        if (dst) {
+            dst[0] = acc_re * kInv4Pi;
+            dst[1] = acc_im * kInv4Pi;
         }
     }
 }

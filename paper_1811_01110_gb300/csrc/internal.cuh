@@ -8,9 +8,20 @@
 namespace tsqbx {
 
 // Warp work item: the targets [slot_begin, slot_begin + n_tgt) of one group
-// (all sharing that group's source list), L lanes per target.
-//   x = group, y = slot_begin, z = n_tgt (<= 32 / L), w = L (1..32)
-using Item = int4;
+// (all sharing that group's source list), L lanes per target, over the slice
+// [src_lo, src_hi) of the group's flattened source list.  part < 0: the item
+// owns the whole list and writes the outputs; part >= 0: it writes partial
+// sums to partial[part + j] (j < n_tgt), combined later in slice order.
+struct __align__(16) Item {
+    int32_t group, slot_begin, n_tgt, L;
+    int32_t src_lo, src_hi, part, pad;
+};
+
+// Combine record: the targets [slot_begin, slot_begin + n_tgt) whose list was
+// cut into n_slices slices; slice k's partials start at part + k * n_tgt.
+struct __align__(16) Combine {
+    int32_t slot_begin, n_tgt, part, n_slices;
+};
 
 constexpr int kWarpsPerBlock = 4;   // independent warps per CTA
 constexpr int kTile = 64;           // sources staged per warp per tile
@@ -18,8 +29,9 @@ constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;  // 1/(4 pi)
 
 // Everything a kernel needs about a plan's geometry (device pointers).
 struct DevGeom {
-    int64_t n_src = 0, n_tgt = 0, n_items = 0;
+    int64_t n_src = 0, n_tgt = 0, n_items = 0, n_combine = 0, n_parts = 0;
     const Item *items = nullptr;
+    const Combine *combine = nullptr;
     const int64_t *grp_off = nullptr;   // [n_group+1] offsets into grp_src
     const int32_t *grp_src = nullptr;   // flattened source indices of each group
     // FP64 source records
@@ -45,6 +57,8 @@ struct DevEval {
     const double2 *wmu_c = nullptr;     // Helmholtz: w_s mu_s (complex)
     double *out_slp = nullptr;          // indexed by target (real or interleaved complex)
     double *out_dlp = nullptr;
+    double *part_slp = nullptr;         // partial sums of sliced items (scratch)
+    double *part_dlp = nullptr;
     int *status = nullptr;              // bit 0: out-of-range source index seen
     double k = 0.0;                     // Helmholtz wavenumber
 };

@@ -32,23 +32,23 @@ laplace_fp64_kernel(const DevGeom g, const DevEval ev)
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;                       // whole warp leaves together
     const Item it = g.items[item];
-    const int L = it.w;
+    const int L = it.L;
     const int j = lane / L, sub = lane - j * L;
-    const bool active = j < it.z;
+    const bool active = j < it.n_tgt;
     double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rho2 = 0;
     if (active) {
-        const double4_32a c = g.slot_c[it.y + j];
-        const double4_32a e = g.slot_e[it.y + j];
+        const double4_32a c = g.slot_c[it.slot_begin + j];
+        const double4_32a e = g.slot_e[it.slot_begin + j];
         cx = c.x; cy = c.y; cz = c.z;
         ex = e.x; ey = e.y; ez = e.z; rho2 = e.w;
     }
-    const int64_t s0 = g.grp_off[it.x];
-    const int ns = (int)(g.grp_off[it.x + 1] - s0);
+    const int64_t s0 = g.grp_off[it.group];
+    const int src_hi = it.src_hi;
     double (*T)[kTile] = tile[warp];
     double acc_s = 0.0, acc_d = 0.0;
 
-    for (int base = 0; base < ns; base += kTile) {
-        const int cnt = min(kTile, ns - base);
+    for (int base = it.src_lo; base < src_hi; base += kTile) {
+        const int cnt = min(kTile, src_hi - base);
         for (int k = lane; k < cnt; k += 32) {
             int s = g.grp_src[s0 + base + k];
             double wm = 0.0;
@@ -105,9 +105,14 @@ laplace_fp64_kernel(const DevGeom g, const DevEval ev)
         if (sub + off < L) { acc_s += vs; acc_d += vd; }
     }
     if (active && sub == 0) {
-        const int t = g.slot_tgt[it.y + j];
-        if (ev.out_slp) ev.out_slp[t] = acc_s * kInv4Pi;
-        if (DLP && ev.out_dlp) ev.out_dlp[t] = acc_d * kInv4Pi;
+        if (it.part < 0) {
+            const int t = g.slot_tgt[it.slot_begin + j];
+            if (ev.out_slp) ev.out_slp[t] = acc_s * kInv4Pi;
+            if (DLP && ev.out_dlp) ev.out_dlp[t] = acc_d * kInv4Pi;
+        } else {
+            ev.part_slp[it.part + j] = acc_s * kInv4Pi;
+            if (DLP) ev.part_dlp[it.part + j] = acc_d * kInv4Pi;
+        }
     }
 }
 

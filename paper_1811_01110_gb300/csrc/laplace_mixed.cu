@@ -35,22 +35,22 @@ laplace_mixed_kernel(const DevGeom g, const DevEval ev)
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
     const Item it = g.items[item];
-    const int L = it.w;
+    const int L = it.L;
     const int j = lane / L, sub = lane - j * L;
-    const bool active = j < it.z;
+    const bool active = j < it.n_tgt;
     float4 ch = make_float4(0, 0, 0, 0), cl = ch, e = ch;
     if (active) {
-        ch = g.slot_chi[it.y + j];
-        cl = g.slot_clo[it.y + j];
-        e = g.slot_ef[it.y + j];
+        ch = g.slot_chi[it.slot_begin + j];
+        cl = g.slot_clo[it.slot_begin + j];
+        e = g.slot_ef[it.slot_begin + j];
     }
-    const int64_t s0 = g.grp_off[it.x];
-    const int ns = (int)(g.grp_off[it.x + 1] - s0);
+    const int64_t s0 = g.grp_off[it.group];
+    const int src_hi = it.src_hi;
     float4 (*T)[kTile] = tile[warp];
     float as = 0.f, ac = 0.f, ds = 0.f, dc = 0.f;     // Kahan pairs (single, double layer)
 
-    for (int base = 0; base < ns; base += kTile) {
-        const int cnt = min(kTile, ns - base);
+    for (int base = it.src_lo; base < src_hi; base += kTile) {
+        const int cnt = min(kTile, src_hi - base);
         for (int k = lane; k < cnt; k += 32) {
             int s = g.grp_src[s0 + base + k];
             float wm = 0.f;
@@ -110,9 +110,14 @@ laplace_mixed_kernel(const DevGeom g, const DevEval ev)
         if (sub + off < L) { acc_s += vs; acc_d += vd; }
     }
     if (active && sub == 0) {
-        const int t = g.slot_tgt[it.y + j];
-        if (ev.out_slp) ev.out_slp[t] = acc_s * kInv4Pi;
-        if (DLP && ev.out_dlp) ev.out_dlp[t] = acc_d * kInv4Pi;
+        if (it.part < 0) {
+            const int t = g.slot_tgt[it.slot_begin + j];
+            if (ev.out_slp) ev.out_slp[t] = acc_s * kInv4Pi;
+            if (DLP && ev.out_dlp) ev.out_dlp[t] = acc_d * kInv4Pi;
+        } else {
+            ev.part_slp[it.part + j] = acc_s * kInv4Pi;
+            if (DLP) ev.part_dlp[it.part + j] = acc_d * kInv4Pi;
+        }
     }
 }
 

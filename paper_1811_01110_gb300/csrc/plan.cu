@@ -60,13 +60,12 @@ __global__ void check_pairs_kernel(const DevGeom g, unsigned long long *n_div,
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
     const Item it = g.items[item];
-    const int64_t s0 = g.grp_off[it.x];
-    const int ns = (int)(g.grp_off[it.x + 1] - s0);
+    const int64_t s0 = g.grp_off[it.group];
     unsigned long long nd = 0, nz = 0;
-    for (int j = 0; j < it.z; ++j) {
-        const double4_32a c = g.slot_c[it.y + j];
-        const double rho2 = g.slot_e[it.y + j].w;
-        for (int k = lane; k < ns; k += 32) {
+    for (int j = 0; j < it.n_tgt; ++j) {
+        const double4_32a c = g.slot_c[it.slot_begin + j];
+        const double rho2 = g.slot_e[it.slot_begin + j].w;
+        for (int k = it.src_lo + lane; k < it.src_hi; k += 32) {
             const int s = g.grp_src[s0 + k];
             if ((unsigned)s >= (unsigned)g.n_src) continue;
             const double4_32a p = g.src_pw[s];
@@ -78,6 +77,31 @@ __global__ void check_pairs_kernel(const DevGeom g, unsigned long long *n_div,
     }
     if (nd) atomicAdd(n_div, nd);
     if (nz) atomicAdd(n_zero, nz);
+}
+
+// Second pass for sliced items: each target's partial sums (one per slice of
+// its group's list) are added in slice order, so results are deterministic.
+__global__ void combine_kernel(const DevGeom g, const double *part_slp, const double *part_dlp,
+                               double *out_slp, double *out_dlp, int width)
+{
+    const int64_t n = g.n_combine * 32;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const Combine r = g.combine[i >> 5];
+        const int j = (int)(i & 31);
+        if (j >= r.n_tgt) continue;
+        const int64_t t = g.slot_tgt[r.slot_begin + j];
+        for (int w = 0; w < width; ++w) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < r.n_slices; ++k) {
+                const int64_t idx = ((int64_t)r.part + (int64_t)k * r.n_tgt + j) * width + w;
+                if (part_slp) a += part_slp[idx];
+                if (part_dlp) b += part_dlp[idx];
+            }
+            if (out_slp) out_slp[t * width + w] = a;
+            if (out_dlp) out_dlp[t * width + w] = b;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ helpers
@@ -142,6 +166,7 @@ struct Slot {
     void *d_density = nullptr;     // device copy of a host density
     void *d_wmu = nullptr;         // w mu scratch (f64, f32 or c128)
     double *d_out[2] = {nullptr, nullptr};
+    double *d_part[2] = {nullptr, nullptr};   // partial sums of sliced items
     int *d_status = nullptr;
     void *h_density = nullptr;     // pinned staging
     void *h_out[2] = {nullptr, nullptr};
@@ -216,7 +241,8 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
     if (o->layers == 0 || (o->layers & ~(uint32_t)(TSQBX_SLP | TSQBX_DLP))) return TSQBX_E_INVAL;
     if (o->p < 0 || o->p > TSQBX_P_MAX) return TSQBX_E_INVAL;
     if (o->precision != TSQBX_FP64 && o->precision != TSQBX_MIXED) return TSQBX_E_INVAL;
-    if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64)
+    if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64 ||
+        o->max_item_iters < 0)
         return TSQBX_E_INVAL;
     if (o->kernel == TSQBX_HELMHOLTZ) {
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
@@ -333,11 +359,19 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             for (int64_t r = G->group_range_start[q]; r < G->group_range_start[q + 1]; ++r)
                 for (int32_t s = G->range_begin[r]; s < G->range_end[r]; ++s) grp_src[w++] = s;
         }
-        // work items, heaviest first
-        struct ItemC { Item it; double cost; };
-        std::vector<ItemC> items;
-        double used = 0.0, offered = 0.0;
-        int64_t n_pairs = 0;
+        // work items, heaviest first; long lists are cut into source slices
+        // so that no warp item exceeds max_iters lane iterations
+        int n_sm = 152;
+        {
+            int dev = 0, v = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+                n_sm = v;
+            cudaGetLastError();
+        }
+        struct Chunk { int64_t q, slot, m; int L; int64_t ns; };
+        std::vector<Chunk> chunks;
+        int64_t n_pairs = 0, total_iters = 0;
         for (int64_t q = 0; q < n_group; ++q) {
             const int64_t nt = tcount[q + 1] - tcount[q];
             if (nt == 0) continue;
@@ -346,10 +380,37 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             const int L = o->lanes_per_target ? o->lanes_per_target : choose_lanes(nt, ns);
             const int64_t tpw = 32 / L;
             for (int64_t b = 0; b < nt; b += tpw) {
-                const int64_t m = std::min(tpw, nt - b);
-                const double cost = (double)((ns + L - 1) / L) + 0.25 * (double)ns / 32.0 + 4.0;
-                items.push_back({make_int4((int)q, (int)(tcount[q] + b), (int)m, L), cost});
-                used += cost * (double)(m * L);
+                chunks.push_back({q, tcount[q] + b, std::min(tpw, nt - b), L, ns});
+                total_iters += (ns + L - 1) / L;
+            }
+        }
+        int64_t max_iters = o->max_item_iters;
+        if (max_iters <= 0)
+            max_iters = std::min<int64_t>(512, std::max<int64_t>(32, total_iters / ((int64_t)n_sm * 48)));
+        struct ItemC { Item it; double cost; };
+        std::vector<ItemC> items;
+        std::vector<Combine> combine_v;
+        int64_t n_parts = 0;
+        double used = 0.0, offered = 0.0;
+        for (const Chunk &c : chunks) {
+            const int64_t iters = (c.ns + c.L - 1) / c.L;
+            const int64_t K = iters > max_iters ? (iters + max_iters - 1) / max_iters : 1;
+            int64_t base = -1;
+            if (K > 1) {
+                base = n_parts;
+                n_parts += K * c.m;
+                if (n_parts > INT32_MAX) { delete P; return TSQBX_E_INVAL; }
+                combine_v.push_back({(int32_t)c.slot, (int32_t)c.m, (int32_t)base, (int32_t)K});
+            }
+            for (int64_t k = 0; k < K; ++k) {
+                const int64_t lo = c.ns * k / K, hi = c.ns * (k + 1) / K;
+                const double cost = (double)((hi - lo + c.L - 1) / c.L) + 0.25 * (double)(hi - lo) / 32.0 + 4.0;
+                Item it;
+                it.group = (int32_t)c.q; it.slot_begin = (int32_t)c.slot; it.n_tgt = (int32_t)c.m; it.L = c.L;
+                it.src_lo = (int32_t)lo; it.src_hi = (int32_t)hi;
+                it.part = K > 1 ? (int32_t)(base + k * c.m) : -1; it.pad = 0;
+                items.push_back({it, cost});
+                used += cost * (double)(c.m * c.L);
                 offered += cost * 32.0;
             }
         }
@@ -409,6 +470,9 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         g.n_tgt = n_tgt;
         g.n_items = (int64_t)item_v.size();
         g.items = P->upload(item_v);
+        g.n_combine = (int64_t)combine_v.size();
+        g.n_parts = n_parts;
+        g.combine = P->upload(combine_v);
         g.grp_off = P->upload(grp_off);
         g.grp_src = P->upload(grp_src);
         g.src_pw = P->upload(src_pw);
@@ -460,6 +524,9 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             s.d_wmu = P->dalloc<char>(P->wmu_bytes);
             if (o->layers & TSQBX_SLP) s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            const size_t part_doubles = (size_t)n_parts * (helm ? 2 : 1);
+            if (n_parts && (o->layers & TSQBX_SLP)) s.d_part[0] = P->dalloc<double>(part_doubles);
+            if (n_parts && (o->layers & TSQBX_DLP)) s.d_part[1] = P->dalloc<double>(part_doubles);
             s.d_status = P->dalloc<int>(1);
             s.h_density = P->halloc(P->density_bytes);
             s.h_out[0] = P->halloc(P->out_bytes);
@@ -553,6 +620,8 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     ev.status = slot.d_status;
     ev.out_slp = (o.layers & TSQBX_SLP) ? d_slp : nullptr;
     ev.out_dlp = (o.layers & TSQBX_DLP) ? d_dlp : nullptr;
+    ev.part_slp = slot.d_part[0];
+    ev.part_dlp = slot.d_part[1];
     ev.k = o.k;
     if (n > 0) {
         if (o.kernel == TSQBX_HELMHOLTZ) {
@@ -579,6 +648,14 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(o.p, slp, dlp, P->g, ev, s);
     else rc = launch_laplace_fp64(o.p, slp, dlp, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
+    if (P->g.n_combine > 0) {
+        const int64_t th = P->g.n_combine * 32;
+        const int cb = (int)std::min<int64_t>((th + 255) / 256, 152 * 8);
+        combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp, ev.part_dlp, ev.out_slp, ev.out_dlp,
+                                          o.kernel == TSQBX_HELMHOLTZ ? 2 : 1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return status_of(e);
+    }
     if (timed) {
         ck(cudaEventRecord(P->k_end, s));
         P->k_timed = true;

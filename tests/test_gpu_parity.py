@@ -59,6 +59,28 @@ def test_laplace_forced_lane_counts(pkg, precision, lanes):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("max_iters", [1, 2, 7, 40])
+def test_laplace_sliced_lists(pkg, precision, max_iters):
+    """Long lists cut into source slices (partials combined in slice order)."""
+    rng = np.random.default_rng(31)
+    g = cloud_geometry(rng, n_ctr=7, n_src=400, q_max=0.5, tgt_per_ctr=13, list_frac=0.8)
+    mu = rng.standard_normal(g.n_src)
+    check_laplace(pkg, g, mu, 6, precision, max_item_iters=max_iters)
+    check_laplace(pkg, g, mu, 6, precision, max_item_iters=max_iters, lanes_per_target=5)
+
+
+def test_helmholtz_sliced_lists(pkg):
+    rng = np.random.default_rng(37)
+    g = cloud_geometry(rng, n_ctr=5, n_src=300, q_max=0.5, tgt_per_ctr=7, list_frac=0.9)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    ref = oracle.tsqbx_helmholtz(g, 8, 4.0, mu)["slp"]
+    for mi in (1, 5, 33):
+        with pkg.Plan(g, "helmholtz", ("slp",), p=8, k=4.0, max_item_iters=mi) as plan:
+            out = plan.eval(mu)["slp"]
+        assert relerr(out, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_laplace_sphere_workload(pkg, precision):
     g, mu = configs.sphere()
     out = check_laplace(pkg, g, mu, 5, precision, layers=("slp",))
