@@ -40,13 +40,23 @@ PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def flops_per_pair(p, precision):
-    """Algorithmic flops per (target, source) pair of the SLP+DLP kernels
-    (FMA = 2): geometry 19 (+6 for the float-float difference in mixed),
-    10 per recurrence step n = 1..p-1, 32 for closing both layers, and 8 for
-    the Kahan updates in mixed."""
-    base = 19 + 10 * (p - 1) + 32
-    return base + (6 + 8 if precision == "mixed" else 0)
+def flops_per_pair(p, precision, dlp=True):
+    """Algorithmic flops per (target, source) pair (FMA = 2) of the Laplace
+    kernels: geometry 19 (d, R^2, 1/R, qx, q2), per recurrence step n = 1..p-1
+    6 for the single layer (+4 for the double layer), closing 3 (+29 for the
+    double layer); mixed precision adds 6 for the float-float difference and 4
+    per layer for the Kahan update."""
+    f = 19 + (10 if dlp else 6) * max(p - 1, 0) + (32 if dlp else 3)
+    if precision == "mixed":
+        f += 6 + (8 if dlp else 4)
+    return f
+
+
+def helmholtz_flops_per_pair(p):
+    """Helmholtz single layer (FP64): geometry and 1/z 20, 13 per order
+    (Hankel factor 5, Legendre 3, complex accumulation 5), closing with e^{iz}
+    and the complex weight 16, sincos counted as 2."""
+    return 20 + 13 * max(p - 1, 0) + 16 + 2 + 12
 
 
 def parse():
@@ -58,6 +68,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target duration of the bounded CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline workload (no batched / Helmholtz / sphere legs)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the automatic schedules")
     return ap.parse_args()
 
 
@@ -229,6 +242,115 @@ def gpu_selector(dev, local_rank):
     return str(local_rank)
 
 
+def roofline(flops_per_launch, kernel_s, precision):
+    peak = PEAK_FP64_TFLOPS if precision == "fp64" else PEAK_FP32_TFLOPS
+    achieved = flops_per_launch / kernel_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "pipe": precision if precision == "fp64" else "fp32",
+            "peak_source": "derived: 152 SMs x %d FMA/clk x 2 flop x 2070 MHz"
+                           % (2 if precision == "fp64" else 128)}
+
+
+def leg_batched(pkg, torch, dev, steps, warmup, flush):
+    """64 ellipsoids (1k-200k sources, Laplace SLP, p in {5,7,9}, mixed) in one
+    persistent launch replayed from a CUDA graph, against the same 64 plans
+    evaluated one after another."""
+    from tsqbx_inputs import configs
+    surfaces = configs.ellipsoid_batch()
+    plans = [pkg.Plan(g, "laplace", ("slp",), p=g.meta["p"], precision="mixed", device=dev.index)
+             for g, _ in surfaces]
+    dens = [torch.from_numpy(mu).to(dev) for _, mu in surfaces]
+    outs = [{"slp": torch.empty(g.n_tgt, dtype=torch.float64, device=dev)} for g, _ in surfaces]
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    res = {}
+    with pkg.Batch(plans, use_graph=True) as batch:
+        info = batch.info()
+        for _ in range(warmup):
+            batch.eval_async(dens, outs, stream=stream)
+        torch.cuda.synchronize()
+        ms, kms = [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.eval_async(dens, outs, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            kms.append(batch.kernel_ms())
+        torch.cuda.synchronize()
+    # the same work as 64 separate evaluations on one stream
+    seq = []
+    for i in range(warmup + steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for pl, d, o in zip(plans, dens, outs):
+            pl.eval_async(d, o, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= warmup:
+            seq.append(e0.elapsed_time(e1))
+    pt = info["n_pair_terms"]
+    t = sum(ms) / 1e3 / steps
+    fl = sum(flops_per_pair(pl.p, "mixed", dlp=False) * pl.info()["n_pairs"] for pl in plans)
+    res = {"workload": "64 seeded ellipsoids (semi-axes U(0.5,2)), %d sources, %d pairs, Laplace SLP, "
+                       "p in {5,7,9}, lists of 50-800 sources per center" % (
+                           sum(g.n_src for g, _ in surfaces), info["n_pairs"]),
+           "value": pt / t, "unit": UNIT, "dtype": "f32 recurrence, f64 sums", "ms_per_step": 1e3 * t,
+           "kernel_ms": sum(kms) / steps, "launches_per_step": info["launches_per_eval"],
+           "persistent_ctas": info["grid_blocks"], "graph": bool(info["graph"]),
+           "sequential_ms_per_step": sum(seq) / steps,
+           "speedup_vs_sequential": (sum(seq) / steps) / (1e3 * t),
+           "roofline": roofline(fl, sum(kms) / steps / 1e3, "mixed")}
+    for pl in plans:
+        pl.close()
+    return res
+
+
+def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
+    """Torus 444 x 166 quads (884,448 sources, 1,768,896 targets), octree
+    lists, Helmholtz single layer k = 10, p = 12, FP64, plane-wave density."""
+    from tsqbx_inputs import configs
+    g, mu, _ = configs.torus_helmholtz()
+    plan = pkg.Plan(g, "helmholtz", ("slp",), p=12, k=10.0, device=dev.index)
+    info = plan.info()
+    dmu = torch.from_numpy(mu).to(dev)
+    out = {"slp": torch.empty(g.n_tgt, dtype=torch.complex128, device=dev)}
+    stream = torch.cuda.Stream(device=dev)
+    step_ms, kern_ms = time_device(plan, dmu, out, stream, steps, warmup, flush, lambda: None)
+    t = sum(kern_ms) / 1e3 / steps
+    res = {"workload": "torus 444x166 quads, 884448 sources, 1768896 targets, octree lists, "
+                       "Helmholtz SLP k=10 p=12", "n_pairs": info["n_pairs"],
+           "value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps), "unit": UNIT, "dtype": "f64",
+           "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
+           "roofline": roofline(helmholtz_flops_per_pair(12) * info["n_pairs"], t, "fp64")}
+    plan.close()
+    return res
+
+
+def leg_sphere(pkg, torch, dev, steps, warmup, flush):
+    """Icosphere (3 subdivisions, 7,680 sources), radius-4h lists, Laplace SLP p = 5, FP64."""
+    from tsqbx_inputs import configs
+    g, mu = configs.sphere()
+    plan = pkg.Plan(g, "laplace", ("slp",), p=5, device=dev.index)
+    info = plan.info()
+    dmu = torch.from_numpy(mu).to(dev)
+    out = {"slp": torch.empty(g.n_tgt, dtype=torch.float64, device=dev)}
+    stream = torch.cuda.Stream(device=dev)
+    step_ms, kern_ms = time_device(plan, dmu, out, stream, steps, warmup, flush, lambda: None)
+    t = sum(kern_ms) / 1e3 / steps
+    res = {"workload": "icosphere 1280 triangles, 7680 sources, radius-4h lists, Laplace SLP p=5",
+           "n_pairs": info["n_pairs"], "value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps),
+           "unit": UNIT, "dtype": "f64", "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
+           "roofline": roofline(flops_per_pair(5, "fp64", dlp=False) * info["n_pairs"], t, "fp64")}
+    plan.close()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -248,9 +370,13 @@ def main():
         mu = mu * (1.0 + 0.01 * rank)
     plans = {prec: pkg.Plan(g, "laplace", ("slp", "dlp"), p=P, precision=prec, device=local_rank)
              for prec in ("fp64", "mixed")}
+    dmu = torch.from_numpy(mu).to(dev)
+    torch.cuda.synchronize()
+    tuning = {}
+    for prec, pl in plans.items():
+        tuning[prec] = pl.autotune(dmu, repeats=3) if not args.no_autotune else pl.get_tuning()
     info = plans["fp64"].info()
     pair_terms = info["n_pair_terms"]
-    dmu = torch.from_numpy(mu).to(dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     outs = {prec: {l: torch.empty(g.n_tgt, dtype=torch.float64, device=dev) for l in ("slp", "dlp")}
@@ -283,19 +409,10 @@ def main():
         t_kern = agg(kern_ms)
         value = pair_terms * args.steps * world / t_step
         kavg = t_kern / args.steps
-        fl = flops_per_pair(P, prec) * info["n_pairs"]
-        peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
-        achieved = fl / kavg / 1e12
-        summary[prec] = {
-            "value": value, "ms_per_step": 1e3 * t_step / args.steps,
-            "kernel_ms": 1e3 * kavg,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "pipe": "fp64" if prec == "fp64" else "fp32",
-                         "peak_source": "derived: 152 SMs x %d FMA/clk x 2 flop x 2070 MHz"
-                                        % (2 if prec == "fp64" else 128),
-                         "flops_per_pair": flops_per_pair(P, prec)},
-        }
+        rf = roofline(flops_per_pair(P, prec) * info["n_pairs"], kavg, prec)
+        rf["flops_per_pair"] = flops_per_pair(P, prec)
+        summary[prec] = {"value": value, "ms_per_step": 1e3 * t_step / args.steps,
+                         "kernel_ms": 1e3 * kavg, "roofline": rf}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -315,6 +432,11 @@ def main():
     e2e = {"value": pair_terms * len(e2e_t) * world / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(host_mu.nbytes),
            "d2h_bytes_per_step": int(2 * g.n_tgt * 8 + 4)}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere)):
+            extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush)
 
     if rank != 0:
         return
@@ -353,11 +475,13 @@ def main():
                   "speedup_vs_fp64": summary["mixed"]["value"] / f["value"]},
         "error_vs_oracle": err or None,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps * 2,
+        "gpu_launches": args.steps * sum(pl.info()["launches_per_eval"] for pl in plans.values()),
+        "tuning": tuning,
         "clocks": clocks,
         "wall_s_timed_region": wall_s,
         "cpu_baseline": cpu,
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     for p_ in plans.values():
         p_.close()

@@ -85,7 +85,10 @@ typedef enum { TSQBX_FP64 = 0, TSQBX_MIXED = 1 } tsqbx_precision;
 
 enum {
     TSQBX_FLAG_ALLOW_DIVERGENT = 1u,  /* accept pairs with |t-c| >= |s-c| (report only) */
-    TSQBX_FLAG_SKIP_CHECK = 2u        /* do not run the per-pair convergence check      */
+    TSQBX_FLAG_SKIP_CHECK = 2u,       /* do not run the per-pair convergence check      */
+    TSQBX_FLAG_USE_TUNED = 4u         /* start from the process-wide tuning cache entry
+                                         matching (kernel, precision, p, layers, list
+                                         shape), if tsqbx_plan_autotune stored one      */
 };
 
 typedef struct {
@@ -142,6 +145,9 @@ typedef struct {
     int64_t list_entries;      /* sum over groups of listed sources                  */
     double lane_utilisation;   /* active lanes / 32 averaged over items (by cost)    */
     size_t device_bytes;       /* device memory held by the plan                     */
+    int64_t n_sliced;          /* target chunks whose list was cut into slices       */
+    int launches_per_eval;     /* kernels one evaluation launches (prep, expansion,
+                                  and the slice combine when n_sliced > 0)          */
 } tsqbx_plan_stats;
 
 /* Create a plan: validates the geometry and options, counts divergent pairs
@@ -202,6 +208,72 @@ TSQBX_API int tsqbx_poll(uint64_t ticket, int timeout_us);
  * yet), TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
 
+/* -------------------------------------------------------------- batches
+ * Many plans evaluated in ONE persistent, load-balanced launch (the plans'
+ * work items merged into one queue sorted by cost; resident warps pop items
+ * with an atomic counter).  All plans must be Laplace, on one device, with the
+ * same precision and layer mask; their orders p may differ.  A batch
+ * snapshots the plans' schedules at creation and uses the plans' device
+ * geometry, so the plans must outlive it; its scratch (w mu per plan, partial
+ * sums, queue head) is its own, so batch and plan evaluations may interleave
+ * on different streams. */
+typedef struct tsqbx_batch_s *tsqbx_batch;
+
+typedef struct {
+    int64_t n_plans, n_items, n_sliced, n_pairs, n_pair_terms;
+    int grid_blocks;            /* persistent CTAs (one wave)                        */
+    int graph;                  /* 1 if evaluations replay a captured CUDA graph     */
+    int launches_per_eval;      /* kernels per evaluation                            */
+    size_t device_bytes;        /* device memory held by the batch itself            */
+} tsqbx_batch_stats;
+
+/* use_graph != 0: capture the launch sequence (pointer-table copy, w mu
+ * preparation of every plan, queue reset, persistent kernel, slice combine)
+ * into a CUDA graph at creation and replay it per evaluation.
+ * Errors: TSQBX_E_INVAL, TSQBX_E_UNSUPPORTED (non-Laplace), TSQBX_E_NOMEM,
+ * TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_batch_create(const tsqbx_plan *plans, int n_plans, int use_graph, tsqbx_batch *out);
+TSQBX_API void tsqbx_batch_destroy(tsqbx_batch batch);
+
+/* Enqueue one evaluation of every plan on `stream` (NULL = the batch's own
+ * stream).  d_density[i], d_out_slp[i], d_out_dlp[i]: DEVICE pointers for
+ * plan i (layouts as tsqbx_eval; out arrays may be NULL for absent layers).
+ * Waits only until the previous evaluation of this batch has read its pointer
+ * table.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_batch_eval_async(tsqbx_batch batch, const void *const *d_density,
+                                     void *const *d_out_slp, void *const *d_out_dlp, void *stream);
+
+/* Waits for the last evaluation; *ms = device time from the queue reset to
+ * the end of the combine (CUDA events in the launch sequence).  Returns
+ * TSQBX_E_KERNEL if a kernel flagged an out-of-range index. */
+TSQBX_API int tsqbx_batch_kernel_ms(tsqbx_batch batch, float *ms);
+TSQBX_API int tsqbx_batch_info(tsqbx_batch batch, tsqbx_batch_stats *stats);
+
+/* ------------------------------------------------------------- tuning
+ * Work decomposition of a plan: lanes per target (0 = chosen per group from
+ * its target and source counts) and the cap on per-lane pair iterations of one
+ * warp item (longer lists are cut into slices). */
+typedef struct {
+    int lanes_per_target;
+    int max_item_iters;
+    float kernel_ms;            /* autotune: measured expansion time of this choice */
+} tsqbx_tuning;
+
+/* Autotuner: times candidate decompositions of this plan (slice caps, then
+ * lane policies) with CUDA events on the plan's stream, evaluating the DEVICE
+ * density d_density `repeats` times each (after one untimed run), keeps the
+ * fastest, records it in the process-wide tuning cache (see
+ * TSQBX_FLAG_USE_TUNED) and returns it in *chosen (may be NULL).  Uses the
+ * plan's slot-0 buffers; do not overlap with other evaluations of the plan.
+ * Errors: TSQBX_E_INVAL, TSQBX_E_NOMEM, TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_plan_autotune(tsqbx_plan plan, const void *d_density, int repeats,
+                                  tsqbx_tuning *chosen);
+
+/* Install a decomposition (e.g. one found by the autotuner) / read the current
+ * one (kernel_ms = 0).  Errors: TSQBX_E_INVAL, TSQBX_E_NOMEM, TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_plan_set_tuning(tsqbx_plan plan, const tsqbx_tuning *tuning);
+TSQBX_API int tsqbx_plan_get_tuning(tsqbx_plan plan, tsqbx_tuning *tuning);
+
 /* ------------------------------------------------ no-allocation evaluation
  * The paper has no counterpart: this entry point serves callers that cannot
  * call cudaMalloc -- e.g. a program whose device memory is owned by its own
@@ -235,6 +307,11 @@ TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
 TSQBX_API int tsqbx_eval_noalloc(const tsqbx_geometry *d_geometry, int p, uint32_t layers,
                                  const double *d_density, double *d_out_slp, double *d_out_dlp,
                                  void *stream);
+
+/* Name of the last CUDA runtime error that a libtsqbx call made on the
+ * calling thread ran into (the detail behind TSQBX_E_CUDA / TSQBX_E_NOMEM);
+ * "no error" if none. */
+TSQBX_API const char *tsqbx_last_error(void);
 
 /* Static description of a status code. */
 TSQBX_API const char *tsqbx_strerror(int status);

@@ -51,7 +51,7 @@ class Plan:
 
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
-                 lanes_per_target=0, n_slots=2, max_item_iters=0):
+                 lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False):
         g = geometry
         self.kernel = kernel
         self.layers = tuple(layers)
@@ -81,7 +81,8 @@ class Plan:
         for name in self.layers:
             mask |= _LAYERS[name]
         flags = (_lib.TSQBX_FLAG_ALLOW_DIVERGENT if allow_divergent else 0) | \
-                (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0)
+                (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0) | \
+                (_lib.TSQBX_FLAG_USE_TUNED if use_tuned else 0)
         opt = _lib.tsqbx_options(_KERNELS[kernel], mask, self.p, float(k), _PRECISIONS[precision],
                                  int(device), flags, int(lanes_per_target), int(n_slots),
                                  int(max_item_iters))
@@ -125,6 +126,24 @@ class Plan:
         ms = ctypes.c_float()
         check(lib().tsqbx_plan_kernel_ms(self._h, ctypes.byref(ms)), "tsqbx_plan_kernel_ms")
         return float(ms.value)
+
+    # -- tuning
+    def autotune(self, density, repeats=3):
+        """tsqbx_plan_autotune on a device density; returns the chosen tuning."""
+        t = _lib.tsqbx_tuning()
+        check(lib().tsqbx_plan_autotune(self._h, self._density_addr(density), int(repeats),
+                                        ctypes.byref(t)), "tsqbx_plan_autotune")
+        return {"lanes_per_target": t.lanes_per_target, "max_item_iters": t.max_item_iters,
+                "kernel_ms": t.kernel_ms}
+
+    def get_tuning(self):
+        t = _lib.tsqbx_tuning()
+        check(lib().tsqbx_plan_get_tuning(self._h, ctypes.byref(t)), "tsqbx_plan_get_tuning")
+        return {"lanes_per_target": t.lanes_per_target, "max_item_iters": t.max_item_iters}
+
+    def set_tuning(self, lanes_per_target=0, max_item_iters=0):
+        t = _lib.tsqbx_tuning(int(lanes_per_target), int(max_item_iters), 0.0)
+        check(lib().tsqbx_plan_set_tuning(self._h, ctypes.byref(t)), "tsqbx_plan_set_tuning")
 
     # -- evaluation
     def _density_addr(self, density):
@@ -181,6 +200,58 @@ class Plan:
         self._inflight = getattr(self, "_inflight", {})
         self._inflight[t.value] = (outs, getattr(self, "_keep_density", None))
         return t.value, outs
+
+
+class Batch:
+    """Many Laplace plans in one persistent launch (tsqbx_batch_*).  The plans
+    must outlive the batch."""
+
+    def __init__(self, plans, use_graph=True):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        check(lib().tsqbx_batch_create(arr, len(self.plans), 1 if use_graph else 0, ctypes.byref(h)),
+              "tsqbx_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tsqbx_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def eval_async(self, densities, outs, stream=None):
+        """densities: list of device tensors; outs: list of {'slp': t, 'dlp': t}."""
+        n = len(self.plans)
+        ptr = lambda t: None if t is None else t.data_ptr()
+        d = (ctypes.c_void_p * n)(*[ptr(x) for x in densities])
+        s = (ctypes.c_void_p * n)(*[ptr(o.get("slp")) for o in outs])
+        dl = (ctypes.c_void_p * n)(*[ptr(o.get("dlp")) for o in outs])
+        handle = None
+        if stream is not None:
+            handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        check(lib().tsqbx_batch_eval_async(self._h, d, s, dl, handle), "tsqbx_batch_eval_async")
+
+    def kernel_ms(self):
+        ms = ctypes.c_float()
+        check(lib().tsqbx_batch_kernel_ms(self._h, ctypes.byref(ms)), "tsqbx_batch_kernel_ms")
+        return float(ms.value)
+
+    def info(self):
+        st = _lib.tsqbx_batch_stats()
+        check(lib().tsqbx_batch_info(self._h, ctypes.byref(st)), "tsqbx_batch_info")
+        return {name: getattr(st, name) for name, _ in st._fields_}
 
 
 def poll(ticket, timeout_us=0):

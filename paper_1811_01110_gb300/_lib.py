@@ -21,7 +21,7 @@ TSQBX_NOALLOC_MAX_SRC = 1048544
 TSQBX_LAPLACE, TSQBX_HELMHOLTZ = 0, 1
 TSQBX_SLP, TSQBX_DLP = 1, 2
 TSQBX_FP64, TSQBX_MIXED = 0, 1
-TSQBX_FLAG_ALLOW_DIVERGENT, TSQBX_FLAG_SKIP_CHECK = 1, 2
+TSQBX_FLAG_ALLOW_DIVERGENT, TSQBX_FLAG_SKIP_CHECK, TSQBX_FLAG_USE_TUNED = 1, 2, 4
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -54,7 +54,21 @@ class tsqbx_plan_stats(ctypes.Structure):
         ("n_items", ctypes.c_int64), ("n_divergent", ctypes.c_int64),
         ("n_coincident", ctypes.c_int64), ("list_entries", ctypes.c_int64),
         ("lane_utilisation", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+        ("n_sliced", ctypes.c_int64), ("launches_per_eval", ctypes.c_int),
     ]
+
+
+class tsqbx_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_plans", ctypes.c_int64), ("n_items", ctypes.c_int64), ("n_sliced", ctypes.c_int64),
+        ("n_pairs", ctypes.c_int64), ("n_pair_terms", ctypes.c_int64), ("grid_blocks", ctypes.c_int),
+        ("graph", ctypes.c_int), ("launches_per_eval", ctypes.c_int), ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+class tsqbx_tuning(ctypes.Structure):
+    _fields_ = [("lanes_per_target", ctypes.c_int), ("max_item_iters", ctypes.c_int),
+                ("kernel_ms", ctypes.c_float)]
 
 
 # (name, restype, argtypes) for every entry point declared in include/tsqbx.h
@@ -72,9 +86,22 @@ _SIGNATURES = [
       ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_poll", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
     ("tsqbx_plan_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("tsqbx_plan_autotune", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tsqbx_tuning)]),
+    ("tsqbx_plan_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_tuning)]),
+    ("tsqbx_plan_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_tuning)]),
+    ("tsqbx_batch_create", ctypes.c_int,
+     [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("tsqbx_batch_destroy", None, [ctypes.c_void_p]),
+    ("tsqbx_batch_eval_async", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+      ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
+    ("tsqbx_batch_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
+    ("tsqbx_batch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_batch_stats)]),
     ("tsqbx_eval_noalloc", ctypes.c_int,
      [ctypes.POINTER(tsqbx_geometry), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("tsqbx_last_error", ctypes.c_char_p, []),
     ("tsqbx_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("tsqbx_version", ctypes.c_int, []),
 ]
@@ -105,7 +132,10 @@ def strerror(code):
 class TsqbxError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        super().__init__(f"{where}: {strerror(code)} ({code})")
+        detail = ""
+        if code in (TSQBX_E_CUDA, TSQBX_E_NOMEM):
+            detail = f" [{lib().tsqbx_last_error().decode()}]"
+        super().__init__(f"{where}: {strerror(code)} ({code}){detail}")
 
 
 def check(code, where):

@@ -1,6 +1,6 @@
 // plan.cu -- host side of libtsqbx: plan construction (validation, grouping of
-// targets into warp work items, packing of source/target records, upload,
-// convergence check), evaluation, and the submit/poll ticket machinery.
+// targets, work schedule, packing and upload of source/target records, the
+// convergence check), evaluation, submit/poll tickets and the autotuner.
 //
 // The C ABI is declared in include/tsqbx.h; every entry point below traps C++
 // exceptions and converts CUDA failures into TSQBX_E_* codes.
@@ -9,14 +9,15 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
-#include "internal.cuh"
-#include "tsqbx.h"
+#include "plan_internal.h"
 
 using namespace tsqbx;
 
@@ -24,7 +25,7 @@ namespace {
 
 // ------------------------------------------------------------- prep kernels
 
-// Per-evaluation source weights times density: w_s mu_s in the form each
+// Per-evaluation source weights times density, w_s mu_s, in the form each
 // kernel family stages.
 __global__ void prep_wmu_fp64(const double4_32a *src_pw, const double *mu, int64_t n, double *out)
 {
@@ -106,34 +107,6 @@ __global__ void combine_kernel(const DevGeom g, const double *part_slp, const do
 
 // ------------------------------------------------------------------ helpers
 
-struct CudaFail {
-    cudaError_t err;
-};
-
-inline void ck(cudaError_t e)
-{
-    if (e != cudaSuccess) throw CudaFail{e};
-}
-
-int status_of(cudaError_t e)
-{
-    if (e == cudaErrorMemoryAllocation) return TSQBX_E_NOMEM;
-    return TSQBX_E_CUDA;
-}
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) ck(cudaSetDevice(dev));
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 bool is_device_ptr(const void *p)
 {
     if (!p) return false;
@@ -156,83 +129,25 @@ void split_ff(double v, float &hi, float &lo)
     lo = (float)(v - (double)hi);
 }
 
-}  // namespace
-
-// ------------------------------------------------------------------- plan
-
-struct Slot {
-    cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    void *d_density = nullptr;     // device copy of a host density
-    void *d_wmu = nullptr;         // w mu scratch (f64, f32 or c128)
-    double *d_out[2] = {nullptr, nullptr};
-    double *d_part[2] = {nullptr, nullptr};   // partial sums of sliced items
-    int *d_status = nullptr;
-    void *h_density = nullptr;     // pinned staging
-    void *h_out[2] = {nullptr, nullptr};
-    int *h_status = nullptr;
-    bool busy = false;
-    uint64_t ticket = 0;
-    void *user_out[2] = {nullptr, nullptr};
-    bool copy_out[2] = {false, false};
-};
-
-struct tsqbx_plan_s {
-    tsqbx_options opt{};
-    DevGeom g;
-    std::vector<void *> dev_allocs;
-    std::vector<void *> host_allocs;
-    size_t device_bytes = 0;
-    tsqbx_plan_stats stats{};
-    std::vector<Slot> slots;
-    std::mutex mu;
-    cudaEvent_t k_begin = nullptr, k_end = nullptr;   // brackets the expansion kernel (slot 0)
-    bool k_timed = false;
-    size_t density_bytes = 0, out_bytes = 0, wmu_bytes = 0;
-
-    template <class T>
-    T *dalloc(size_t count)
-    {
-        if (count == 0) count = 1;
-        void *p = nullptr;
-        ck(cudaMalloc(&p, count * sizeof(T)));
-        dev_allocs.push_back(p);
-        device_bytes += count * sizeof(T);
-        return static_cast<T *>(p);
-    }
-    template <class T>
-    T *upload(const std::vector<T> &v)
-    {
-        T *p = dalloc<T>(v.size());
-        if (!v.empty()) ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-        return p;
-    }
-    void *halloc(size_t bytes)
-    {
-        void *p = nullptr;
-        ck(cudaMallocHost(&p, bytes ? bytes : 1));
-        host_allocs.push_back(p);
-        return p;
-    }
-    ~tsqbx_plan_s()
-    {
-        for (auto &s : slots) {
-            if (s.stream) cudaStreamSynchronize(s.stream);
-            if (s.done) cudaEventDestroy(s.done);
-            if (s.stream) cudaStreamDestroy(s.stream);
-        }
-        if (k_begin) cudaEventDestroy(k_begin);
-        if (k_end) cudaEventDestroy(k_end);
-        for (void *p : dev_allocs) cudaFree(p);
-        for (void *p : host_allocs) cudaFreeHost(p);
-    }
-};
-
-namespace {
-
 std::mutex g_ticket_mu;
 std::unordered_map<uint64_t, std::pair<tsqbx_plan, int>> g_tickets;
 std::atomic<uint64_t> g_next_ticket{1};
+
+// Process-wide tuning cache: (kernel, precision, p, layers, list shape) -> tuning.
+using TuneKey = std::tuple<int, int, int, unsigned, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, tsqbx_tuning> g_tune_cache;
+
+TuneKey tune_key(tsqbx_plan P)
+{
+    // list shape: half-octave buckets of the mean sources per group and the
+    // mean targets per group (what the lane choice and slicing depend on)
+    const double ns = P->list_hist.size() > 0 ? P->list_hist[0] : 0.0;
+    const double nt = P->list_hist.size() > 1 ? P->list_hist[1] : 0.0;
+    const int bs = ns > 0 ? (int)std::lround(2.0 * std::log2(ns)) : -1;
+    const int bt = nt > 0 ? (int)std::lround(2.0 * std::log2(nt)) : -1;
+    return TuneKey{(int)P->opt.kernel, (int)P->opt.precision, P->opt.p, P->opt.layers, bs, bt};
+}
 
 int validate(const tsqbx_geometry *G, const tsqbx_options *o)
 {
@@ -279,8 +194,28 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
     return TSQBX_OK;
 }
 
-// Lanes per target for a group of nt targets sharing ns sources: minimise the
-// warp-time estimate  items(L) * (ceil(ns / L) + staging + setup).
+void fill_stats(tsqbx_plan P)
+{
+    tsqbx_plan_stats &st = P->stats;
+    st.n_items = P->g.n_items;
+    st.lane_utilisation = P->sched.lane_utilisation;
+    st.device_bytes = P->device_bytes;
+    st.n_sliced = (int64_t)P->sched.combine.size();
+    st.launches_per_eval = (P->g.n_src > 0 ? 1 : 0) + (P->g.n_items > 0 ? 1 : 0) + (st.n_sliced > 0 ? 1 : 0);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- schedules
+
+namespace tsqbx {
+
+static thread_local const char *t_last_error = "no error";
+
+void note_cuda_error(cudaError_t e) { t_last_error = cudaGetErrorName(e); }
+
+int cost_bucket(double cost) { return cost > 0 ? (int)std::floor(2.0 * std::log2(cost)) : -1; }
+
 int choose_lanes(int64_t nt, int64_t ns)
 {
     int best = 1;
@@ -294,11 +229,165 @@ int choose_lanes(int64_t nt, int64_t ns)
     return best;
 }
 
-}  // namespace
+int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
+                   int n_sm, Schedule &out)
+{
+    struct Chunk { int64_t q, slot, m; int L; int64_t ns; };
+    std::vector<Chunk> chunks;
+    int64_t total_iters = 0;
+    for (const GroupWork &w : groups) {
+        const int L = lanes_policy ? lanes_policy : choose_lanes(w.nt, w.ns);
+        const int64_t tpw = 32 / L;
+        for (int64_t b = 0; b < w.nt; b += tpw) {
+            chunks.push_back({w.q, w.slot_begin + b, std::min(tpw, w.nt - b), L, w.ns});
+            total_iters += (w.ns + L - 1) / L;
+        }
+    }
+    if (max_iters <= 0)
+        max_iters = std::min<int64_t>(512, std::max<int64_t>(32, total_iters / ((int64_t)n_sm * 48)));
+    Schedule s;
+    s.lanes_policy = lanes_policy;
+    s.max_iters = max_iters;
+    double used = 0.0, offered = 0.0;
+    for (const Chunk &c : chunks) {
+        const int64_t iters = (c.ns + c.L - 1) / c.L;
+        const int64_t K = iters > max_iters ? (iters + max_iters - 1) / max_iters : 1;
+        int64_t base = -1;
+        if (K > 1) {
+            base = s.n_parts;
+            s.n_parts += K * c.m;
+            if (s.n_parts > INT32_MAX) return TSQBX_E_INVAL;
+            s.combine.push_back({(int32_t)c.slot, (int32_t)c.m, (int32_t)base, (int32_t)K});
+        }
+        for (int64_t k = 0; k < K; ++k) {
+            const int64_t lo = c.ns * k / K, hi = c.ns * (k + 1) / K;
+            const double cost = (double)((hi - lo + c.L - 1) / c.L) + 0.25 * (double)(hi - lo) / 32.0 + 4.0;
+            Item it;
+            it.group = (int32_t)c.q;
+            it.slot_begin = (int32_t)c.slot;
+            it.n_tgt = (int32_t)c.m;
+            it.L = c.L;
+            it.src_lo = (int32_t)lo;
+            it.src_hi = (int32_t)hi;
+            it.part = K > 1 ? (int32_t)(base + k * c.m) : -1;
+            it.pad = 0;
+            s.items.push_back({it, cost});
+            used += cost * (double)(c.m * c.L);
+            offered += cost * 32.0;
+        }
+    }
+    // heaviest first, by half-octave cost bucket; within a bucket the items
+    // keep list order, so neighbouring groups (which share many sources) run
+    // close together in time and share cached source data
+    std::stable_sort(s.items.begin(), s.items.end(), [](const Schedule::Entry &a, const Schedule::Entry &b) {
+        return cost_bucket(a.cost) > cost_bucket(b.cost);
+    });
+    s.lane_utilisation = offered > 0 ? used / offered : 1.0;
+    out = std::move(s);
+    return TSQBX_OK;
+}
+
+void apply_schedule(tsqbx_plan P, Schedule &&s)
+{
+    const bool helm = P->opt.kernel == TSQBX_HELMHOLTZ;
+    std::vector<Item> items(s.items.size());
+    for (size_t i = 0; i < items.size(); ++i) items[i] = s.items[i].it;
+    if (P->g.items) P->dfree(P->g.items);
+    if (P->g.combine) P->dfree(P->g.combine);
+    P->g.items = nullptr;
+    P->g.combine = nullptr;
+    for (Slot &sl : P->slots)
+        for (int l = 0; l < 2; ++l) {
+            if (sl.d_part[l]) P->dfree(sl.d_part[l]);
+            sl.d_part[l] = nullptr;
+        }
+    P->g.items = P->upload(items);
+    P->g.combine = P->upload(s.combine);
+    P->g.n_items = (int64_t)items.size();
+    P->g.n_combine = (int64_t)s.combine.size();
+    P->g.n_parts = s.n_parts;
+    const size_t part_doubles = (size_t)s.n_parts * (helm ? 2 : 1);
+    for (Slot &sl : P->slots) {
+        if (s.n_parts && (P->opt.layers & TSQBX_SLP)) sl.d_part[0] = P->dalloc<double>(part_doubles);
+        if (s.n_parts && (P->opt.layers & TSQBX_DLP)) sl.d_part[1] = P->dalloc<double>(part_doubles);
+    }
+    P->sched = std::move(s);
+    fill_stats(P);
+}
+
+int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
+            cudaStream_t s, bool timed)
+{
+    const tsqbx_options &o = P->opt;
+    const int64_t n = P->g.n_src;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)P->n_sm * 16);
+    DevEval ev;
+    ev.status = slot.d_status;
+    ev.out_slp = (o.layers & TSQBX_SLP) ? d_slp : nullptr;
+    ev.out_dlp = (o.layers & TSQBX_DLP) ? d_dlp : nullptr;
+    ev.part_slp = slot.d_part[0];
+    ev.part_dlp = slot.d_part[1];
+    ev.k = o.k;
+    if (n > 0) {
+        if (o.kernel == TSQBX_HELMHOLTZ) {
+            prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double2 *>(d_density), n,
+                                                     static_cast<double2 *>(slot.d_wmu));
+        } else if (o.precision == TSQBX_MIXED) {
+            prep_wmu_f32<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double *>(d_density), n,
+                                                    static_cast<float *>(slot.d_wmu));
+        } else {
+            prep_wmu_fp64<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double *>(d_density), n,
+                                                     static_cast<double *>(slot.d_wmu));
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return status_of(e);
+    }
+    ev.wmu = static_cast<const double *>(slot.d_wmu);
+    ev.wmu_f = static_cast<const float *>(slot.d_wmu);
+    ev.wmu_c = static_cast<const double2 *>(slot.d_wmu);
+    const bool slp = (o.layers & TSQBX_SLP) != 0, dlp = (o.layers & TSQBX_DLP) != 0;
+    if (timed) ck(cudaEventRecord(P->k_begin, s));
+    int rc;
+    if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(o.p, slp, dlp, P->g, ev, s);
+    else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(o.p, slp, dlp, P->g, ev, s);
+    else rc = launch_laplace_fp64(o.p, slp, dlp, P->g, ev, s);
+    if (rc != 0) return status_of((cudaError_t)rc);
+    if (P->g.n_combine > 0) {
+        const int64_t th = P->g.n_combine * 32;
+        const int cb = (int)std::min<int64_t>((th + 255) / 256, (int64_t)P->n_sm * 8);
+        combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp, ev.part_dlp, ev.out_slp, ev.out_dlp,
+                                          o.kernel == TSQBX_HELMHOLTZ ? 2 : 1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return status_of(e);
+    }
+    if (timed) {
+        ck(cudaEventRecord(P->k_end, s));
+        P->k_timed = true;
+    }
+    return TSQBX_OK;
+}
+
+}  // namespace tsqbx
+
+tsqbx_plan_s::~tsqbx_plan_s()
+{
+    for (auto &s : slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    if (k_begin) cudaEventDestroy(k_begin);
+    if (k_end) cudaEventDestroy(k_end);
+    for (auto &kv : dev_allocs) cudaFree(kv.first);
+    for (void *p : host_allocs) cudaFreeHost(p);
+}
 
 extern "C" {
 
-int tsqbx_version(void) { return 10000; }
+int tsqbx_version(void) { return 10100; }
+
+const char *tsqbx_last_error(void) { return t_last_error; }
 
 const char *tsqbx_strerror(int status)
 {
@@ -331,6 +420,12 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         P = new tsqbx_plan_s;
         P->opt = *o;
         if (P->opt.n_slots == 0) P->opt.n_slots = 2;
+        {
+            int v = 0;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, o->device) == cudaSuccess && v > 0)
+                P->n_sm = v;
+            cudaGetLastError();
+        }
         const bool dlp = (o->layers & TSQBX_DLP) != 0;
         const bool mixed = o->precision == TSQBX_MIXED;
         const int64_t n_src = G->n_src, n_tgt = G->n_tgt, n_group = G->n_group;
@@ -359,65 +454,18 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             for (int64_t r = G->group_range_start[q]; r < G->group_range_start[q + 1]; ++r)
                 for (int32_t s = G->range_begin[r]; s < G->range_end[r]; ++s) grp_src[w++] = s;
         }
-        // work items, heaviest first; long lists are cut into source slices
-        // so that no warp item exceeds max_iters lane iterations
-        int n_sm = 152;
-        {
-            int dev = 0, v = 0;
-            if (cudaGetDevice(&dev) == cudaSuccess &&
-                cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-                n_sm = v;
-            cudaGetLastError();
-        }
-        struct Chunk { int64_t q, slot, m; int L; int64_t ns; };
-        std::vector<Chunk> chunks;
-        int64_t n_pairs = 0, total_iters = 0;
+        int64_t n_pairs = 0, n_busy = 0;
+        double sum_ns = 0.0;
         for (int64_t q = 0; q < n_group; ++q) {
             const int64_t nt = tcount[q + 1] - tcount[q];
             if (nt == 0) continue;
             const int64_t ns = grp_off[q + 1] - grp_off[q];
+            P->groups.push_back({q, tcount[q], nt, ns});
             n_pairs += nt * ns;
-            const int L = o->lanes_per_target ? o->lanes_per_target : choose_lanes(nt, ns);
-            const int64_t tpw = 32 / L;
-            for (int64_t b = 0; b < nt; b += tpw) {
-                chunks.push_back({q, tcount[q] + b, std::min(tpw, nt - b), L, ns});
-                total_iters += (ns + L - 1) / L;
-            }
+            sum_ns += (double)ns;
+            ++n_busy;
         }
-        int64_t max_iters = o->max_item_iters;
-        if (max_iters <= 0)
-            max_iters = std::min<int64_t>(512, std::max<int64_t>(32, total_iters / ((int64_t)n_sm * 48)));
-        struct ItemC { Item it; double cost; };
-        std::vector<ItemC> items;
-        std::vector<Combine> combine_v;
-        int64_t n_parts = 0;
-        double used = 0.0, offered = 0.0;
-        for (const Chunk &c : chunks) {
-            const int64_t iters = (c.ns + c.L - 1) / c.L;
-            const int64_t K = iters > max_iters ? (iters + max_iters - 1) / max_iters : 1;
-            int64_t base = -1;
-            if (K > 1) {
-                base = n_parts;
-                n_parts += K * c.m;
-                if (n_parts > INT32_MAX) { delete P; return TSQBX_E_INVAL; }
-                combine_v.push_back({(int32_t)c.slot, (int32_t)c.m, (int32_t)base, (int32_t)K});
-            }
-            for (int64_t k = 0; k < K; ++k) {
-                const int64_t lo = c.ns * k / K, hi = c.ns * (k + 1) / K;
-                const double cost = (double)((hi - lo + c.L - 1) / c.L) + 0.25 * (double)(hi - lo) / 32.0 + 4.0;
-                Item it;
-                it.group = (int32_t)c.q; it.slot_begin = (int32_t)c.slot; it.n_tgt = (int32_t)c.m; it.L = c.L;
-                it.src_lo = (int32_t)lo; it.src_hi = (int32_t)hi;
-                it.part = K > 1 ? (int32_t)(base + k * c.m) : -1; it.pad = 0;
-                items.push_back({it, cost});
-                used += cost * (double)(c.m * c.L);
-                offered += cost * 32.0;
-            }
-        }
-        std::stable_sort(items.begin(), items.end(),
-                         [](const ItemC &a, const ItemC &b) { return a.cost > b.cost; });
-        std::vector<Item> item_v(items.size());
-        for (size_t i = 0; i < items.size(); ++i) item_v[i] = items[i].it;
+        P->list_hist = {n_busy ? sum_ns / n_busy : 0.0, n_busy ? (double)n_tgt / n_busy : 0.0};
 
         // target slot records
         std::vector<double4_32a> slot_c(n_tgt), slot_e(n_tgt);
@@ -464,15 +512,10 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
                 src_lo[s] = make_float4(l[0], l[1], l[2], 0.f);
             }
         }
-        // upload
+        // upload geometry
         DevGeom &g = P->g;
         g.n_src = n_src;
         g.n_tgt = n_tgt;
-        g.n_items = (int64_t)item_v.size();
-        g.items = P->upload(item_v);
-        g.n_combine = (int64_t)combine_v.size();
-        g.n_parts = n_parts;
-        g.combine = P->upload(combine_v);
         g.grp_off = P->upload(grp_off);
         g.grp_src = P->upload(grp_src);
         g.src_pw = P->upload(src_pw);
@@ -489,20 +532,57 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         g.slot_c = P->upload(slot_c);
         g.slot_e = P->upload(slot_e);
 
+        // evaluation slots (slot 0 serves tsqbx_eval / tsqbx_eval_async)
+        const bool helm = o->kernel == TSQBX_HELMHOLTZ;
+        P->density_bytes = (size_t)n_src * (helm ? 2 : 1) * sizeof(double);
+        P->out_bytes = (size_t)n_tgt * (helm ? 2 : 1) * sizeof(double);
+        P->wmu_bytes = (size_t)n_src * (helm ? sizeof(double2) : mixed ? sizeof(float) : sizeof(double));
+        P->slots.resize(P->opt.n_slots + 1);
+        for (auto &s : P->slots) {
+            ck(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+            ck(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+            s.d_density = P->dalloc<char>(P->density_bytes);
+            s.d_wmu = P->dalloc<char>(P->wmu_bytes);
+            if (o->layers & TSQBX_SLP) s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            s.d_status = P->dalloc<int>(1);
+            s.h_density = P->halloc(P->density_bytes);
+            s.h_out[0] = P->halloc(P->out_bytes);
+            s.h_out[1] = P->halloc(P->out_bytes);
+            s.h_status = static_cast<int *>(P->halloc(sizeof(int)));
+        }
+        ck(cudaEventCreate(&P->k_begin));
+        ck(cudaEventCreate(&P->k_end));
+
+        // work schedule: options, else a cached tuning, else automatic
+        int lanes = o->lanes_per_target;
+        int64_t max_iters = o->max_item_iters;
+        if ((o->flags & TSQBX_FLAG_USE_TUNED) && !lanes && !max_iters) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(tune_key(P));
+            if (it != g_tune_cache.end()) {
+                lanes = it->second.lanes_per_target;
+                max_iters = it->second.max_item_iters;
+            }
+        }
+        Schedule sched;
+        if ((rc = build_schedule(P->groups, lanes, max_iters, P->n_sm, sched)) != TSQBX_OK) {
+            delete P;
+            return rc;
+        }
+        apply_schedule(P, std::move(sched));
+
         // convergence check on the device
         int64_t n_div = 0, n_zero = 0;
         if (!(o->flags & TSQBX_FLAG_SKIP_CHECK) && g.n_items > 0) {
-            unsigned long long *cnt = nullptr;
-            ck(cudaMalloc(&cnt, 2 * sizeof(unsigned long long)));
+            unsigned long long *cnt = P->dalloc<unsigned long long>(2);
             ck(cudaMemset(cnt, 0, 2 * sizeof(unsigned long long)));
             const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
             check_pairs_kernel<<<(unsigned)blocks, kWarpsPerBlock * 32>>>(g, cnt, cnt + 1);
+            ck(cudaGetLastError());
             unsigned long long h[2] = {0, 0};
-            cudaError_t e1 = cudaGetLastError();
-            cudaError_t e2 = cudaMemcpy(h, cnt, sizeof(h), cudaMemcpyDeviceToHost);
-            cudaFree(cnt);
-            ck(e1);
-            ck(e2);
+            ck(cudaMemcpy(h, cnt, sizeof(h), cudaMemcpyDeviceToHost));
+            P->dfree(cnt);
             n_div = (int64_t)h[0];
             n_zero = (int64_t)h[1];
             if (n_zero > 0 || (n_div > 0 && !(o->flags & TSQBX_FLAG_ALLOW_DIVERGENT))) {
@@ -511,32 +591,6 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             }
         }
 
-        // evaluation slots
-        const bool helm = o->kernel == TSQBX_HELMHOLTZ;
-        P->density_bytes = (size_t)n_src * (helm ? 2 : 1) * sizeof(double);
-        P->out_bytes = (size_t)n_tgt * (helm ? 2 : 1) * sizeof(double);
-        P->wmu_bytes = (size_t)n_src * (helm ? sizeof(double2) : mixed ? sizeof(float) : sizeof(double));
-        P->slots.resize(P->opt.n_slots + 1);   // slot 0 serves tsqbx_eval / tsqbx_eval_async
-        for (auto &s : P->slots) {
-            ck(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
-            ck(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
-            s.d_density = P->dalloc<char>(P->density_bytes);
-            s.d_wmu = P->dalloc<char>(P->wmu_bytes);
-            if (o->layers & TSQBX_SLP) s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
-            if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
-            const size_t part_doubles = (size_t)n_parts * (helm ? 2 : 1);
-            if (n_parts && (o->layers & TSQBX_SLP)) s.d_part[0] = P->dalloc<double>(part_doubles);
-            if (n_parts && (o->layers & TSQBX_DLP)) s.d_part[1] = P->dalloc<double>(part_doubles);
-            s.d_status = P->dalloc<int>(1);
-            s.h_density = P->halloc(P->density_bytes);
-            s.h_out[0] = P->halloc(P->out_bytes);
-            s.h_out[1] = P->halloc(P->out_bytes);
-            s.h_status = static_cast<int *>(P->halloc(sizeof(int)));
-        }
-
-        ck(cudaEventCreate(&P->k_begin));
-        ck(cudaEventCreate(&P->k_end));
-
         tsqbx_plan_stats &st = P->stats;
         st.n_src = n_src;
         st.n_ctr = G->n_ctr;
@@ -544,12 +598,10 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         st.n_group = n_group;
         st.n_pairs = n_pairs;
         st.n_pair_terms = n_pairs * (int64_t)(o->p + 1);
-        st.n_items = g.n_items;
         st.n_divergent = n_div;
         st.n_coincident = n_zero;
         st.list_entries = grp_off[n_group];
-        st.lane_utilisation = offered > 0 ? used / offered : 1.0;
-        st.device_bytes = P->device_bytes;
+        fill_stats(P);
         *out = P;
         return TSQBX_OK;
     } catch (const CudaFail &f) {
@@ -590,11 +642,16 @@ int tsqbx_plan_info(tsqbx_plan P, tsqbx_plan_stats *st)
 int tsqbx_plan_kernel_ms(tsqbx_plan P, float *ms)
 {
     if (!P || !ms || !P->k_timed) return TSQBX_E_INVAL;
-    DeviceGuard dg(P->opt.device);
-    cudaError_t e = cudaEventSynchronize(P->k_end);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, P->k_begin, P->k_end);
-    if (e != cudaSuccess) { cudaGetLastError(); return status_of(e); }
-    return TSQBX_OK;
+    try {
+        DeviceGuard dg(P->opt.device);
+        cudaError_t e = cudaEventSynchronize(P->k_end);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, P->k_begin, P->k_end);
+        if (e != cudaSuccess) { cudaGetLastError(); return status_of(e); }
+        return TSQBX_OK;
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    }
 }
 
 int tsqbx_plan_footprint(tsqbx_plan P, size_t *bytes)
@@ -604,64 +661,101 @@ int tsqbx_plan_footprint(tsqbx_plan P, size_t *bytes)
     return TSQBX_OK;
 }
 
+int tsqbx_plan_get_tuning(tsqbx_plan P, tsqbx_tuning *t)
+{
+    if (!P || !t) return TSQBX_E_INVAL;
+    t->lanes_per_target = P->sched.lanes_policy;
+    t->max_item_iters = (int)P->sched.max_iters;
+    t->kernel_ms = 0.f;
+    return TSQBX_OK;
+}
+
+int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
+{
+    if (!P || !t || t->lanes_per_target < 0 || t->lanes_per_target > 32 || t->max_item_iters < 0)
+        return TSQBX_E_INVAL;
+    try {
+        DeviceGuard dg(P->opt.device);
+        std::lock_guard<std::mutex> lk(P->mu);
+        for (Slot &s : P->slots) ck(cudaStreamSynchronize(s.stream));
+        Schedule sched;
+        int rc = build_schedule(P->groups, t->lanes_per_target, t->max_item_iters, P->n_sm, sched);
+        if (rc) return rc;
+        apply_schedule(P, std::move(sched));
+        return TSQBX_OK;
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    } catch (const std::bad_alloc &) {
+        return TSQBX_E_NOMEM;
+    }
+}
+
+int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_tuning *chosen)
+{
+    if (!P || (P->g.n_src && !d_density) || repeats < 1) return TSQBX_E_INVAL;
+    try {
+        DeviceGuard dg(P->opt.device);
+        std::lock_guard<std::mutex> lk(P->mu);
+        Slot &slot = P->slots[0];
+        for (Slot &s : P->slots) ck(cudaStreamSynchronize(s.stream));
+        auto time_current = [&](float &median_ms) -> int {
+            float acc[64];
+            const int reps = std::min(repeats, 64);
+            for (int r = -1; r < reps; ++r) {
+                int rc = enqueue(P, slot, d_density, slot.d_out[0], slot.d_out[1], slot.stream, true);
+                if (rc) return rc;
+                ck(cudaEventSynchronize(P->k_end));
+                float ms = 0.f;
+                ck(cudaEventElapsedTime(&ms, P->k_begin, P->k_end));
+                if (r >= 0) acc[r] = ms;
+            }
+            std::sort(acc, acc + reps);
+            median_ms = acc[reps / 2];
+            return TSQBX_OK;
+        };
+        struct Cand { int lanes; int64_t iters; float ms; };
+        Cand best{P->sched.lanes_policy, P->sched.max_iters, 0.f};
+        int rc = time_current(best.ms);
+        if (rc) return rc;
+        auto trial = [&](int lanes, int64_t iters) -> int {
+            Schedule sched;
+            int r = build_schedule(P->groups, lanes, iters, P->n_sm, sched);
+            if (r) return r;
+            apply_schedule(P, std::move(sched));
+            float ms = 0.f;
+            if ((r = time_current(ms)) != TSQBX_OK) return r;
+            if (ms < best.ms) best = {lanes, P->sched.max_iters, ms};
+            return TSQBX_OK;
+        };
+        // stage 1: slice caps with the current lane policy; stage 2: lane
+        // policies at the best cap
+        for (int64_t iters : {64, 128, 256, 512, 1024, 2048})
+            if ((rc = trial(best.lanes, iters)) != TSQBX_OK) return rc;
+        const int64_t cap = best.iters;
+        for (int lanes : {0, 1, 2, 4, 8, 16})
+            if ((rc = trial(lanes, cap)) != TSQBX_OK) return rc;
+        Schedule sched;
+        if ((rc = build_schedule(P->groups, best.lanes, best.iters, P->n_sm, sched)) != TSQBX_OK) return rc;
+        apply_schedule(P, std::move(sched));
+        tsqbx_tuning t{best.lanes, (int)best.iters, best.ms};
+        {
+            std::lock_guard<std::mutex> tl(g_tune_mu);
+            g_tune_cache[tune_key(P)] = t;
+        }
+        if (chosen) *chosen = t;
+        return TSQBX_OK;
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    } catch (const std::bad_alloc &) {
+        return TSQBX_E_NOMEM;
+    }
+}
+
 }  // extern "C"
 
 namespace {
-
-// Enqueue prep + kernel for one evaluation on stream s using slot scratch.
-int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
-            cudaStream_t s)
-{
-    const tsqbx_options &o = P->opt;
-    const int64_t n = P->g.n_src;
-    const int threads = 256;
-    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 16);
-    DevEval ev;
-    ev.status = slot.d_status;
-    ev.out_slp = (o.layers & TSQBX_SLP) ? d_slp : nullptr;
-    ev.out_dlp = (o.layers & TSQBX_DLP) ? d_dlp : nullptr;
-    ev.part_slp = slot.d_part[0];
-    ev.part_dlp = slot.d_part[1];
-    ev.k = o.k;
-    if (n > 0) {
-        if (o.kernel == TSQBX_HELMHOLTZ) {
-            prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double2 *>(d_density), n,
-                                                     static_cast<double2 *>(slot.d_wmu));
-        } else if (o.precision == TSQBX_MIXED) {
-            prep_wmu_f32<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double *>(d_density), n,
-                                                    static_cast<float *>(slot.d_wmu));
-        } else {
-            prep_wmu_fp64<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double *>(d_density), n,
-                                                     static_cast<double *>(slot.d_wmu));
-        }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return status_of(e);
-    }
-    ev.wmu = static_cast<const double *>(slot.d_wmu);
-    ev.wmu_f = static_cast<const float *>(slot.d_wmu);
-    ev.wmu_c = static_cast<const double2 *>(slot.d_wmu);
-    const bool slp = (o.layers & TSQBX_SLP) != 0, dlp = (o.layers & TSQBX_DLP) != 0;
-    const bool timed = &slot == &P->slots[0];
-    if (timed) ck(cudaEventRecord(P->k_begin, s));
-    int rc;
-    if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(o.p, slp, dlp, P->g, ev, s);
-    else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(o.p, slp, dlp, P->g, ev, s);
-    else rc = launch_laplace_fp64(o.p, slp, dlp, P->g, ev, s);
-    if (rc != 0) return status_of((cudaError_t)rc);
-    if (P->g.n_combine > 0) {
-        const int64_t th = P->g.n_combine * 32;
-        const int cb = (int)std::min<int64_t>((th + 255) / 256, 152 * 8);
-        combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp, ev.part_dlp, ev.out_slp, ev.out_dlp,
-                                          o.kernel == TSQBX_HELMHOLTZ ? 2 : 1);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return status_of(e);
-    }
-    if (timed) {
-        ck(cudaEventRecord(P->k_end, s));
-        P->k_timed = true;
-    }
-    return TSQBX_OK;
-}
 
 bool layer_args_ok(tsqbx_plan P, const void *out_slp, const void *out_dlp)
 {
@@ -672,7 +766,7 @@ bool layer_args_ok(tsqbx_plan P, const void *out_slp, const void *out_dlp)
 
 // Stage inputs, enqueue, and (for host outputs) copy back into pinned
 // staging; records slot.done.  Host outputs are delivered by finish().
-int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *out_dlp)
+int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *out_dlp, bool timed)
 {
     const void *d_density = density;
     if (P->g.n_src && !is_device_ptr(density)) {
@@ -691,7 +785,7 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
         else { d_outs[l] = slot.d_out[l]; slot.copy_out[l] = true; }
     }
     ck(cudaMemsetAsync(slot.d_status, 0, sizeof(int), slot.stream));
-    int rc = enqueue(P, slot, d_density, d_outs[0], d_outs[1], slot.stream);
+    int rc = enqueue(P, slot, d_density, d_outs[0], d_outs[1], slot.stream, timed);
     if (rc) return rc;
     for (int l = 0; l < 2; ++l)
         if (slot.copy_out[l] && P->out_bytes)
@@ -720,7 +814,7 @@ int tsqbx_eval(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp)
         DeviceGuard dg(P->opt.device);
         std::lock_guard<std::mutex> lk(P->mu);
         Slot &slot = P->slots[0];
-        int rc = start(P, slot, density, out_slp, out_dlp);
+        int rc = start(P, slot, density, out_slp, out_dlp, true);
         if (rc) return rc;
         ck(cudaEventSynchronize(slot.done));
         return finish(P, slot);
@@ -739,7 +833,8 @@ int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void 
         DeviceGuard dg(P->opt.device);
         Slot &slot = P->slots[0];
         cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : slot.stream;
-        return enqueue(P, slot, d_density, static_cast<double *>(d_out_slp), static_cast<double *>(d_out_dlp), s);
+        return enqueue(P, slot, d_density, static_cast<double *>(d_out_slp), static_cast<double *>(d_out_dlp),
+                       s, true);
     } catch (const CudaFail &f) {
         cudaGetLastError();
         return status_of(f.err);
@@ -760,7 +855,7 @@ int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp
             if (!P->slots[i].busy) { idx = (int)i; break; }
         if (idx < 0) return TSQBX_E_BUSY;
         Slot &slot = P->slots[idx];
-        int rc = start(P, slot, density, out_slp, out_dlp);
+        int rc = start(P, slot, density, out_slp, out_dlp, false);
         if (rc) return rc;
         slot.busy = true;
         slot.ticket = g_next_ticket.fetch_add(1);

@@ -1,0 +1,152 @@
+// plan_internal.h -- host-side plan structures shared by plan.cu (plans,
+// evaluation, tickets, tuning) and batch.cu (persistent batched launches).
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.cuh"
+#include "tsqbx.h"
+
+namespace tsqbx {
+
+struct CudaFail {
+    cudaError_t err;
+};
+
+inline void ck(cudaError_t e)
+{
+    if (e != cudaSuccess) throw CudaFail{e};
+}
+
+// Name of the last CUDA error a library call on this thread ran into.
+void note_cuda_error(cudaError_t e);
+
+inline int status_of(cudaError_t e)
+{
+    note_cuda_error(e);
+    return e == cudaErrorMemoryAllocation ? TSQBX_E_NOMEM : TSQBX_E_CUDA;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) ck(cudaSetDevice(dev));
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// One group's share of the work: its targets are the slots
+// [slot_begin, slot_begin + nt) and it lists ns sources.
+struct GroupWork {
+    int64_t q, slot_begin, nt, ns;
+};
+
+// How the work is cut into warp items.
+struct Schedule {
+    struct Entry { Item it; double cost; };
+    std::vector<Entry> items;          // sorted by cost, heaviest first
+    std::vector<Combine> combine;
+    int64_t n_parts = 0;
+    int lanes_policy = 0;              // 0 = per-group choice, else forced L
+    int64_t max_iters = 0;             // cap on lane iterations per item
+    double lane_utilisation = 1.0;
+};
+
+// Half-octave bucket of an item's estimated cost (queue order key).
+int cost_bucket(double cost);
+// Lanes per target chosen for a group (items * (lane iterations + staging)).
+int choose_lanes(int64_t nt, int64_t ns);
+// Build the schedule; max_iters <= 0 picks the automatic cap.
+int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
+                   int n_sm, Schedule &out);
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void *d_density = nullptr;     // device copy of a host density
+    void *d_wmu = nullptr;         // w mu scratch (f64, f32 or c128)
+    double *d_out[2] = {nullptr, nullptr};
+    double *d_part[2] = {nullptr, nullptr};   // partial sums of sliced items
+    int *d_status = nullptr;
+    void *h_density = nullptr;     // pinned staging
+    void *h_out[2] = {nullptr, nullptr};
+    int *h_status = nullptr;
+    bool busy = false;
+    uint64_t ticket = 0;
+    void *user_out[2] = {nullptr, nullptr};
+    bool copy_out[2] = {false, false};
+};
+
+}  // namespace tsqbx
+
+struct tsqbx_plan_s {
+    tsqbx_options opt{};
+    tsqbx::DevGeom g;
+    std::unordered_map<void *, size_t> dev_allocs;
+    std::vector<void *> host_allocs;
+    size_t device_bytes = 0;
+    tsqbx_plan_stats stats{};
+    std::vector<tsqbx::Slot> slots;
+    std::mutex mu;
+    size_t density_bytes = 0, out_bytes = 0, wmu_bytes = 0;
+    cudaEvent_t k_begin = nullptr, k_end = nullptr;   // brackets the expansion (slot 0)
+    bool k_timed = false;
+    int n_sm = 152;
+    std::vector<tsqbx::GroupWork> groups;             // kept for rescheduling
+    tsqbx::Schedule sched;                            // host copy of the current items
+    std::vector<double> list_hist;                    // tuning-cache signature
+
+    template <class T>
+    T *dalloc(size_t count)
+    {
+        if (count == 0) count = 1;
+        void *p = nullptr;
+        tsqbx::ck(cudaMalloc(&p, count * sizeof(T)));
+        dev_allocs[p] = count * sizeof(T);
+        device_bytes += count * sizeof(T);
+        return static_cast<T *>(p);
+    }
+    void dfree(const void *cp)
+    {
+        void *p = const_cast<void *>(cp);
+        auto it = dev_allocs.find(p);
+        if (it == dev_allocs.end()) return;
+        device_bytes -= it->second;
+        dev_allocs.erase(it);
+        cudaFree(p);
+    }
+    template <class T>
+    T *upload(const std::vector<T> &v)
+    {
+        T *p = dalloc<T>(v.size());
+        if (!v.empty()) tsqbx::ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return p;
+    }
+    void *halloc(size_t bytes)
+    {
+        void *p = nullptr;
+        tsqbx::ck(cudaMallocHost(&p, bytes ? bytes : 1));
+        host_allocs.push_back(p);
+        return p;
+    }
+    ~tsqbx_plan_s();
+};
+
+namespace tsqbx {
+
+// Install a schedule on a plan: upload items and combine records, size the
+// partial-sum buffers of every slot (frees what the old schedule used).
+void apply_schedule(tsqbx_plan P, Schedule &&s);
+// Enqueue prep + expansion (+ combine) for one evaluation on stream s.
+int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
+            cudaStream_t s, bool timed);
+
+}  // namespace tsqbx

@@ -69,6 +69,16 @@ def test_laplace_sliced_lists(pkg, precision, max_iters):
     check_laplace(pkg, g, mu, 6, precision, max_item_iters=max_iters, lanes_per_target=5)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("p,max_iters", [(0, 0), (4, 0), (9, 0), (9, 2), (13, 5)])
+def test_laplace_single_target_groups(pkg, precision, p, max_iters):
+    """One target per group: the direct-load path (no shared-memory staging)."""
+    rng = np.random.default_rng(61 + p)
+    g = cloud_geometry(rng, n_ctr=40, n_src=500, q_max=0.6, tgt_per_ctr=1, list_frac=0.5)
+    mu = rng.standard_normal(g.n_src)
+    check_laplace(pkg, g, mu, p, precision, max_item_iters=max_iters)
+
+
 def test_helmholtz_sliced_lists(pkg):
     rng = np.random.default_rng(37)
     g = cloud_geometry(rng, n_ctr=5, n_src=300, q_max=0.5, tgt_per_ctr=7, list_frac=0.9)

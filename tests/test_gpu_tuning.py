@@ -1,0 +1,59 @@
+"""Autotuner and schedule controls (tsqbx_plan_autotune / set / get tuning)."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import cloud_geometry
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_01110_gb300 as pkg
+    pkg.lib()
+    return torch, pkg
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_autotune_keeps_results_and_caches(env, precision, tol):
+    torch, pkg = env
+    rng = np.random.default_rng(41)
+    g = cloud_geometry(rng, n_ctr=30, n_src=600, q_max=0.5, tgt_per_ctr=9, list_frac=0.6)
+    mu = rng.standard_normal(g.n_src)
+    ref = oracle.tsqbx_laplace(g, 7, mu, slp=True, dlp=True)
+    with pkg.Plan(g, "laplace", ("slp", "dlp"), p=7, precision=precision) as plan:
+        t = plan.autotune(torch.from_numpy(mu).cuda(), repeats=3)
+        assert t["max_item_iters"] in (64, 128, 256, 512, 1024, 2048) or t["max_item_iters"] > 0
+        assert t["lanes_per_target"] in (0, 1, 2, 4, 8, 16)
+        assert t["kernel_ms"] > 0
+        assert plan.get_tuning()["max_item_iters"] == t["max_item_iters"]
+        out = plan.eval(mu)
+        for l in ("slp", "dlp"):
+            assert relerr(out[l], ref[l]) <= tol
+    # a new plan with the same shape starts from the cached choice
+    with pkg.Plan(g, "laplace", ("slp", "dlp"), p=7, precision=precision, use_tuned=True) as plan2:
+        assert plan2.get_tuning() == {"lanes_per_target": t["lanes_per_target"],
+                                      "max_item_iters": t["max_item_iters"]}
+
+
+def test_set_tuning_roundtrip(env):
+    torch, pkg = env
+    rng = np.random.default_rng(43)
+    g = cloud_geometry(rng, n_ctr=10, n_src=300, tgt_per_ctr=5)
+    mu = rng.standard_normal(g.n_src)
+    ref = oracle.tsqbx_laplace(g, 5, mu)["slp"]
+    with pkg.Plan(g, "laplace", ("slp",), p=5) as plan:
+        for lanes, iters in ((1, 3), (4, 50), (0, 1), (32, 1000)):
+            plan.set_tuning(lanes, iters)
+            assert plan.get_tuning() == {"lanes_per_target": lanes, "max_item_iters": iters}
+            assert relerr(plan.eval(mu)["slp"], ref) <= 1e-12
+        info = plan.info()
+        assert info["launches_per_eval"] in (2, 3)

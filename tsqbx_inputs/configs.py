@@ -102,23 +102,28 @@ def _torus_core(c, R=1.0):
 
 def ellipsoid(freq, axes, list_len_range=(50, 800), rng=None, seed_offset=0):
     """One ellipsoid of the batched workload: geodesic sphere of frequency freq
-    scaled by axes, one center per node (alternating sides), nearest lists with
-    log-uniform lengths."""
+    (20 freq^2 triangles, 120 freq^2 sources) scaled by axes, one center per
+    node (alternating sides).  Each center is its own group and lists one
+    window of consecutive sources in Morton order (spatially local) around its
+    node, of log-uniform length in list_len_range."""
     rng = rng if rng is not None else np.random.default_rng(BASE_SEED + 3 + seed_offset)
     V, F = mesh.geodesic_sphere(freq)
     V = V * np.asarray(axes)[None, :]
     F = mesh.orient_outward(V, F, lambda c: np.zeros_like(c))
     xyz, w, nrm, h = _surface_nodes(V, F)
-    sign = np.where(np.arange(len(xyz)) % 2 == 0, 1.0, -1.0)
+    n = len(xyz)
+    sign = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
     C, Rr, T, Tn, node = mesh.centers_and_targets(xyz, nrm, h, [sign])
     lo, hi = np.log(list_len_range[0]), np.log(list_len_range[1])
-    counts = np.minimum(np.exp(rng.uniform(lo, hi, len(C))).astype(np.int64), len(xyz))
-    grs, rb, re = L.nearest_lists(xyz, C, counts)
-    n = len(C)
+    counts = np.minimum(np.exp(rng.uniform(lo, hi, len(C))).astype(np.int64), n)
+    rb = np.clip(node - counts // 2, 0, None)
+    rb = np.minimum(rb, n - counts).astype(np.int32)
+    re = (rb + counts).astype(np.int32)
+    m = len(C)
     g = Geometry(np.ascontiguousarray(xyz.T), w, np.ascontiguousarray(nrm.T),
                  np.ascontiguousarray(C.T), Rr, np.ascontiguousarray(T.T),
-                 np.arange(n, dtype=np.int32), np.ascontiguousarray(Tn.T),
-                 np.arange(n, dtype=np.int32), grs, rb, re)
+                 np.arange(m, dtype=np.int32), np.ascontiguousarray(Tn.T),
+                 np.arange(m, dtype=np.int32), np.arange(m + 1, dtype=np.int64), rb, re)
     g.meta.update(name=f"ellipsoid-f{freq}", kernel="laplace")
     return g, dens.sphere_density(xyz, rng)
 
