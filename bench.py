@@ -351,6 +351,73 @@ def leg_sphere(pkg, torch, dev, steps, warmup, flush):
     return res
 
 
+def leg_serving(pkg, duration_s=6.0, rate=200.0, seed=20191114):
+    """Serving: Poisson arrivals over 16 resident geometries (5k-300k sources);
+    each request a Laplace FP64, Laplace mixed or Helmholtz (k in {1,5,10})
+    single-layer evaluation with p in {5,9,12} and a new seeded density.
+    Plans are built first (warm start); if the offered rate exceeds capacity
+    a second phase runs at 80 % of the measured capacity."""
+    import threading
+    from tsqbx_inputs import configs
+    geoms = configs.serving_geometries()
+    kinds = [("laplace", "fp64", 0.0), ("laplace", "mixed", 0.0), ("helmholtz", "fp64", 1.0),
+             ("helmholtz", "fp64", 5.0), ("helmholtz", "fp64", 10.0)]
+    srv = pkg.Server(hbm_budget=96 << 30, max_inflight=64)
+    gids = [srv.add_geometry(g, with_normals=False) for g in geoms]
+    for gid in gids:
+        for kernel, prec, k in (("laplace", "fp64", 0.0), ("laplace", "mixed", 0.0), ("helmholtz", "fp64", 1.0)):
+            srv.prepare(gid, kernel, ("slp",), 5, k, prec)
+    rng = np.random.default_rng(seed)
+    dens_pool = [rng.standard_normal(g.n_src) for g in geoms]
+
+    def phase(rate_hz, seconds):
+        srv.reset_stats()
+        n = int(rate_hz * seconds)
+        gaps = rng.exponential(1.0 / rate_hz, n)
+        reqs = []
+        t0 = time.perf_counter()
+        due = t0
+        for i in range(n):
+            due += gaps[i]
+            now = time.perf_counter()
+            if due > now:
+                time.sleep(due - now)
+            gi = int(rng.integers(len(geoms)))
+            kernel, prec, k = kinds[int(rng.integers(len(kinds)))]
+            p = int(rng.choice([5, 9, 12]))
+            mu = dens_pool[gi] * (1.0 + 0.01 * i)
+            if kernel == "helmholtz":
+                mu = mu * np.exp(1j * 0.1 * i)
+            rid, _ = srv.submit(gids[gi], mu, kernel, ("slp",), p, k, prec)
+            reqs.append(rid)
+        t_submit = time.perf_counter() - t0
+        for rid in reqs:
+            srv.poll(rid, timeout_us=-1)
+        st = srv.stats()
+        return {"offered_req_per_s": rate_hz, "requests": n, "submit_s": t_submit,
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                "completed": st["completed"], "failed": st["failed"], "rejected": st["rejected"],
+                "achieved_req_per_s": st["completed"] / max(st["span_s"], 1e-9),
+                "pair_terms_per_s": st["pair_terms_completed"] / max(st["span_s"], 1e-9),
+                "span_s": st["span_s"]}
+
+    first = phase(rate, duration_s)
+    res = {"workload": "16 resident geometries (spheres, ellipsoids, tori; %d-%d sources), Poisson "
+                       "arrivals, Laplace FP64 / mixed or Helmholtz k in {1,5,10}, SLP, p in {5,9,12}"
+                       % (min(g.n_src for g in geoms), max(g.n_src for g in geoms)),
+           "offered": first}
+    capacity = first["achieved_req_per_s"]
+    saturated = first["span_s"] > 1.15 * first["submit_s"]
+    res["saturated_at_offered_rate"] = bool(saturated)
+    if saturated:
+        res["sustainable"] = phase(0.8 * capacity, duration_s)
+    st = srv.stats()
+    res["plans_resident"] = st["plans_resident"]
+    res["resident_bytes"] = st["resident_bytes"]
+    srv.close()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -437,6 +504,7 @@ def main():
     if not args.no_extras and rank == 0:
         for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere)):
             extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush)
+        extras["serving"] = leg_serving(pkg)
 
     if rank != 0:
         return

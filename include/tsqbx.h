@@ -177,6 +177,15 @@ TSQBX_API int tsqbx_plan_footprint(tsqbx_plan plan, size_t *bytes);
  * outputs are written.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA, TSQBX_E_KERNEL. */
 TSQBX_API int tsqbx_eval(tsqbx_plan plan, const void *density, void *out_slp, void *out_dlp);
 
+/* tsqbx_eval / tsqbx_submit with the expansion order p (0..TSQBX_P_MAX) and,
+ * for Helmholtz, the wavenumber k (> 0) chosen per call: the plan's geometry,
+ * lists and schedule do not depend on them, so one plan serves every order
+ * and wavenumber.  Errors as tsqbx_eval / tsqbx_submit. */
+TSQBX_API int tsqbx_eval_pk(tsqbx_plan plan, int p, double k, const void *density, void *out_slp,
+                            void *out_dlp);
+TSQBX_API int tsqbx_submit_pk(tsqbx_plan plan, int p, double k, const void *density, void *out_slp,
+                              void *out_dlp, uint64_t *ticket);
+
 /* Asynchronous evaluation on DEVICE pointers only (same layouts as
  * tsqbx_eval), enqueued on `stream` (a cudaStream_t; NULL = the plan's own
  * stream).  Returns once the work is enqueued; the caller orders later work
@@ -248,6 +257,54 @@ TSQBX_API int tsqbx_batch_eval_async(tsqbx_batch batch, const void *const *d_den
  * TSQBX_E_KERNEL if a kernel flagged an out-of-range index. */
 TSQBX_API int tsqbx_batch_kernel_ms(tsqbx_batch batch, float *ms);
 TSQBX_API int tsqbx_batch_info(tsqbx_batch batch, tsqbx_batch_stats *stats);
+
+/* -------------------------------------------------------------- serving
+ * A request-serving runtime: geometries are registered once; requests (one
+ * evaluation of one geometry with a kernel variant and a density) arrive at
+ * any time and are admitted as soon as their plan -- created on first use and
+ * keyed by (geometry, kernel, layers, precision); p and k are per request --
+ * has a free slot and
+ * the resident plans fit the HBM budget (idle plans are evicted least recently
+ * used).  Started requests run on their own plan slots and streams, so work
+ * that arrives while other requests are on the GPU overlaps with them
+ * (continuous batching).  A worker thread owned by the server does the
+ * admission and completion bookkeeping. */
+typedef struct tsqbx_server_s *tsqbx_server;
+
+typedef struct {
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency, arrival to completion   */
+    int64_t completed, failed, rejected;     /* rejected: could never be admitted */
+    int64_t queued, running;
+    int64_t plans_resident, plans_created, plans_evicted;
+    size_t resident_bytes;
+    int64_t pair_terms_completed;
+    double span_s;                           /* first arrival to last completion */
+} tsqbx_server_stats;
+
+/* hbm_budget_bytes: cap on the device memory of resident plans; max_inflight:
+ * cap on requests running at once.  Errors: TSQBX_E_INVAL, TSQBX_E_NOMEM. */
+TSQBX_API int tsqbx_server_create(int device, size_t hbm_budget_bytes, int max_inflight, tsqbx_server *out);
+/* Waits for running requests, stops the worker, frees every plan. */
+TSQBX_API void tsqbx_server_destroy(tsqbx_server server);
+/* Copies the geometry (host arrays, tsqbx_geometry layout); *geom_id names it. */
+TSQBX_API int tsqbx_server_add_geometry(tsqbx_server server, const tsqbx_geometry *geometry, int *geom_id);
+/* Builds (or refreshes in the LRU order) the plan for a variant ahead of
+ * requests.  Errors: TSQBX_E_INVAL, TSQBX_E_NOMEM (larger than the budget),
+ * TSQBX_E_BUSY (budget held by running work), plan-creation errors. */
+TSQBX_API int tsqbx_server_prepare(tsqbx_server server, int geom_id, const tsqbx_options *options);
+/* Queue one evaluation.  options: kernel, layers, p, k, precision (+ tuning
+ * fields); device is the server's.  The density (host, layout as tsqbx_eval)
+ * is copied before return; out_slp / out_dlp are HOST buffers written before
+ * the request reports completion and must stay valid until then. */
+TSQBX_API int tsqbx_server_submit(tsqbx_server server, int geom_id, const tsqbx_options *options,
+                                  const void *density, void *out_slp, void *out_dlp, uint64_t *request);
+/* 0 once the request completed (its outputs written; the request is then
+ * retired), TSQBX_PENDING (timeout_us == 0), TSQBX_E_TIMEOUT, or the
+ * request's failure code (e.g. TSQBX_E_NOMEM if it could never fit). */
+TSQBX_API int tsqbx_server_poll(tsqbx_server server, uint64_t request, int timeout_us);
+TSQBX_API int tsqbx_server_get_stats(tsqbx_server server, tsqbx_server_stats *stats);
+/* Clears latency samples and counters (e.g. after a warm-up phase). */
+TSQBX_API int tsqbx_server_reset_stats(tsqbx_server server);
 
 /* ------------------------------------------------------------- tuning
  * Work decomposition of a plan: lanes per target (0 = chosen per group from

@@ -46,46 +46,58 @@ def _addr(x, nbytes, what):
     return ctypes.c_void_p(x.ctypes.data)
 
 
+def marshal_geometry(g, with_normals=True):
+    """tsqbx_geometry view of a geometry object (host numpy arrays); returns
+    (struct, keep) where keep holds the contiguous copies alive."""
+    f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    keep = dict(src_xyz=f64(g.src_xyz), src_weight=f64(g.src_weight),
+                src_normal=f64(g.src_normal) if with_normals else None,
+                ctr_xyz=f64(g.ctr_xyz), ctr_radius=f64(getattr(g, "ctr_radius", None)),
+                tgt_xyz=f64(g.tgt_xyz), tgt_center=i32(g.tgt_center), ctr_group=i32(g.ctr_group),
+                group_range_start=np.ascontiguousarray(g.group_range_start, dtype=np.int64),
+                range_begin=i32(g.range_begin), range_end=i32(g.range_end))
+    n_tgt = int(keep["tgt_xyz"].shape[1]) if keep["tgt_xyz"].ndim == 2 else 0
+    geo = _lib.tsqbx_geometry(
+        int(keep["src_weight"].shape[0]), _ptr(keep["src_xyz"], ctypes.c_double),
+        _ptr(keep["src_weight"], ctypes.c_double), _ptr(keep["src_normal"], ctypes.c_double),
+        int(keep["ctr_xyz"].shape[1]), _ptr(keep["ctr_xyz"], ctypes.c_double),
+        _ptr(keep["ctr_radius"], ctypes.c_double),
+        n_tgt, _ptr(keep["tgt_xyz"], ctypes.c_double), _ptr(keep["tgt_center"], ctypes.c_int32),
+        int(keep["group_range_start"].shape[0] - 1), _ptr(keep["ctr_group"], ctypes.c_int32),
+        _ptr(keep["group_range_start"], ctypes.c_int64),
+        _ptr(keep["range_begin"], ctypes.c_int32), _ptr(keep["range_end"], ctypes.c_int32))
+    return geo, keep
+
+
+def make_options(kernel="laplace", layers=("slp",), p=5, k=0.0, precision="fp64", device=0, flags=0,
+                 lanes_per_target=0, n_slots=2, max_item_iters=0):
+    mask = 0
+    for name in layers:
+        mask |= _LAYERS[name]
+    return _lib.tsqbx_options(_KERNELS[kernel], mask, int(p), float(k), _PRECISIONS[precision],
+                              int(device), int(flags), int(lanes_per_target), int(n_slots),
+                              int(max_item_iters))
+
+
 class Plan:
     """A device-resident TSQBX evaluation plan (tsqbx_plan_create)."""
 
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
                  lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False):
-        g = geometry
         self.kernel = kernel
         self.layers = tuple(layers)
         self.p = int(p)
+        self.k = float(k)
         self.complex = kernel == "helmholtz"
-        f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
-        i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
-        keep = dict(src_xyz=f64(g.src_xyz), src_weight=f64(g.src_weight),
-                    src_normal=f64(g.src_normal) if "dlp" in self.layers else None,
-                    ctr_xyz=f64(g.ctr_xyz), ctr_radius=f64(getattr(g, "ctr_radius", None)),
-                    tgt_xyz=f64(g.tgt_xyz), tgt_center=i32(g.tgt_center),
-                    ctr_group=i32(g.ctr_group),
-                    group_range_start=np.ascontiguousarray(g.group_range_start, dtype=np.int64),
-                    range_begin=i32(g.range_begin), range_end=i32(g.range_end))
-        self.n_src = int(keep["src_weight"].shape[0])
-        self.n_tgt = int(keep["tgt_xyz"].shape[1]) if keep["tgt_xyz"].ndim == 2 else 0
-        geo = _lib.tsqbx_geometry(
-            self.n_src, _ptr(keep["src_xyz"], ctypes.c_double), _ptr(keep["src_weight"], ctypes.c_double),
-            _ptr(keep["src_normal"], ctypes.c_double),
-            int(keep["ctr_xyz"].shape[1]), _ptr(keep["ctr_xyz"], ctypes.c_double),
-            _ptr(keep["ctr_radius"], ctypes.c_double),
-            self.n_tgt, _ptr(keep["tgt_xyz"], ctypes.c_double), _ptr(keep["tgt_center"], ctypes.c_int32),
-            int(keep["group_range_start"].shape[0] - 1), _ptr(keep["ctr_group"], ctypes.c_int32),
-            _ptr(keep["group_range_start"], ctypes.c_int64),
-            _ptr(keep["range_begin"], ctypes.c_int32), _ptr(keep["range_end"], ctypes.c_int32))
-        mask = 0
-        for name in self.layers:
-            mask |= _LAYERS[name]
+        geo, keep = marshal_geometry(geometry, with_normals="dlp" in self.layers)
+        self.n_src, self.n_tgt = int(geo.n_src), int(geo.n_tgt)
         flags = (_lib.TSQBX_FLAG_ALLOW_DIVERGENT if allow_divergent else 0) | \
                 (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0) | \
                 (_lib.TSQBX_FLAG_USE_TUNED if use_tuned else 0)
-        opt = _lib.tsqbx_options(_KERNELS[kernel], mask, self.p, float(k), _PRECISIONS[precision],
-                                 int(device), flags, int(lanes_per_target), int(n_slots),
-                                 int(max_item_iters))
+        opt = make_options(kernel, self.layers, self.p, k, precision, device, flags,
+                           lanes_per_target, n_slots, max_item_iters)
         h = ctypes.c_void_p()
         check(lib().tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)),
               "tsqbx_plan_create")
@@ -169,13 +181,20 @@ class Plan:
         nb = self.n_tgt * 8 * self.width
         return (_addr(outs.get("slp"), nb, "out_slp"), _addr(outs.get("dlp"), nb, "out_dlp"))
 
-    def eval(self, density, out=None):
-        """Blocking evaluation (tsqbx_eval).  density: numpy (host) or torch
-        CUDA tensor; returns a dict of outputs of the same kind."""
+    def eval(self, density, out=None, p=None, k=None):
+        """Blocking evaluation (tsqbx_eval; tsqbx_eval_pk when p or k is given).
+        density: numpy (host) or torch CUDA tensor; returns a dict of outputs
+        of the same kind."""
         like = density if _is_torch(density) and density.is_cuda else None
         outs = out if out is not None else self._alloc_out(like)
         a_slp, a_dlp = self._out_addrs(outs)
-        check(lib().tsqbx_eval(self._h, self._density_addr(density), a_slp, a_dlp), "tsqbx_eval")
+        d = self._density_addr(density)
+        if p is None and k is None:
+            check(lib().tsqbx_eval(self._h, d, a_slp, a_dlp), "tsqbx_eval")
+        else:
+            pp = self.p if p is None else int(p)
+            kk = self.k if k is None else float(k)
+            check(lib().tsqbx_eval_pk(self._h, pp, kk, d, a_slp, a_dlp), "tsqbx_eval_pk")
         return outs
 
     def eval_async(self, density, out, stream=None):
@@ -252,6 +271,85 @@ class Batch:
         st = _lib.tsqbx_batch_stats()
         check(lib().tsqbx_batch_info(self._h, ctypes.byref(st)), "tsqbx_batch_info")
         return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+class Server:
+    """Request-serving runtime (tsqbx_server_*): register geometries, submit
+    evaluations as they arrive, poll for completion, read p50/p99 latency."""
+
+    def __init__(self, device=0, hbm_budget=16 << 30, max_inflight=64):
+        h = ctypes.c_void_p()
+        check(lib().tsqbx_server_create(int(device), int(hbm_budget), int(max_inflight), ctypes.byref(h)),
+              "tsqbx_server_create")
+        self._h = h
+        self._geoms = {}
+        self._pending = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tsqbx_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_geometry(self, g, with_normals=True):
+        geo, keep = marshal_geometry(g, with_normals)
+        gid = ctypes.c_int()
+        check(lib().tsqbx_server_add_geometry(self._h, ctypes.byref(geo), ctypes.byref(gid)),
+              "tsqbx_server_add_geometry")
+        self._geoms[gid.value] = (int(geo.n_src), int(geo.n_tgt))
+        return gid.value
+
+    def prepare(self, gid, kernel="laplace", layers=("slp",), p=5, k=0.0, precision="fp64"):
+        opt = make_options(kernel, layers, p, k, precision)
+        check(lib().tsqbx_server_prepare(self._h, int(gid), ctypes.byref(opt)), "tsqbx_server_prepare")
+
+    def submit(self, gid, density, kernel="laplace", layers=("slp",), p=5, k=0.0, precision="fp64"):
+        """Queue a request; returns (request_id, outs) with host output arrays
+        that are valid once poll() returns True."""
+        if gid not in self._geoms:
+            raise TsqbxError(_lib.TSQBX_E_INVAL, "tsqbx_server_submit")
+        n_src, n_tgt = self._geoms[gid]
+        cplx = kernel == "helmholtz"
+        dens = np.ascontiguousarray(density, dtype=np.complex128 if cplx else np.float64)
+        outs = {l: np.empty(n_tgt, dtype=np.complex128 if cplx else np.float64) for l in layers}
+        opt = make_options(kernel, layers, p, k, precision)
+        rid = ctypes.c_uint64()
+        check(lib().tsqbx_server_submit(self._h, int(gid), ctypes.byref(opt), ctypes.c_void_p(dens.ctypes.data),
+                                        None if "slp" not in outs else ctypes.c_void_p(outs["slp"].ctypes.data),
+                                        None if "dlp" not in outs else ctypes.c_void_p(outs["dlp"].ctypes.data),
+                                        ctypes.byref(rid)), "tsqbx_server_submit")
+        self._pending[rid.value] = outs
+        return rid.value, outs
+
+    def poll(self, rid, timeout_us=0):
+        """True once done (raises TsqbxError if the request failed), False while pending."""
+        rc = lib().tsqbx_server_poll(self._h, ctypes.c_uint64(rid), int(timeout_us))
+        if rc == _lib.TSQBX_PENDING:
+            return False
+        if rc == _lib.TSQBX_E_TIMEOUT:
+            return False
+        self._pending.pop(rid, None)
+        check(rc, "tsqbx_server_poll")
+        return True
+
+    def stats(self):
+        st = _lib.tsqbx_server_stats()
+        check(lib().tsqbx_server_get_stats(self._h, ctypes.byref(st)), "tsqbx_server_get_stats")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def reset_stats(self):
+        check(lib().tsqbx_server_reset_stats(self._h), "tsqbx_server_reset_stats")
 
 
 def poll(ticket, timeout_us=0):

@@ -66,6 +66,17 @@ class tsqbx_batch_stats(ctypes.Structure):
     ]
 
 
+class tsqbx_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+        ("max_ms", ctypes.c_double), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+        ("rejected", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+        ("plans_resident", ctypes.c_int64), ("plans_created", ctypes.c_int64),
+        ("plans_evicted", ctypes.c_int64), ("resident_bytes", ctypes.c_size_t),
+        ("pair_terms_completed", ctypes.c_int64), ("span_s", ctypes.c_double),
+    ]
+
+
 class tsqbx_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_target", ctypes.c_int), ("max_item_iters", ctypes.c_int),
                 ("kernel_ms", ctypes.c_float)]
@@ -85,6 +96,11 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
       ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_poll", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    ("tsqbx_eval_pk", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("tsqbx_submit_pk", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_plan_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     ("tsqbx_plan_autotune", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tsqbx_tuning)]),
@@ -98,6 +114,19 @@ _SIGNATURES = [
       ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     ("tsqbx_batch_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     ("tsqbx_batch_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_batch_stats)]),
+    ("tsqbx_server_create", ctypes.c_int,
+     [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("tsqbx_server_destroy", None, [ctypes.c_void_p]),
+    ("tsqbx_server_add_geometry", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.POINTER(tsqbx_geometry), ctypes.POINTER(ctypes.c_int)]),
+    ("tsqbx_server_prepare", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tsqbx_options)]),
+    ("tsqbx_server_submit", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tsqbx_options), ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    ("tsqbx_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]),
+    ("tsqbx_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_server_stats)]),
+    ("tsqbx_server_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
     ("tsqbx_eval_noalloc", ctypes.c_int,
      [ctypes.POINTER(tsqbx_geometry), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

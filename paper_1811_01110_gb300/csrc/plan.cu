@@ -316,7 +316,7 @@ void apply_schedule(tsqbx_plan P, Schedule &&s)
 }
 
 int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
-            cudaStream_t s, bool timed)
+            cudaStream_t s, bool timed, int p, double k)
 {
     const tsqbx_options &o = P->opt;
     const int64_t n = P->g.n_src;
@@ -328,7 +328,7 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     ev.out_dlp = (o.layers & TSQBX_DLP) ? d_dlp : nullptr;
     ev.part_slp = slot.d_part[0];
     ev.part_dlp = slot.d_part[1];
-    ev.k = o.k;
+    ev.k = k;
     if (n > 0) {
         if (o.kernel == TSQBX_HELMHOLTZ) {
             prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double2 *>(d_density), n,
@@ -349,9 +349,9 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     const bool slp = (o.layers & TSQBX_SLP) != 0, dlp = (o.layers & TSQBX_DLP) != 0;
     if (timed) ck(cudaEventRecord(P->k_begin, s));
     int rc;
-    if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(o.p, slp, dlp, P->g, ev, s);
-    else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(o.p, slp, dlp, P->g, ev, s);
-    else rc = launch_laplace_fp64(o.p, slp, dlp, P->g, ev, s);
+    if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(p, slp, dlp, P->g, ev, s);
+    else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(p, slp, dlp, P->g, ev, s);
+    else rc = launch_laplace_fp64(p, slp, dlp, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
     if (P->g.n_combine > 0) {
         const int64_t th = P->g.n_combine * 32;
@@ -703,7 +703,8 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
             float acc[64];
             const int reps = std::min(repeats, 64);
             for (int r = -1; r < reps; ++r) {
-                int rc = enqueue(P, slot, d_density, slot.d_out[0], slot.d_out[1], slot.stream, true);
+                int rc = enqueue(P, slot, d_density, slot.d_out[0], slot.d_out[1], slot.stream, true,
+                                 P->opt.p, P->opt.k);
                 if (rc) return rc;
                 ck(cudaEventSynchronize(P->k_end));
                 float ms = 0.f;
@@ -757,6 +758,12 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
 
 namespace {
 
+bool pk_ok(tsqbx_plan P, int p, double k)
+{
+    if (p < 0 || p > TSQBX_P_MAX) return false;
+    return P->opt.kernel != TSQBX_HELMHOLTZ || (k > 0.0 && std::isfinite(k));
+}
+
 bool layer_args_ok(tsqbx_plan P, const void *out_slp, const void *out_dlp)
 {
     if ((P->opt.layers & TSQBX_SLP) && !out_slp && P->g.n_tgt) return false;
@@ -766,7 +773,8 @@ bool layer_args_ok(tsqbx_plan P, const void *out_slp, const void *out_dlp)
 
 // Stage inputs, enqueue, and (for host outputs) copy back into pinned
 // staging; records slot.done.  Host outputs are delivered by finish().
-int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *out_dlp, bool timed)
+int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *out_dlp, bool timed, int p,
+          double k)
 {
     const void *d_density = density;
     if (P->g.n_src && !is_device_ptr(density)) {
@@ -785,7 +793,7 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
         else { d_outs[l] = slot.d_out[l]; slot.copy_out[l] = true; }
     }
     ck(cudaMemsetAsync(slot.d_status, 0, sizeof(int), slot.stream));
-    int rc = enqueue(P, slot, d_density, d_outs[0], d_outs[1], slot.stream, timed);
+    int rc = enqueue(P, slot, d_density, d_outs[0], d_outs[1], slot.stream, timed, p, k);
     if (rc) return rc;
     for (int l = 0; l < 2; ++l)
         if (slot.copy_out[l] && P->out_bytes)
@@ -807,14 +815,15 @@ int finish(tsqbx_plan P, Slot &slot)
 
 extern "C" {
 
-int tsqbx_eval(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp)
+int tsqbx_eval_pk(tsqbx_plan P, int p, double k, const void *density, void *out_slp, void *out_dlp)
 {
-    if (!P || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp)) return TSQBX_E_INVAL;
+    if (!P || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp) || !pk_ok(P, p, k))
+        return TSQBX_E_INVAL;
     try {
         DeviceGuard dg(P->opt.device);
         std::lock_guard<std::mutex> lk(P->mu);
         Slot &slot = P->slots[0];
-        int rc = start(P, slot, density, out_slp, out_dlp, true);
+        int rc = start(P, slot, density, out_slp, out_dlp, true, p, k);
         if (rc) return rc;
         ck(cudaEventSynchronize(slot.done));
         return finish(P, slot);
@@ -826,6 +835,12 @@ int tsqbx_eval(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp)
     }
 }
 
+int tsqbx_eval(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp)
+{
+    if (!P) return TSQBX_E_INVAL;
+    return tsqbx_eval_pk(P, P->opt.p, P->opt.k, density, out_slp, out_dlp);
+}
+
 int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void *d_out_dlp, void *stream)
 {
     if (!P || (P->g.n_src && !d_density) || !layer_args_ok(P, d_out_slp, d_out_dlp)) return TSQBX_E_INVAL;
@@ -834,7 +849,7 @@ int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void 
         Slot &slot = P->slots[0];
         cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : slot.stream;
         return enqueue(P, slot, d_density, static_cast<double *>(d_out_slp), static_cast<double *>(d_out_dlp),
-                       s, true);
+                       s, true, P->opt.p, P->opt.k);
     } catch (const CudaFail &f) {
         cudaGetLastError();
         return status_of(f.err);
@@ -843,9 +858,10 @@ int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void 
     }
 }
 
-int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp, uint64_t *ticket)
+int tsqbx_submit_pk(tsqbx_plan P, int p, double k, const void *density, void *out_slp, void *out_dlp,
+                    uint64_t *ticket)
 {
-    if (!P || !ticket || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp))
+    if (!P || !ticket || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp) || !pk_ok(P, p, k))
         return TSQBX_E_INVAL;
     try {
         DeviceGuard dg(P->opt.device);
@@ -855,7 +871,7 @@ int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp
             if (!P->slots[i].busy) { idx = (int)i; break; }
         if (idx < 0) return TSQBX_E_BUSY;
         Slot &slot = P->slots[idx];
-        int rc = start(P, slot, density, out_slp, out_dlp, false);
+        int rc = start(P, slot, density, out_slp, out_dlp, false, p, k);
         if (rc) return rc;
         slot.busy = true;
         slot.ticket = g_next_ticket.fetch_add(1);
@@ -871,6 +887,12 @@ int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp
     } catch (...) {
         return TSQBX_E_CUDA;
     }
+}
+
+int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp, uint64_t *ticket)
+{
+    if (!P) return TSQBX_E_INVAL;
+    return tsqbx_submit_pk(P, P->opt.p, P->opt.k, density, out_slp, out_dlp, ticket);
 }
 
 int tsqbx_poll(uint64_t ticket, int timeout_us)

@@ -145,8 +145,9 @@ namespace tsqbx {
 // Install a schedule on a plan: upload items and combine records, size the
 // partial-sum buffers of every slot (frees what the old schedule used).
 void apply_schedule(tsqbx_plan P, Schedule &&s);
-// Enqueue prep + expansion (+ combine) for one evaluation on stream s.
+// Enqueue prep + expansion (+ combine) for one evaluation on stream s, with
+// expansion order p and (Helmholtz) wavenumber k.
 int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
-            cudaStream_t s, bool timed);
+            cudaStream_t s, bool timed, int p, double k);
 
 }  // namespace tsqbx

@@ -142,3 +142,26 @@ def ellipsoid_batch(n_surfaces=64, min_src=1000, max_src=200000, seed_offset=0):
         g.meta["p"] = p
         out.append((g, mu))
     return out
+
+
+def serving_geometries(n=16, min_src=5000, max_src=300000, seed_offset=0):
+    """The resident geometries of the serving workload: n surfaces with
+    log-uniform source counts in [min_src, max_src], cycling through spheres
+    and ellipsoids (one center per node, per-center Morton-window lists) and
+    tori (two centers per node, octree lists)."""
+    rng = np.random.default_rng(BASE_SEED + 4 + seed_offset)
+    out = []
+    for i in range(n):
+        target = float(np.exp(rng.uniform(np.log(min_src), np.log(max_src))))
+        kind = i % 3
+        if kind == 2:                                  # torus: 12 nu nv sources, nv ~ 3 nu / 8
+            nu = int(max(16, round(np.sqrt(target / 12.0 * 8.0 / 3.0))))
+            nv = int(max(6, round(3 * nu / 8)))
+            g, _, _ = torus(nu, nv, seed_offset=100 + i)
+        else:
+            freq = int(max(3, round(np.sqrt(target / 120.0))))
+            axes = np.ones(3) if kind == 0 else rng.uniform(0.5, 2.0, 3)
+            g, _ = ellipsoid(freq, axes, rng=rng)
+        g.meta["serving_index"] = i
+        out.append(g)
+    return out
