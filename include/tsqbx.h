@@ -80,8 +80,13 @@ enum { TSQBX_SLP = 1u, TSQBX_DLP = 2u };
  * MIXED (Laplace only): coordinates differenced in float-float, the
  *       recurrence and geometry ratios in FP32, per-lane sums Kahan-
  *       compensated in FP32 and per-target reduction in FP64 (results within
- *       1e-6 relative of an FP64 reference). */
-typedef enum { TSQBX_FP64 = 0, TSQBX_MIXED = 1 } tsqbx_precision;
+ *       1e-6 relative of an FP64 reference).
+ * DF64 (Laplace only): every step in double-float arithmetic (pairs of FP32
+ *       values, ~48-bit significands) on the FP32 pipes, geometry differenced
+ *       in FP64 against a per-item reference point; results within the FP64
+ *       bound (1e-12 relative).  On GPUs whose FP64 rate is a small fraction
+ *       of FP32 (GB300: 1/61) this reaches FP64-class accuracy faster. */
+typedef enum { TSQBX_FP64 = 0, TSQBX_MIXED = 1, TSQBX_DF64 = 2 } tsqbx_precision;
 
 enum {
     TSQBX_FLAG_ALLOW_DIVERGENT = 1u,  /* accept pairs with |t-c| >= |s-c| (report only) */

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import TsqbxError, check, lib, strerror  # noqa: F401
 
 _KERNELS = {"laplace": _lib.TSQBX_LAPLACE, "helmholtz": _lib.TSQBX_HELMHOLTZ}
-_PRECISIONS = {"fp64": _lib.TSQBX_FP64, "mixed": _lib.TSQBX_MIXED}
+_PRECISIONS = {"fp64": _lib.TSQBX_FP64, "mixed": _lib.TSQBX_MIXED, "df64": _lib.TSQBX_DF64}
 _LAYERS = {"slp": _lib.TSQBX_SLP, "dlp": _lib.TSQBX_DLP}
 
 

@@ -20,7 +20,7 @@ TSQBX_E_TOO_LARGE = -10
 TSQBX_NOALLOC_MAX_SRC = 1048544
 TSQBX_LAPLACE, TSQBX_HELMHOLTZ = 0, 1
 TSQBX_SLP, TSQBX_DLP = 1, 2
-TSQBX_FP64, TSQBX_MIXED = 0, 1
+TSQBX_FP64, TSQBX_MIXED, TSQBX_DF64 = 0, 1, 2
 TSQBX_FLAG_ALLOW_DIVERGENT, TSQBX_FLAG_SKIP_CHECK, TSQBX_FLAG_USE_TUNED = 1, 2, 4
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -70,6 +70,7 @@ int launch_laplace_mixed(int p, bool slp, bool dlp, const DevGeom &g, const DevE
                          cudaStream_t s);
 int launch_helmholtz_fp64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e,
                           cudaStream_t s);
+int launch_laplace_df64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s);
 
 // Legendre three-term recurrence in the scaled form used by every kernel:
 //   Q_n = (rho/R)^n P_n(x) = kappa_n T_n,

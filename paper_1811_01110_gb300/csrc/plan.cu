@@ -155,7 +155,8 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
     if (o->kernel != TSQBX_LAPLACE && o->kernel != TSQBX_HELMHOLTZ) return TSQBX_E_INVAL;
     if (o->layers == 0 || (o->layers & ~(uint32_t)(TSQBX_SLP | TSQBX_DLP))) return TSQBX_E_INVAL;
     if (o->p < 0 || o->p > TSQBX_P_MAX) return TSQBX_E_INVAL;
-    if (o->precision != TSQBX_FP64 && o->precision != TSQBX_MIXED) return TSQBX_E_INVAL;
+    if (o->precision != TSQBX_FP64 && o->precision != TSQBX_MIXED && o->precision != TSQBX_DF64)
+        return TSQBX_E_INVAL;
     if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64 ||
         o->max_item_iters < 0)
         return TSQBX_E_INVAL;
@@ -351,6 +352,7 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     int rc;
     if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(p, slp, dlp, P->g, ev, s);
     else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(p, slp, dlp, P->g, ev, s);
+    else if (o.precision == TSQBX_DF64) rc = launch_laplace_df64(p, slp, dlp, P->g, ev, s);
     else rc = launch_laplace_fp64(p, slp, dlp, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
     if (P->g.n_combine > 0) {

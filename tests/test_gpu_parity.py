@@ -12,7 +12,7 @@ from tsqbx_inputs import configs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "mixed": 1e-6}
+TOL = {"fp64": 1e-12, "mixed": 1e-6, "df64": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +39,7 @@ def check_laplace(pkg, g, mu, p, precision, layers=("slp", "dlp"), **kw):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
 @pytest.mark.parametrize("p", list(range(0, 21)))
 def test_laplace_every_order(pkg, precision, p):
     rng = np.random.default_rng(100 + p)
@@ -48,7 +48,7 @@ def test_laplace_every_order(pkg, precision, p):
     check_laplace(pkg, g, mu, p, precision)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
 @pytest.mark.parametrize("lanes", [1, 2, 3, 5, 8, 16, 32])
 def test_laplace_forced_lane_counts(pkg, precision, lanes):
     """Every lanes-per-target value, groups of 1..40 targets (ragged items)."""
@@ -58,7 +58,7 @@ def test_laplace_forced_lane_counts(pkg, precision, lanes):
     check_laplace(pkg, g, mu, 9, precision, lanes_per_target=lanes)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
 @pytest.mark.parametrize("max_iters", [1, 2, 7, 40])
 def test_laplace_sliced_lists(pkg, precision, max_iters):
     """Long lists cut into source slices (partials combined in slice order)."""
@@ -69,7 +69,7 @@ def test_laplace_sliced_lists(pkg, precision, max_iters):
     check_laplace(pkg, g, mu, 6, precision, max_item_iters=max_iters, lanes_per_target=5)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
 @pytest.mark.parametrize("p,max_iters", [(0, 0), (4, 0), (9, 0), (9, 2), (13, 5)])
 def test_laplace_single_target_groups(pkg, precision, p, max_iters):
     """One target per group: the direct-load path (no shared-memory staging)."""
@@ -90,14 +90,14 @@ def test_helmholtz_sliced_lists(pkg):
         assert relerr(out, ref) <= 1e-12
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
 def test_laplace_sphere_workload(pkg, precision):
     g, mu = configs.sphere()
     out = check_laplace(pkg, g, mu, 5, precision, layers=("slp",))
     assert np.all(np.isfinite(out["slp"]))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
 def test_laplace_small_torus_octree_lists(pkg, precision):
     g, mu, _ = configs.torus(48, 18)
     check_laplace(pkg, g, mu, 9, precision)
@@ -111,7 +111,7 @@ def test_laplace_full_torus_sampled_targets(pkg):
     rng = np.random.default_rng(3)
     idx = np.sort(rng.choice(g.n_tgt, 600, replace=False))
     ref = oracle.tsqbx_laplace(g, 9, mu, subset=idx, slp=True, dlp=True)
-    for precision in ("fp64", "mixed"):
+    for precision in ("fp64", "mixed", "df64"):
         with pkg.Plan(g, "laplace", ("slp", "dlp"), p=9, precision=precision) as plan:
             out = plan.eval(mu)
             info = plan.info()
@@ -137,6 +137,7 @@ def test_edge_cases(pkg):
     out = check_laplace(pkg, g, mu, 7, "fp64")
     assert np.all(out["slp"][g.ctr_group[g.tgt_center] == 0] == 0.0)
     check_laplace(pkg, g, mu, 7, "mixed")
+    check_laplace(pkg, g, mu, 7, "df64")
 
 
 def test_no_targets_and_no_sources(pkg):
@@ -199,7 +200,7 @@ def test_paths_agree_and_are_deterministic(pkg):
     rng = np.random.default_rng(21)
     g = cloud_geometry(rng, n_ctr=20, n_src=200, tgt_per_ctr=4)
     mu = rng.standard_normal(g.n_src)
-    for precision in ("fp64", "mixed"):
+    for precision in ("fp64", "mixed", "df64"):
         with pkg.Plan(g, "laplace", ("slp", "dlp"), p=8, precision=precision) as plan:
             a = plan.eval(mu)
             b = plan.eval(mu)
