@@ -13,6 +13,10 @@
  *   Laplace double layer   n_s . grad_s G^(p)                         (Appendix A)
  *   Helmholtz single layer G_k^(p) = ik/(4 pi) sum_{n<=p} (2n+1) j_n(k|t-c|)
  *                                     h_n(k|s-c|) P_n(cos g)         (Appendix A)
+ *   Helmholtz double layer n_s . grad_s G_k^(p)
+ *   S' (either kernel)     n_t . grad_t G^(p), n_t . grad_t G_k^(p), the
+ *                          target-normal derivative with the center c held
+ *                          fixed (Appendix A)
  *
  * g is the angle between s-c and t-c, j_n / h_n the spherical Bessel and
  * Hankel functions of the first kind.  The result is the near part
@@ -72,8 +76,10 @@ enum {
 /* ------------------------------------------------------------- options */
 typedef enum { TSQBX_LAPLACE = 0, TSQBX_HELMHOLTZ = 1 } tsqbx_kernel;
 
-/* layer mask: single layer, double layer (source-normal derivative) */
-enum { TSQBX_SLP = 1u, TSQBX_DLP = 2u };
+/* layer mask: single layer, double layer (source-normal derivative
+ * n_s . grad_s), and S' (target-normal derivative n_t . grad_t, Appendix A;
+ * needs tgt_normal and the *_pk entry points, which take an S' output) */
+enum { TSQBX_SLP = 1u, TSQBX_DLP = 2u, TSQBX_SP = 4u };
 
 /* FP64: every step in double precision (results within 1e-12 relative of an
  *       FP64 reference).
@@ -98,7 +104,7 @@ enum {
 
 typedef struct {
     tsqbx_kernel kernel;
-    uint32_t layers;            /* TSQBX_SLP | TSQBX_DLP (Helmholtz: TSQBX_SLP)       */
+    uint32_t layers;            /* TSQBX_SLP | TSQBX_DLP | TSQBX_SP                   */
     int p;                      /* expansion order, 0 <= p <= TSQBX_P_MAX             */
     double k;                   /* Helmholtz wavenumber (> 0); ignored for Laplace    */
     tsqbx_precision precision;
@@ -135,6 +141,7 @@ typedef struct {
     const int64_t *group_range_start; /* [n_group+1] CSR offsets, [0] == 0         */
     const int32_t *range_begin;     /* [nnz] first source of each range            */
     const int32_t *range_end;       /* [nnz] one past the last source              */
+    const double *tgt_normal;       /* [3][n_tgt] unit normals; NULL without S'    */
 } tsqbx_geometry;
 
 typedef struct tsqbx_plan_s *tsqbx_plan;
@@ -185,11 +192,14 @@ TSQBX_API int tsqbx_eval(tsqbx_plan plan, const void *density, void *out_slp, vo
 /* tsqbx_eval / tsqbx_submit with the expansion order p (0..TSQBX_P_MAX) and,
  * for Helmholtz, the wavenumber k (> 0) chosen per call: the plan's geometry,
  * lists and schedule do not depend on them, so one plan serves every order
- * and wavenumber.  Errors as tsqbx_eval / tsqbx_submit. */
+ * and wavenumber.  out_sp receives S' (n_t . grad_t G, layout as out_slp)
+ * when the plan's mask has TSQBX_SP; it may be NULL, and then S' is not
+ * formed.  tsqbx_eval, tsqbx_submit and tsqbx_eval_async form the single and
+ * double layers only.  Errors as tsqbx_eval / tsqbx_submit. */
 TSQBX_API int tsqbx_eval_pk(tsqbx_plan plan, int p, double k, const void *density, void *out_slp,
-                            void *out_dlp);
+                            void *out_dlp, void *out_sp);
 TSQBX_API int tsqbx_submit_pk(tsqbx_plan plan, int p, double k, const void *density, void *out_slp,
-                              void *out_dlp, uint64_t *ticket);
+                              void *out_dlp, void *out_sp, uint64_t *ticket);
 
 /* Asynchronous evaluation on DEVICE pointers only (same layouts as
  * tsqbx_eval), enqueued on `stream` (a cudaStream_t; NULL = the plan's own
@@ -251,8 +261,8 @@ TSQBX_API void tsqbx_batch_destroy(tsqbx_batch batch);
 
 /* Enqueue one evaluation of every plan on `stream` (NULL = the batch's own
  * stream).  d_density[i], d_out_slp[i], d_out_dlp[i]: DEVICE pointers for
- * plan i (layouts as tsqbx_eval; out arrays may be NULL for absent layers).
- * Waits only until the previous evaluation of this batch has read its pointer
+ * plan i (layouts as tsqbx_eval; out arrays may be NULL for absent layers;
+ * a batch forms the single and double layers only, never S').  Waits only until the previous evaluation of this batch has read its pointer
  * table.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_batch_eval_async(tsqbx_batch batch, const void *const *d_density,
                                      void *const *d_out_slp, void *const *d_out_dlp, void *stream);
@@ -299,10 +309,12 @@ TSQBX_API int tsqbx_server_add_geometry(tsqbx_server server, const tsqbx_geometr
 TSQBX_API int tsqbx_server_prepare(tsqbx_server server, int geom_id, const tsqbx_options *options);
 /* Queue one evaluation.  options: kernel, layers, p, k, precision (+ tuning
  * fields); device is the server's.  The density (host, layout as tsqbx_eval)
- * is copied before return; out_slp / out_dlp are HOST buffers written before
- * the request reports completion and must stay valid until then. */
+ * is copied before return; out_slp / out_dlp / out_sp (S', required when the
+ * mask has TSQBX_SP) are HOST buffers written before the request reports
+ * completion and must stay valid until then. */
 TSQBX_API int tsqbx_server_submit(tsqbx_server server, int geom_id, const tsqbx_options *options,
-                                  const void *density, void *out_slp, void *out_dlp, uint64_t *request);
+                                  const void *density, void *out_slp, void *out_dlp, void *out_sp,
+                                  uint64_t *request);
 /* 0 once the request completed (its outputs written; the request is then
  * retired), TSQBX_PENDING (timeout_us == 0), TSQBX_E_TIMEOUT, or the
  * request's failure code (e.g. TSQBX_E_NOMEM if it could never fit). */

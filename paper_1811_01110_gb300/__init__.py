@@ -8,6 +8,10 @@ memory) and raises on error codes.
     plan = Plan(geometry, kernel="laplace", layers=("slp", "dlp"), p=9,
                 precision="fp64")
     u = plan.eval(density)             # {'slp': ndarray, 'dlp': ndarray}
+
+Layers: "slp" (single layer), "dlp" (double layer, source-normal
+derivative), "sp" (S', the target-normal derivative of the single layer;
+needs geometry.tgt_normal).
 """
 import ctypes
 
@@ -18,7 +22,7 @@ from ._lib import TsqbxError, check, lib, strerror  # noqa: F401
 
 _KERNELS = {"laplace": _lib.TSQBX_LAPLACE, "helmholtz": _lib.TSQBX_HELMHOLTZ}
 _PRECISIONS = {"fp64": _lib.TSQBX_FP64, "mixed": _lib.TSQBX_MIXED, "df64": _lib.TSQBX_DF64}
-_LAYERS = {"slp": _lib.TSQBX_SLP, "dlp": _lib.TSQBX_DLP}
+_LAYERS = {"slp": _lib.TSQBX_SLP, "dlp": _lib.TSQBX_DLP, "sp": _lib.TSQBX_SP}
 
 
 def _ptr(a, ctype):
@@ -46,7 +50,7 @@ def _addr(x, nbytes, what):
     return ctypes.c_void_p(x.ctypes.data)
 
 
-def marshal_geometry(g, with_normals=True):
+def marshal_geometry(g, with_normals=True, with_tgt_normals=False):
     """tsqbx_geometry view of a geometry object (host numpy arrays); returns
     (struct, keep) where keep holds the contiguous copies alive."""
     f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
@@ -56,7 +60,8 @@ def marshal_geometry(g, with_normals=True):
                 ctr_xyz=f64(g.ctr_xyz), ctr_radius=f64(getattr(g, "ctr_radius", None)),
                 tgt_xyz=f64(g.tgt_xyz), tgt_center=i32(g.tgt_center), ctr_group=i32(g.ctr_group),
                 group_range_start=np.ascontiguousarray(g.group_range_start, dtype=np.int64),
-                range_begin=i32(g.range_begin), range_end=i32(g.range_end))
+                range_begin=i32(g.range_begin), range_end=i32(g.range_end),
+                tgt_normal=f64(getattr(g, "tgt_normal", None)) if with_tgt_normals else None)
     n_tgt = int(keep["tgt_xyz"].shape[1]) if keep["tgt_xyz"].ndim == 2 else 0
     geo = _lib.tsqbx_geometry(
         int(keep["src_weight"].shape[0]), _ptr(keep["src_xyz"], ctypes.c_double),
@@ -66,7 +71,8 @@ def marshal_geometry(g, with_normals=True):
         n_tgt, _ptr(keep["tgt_xyz"], ctypes.c_double), _ptr(keep["tgt_center"], ctypes.c_int32),
         int(keep["group_range_start"].shape[0] - 1), _ptr(keep["ctr_group"], ctypes.c_int32),
         _ptr(keep["group_range_start"], ctypes.c_int64),
-        _ptr(keep["range_begin"], ctypes.c_int32), _ptr(keep["range_end"], ctypes.c_int32))
+        _ptr(keep["range_begin"], ctypes.c_int32), _ptr(keep["range_end"], ctypes.c_int32),
+        _ptr(keep["tgt_normal"], ctypes.c_double))
     return geo, keep
 
 
@@ -91,7 +97,8 @@ class Plan:
         self.p = int(p)
         self.k = float(k)
         self.complex = kernel == "helmholtz"
-        geo, keep = marshal_geometry(geometry, with_normals="dlp" in self.layers)
+        geo, keep = marshal_geometry(geometry, with_normals="dlp" in self.layers,
+                                     with_tgt_normals="sp" in self.layers)
         self.n_src, self.n_tgt = int(geo.n_src), int(geo.n_tgt)
         flags = (_lib.TSQBX_FLAG_ALLOW_DIVERGENT if allow_divergent else 0) | \
                 (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0) | \
@@ -179,43 +186,50 @@ class Plan:
 
     def _out_addrs(self, outs):
         nb = self.n_tgt * 8 * self.width
-        return (_addr(outs.get("slp"), nb, "out_slp"), _addr(outs.get("dlp"), nb, "out_dlp"))
+        return (_addr(outs.get("slp"), nb, "out_slp"), _addr(outs.get("dlp"), nb, "out_dlp"),
+                _addr(outs.get("sp"), nb, "out_sp"))
 
     def eval(self, density, out=None, p=None, k=None):
-        """Blocking evaluation (tsqbx_eval; tsqbx_eval_pk when p or k is given).
-        density: numpy (host) or torch CUDA tensor; returns a dict of outputs
-        of the same kind."""
+        """Blocking evaluation (tsqbx_eval; tsqbx_eval_pk when p or k is given
+        or the plan forms S').  density: numpy (host) or torch CUDA tensor;
+        returns a dict of outputs of the same kind."""
         like = density if _is_torch(density) and density.is_cuda else None
         outs = out if out is not None else self._alloc_out(like)
-        a_slp, a_dlp = self._out_addrs(outs)
+        a_slp, a_dlp, a_sp = self._out_addrs(outs)
         d = self._density_addr(density)
-        if p is None and k is None:
+        if p is None and k is None and a_sp is None:
             check(lib().tsqbx_eval(self._h, d, a_slp, a_dlp), "tsqbx_eval")
         else:
             pp = self.p if p is None else int(p)
             kk = self.k if k is None else float(k)
-            check(lib().tsqbx_eval_pk(self._h, pp, kk, d, a_slp, a_dlp), "tsqbx_eval_pk")
+            check(lib().tsqbx_eval_pk(self._h, pp, kk, d, a_slp, a_dlp, a_sp), "tsqbx_eval_pk")
         return outs
 
     def eval_async(self, density, out, stream=None):
-        """Enqueue on a CUDA stream (tsqbx_eval_async); device tensors only.
+        """Enqueue on a CUDA stream (tsqbx_eval_async); device tensors only;
+        single and double layers only (an "sp" entry of out is not written).
         stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
         handle = None
         if stream is not None:
             handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-        a_slp, a_dlp = self._out_addrs(out)
+        a_slp, a_dlp, _ = self._out_addrs(out)
         check(lib().tsqbx_eval_async(self._h, self._density_addr(density), a_slp, a_dlp, handle),
               "tsqbx_eval_async")
         return out
 
     def submit(self, density, out=None):
-        """tsqbx_submit: returns (ticket, outs); outs are valid once poll() returns True."""
+        """tsqbx_submit (tsqbx_submit_pk when the plan forms S'): returns
+        (ticket, outs); outs are valid once poll() returns True."""
         like = density if _is_torch(density) and density.is_cuda else None
         outs = out if out is not None else self._alloc_out(like)
-        a_slp, a_dlp = self._out_addrs(outs)
+        a_slp, a_dlp, a_sp = self._out_addrs(outs)
         t = ctypes.c_uint64()
-        check(lib().tsqbx_submit(self._h, self._density_addr(density), a_slp, a_dlp, ctypes.byref(t)),
-              "tsqbx_submit")
+        if a_sp is None:
+            check(lib().tsqbx_submit(self._h, self._density_addr(density), a_slp, a_dlp, ctypes.byref(t)),
+                  "tsqbx_submit")
+        else:
+            check(lib().tsqbx_submit_pk(self._h, self.p, self.k, self._density_addr(density), a_slp, a_dlp,
+                                        a_sp, ctypes.byref(t)), "tsqbx_submit_pk")
         self._inflight = getattr(self, "_inflight", {})
         self._inflight[t.value] = (outs, getattr(self, "_keep_density", None))
         return t.value, outs
@@ -303,7 +317,8 @@ class Server:
         self.close()
 
     def add_geometry(self, g, with_normals=True):
-        geo, keep = marshal_geometry(g, with_normals)
+        geo, keep = marshal_geometry(g, with_normals,
+                                     with_tgt_normals=with_normals and getattr(g, "tgt_normal", None) is not None)
         gid = ctypes.c_int()
         check(lib().tsqbx_server_add_geometry(self._h, ctypes.byref(geo), ctypes.byref(gid)),
               "tsqbx_server_add_geometry")
@@ -328,6 +343,7 @@ class Server:
         check(lib().tsqbx_server_submit(self._h, int(gid), ctypes.byref(opt), ctypes.c_void_p(dens.ctypes.data),
                                         None if "slp" not in outs else ctypes.c_void_p(outs["slp"].ctypes.data),
                                         None if "dlp" not in outs else ctypes.c_void_p(outs["dlp"].ctypes.data),
+                                        None if "sp" not in outs else ctypes.c_void_p(outs["sp"].ctypes.data),
                                         ctypes.byref(rid)), "tsqbx_server_submit")
         self._pending[rid.value] = outs
         return rid.value, outs

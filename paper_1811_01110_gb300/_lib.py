@@ -19,7 +19,7 @@ TSQBX_E_UNSUPPORTED = -9
 TSQBX_E_TOO_LARGE = -10
 TSQBX_NOALLOC_MAX_SRC = 1048544
 TSQBX_LAPLACE, TSQBX_HELMHOLTZ = 0, 1
-TSQBX_SLP, TSQBX_DLP = 1, 2
+TSQBX_SLP, TSQBX_DLP, TSQBX_SP = 1, 2, 4
 TSQBX_FP64, TSQBX_MIXED, TSQBX_DF64 = 0, 1, 2
 TSQBX_FLAG_ALLOW_DIVERGENT, TSQBX_FLAG_SKIP_CHECK, TSQBX_FLAG_USE_TUNED = 1, 2, 4
 
@@ -34,7 +34,7 @@ class tsqbx_geometry(ctypes.Structure):
         ("n_ctr", ctypes.c_int64), ("ctr_xyz", _dp), ("ctr_radius", _dp),
         ("n_tgt", ctypes.c_int64), ("tgt_xyz", _dp), ("tgt_center", _i32p),
         ("n_group", ctypes.c_int64), ("ctr_group", _i32p), ("group_range_start", _i64p),
-        ("range_begin", _i32p), ("range_end", _i32p),
+        ("range_begin", _i32p), ("range_end", _i32p), ("tgt_normal", _dp),
     ]
 
 
@@ -97,10 +97,11 @@ _SIGNATURES = [
       ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_poll", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
     ("tsqbx_eval_pk", ctypes.c_int,
-     [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+     [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_void_p]),
     ("tsqbx_submit_pk", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-      ctypes.POINTER(ctypes.c_uint64)]),
+      ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_plan_kernel_ms", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     ("tsqbx_plan_autotune", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tsqbx_tuning)]),
@@ -123,7 +124,7 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tsqbx_options)]),
     ("tsqbx_server_submit", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(tsqbx_options), ctypes.c_void_p, ctypes.c_void_p,
-      ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+      ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]),
     ("tsqbx_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_server_stats)]),
     ("tsqbx_server_reset_stats", ctypes.c_int, [ctypes.c_void_p]),

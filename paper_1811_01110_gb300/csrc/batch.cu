@@ -58,14 +58,14 @@ template <bool DLP, int... Ps>
 __device__ __forceinline__ void run_item_fp64(int p, const DevGeom &g, const DevEval &ev, const Item &it,
                                               double (*T)[kTile], int lane, std::integer_sequence<int, Ps...>)
 {
-    ((p == Ps ? (laplace_fp64_item<Ps, DLP>(g, ev, it, T, lane), 0) : 0), ...);
+    ((p == Ps ? (laplace_fp64_item<Ps, DLP, false>(g, ev, it, T, lane), 0) : 0), ...);
 }
 
 template <bool DLP, int... Ps>
 __device__ __forceinline__ void run_item_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
                                                float4 (*T)[kTile], int lane, std::integer_sequence<int, Ps...>)
 {
-    ((p == Ps ? (laplace_mixed_item<Ps, DLP>(g, ev, it, T, lane), 0) : 0), ...);
+    ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, T, lane), 0) : 0), ...);
 }
 
 template <bool MIXED, bool DLP>

@@ -1,0 +1,275 @@
+// helmholtz_items.cuh -- the Helmholtz TSQBX kernel (arithmetic described in
+// helmholtz.cu) and its dispatch over p.  helmholtz.cu instantiates the
+// single/double-layer variants, helmholtz_sp.cu the ones that also form S'.
+#pragma once
+
+#include <utility>
+
+#include "internal.cuh"
+
+namespace tsqbx {
+namespace {
+
+// Per-target radial factors, orders 0..P (z = k rho):
+//   cj[n]  = (2n+1) kappa_n j_n(z)
+//   caj[n] = (2n+1) kappa_n k j_n'(z) (that.n_t)        (S' only)
+// j_n by Miller's downward recurrence (f_{n-1} = (2n+1)/z f_n - f_{n+1}),
+// started P + 20 + ceil(z) orders up and normalised against j_0 = sin z / z
+// or j_1 = sin z / z^2 - cos z / z, whichever is larger; j_n' = (n/z) j_n -
+// j_{n+1} (the run also yields j_{P+1}).  z = 0: j_0 = 1, j_1' = 1/3, rest 0.
+template <int P, bool SP>
+__device__ __forceinline__ void helmholtz_target_factors(double k, double rho, double tdot, double (&cj)[P + 1],
+                                                         double (&caj)[SP ? P + 1 : 1])
+{
+    const double z = k * rho;
+    double jn[P + 2];
+    if (z == 0.0) {
+        jn[0] = 1.0;
+#pragma unroll
+        for (int n = 1; n <= P + 1; ++n) jn[n] = 0.0;
+    } else {
+        const double zinv = 1.0 / z;
+        const int N = P + 20 + (int)fmin(ceil(z), 1.0e6);   // no int overflow for huge k rho
+        double fa = 0.0, fb = 1e-30;           // f_{n+1}, f_n
+        for (int n = N; n > P; --n) {
+            const double fnew = (2.0 * n + 1.0) * zinv * fb - fa;
+            fa = fb;
+            fb = fnew;
+            if (fabs(fb) > 1e200) { fa *= 1e-200; fb *= 1e-200; }
+        }
+        jn[P + 1] = fa;
+        jn[P] = fb;
+#pragma unroll
+        for (int n = P; n >= 1; --n) {
+            jn[n - 1] = (2.0 * n + 1.0) * zinv * jn[n] - jn[n + 1];
+            if (fabs(jn[n - 1]) > 1e200) {
+#pragma unroll
+                for (int m = 0; m <= P + 1; ++m)
+                    if (m >= n - 1) jn[m] *= 1e-200;
+            }
+        }
+        double sn, cs;
+        sincos(z, &sn, &cs);
+        const double j0 = sn * zinv;
+        const double j1 = (sn * zinv - cs) * zinv;
+        const double scale = fabs(j1) > fabs(j0) ? j1 / jn[1] : j0 / jn[0];
+#pragma unroll
+        for (int n = 0; n <= P + 1; ++n) jn[n] *= scale;
+    }
+#pragma unroll
+    for (int n = 0; n <= P; ++n) cj[n] = (2.0 * n + 1.0) * rec_kappa(n) * jn[n];
+    if (SP) {
+        const double zinv = z == 0.0 ? 0.0 : 1.0 / z;
+#pragma unroll
+        for (int n = 0; n <= P; ++n) {
+            double jd = z == 0.0 ? (n == 1 ? 1.0 / 3.0 : 0.0) : fma(n * zinv, jn[n], -jn[n + 1]);
+            caj[SP ? n : 0] = (2.0 * n + 1.0) * rec_kappa(n) * k * jd * tdot;
+        }
+    }
+}
+
+// Complex helpers on (re, im) pairs.
+__device__ __forceinline__ void cfma(double c, double gr, double gi, double &ar, double &ai)
+{
+    ar = fma(c, gr, ar);
+    ai = fma(c, gi, ai);
+}
+
+template <int P, bool DLP, bool SP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+helmholtz_kernel(const DevGeom g, const DevEval ev)
+{
+    constexpr int kRows = DLP ? 8 : 5;
+    __shared__ double tile[kWarpsPerBlock][kRows][kTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (item >= g.n_items) return;
+    const Item it = g.items[item];
+    const int L = it.L;
+    const int j = lane / L, sub = lane - j * L;
+    const bool active = j < it.n_tgt;
+    const double k = ev.k, kinv = 1.0 / ev.k;
+    double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rhoinv = 0;
+    double tx = 0, ty = 0, tz = 0, tdot = 0, b1 = 0;   // n_t, that.n_t, rho = 0 limit of k j_1/rho
+    double cj[P + 1];
+    double caj[SP ? P + 1 : 1];
+#pragma unroll
+    for (int n = 0; n <= P; ++n) cj[n] = 0.0;
+#pragma unroll
+    for (int n = 0; n < (SP ? P + 1 : 1); ++n) caj[n] = 0.0;
+    if (active) {
+        const double4_32a c = g.slot_c[it.slot_begin + j];
+        const double4_32a e = g.slot_e[it.slot_begin + j];
+        cx = c.x; cy = c.y; cz = c.z;
+        ex = e.x; ey = e.y; ez = e.z;
+        const double rho = sqrt(e.w);
+        rhoinv = rho > 0.0 ? 1.0 / rho : 0.0;
+        if (SP) {
+            const double4_32a tn = g.slot_n[it.slot_begin + j];
+            tx = tn.x; ty = tn.y; tz = tn.z;
+            tdot = fma(ex, tx, fma(ey, ty, ez * tz)) * rhoinv;
+            b1 = (rho > 0.0 || P < 1) ? 0.0 : k;
+        }
+        helmholtz_target_factors<P, SP>(k, rho, tdot, cj, caj);
+    }
+    const int64_t s0 = g.grp_off[it.group];
+    const int src_hi = it.src_hi;
+    double (*T)[kTile] = tile[warp];
+    double acc_re = 0.0, acc_im = 0.0, dacc_re = 0.0, dacc_im = 0.0, pacc_re = 0.0, pacc_im = 0.0;
+
+    for (int base = it.src_lo; base < src_hi; base += kTile) {
+        const int cnt = min(kTile, src_hi - base);
+        for (int kk = lane; kk < cnt; kk += 32) {
+            int s = g.grp_src[s0 + base + kk];
+            double2 wm = make_double2(0.0, 0.0);
+            if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
+            else wm = ev.wmu_c[s];
+            const double4_32a pw = g.src_pw[s];
+            T[0][kk] = pw.x; T[1][kk] = pw.y; T[2][kk] = pw.z;
+            T[3][kk] = wm.x; T[4][kk] = wm.y;
+            if (DLP) {
+                const double4_32a n = g.src_n[s];
+                T[kRows - 3][kk] = n.x; T[kRows - 2][kk] = n.y; T[kRows - 1][kk] = n.z;
+            }
+        }
+        __syncwarp();
+        if (active) {
+            for (int kk = sub; kk < cnt; kk += L) {
+                const double dx = T[0][kk] - cx, dy = T[1][kk] - cy, dz = T[2][kk] - cz;
+                const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
+                const double rinv = rsqrt(R2);
+                const double x = fma(dx, ex, fma(dy, ey, dz * ez)) * rinv * rhoinv;
+                const double w = rinv * kinv;               // 1/z
+                const double z = k * (R2 * rinv);
+                // Sums over n of g_n (h_n = e^{iz} g_n) times
+                //   A : cj T_n            (single layer)
+                //   D1: cj T_n g'_n-part  (double layer, radial: h_n' = e^{iz} gd_n,
+                //                          gd_n = g_{n-1} - (n+1) w g_n, gd_0 = -g_1)
+                //   D2: cj T'_n           (angular part, shared by double layer and S')
+                //   Pa: caj T_n           (S', radial part)
+                double Ar, Ai, D1r = 0, D1i = 0, D2r = 0, D2i = 0, Par = 0, Pai = 0;
+                double gmr = 0.0, gmi = -w;                 // g_0
+                double gr = -w, gi = -w * w;                // g_1
+                Ar = 0.0; Ai = -cj[0] * w;
+                if (DLP) cfma(-cj[0], gr, gi, D1r, D1i);
+                if (SP) Pai = -caj[0] * w;
+                double Tm = 1.0, Tc = x;                    // T_{n-1}, T_n
+                double Um = 0.0, Uc = 1.0;                  // T'_{n-1}, T'_n
+                if (P >= 1) {
+                    const double c1 = cj[1] * x;
+                    cfma(c1, gr, gi, Ar, Ai);
+                    if (DLP) {
+                        const double t = 2.0 * w;
+                        cfma(c1, fma(-t, gr, gmr), fma(-t, gi, gmi), D1r, D1i);
+                    }
+                    if (DLP || SP) cfma(cj[1], gr, gi, D2r, D2i);
+                    if (SP) cfma(caj[SP ? 1 : 0] * x, gr, gi, Par, Pai);
+                }
+#pragma unroll
+                for (int n = 1; n < P; ++n) {
+                    const double t = (2.0 * n + 1.0) * w;
+                    const double nr = fma(t, gr, -gmr), ni = fma(t, gi, -gmi);
+                    gmr = gr; gmi = gi; gr = nr; gi = ni;
+                    const double Tn = fma(x, Tc, -rec_beta(n) * Tm);
+                    if (DLP || SP) {
+                        const double Un = fma(-rec_beta(n), Um, fma(x, Uc, Tc));
+                        Um = Uc; Uc = Un;
+                        cfma(cj[n + 1] * Un, gr, gi, D2r, D2i);
+                    }
+                    Tm = Tc; Tc = Tn;
+                    const double c = cj[n + 1] * Tn;
+                    cfma(c, gr, gi, Ar, Ai);
+                    if (DLP) {
+                        const double tt = (n + 2.0) * w;
+                        cfma(c, fma(-tt, gr, gmr), fma(-tt, gi, gmi), D1r, D1i);
+                    }
+                    if (SP) cfma(caj[SP ? n + 1 : 0] * Tn, gr, gi, Par, Pai);
+                }
+                double sn, cs;
+                sincos(z, &sn, &cs);
+                const double wr = T[3][kk], wi = T[4][kk];
+                // out += ik e^{iz} (X) (w mu):  with v = e^{iz} X, ik v = (-k v_i, k v_r)
+                auto accumulate = [&](double Xr, double Xi, double &or_, double &oi) {
+                    const double vr = fma(cs, Xr, -sn * Xi), vi = fma(sn, Xr, cs * Xi);
+                    const double ur = -k * vi, ui = k * vr;
+                    or_ = fma(ur, wr, fma(-ui, wi, or_));
+                    oi = fma(ur, wi, fma(ui, wr, oi));
+                };
+                accumulate(Ar, Ai, acc_re, acc_im);
+                if (DLP) {
+                    // n_s.grad_s: R' = a/R, x' = (1/R) ((e.n_s)/rho - (a/R) x), a = d.n_s
+                    const double nx = T[kRows - 3][kk], ny = T[kRows - 2][kk], nz = T[kRows - 1][kk];
+                    const double ah = fma(dx, nx, fma(dy, ny, dz * nz)) * rinv;
+                    const double u = (fma(ex, nx, fma(ey, ny, ez * nz)) * rhoinv - ah * x) * rinv;
+                    const double kah = k * ah;
+                    accumulate(fma(kah, D1r, u * D2r), fma(kah, D1i, u * D2i), dacc_re, dacc_im);
+                }
+                if (SP) {
+                    // n_t.grad_t: rho' = that.n_t, x' = (1/rho) ((d.n_t)/R - (that.n_t) x)
+                    const double C = fma(dx, tx, fma(dy, ty, dz * tz)) * rinv - tdot * x;
+                    // (1/rho) sum cj T'_n g_n, plus the rho = 0 limit of the n = 1 term
+                    const double Br = fma(rhoinv, D2r, b1 * (P >= 1 ? -w : 0.0));
+                    const double Bi = fma(rhoinv, D2i, b1 * (P >= 1 ? -w * w : 0.0));
+                    accumulate(fma(C, Br, Par), fma(C, Bi, Pai), pacc_re, pacc_im);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    for (int off = 1; off < L; off <<= 1) {
+        const double vr = __shfl_down_sync(0xffffffffu, acc_re, off);
+        const double vi = __shfl_down_sync(0xffffffffu, acc_im, off);
+        const double dr = DLP ? __shfl_down_sync(0xffffffffu, dacc_re, off) : 0.0;
+        const double di = DLP ? __shfl_down_sync(0xffffffffu, dacc_im, off) : 0.0;
+        const double pr = SP ? __shfl_down_sync(0xffffffffu, pacc_re, off) : 0.0;
+        const double pi = SP ? __shfl_down_sync(0xffffffffu, pacc_im, off) : 0.0;
+        if (sub + off < L) {
+            acc_re += vr; acc_im += vi;
+            dacc_re += dr; dacc_im += di;
+            pacc_re += pr; pacc_im += pi;
+        }
+    }
+    if (active && sub == 0) {
+        auto put = [&](double *out, double *part, double re, double im) {
+            double *dst = nullptr;
+            if (it.part < 0) {
+                if (out) dst = out + 2 * (int64_t)g.slot_tgt[it.slot_begin + j];
+            } else if (part) {
+                dst = part + 2 * ((int64_t)it.part + j);
+            }
+            if (dst) {
+                dst[0] = re * kInv4Pi;
+                dst[1] = im * kInv4Pi;
+            }
+        };
+        put(ev.out_slp, ev.part_slp, acc_re, acc_im);
+        if (DLP) put(ev.out_dlp, ev.part_dlp, dacc_re, dacc_im);
+        if (SP) put(ev.out_sp, ev.part_sp, pacc_re, pacc_im);
+    }
+}
+
+template <bool SP, int P>
+int launch_helm_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks == 0) return 0;
+    if (dlp) helmholtz_kernel<P, true, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    else     helmholtz_kernel<P, false, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    return (int)cudaGetLastError();
+}
+
+template <bool SP, int... Ps>
+int dispatch_helm(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s,
+                  std::integer_sequence<int, Ps...>)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    ((p == Ps ? (rc = launch_helm_p<SP, Ps>(dlp, g, e, s), 0) : 0), ...);
+    return rc;
+}
+
+}  // namespace
+
+// Defined in helmholtz_sp.cu.
+int launch_helmholtz_fp64_sp(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s);
+
+}  // namespace tsqbx

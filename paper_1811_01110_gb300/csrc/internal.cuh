@@ -48,6 +48,8 @@ struct DevGeom {
     const float4 *slot_chi = nullptr;   // float-float center
     const float4 *slot_clo = nullptr;
     const float4 *slot_ef = nullptr;    // {ex, ey, ez, rho^2} rounded to FP32
+    const double4_32a *slot_n = nullptr;    // target normal {nx, ny, nz, 0} (S')
+    const float4 *slot_nf = nullptr;    // target normal rounded to FP32 (mixed S')
 };
 
 // Per-evaluation buffers (device pointers).
@@ -57,20 +59,20 @@ struct DevEval {
     const double2 *wmu_c = nullptr;     // Helmholtz: w_s mu_s (complex)
     double *out_slp = nullptr;          // indexed by target (real or interleaved complex)
     double *out_dlp = nullptr;
+    double *out_sp = nullptr;
     double *part_slp = nullptr;         // partial sums of sliced items (scratch)
     double *part_dlp = nullptr;
+    double *part_sp = nullptr;
     int *status = nullptr;              // bit 0: out-of-range source index seen
     double k = 0.0;                     // Helmholtz wavenumber
 };
 
 // Launchers (one per translation unit).  Return a cudaError_t as int.
-int launch_laplace_fp64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e,
-                        cudaStream_t s);
-int launch_laplace_mixed(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e,
-                         cudaStream_t s);
-int launch_helmholtz_fp64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e,
-                          cudaStream_t s);
-int launch_laplace_df64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s);
+// Layer mask as in tsqbx.h (1 = single layer, 2 = double layer, 4 = S').
+int launch_laplace_fp64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
+int launch_laplace_mixed(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
+int launch_laplace_df64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
+int launch_helmholtz_fp64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 
 // Legendre three-term recurrence in the scaled form used by every kernel:
 //   Q_n = (rho/R)^n P_n(x) = kappa_n T_n,

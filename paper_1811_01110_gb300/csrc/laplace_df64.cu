@@ -3,212 +3,23 @@
 //
 // Same expansion and warp mapping as laplace_fp64.cu (Appendix A; scaled
 // Bonnet recurrence T_{n+1} = qx T_n - beta_n q2 T_{n-1}, Q_n = kappa_n T_n;
-// double layer through Q'_{n+1} = q2 Q'_{n-1} + (2n+1) Q_n), every quantity a
+// double layer through Q'_{n+1} = q2 Q'_{n-1} + (2n+1) Q_n; S' through the
+// recurrence differentiated along n_t), every quantity a
 // double-float.  Geometry: each item picks a reference point (its first
 // target's center) and forms s - ref and c - ref in FP64 before splitting
 // them into double-floats, so d = s - c keeps ~48 significant bits relative
 // to |d| itself.  The recurrence constants are exact double-float splits of
 // their double values.  Per-lane sums are double-floats; lanes of a target
 // are combined in FP64.
-#include <utility>
-
-#include "dfloat.cuh"
-#include "internal.cuh"
+#include "laplace_df_items.cuh"
 
 namespace tsqbx {
-namespace {
 
-struct df3 {
-    df x, y, z;
-};
-
-__device__ __forceinline__ df3 df3_from(double x, double y, double z)
+int launch_laplace_df64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
-    return {df_from_double(x), df_from_double(y), df_from_double(z)};
-}
-
-__device__ __forceinline__ df df_dot(const df3 &a, const df3 &b)
-{
-    return df_add(df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_mul(a.z, b.z));
-}
-
-template <int P, bool DLP>
-__device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df wm, const df3 &n, df &acc_s,
-                                        df &acc_d)
-{
-    const df R2 = df_dot(d, d);
-    const df rinv = df_rsqrt(R2);
-    const df r2inv = df_mul(rinv, rinv);
-    const df qx = df_mul(df_dot(d, e), r2inv);
-    const df q2 = df_mul(rho2, r2inv);
-    df S0{1.f, 0.f}, S2{0.f, 0.f};
-    df Tm{1.f, 0.f}, Tc{1.f, 0.f}, Dm{0.f, 0.f}, Dc{0.f, 0.f};
-    if (P >= 1) { S0 = df_add(S0, qx); S2 = df{1.f, 0.f}; Tc = qx; Dc = df{1.f, 0.f}; }
-#pragma unroll
-    for (int n = 1; n < P; ++n) {
-        const df bq = df_mul(df_of(df_const(rec_beta(n))), q2);
-        const df Tn = df_sub(df_mul(qx, Tc), df_mul(bq, Tm));
-        S0 = df_add(S0, df_mul(df_of(df_const(rec_kappa(n + 1))), Tn));
-        if (DLP) {
-            const df Dn = df_add(df_mul(q2, Dm), df_mul(df_of(df_const((2.0 * n + 1.0) * rec_kappa(n))), Tc));
-            S2 = df_add(S2, Dn);
-            Dm = Dc; Dc = Dn;
-        }
-        Tm = Tc; Tc = Tn;
-    }
-    acc_s = df_add(acc_s, df_mul(df_mul(wm, rinv), S0));
-    if (DLP) {
-        const df Dp1 = df_add(df_mul(q2, Dm), df_mul(df_of(df_const((2.0 * P + 1.0) * rec_kappa(P))), Tc));
-        // S1 = sum (n+1) Q_n = ((1 - q2) S2 + Q'_{p+1} + q2 Q'_p + S0) / 2
-        const df S1 = df_mul_f(df_add(df_add(df_sub(S2, df_mul(q2, S2)), Dp1), df_add(df_mul(q2, Dc), S0)), 0.5f);
-        const df a = df_dot(d, n);
-        const df b = df_dot(e, n);
-        const df val = df_sub(df_mul(df_sub(b, df_mul(a, qx)), S2), df_mul(a, S1));
-        acc_d = df_add(acc_d, df_mul(df_mul(wm, df_mul(rinv, r2inv)), val));
-    }
-}
-
-template <bool DLP>
-__device__ __forceinline__ void write_df_result(const DevGeom &g, const DevEval &ev, const Item &it, int j,
-                                                double acc_s, double acc_d)
-{
-    if (it.part < 0) {
-        const int t = g.slot_tgt[it.slot_begin + j];
-        if (ev.out_slp) ev.out_slp[t] = acc_s * kInv4Pi;
-        if (DLP && ev.out_dlp) ev.out_dlp[t] = acc_d * kInv4Pi;
-    } else {
-        ev.part_slp[it.part + j] = acc_s * kInv4Pi;
-        if (DLP) ev.part_dlp[it.part + j] = acc_d * kInv4Pi;
-    }
-}
-
-template <int P, bool DLP>
-__device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                float4 (*T)[kTile], const int lane)
-{
-    const int64_t s0 = g.grp_off[it.group];
-    const int src_hi = it.src_hi;
-    df acc_s{0.f, 0.f}, acc_d{0.f, 0.f};
-    const df3 zero3{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    if (it.n_tgt == 1) {                                   // direct loads, all 32 lanes
-        const double4_32a c = g.slot_c[it.slot_begin];
-        const double4_32a e4 = g.slot_e[it.slot_begin];
-        const df3 e = df3_from(e4.x, e4.y, e4.z);
-        const df rho2 = df_from_double(e4.w);
-#pragma unroll 1
-        for (int k = it.src_lo + lane; k < src_hi; k += 32) {
-            int s = g.grp_src[s0 + k];
-            double wmd = 0.0;
-            if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
-            else wmd = ev.wmu[s];
-            const double4_32a pw = g.src_pw[s];
-            const df3 d = df3_from(pw.x - c.x, pw.y - c.y, pw.z - c.z);
-            df3 n = zero3;
-            if (DLP) { const double4_32a nn = g.src_n[s]; n = df3_from(nn.x, nn.y, nn.z); }
-            pair_df<P, DLP>(d, e, rho2, df_from_double(wmd), n, acc_s, acc_d);
-        }
-        double vs = df_to_double(acc_s), vd = df_to_double(acc_d);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            vs += __shfl_xor_sync(0xffffffffu, vs, off);
-            vd += __shfl_xor_sync(0xffffffffu, vd, off);
-        }
-        if (lane == 0) write_df_result<DLP>(g, ev, it, 0, vs, vd);
-        return;
-    }
-    const int L = it.L;
-    const int j = lane / L, sub = lane - j * L;
-    const bool active = j < it.n_tgt;
-    const double4_32a ref = g.slot_c[it.slot_begin];      // item reference point
-    df3 crel = zero3, e = zero3;
-    df rho2{0.f, 0.f};
-    if (active) {
-        const double4_32a c = g.slot_c[it.slot_begin + j];
-        const double4_32a e4 = g.slot_e[it.slot_begin + j];
-        crel = df3_from(c.x - ref.x, c.y - ref.y, c.z - ref.z);
-        e = df3_from(e4.x, e4.y, e4.z);
-        rho2 = df_from_double(e4.w);
-    }
-    for (int base = it.src_lo; base < src_hi; base += kTile) {
-        const int cnt = min(kTile, src_hi - base);
-        for (int k = lane; k < cnt; k += 32) {
-            int s = g.grp_src[s0 + base + k];
-            double wmd = 0.0;
-            if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
-            else wmd = ev.wmu[s];
-            const double4_32a pw = g.src_pw[s];
-            const df3 r = df3_from(pw.x - ref.x, pw.y - ref.y, pw.z - ref.z);
-            const df w = df_from_double(wmd);
-            T[0][k] = make_float4(r.x.hi, r.y.hi, r.z.hi, w.hi);
-            T[1][k] = make_float4(r.x.lo, r.y.lo, r.z.lo, w.lo);
-            if (DLP) {
-                const double4_32a nn = g.src_n[s];
-                const df3 n = df3_from(nn.x, nn.y, nn.z);
-                T[2][k] = make_float4(n.x.hi, n.y.hi, n.z.hi, 0.f);
-                T[3][k] = make_float4(n.x.lo, n.y.lo, n.z.lo, 0.f);
-            }
-        }
-        __syncwarp();
-        if (active) {
-            for (int k = sub; k < cnt; k += L) {
-                const float4 a = T[0][k], b = T[1][k];
-                const df3 d{df_sub(df{a.x, b.x}, crel.x), df_sub(df{a.y, b.y}, crel.y),
-                            df_sub(df{a.z, b.z}, crel.z)};
-                df3 n = zero3;
-                if (DLP) {
-                    const float4 c = T[2][k], h = T[3][k];
-                    n = df3{{c.x, h.x}, {c.y, h.y}, {c.z, h.z}};
-                }
-                pair_df<P, DLP>(d, e, rho2, df{a.w, b.w}, n, acc_s, acc_d);
-            }
-        }
-        __syncwarp();
-    }
-    double vs = df_to_double(acc_s), vd = df_to_double(acc_d);
-    for (int off = 1; off < L; off <<= 1) {
-        const double ts = __shfl_down_sync(0xffffffffu, vs, off);
-        const double td = __shfl_down_sync(0xffffffffu, vd, off);
-        if (sub + off < L) { vs += ts; vd += td; }
-    }
-    if (active && sub == 0) write_df_result<DLP>(g, ev, it, j, vs, vd);
-}
-
-template <int P, bool DLP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-laplace_df_kernel(const DevGeom g, const DevEval ev)
-{
-    __shared__ float4 tile[kWarpsPerBlock][DLP ? 4 : 2][kTile];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-    if (item >= g.n_items) return;
-    laplace_df_item<P, DLP>(g, ev, g.items[item], tile[warp], lane);
-}
-
-template <int P>
-int launch_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
-{
-    const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (blocks == 0) return 0;
-    if (dlp) laplace_df_kernel<P, true><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
-    else     laplace_df_kernel<P, false><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
-    return (int)cudaGetLastError();
-}
-
-template <int... Ps>
-int dispatch(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s,
-             std::integer_sequence<int, Ps...>)
-{
-    int rc = (int)cudaErrorInvalidValue;
-    ((p == Ps ? (rc = launch_p<Ps>(dlp, g, e, s), 0) : 0), ...);
-    return rc;
-}
-
-}  // namespace
-
-int launch_laplace_df64(int p, bool slp, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
-{
-    (void)slp;
-    return dispatch(p, dlp, g, e, s, std::make_integer_sequence<int, 21>{});
+    const bool dlp = (layers & 2u) != 0;
+    if (layers & 4u) return launch_laplace_df64_sp(p, dlp, g, e, s);
+    return dispatch_df<false>(p, dlp, g, e, s, std::make_integer_sequence<int, 21>{});
 }
 
 }  // namespace tsqbx

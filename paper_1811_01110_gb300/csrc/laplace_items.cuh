@@ -26,20 +26,27 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 }
 
 // One (target, source) pair in FP64: d = s - c, e = t - c, wm = w mu, n = n_s.
-template <int P, bool DLP>
+// S' (target-normal derivative): the recurrence differentiated along n_t,
+// T'_{n+1} = qx' T_n + qx T'_n - beta_n (q2' T_{n-1} + q2 T'_{n-1}) with
+// qx' = (d.n_t)/R^2 and q2' = 2 (e.n_t)/R^2 (f2 = 2 e.n_t, per target), so
+// n_t.grad_t G^(p) = (1/4pi)(1/R) sum kappa_n T'_n -- no division by rho.
+template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, double ex, double ey, double ez,
                                           double rho2, double wm, double nx, double ny, double nz,
-                                          double &acc_s, double &acc_d)
+                                          double tx, double ty, double tz, double f2,
+                                          double &acc_s, double &acc_d, double &acc_p)
 {
     const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
     const double rinv = rsqrt(R2);
     const double r2inv = rinv * rinv;
     const double qx = fma(dx, ex, fma(dy, ey, dz * ez)) * r2inv;
     const double q2 = rho2 * r2inv;
-    // n = 0 (and n = 1 when P >= 1); T_{n-1}, T_n, Q'_{n-1}, Q'_n
-    double S0 = 1.0, S2 = 0.0;
-    double Tm = 1.0, Tc = 1.0, Dm = 0.0, Dc = 0.0;
-    if (P >= 1) { S0 += qx; S2 = 1.0; Tc = qx; Dc = 1.0; }
+    const double qxp = SP ? fma(dx, tx, fma(dy, ty, dz * tz)) * r2inv : 0.0;
+    const double q2p = SP ? f2 * r2inv : 0.0;
+    // n = 0 (and n = 1 when P >= 1); T_{n-1}, T_n, Q'_{n-1}, Q'_n, T'_{n-1}, T'_n
+    double S0 = 1.0, S2 = 0.0, S3 = 0.0;
+    double Tm = 1.0, Tc = 1.0, Dm = 0.0, Dc = 0.0, Pm = 0.0, Pc = 0.0;
+    if (P >= 1) { S0 += qx; S2 = 1.0; Tc = qx; Dc = 1.0; Pc = qxp; S3 = qxp; }
 #pragma unroll
     for (int n = 1; n < P; ++n) {
         const double Tn = fma(qx, Tc, -(rec_beta(n) * q2) * Tm);
@@ -49,9 +56,15 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
             S2 += Dn;
             Dm = Dc; Dc = Dn;
         }
+        if (SP) {
+            const double Pn = fma(qxp, Tc, fma(qx, Pc, -rec_beta(n) * fma(q2p, Tm, q2 * Pm)));
+            S3 = fma(rec_kappa(n + 1), Pn, S3);
+            Pm = Pc; Pc = Pn;
+        }
         Tm = Tc; Tc = Tn;
     }
     acc_s = fma(wm * rinv, S0, acc_s);
+    if (SP) acc_p = fma(wm * rinv, S3, acc_p);
     if (DLP) {
         const double Dp1 = fma(q2, Dm, ((2.0 * P + 1.0) * rec_kappa(P)) * Tc);
         const double S1 = 0.5 * (fma(-q2, S2, S2) + Dp1 + fma(q2, Dc, S0));
@@ -63,11 +76,12 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
 }
 
 // One pair in mixed precision: h/l = source hi/lo (h.w = w mu), ch/cl = center
-// hi/lo, e = {t - c, rho^2}, nn = n_s; Kahan-compensated FP32 sums.
-template <int P, bool DLP>
+// hi/lo, e = {t - c, rho^2}, nn = n_s, tn = {n_t, 2 e.n_t}; Kahan-compensated
+// FP32 sums (as/ac single layer, ds/dc double layer, ps/pc S').
+template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, const float4 &ch, const float4 &cl,
-                                           const float4 &e, const float4 &nn, float &as, float &ac,
-                                           float &ds, float &dc)
+                                           const float4 &e, const float4 &nn, const float4 &tn, float &as,
+                                           float &ac, float &ds, float &dc, float &ps, float &pc)
 {
     const float dx = __fadd_rn(__fsub_rn(h.x, ch.x), __fsub_rn(l.x, cl.x));
     const float dy = __fadd_rn(__fsub_rn(h.y, ch.y), __fsub_rn(l.y, cl.y));
@@ -77,9 +91,11 @@ __device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, con
     const float r2inv = rinv * rinv;
     const float qx = fmaf(dx, e.x, fmaf(dy, e.y, dz * e.z)) * r2inv;
     const float q2 = e.w * r2inv;
-    float S0 = 1.f, S2 = 0.f;
-    float Tm = 1.f, Tc = 1.f, Dm = 0.f, Dc = 0.f;
-    if (P >= 1) { S0 += qx; S2 = 1.f; Tc = qx; Dc = 1.f; }
+    const float qxp = SP ? fmaf(dx, tn.x, fmaf(dy, tn.y, dz * tn.z)) * r2inv : 0.f;
+    const float q2p = SP ? tn.w * r2inv : 0.f;
+    float S0 = 1.f, S2 = 0.f, S3 = 0.f;
+    float Tm = 1.f, Tc = 1.f, Dm = 0.f, Dc = 0.f, Pm = 0.f, Pc = 0.f;
+    if (P >= 1) { S0 += qx; S2 = 1.f; Tc = qx; Dc = 1.f; Pc = qxp; S3 = qxp; }
 #pragma unroll
     for (int n = 1; n < P; ++n) {
         const float Tn = fmaf(qx, Tc, -((float)rec_beta(n) * q2) * Tm);
@@ -89,9 +105,15 @@ __device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, con
             S2 += Dn;
             Dm = Dc; Dc = Dn;
         }
+        if (SP) {
+            const float Pn = fmaf(qxp, Tc, fmaf(qx, Pc, -(float)rec_beta(n) * fmaf(q2p, Tm, q2 * Pm)));
+            S3 = fmaf((float)rec_kappa(n + 1), Pn, S3);
+            Pm = Pc; Pc = Pn;
+        }
         Tm = Tc; Tc = Tn;
     }
     kahan_add(as, ac, h.w * rinv * S0);
+    if (SP) kahan_add(ps, pc, h.w * rinv * S3);
     if (DLP) {
         const float Dp1 = fmaf(q2, Dm, (float)((2.0 * P + 1.0) * rec_kappa(P)) * Tc);
         const float S1 = 0.5f * (fmaf(-q2, S2, S2) + Dp1 + fmaf(q2, Dc, S0));
@@ -104,18 +126,30 @@ __device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, con
 
 // Write a target's sums (target j of the item): to the outputs, or to the
 // partial-sum slots when the item is one slice of a longer list.
-template <bool DLP>
+template <bool DLP, bool SP>
 __device__ __forceinline__ void write_item_result(const DevGeom &g, const DevEval &ev, const Item &it, int j,
-                                                  double acc_s, double acc_d)
+                                                  double acc_s, double acc_d, double acc_p)
 {
     if (it.part < 0) {
         const int t = g.slot_tgt[it.slot_begin + j];
         if (ev.out_slp) ev.out_slp[t] = acc_s * kInv4Pi;
         if (DLP && ev.out_dlp) ev.out_dlp[t] = acc_d * kInv4Pi;
+        if (SP && ev.out_sp) ev.out_sp[t] = acc_p * kInv4Pi;
     } else {
-        ev.part_slp[it.part + j] = acc_s * kInv4Pi;
-        if (DLP) ev.part_dlp[it.part + j] = acc_d * kInv4Pi;
+        if (ev.part_slp) ev.part_slp[it.part + j] = acc_s * kInv4Pi;
+        if (DLP && ev.part_dlp) ev.part_dlp[it.part + j] = acc_d * kInv4Pi;
+        if (SP && ev.part_sp) ev.part_sp[it.part + j] = acc_p * kInv4Pi;
     }
+}
+
+// Segmented sum over the L lanes of each target (lane sub == 0 gets it).
+__device__ __forceinline__ double segment_sum(double v, int sub, int L)
+{
+    for (int off = 1; off < L; off <<= 1) {
+        const double u = __shfl_down_sync(0xffffffffu, v, off);
+        if (sub + off < L) v += u;
+    }
+    return v;
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -125,16 +159,22 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <int P, bool DLP>
+template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEval &ev, const Item &it,
                                                   double (*T)[kTile], const int lane)
 {
     const int64_t s0 = g.grp_off[it.group];
     const int src_hi = it.src_hi;
-    double acc_s = 0.0, acc_d = 0.0;
+    double acc_s = 0.0, acc_d = 0.0, acc_p = 0.0;
     if (it.n_tgt == 1) {                                   // direct loads, all 32 lanes
         const double4_32a c = g.slot_c[it.slot_begin];
         const double4_32a e = g.slot_e[it.slot_begin];
+        double tx = 0, ty = 0, tz = 0, f2 = 0;
+        if (SP) {
+            const double4_32a tn = g.slot_n[it.slot_begin];
+            tx = tn.x; ty = tn.y; tz = tn.z;
+            f2 = 2.0 * fma(e.x, tx, fma(e.y, ty, e.z * tz));
+        }
 #pragma unroll 2
         for (int k = it.src_lo + lane; k < src_hi; k += 32) {
             int s = g.grp_src[s0 + k];
@@ -144,23 +184,29 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
             const double4_32a pw = g.src_pw[s];
             double nx = 0, ny = 0, nz = 0;
             if (DLP) { const double4_32a n = g.src_n[s]; nx = n.x; ny = n.y; nz = n.z; }
-            pair_fp64<P, DLP>(pw.x - c.x, pw.y - c.y, pw.z - c.z, e.x, e.y, e.z, e.w, wm, nx, ny, nz,
-                              acc_s, acc_d);
+            pair_fp64<P, DLP, SP>(pw.x - c.x, pw.y - c.y, pw.z - c.z, e.x, e.y, e.z, e.w, wm, nx, ny, nz,
+                                  tx, ty, tz, f2, acc_s, acc_d, acc_p);
         }
         acc_s = warp_sum(acc_s);
         if (DLP) acc_d = warp_sum(acc_d);
-        if (lane == 0) write_item_result<DLP>(g, ev, it, 0, acc_s, acc_d);
+        if (SP) acc_p = warp_sum(acc_p);
+        if (lane == 0) write_item_result<DLP, SP>(g, ev, it, 0, acc_s, acc_d, acc_p);
         return;
     }
     const int L = it.L;
     const int j = lane / L, sub = lane - j * L;
     const bool active = j < it.n_tgt;
-    double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rho2 = 0;
+    double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rho2 = 0, tx = 0, ty = 0, tz = 0, f2 = 0;
     if (active) {
         const double4_32a c = g.slot_c[it.slot_begin + j];
         const double4_32a e = g.slot_e[it.slot_begin + j];
         cx = c.x; cy = c.y; cz = c.z;
         ex = e.x; ey = e.y; ez = e.z; rho2 = e.w;
+        if (SP) {
+            const double4_32a tn = g.slot_n[it.slot_begin + j];
+            tx = tn.x; ty = tn.y; tz = tn.z;
+            f2 = 2.0 * fma(ex, tx, fma(ey, ty, ez * tz));
+        }
     }
     for (int base = it.src_lo; base < src_hi; base += kTile) {
         const int cnt = min(kTile, src_hi - base);
@@ -179,32 +225,35 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
         __syncwarp();
         if (active) {
             for (int k = sub; k < cnt; k += L)
-                pair_fp64<P, DLP>(T[0][k] - cx, T[1][k] - cy, T[2][k] - cz, ex, ey, ez, rho2, T[3][k],
-                                  DLP ? T[4][k] : 0.0, DLP ? T[5][k] : 0.0, DLP ? T[6][k] : 0.0,
-                                  acc_s, acc_d);
+                pair_fp64<P, DLP, SP>(T[0][k] - cx, T[1][k] - cy, T[2][k] - cz, ex, ey, ez, rho2, T[3][k],
+                                      DLP ? T[4][k] : 0.0, DLP ? T[5][k] : 0.0, DLP ? T[6][k] : 0.0,
+                                      tx, ty, tz, f2, acc_s, acc_d, acc_p);
         }
         __syncwarp();
     }
-    for (int off = 1; off < L; off <<= 1) {
-        const double vs = __shfl_down_sync(0xffffffffu, acc_s, off);
-        const double vd = __shfl_down_sync(0xffffffffu, acc_d, off);
-        if (sub + off < L) { acc_s += vs; acc_d += vd; }
-    }
-    if (active && sub == 0) write_item_result<DLP>(g, ev, it, j, acc_s, acc_d);
+    acc_s = segment_sum(acc_s, sub, L);
+    if (DLP) acc_d = segment_sum(acc_d, sub, L);
+    if (SP) acc_p = segment_sum(acc_p, sub, L);
+    if (active && sub == 0) write_item_result<DLP, SP>(g, ev, it, j, acc_s, acc_d, acc_p);
 }
 
-template <int P, bool DLP>
+template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEval &ev, const Item &it,
                                                    float4 (*T)[kTile], const int lane)
 {
     const int64_t s0 = g.grp_off[it.group];
     const int src_hi = it.src_hi;
-    float as = 0.f, ac = 0.f, ds = 0.f, dc = 0.f;     // Kahan pairs (single, double layer)
+    float as = 0.f, ac = 0.f, ds = 0.f, dc = 0.f, ps = 0.f, pc = 0.f;   // Kahan pairs
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     if (it.n_tgt == 1) {                               // direct loads, all 32 lanes
         const float4 ch = g.slot_chi[it.slot_begin];
         const float4 cl = g.slot_clo[it.slot_begin];
         const float4 e = g.slot_ef[it.slot_begin];
+        float4 tn = zero;
+        if (SP) {
+            tn = g.slot_nf[it.slot_begin];
+            tn.w = 2.f * fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));
+        }
 #pragma unroll 2
         for (int k = it.src_lo + lane; k < src_hi; k += 32) {
             int s = g.grp_src[s0 + k];
@@ -215,21 +264,26 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
             h.w = wm;
             const float4 l = g.src_lo[s];
             const float4 nn = DLP ? g.src_nf[s] : zero;
-            pair_mixed<P, DLP>(h, l, ch, cl, e, nn, as, ac, ds, dc);
+            pair_mixed<P, DLP, SP>(h, l, ch, cl, e, nn, tn, as, ac, ds, dc, ps, pc);
         }
-        double acc_s = warp_sum((double)as - (double)ac);
-        double acc_d = DLP ? warp_sum((double)ds - (double)dc) : 0.0;
-        if (lane == 0) write_item_result<DLP>(g, ev, it, 0, acc_s, acc_d);
+        const double acc_s = warp_sum((double)as - (double)ac);
+        const double acc_d = DLP ? warp_sum((double)ds - (double)dc) : 0.0;
+        const double acc_p = SP ? warp_sum((double)ps - (double)pc) : 0.0;
+        if (lane == 0) write_item_result<DLP, SP>(g, ev, it, 0, acc_s, acc_d, acc_p);
         return;
     }
     const int L = it.L;
     const int j = lane / L, sub = lane - j * L;
     const bool active = j < it.n_tgt;
-    float4 ch = zero, cl = zero, e = zero;
+    float4 ch = zero, cl = zero, e = zero, tn = zero;
     if (active) {
         ch = g.slot_chi[it.slot_begin + j];
         cl = g.slot_clo[it.slot_begin + j];
         e = g.slot_ef[it.slot_begin + j];
+        if (SP) {
+            tn = g.slot_nf[it.slot_begin + j];
+            tn.w = 2.f * fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));
+        }
     }
     for (int base = it.src_lo; base < src_hi; base += kTile) {
         const int cnt = min(kTile, src_hi - base);
@@ -247,18 +301,15 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         __syncwarp();
         if (active) {
             for (int k = sub; k < cnt; k += L)
-                pair_mixed<P, DLP>(T[0][k], T[1][k], ch, cl, e, DLP ? T[2][k] : zero, as, ac, ds, dc);
+                pair_mixed<P, DLP, SP>(T[0][k], T[1][k], ch, cl, e, DLP ? T[2][k] : zero, tn, as, ac, ds, dc,
+                                       ps, pc);
         }
         __syncwarp();
     }
-    double acc_s = (double)as - (double)ac;
-    double acc_d = (double)ds - (double)dc;
-    for (int off = 1; off < L; off <<= 1) {
-        const double vs = __shfl_down_sync(0xffffffffu, acc_s, off);
-        const double vd = __shfl_down_sync(0xffffffffu, acc_d, off);
-        if (sub + off < L) { acc_s += vs; acc_d += vd; }
-    }
-    if (active && sub == 0) write_item_result<DLP>(g, ev, it, j, acc_s, acc_d);
+    const double acc_s = segment_sum((double)as - (double)ac, sub, L);
+    const double acc_d = DLP ? segment_sum((double)ds - (double)dc, sub, L) : 0.0;
+    const double acc_p = SP ? segment_sum((double)ps - (double)pc, sub, L) : 0.0;
+    if (active && sub == 0) write_item_result<DLP, SP>(g, ev, it, j, acc_s, acc_d, acc_p);
 }
 
 }  // namespace tsqbx

@@ -1,0 +1,77 @@
+// laplace_launch.cuh -- the one-plan Laplace kernels (one warp per work item)
+// and their dispatch over the expansion order p.  Each translation unit
+// instantiates the variants it owns: laplace_fp64.cu / laplace_mixed.cu the
+// single/double-layer ones, laplace_fp64_sp.cu / laplace_mixed_sp.cu the ones
+// that also form S' (the target-normal derivative), so the four compile in
+// parallel.
+#pragma once
+
+#include <utility>
+
+#include "laplace_items.cuh"
+
+namespace tsqbx {
+namespace {
+
+template <int P, bool DLP, bool SP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+laplace_fp64_kernel(const DevGeom g, const DevEval ev)
+{
+    __shared__ double tile[kWarpsPerBlock][DLP ? 7 : 4][kTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (item >= g.n_items) return;                       // whole warp leaves together
+    laplace_fp64_item<P, DLP, SP>(g, ev, g.items[item], tile[warp], lane);
+}
+
+template <int P, bool DLP, bool SP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+laplace_mixed_kernel(const DevGeom g, const DevEval ev)
+{
+    __shared__ float4 tile[kWarpsPerBlock][DLP ? 3 : 2][kTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (item >= g.n_items) return;
+    laplace_mixed_item<P, DLP, SP>(g, ev, g.items[item], tile[warp], lane);
+}
+
+template <bool MIXED, int P, bool DLP, bool SP>
+void launch_one(unsigned blocks, const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    if (MIXED) laplace_mixed_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    else       laplace_fp64_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+}
+
+template <bool MIXED, bool SP, int P>
+int launch_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks == 0) return 0;
+    if (dlp) launch_one<MIXED, P, true, SP>((unsigned)blocks, g, e, s);
+    else     launch_one<MIXED, P, false, SP>((unsigned)blocks, g, e, s);
+    return (int)cudaGetLastError();
+}
+
+template <bool MIXED, bool SP, int... Ps>
+int dispatch_p(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s,
+               std::integer_sequence<int, Ps...>)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    ((p == Ps ? (rc = launch_p<MIXED, SP, Ps>(dlp, g, e, s), 0) : 0), ...);
+    return rc;
+}
+
+// p in [0, 20]; any other p returns cudaErrorInvalidValue.
+template <bool MIXED, bool SP>
+int laplace_dispatch(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    return dispatch_p<MIXED, SP>(p, dlp, g, e, s, std::make_integer_sequence<int, 21>{});
+}
+
+}  // namespace
+
+// Defined in laplace_fp64_sp.cu / laplace_mixed_sp.cu.
+int launch_laplace_fp64_sp(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s);
+int launch_laplace_mixed_sp(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s);
+
+}  // namespace tsqbx

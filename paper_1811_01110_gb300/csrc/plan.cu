@@ -83,7 +83,8 @@ __global__ void check_pairs_kernel(const DevGeom g, unsigned long long *n_div,
 // Second pass for sliced items: each target's partial sums (one per slice of
 // its group's list) are added in slice order, so results are deterministic.
 __global__ void combine_kernel(const DevGeom g, const double *part_slp, const double *part_dlp,
-                               double *out_slp, double *out_dlp, int width)
+                               const double *part_sp, double *out_slp, double *out_dlp, double *out_sp,
+                               int width)
 {
     const int64_t n = g.n_combine * 32;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -93,14 +94,16 @@ __global__ void combine_kernel(const DevGeom g, const double *part_slp, const do
         if (j >= r.n_tgt) continue;
         const int64_t t = g.slot_tgt[r.slot_begin + j];
         for (int w = 0; w < width; ++w) {
-            double a = 0.0, b = 0.0;
+            double a = 0.0, b = 0.0, c = 0.0;
             for (int k = 0; k < r.n_slices; ++k) {
                 const int64_t idx = ((int64_t)r.part + (int64_t)k * r.n_tgt + j) * width + w;
                 if (part_slp) a += part_slp[idx];
                 if (part_dlp) b += part_dlp[idx];
+                if (part_sp) c += part_sp[idx];
             }
             if (out_slp) out_slp[t * width + w] = a;
             if (out_dlp) out_dlp[t * width + w] = b;
+            if (out_sp) out_sp[t * width + w] = c;
         }
     }
 }
@@ -153,7 +156,7 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
 {
     if (!G || !o) return TSQBX_E_INVAL;
     if (o->kernel != TSQBX_LAPLACE && o->kernel != TSQBX_HELMHOLTZ) return TSQBX_E_INVAL;
-    if (o->layers == 0 || (o->layers & ~(uint32_t)(TSQBX_SLP | TSQBX_DLP))) return TSQBX_E_INVAL;
+    if (o->layers == 0 || (o->layers & ~(uint32_t)(TSQBX_SLP | TSQBX_DLP | TSQBX_SP))) return TSQBX_E_INVAL;
     if (o->p < 0 || o->p > TSQBX_P_MAX) return TSQBX_E_INVAL;
     if (o->precision != TSQBX_FP64 && o->precision != TSQBX_MIXED && o->precision != TSQBX_DF64)
         return TSQBX_E_INVAL;
@@ -163,7 +166,6 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
     if (o->kernel == TSQBX_HELMHOLTZ) {
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
         if (o->precision != TSQBX_FP64) return TSQBX_E_UNSUPPORTED;
-        if (o->layers != TSQBX_SLP) return TSQBX_E_UNSUPPORTED;
     }
     if (G->n_src < 0 || G->n_ctr < 0 || G->n_tgt < 0 || G->n_group < 0) return TSQBX_E_INVAL;
     if (G->n_src > INT32_MAX || G->n_ctr > INT32_MAX || G->n_tgt > INT32_MAX || G->n_group > INT32_MAX)
@@ -173,6 +175,7 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         !G->group_range_start)
         return TSQBX_E_INVAL;
     if ((o->layers & TSQBX_DLP) && G->n_src && !G->src_normal) return TSQBX_E_INVAL;
+    if ((o->layers & TSQBX_SP) && G->n_tgt && !G->tgt_normal) return TSQBX_E_INVAL;
     if (G->group_range_start[0] != 0) return TSQBX_E_INVAL;
     for (int64_t q = 0; q < G->n_group; ++q)
         if (G->group_range_start[q + 1] < G->group_range_start[q]) return TSQBX_E_INVAL;
@@ -182,9 +185,11 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         if (G->range_begin[i] < 0 || G->range_end[i] < G->range_begin[i] ||
             G->range_end[i] > G->n_src)
             return TSQBX_E_INVAL;
-    for (int64_t t = 0; t < G->n_tgt; ++t)
+    for (int64_t t = 0; t < G->n_tgt; ++t) {
         if (G->tgt_center[t] < 0 || G->tgt_center[t] >= G->n_ctr || !finite3(G->tgt_xyz, G->n_tgt, t))
             return TSQBX_E_INVAL;
+        if ((o->layers & TSQBX_SP) && !finite3(G->tgt_normal, G->n_tgt, t)) return TSQBX_E_INVAL;
+    }
     for (int64_t c = 0; c < G->n_ctr; ++c)
         if (G->ctr_group[c] < 0 || G->ctr_group[c] >= G->n_group || !finite3(G->ctr_xyz, G->n_ctr, c))
             return TSQBX_E_INVAL;
@@ -298,7 +303,7 @@ void apply_schedule(tsqbx_plan P, Schedule &&s)
     P->g.items = nullptr;
     P->g.combine = nullptr;
     for (Slot &sl : P->slots)
-        for (int l = 0; l < 2; ++l) {
+        for (int l = 0; l < 3; ++l) {
             if (sl.d_part[l]) P->dfree(sl.d_part[l]);
             sl.d_part[l] = nullptr;
         }
@@ -311,12 +316,13 @@ void apply_schedule(tsqbx_plan P, Schedule &&s)
     for (Slot &sl : P->slots) {
         if (s.n_parts && (P->opt.layers & TSQBX_SLP)) sl.d_part[0] = P->dalloc<double>(part_doubles);
         if (s.n_parts && (P->opt.layers & TSQBX_DLP)) sl.d_part[1] = P->dalloc<double>(part_doubles);
+        if (s.n_parts && (P->opt.layers & TSQBX_SP)) sl.d_part[2] = P->dalloc<double>(part_doubles);
     }
     P->sched = std::move(s);
     fill_stats(P);
 }
 
-int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
+int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp, double *d_sp,
             cudaStream_t s, bool timed, int p, double k)
 {
     const tsqbx_options &o = P->opt;
@@ -327,8 +333,10 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     ev.status = slot.d_status;
     ev.out_slp = (o.layers & TSQBX_SLP) ? d_slp : nullptr;
     ev.out_dlp = (o.layers & TSQBX_DLP) ? d_dlp : nullptr;
+    ev.out_sp = (o.layers & TSQBX_SP) ? d_sp : nullptr;
     ev.part_slp = slot.d_part[0];
     ev.part_dlp = slot.d_part[1];
+    ev.part_sp = ev.out_sp ? slot.d_part[2] : nullptr;
     ev.k = k;
     if (n > 0) {
         if (o.kernel == TSQBX_HELMHOLTZ) {
@@ -347,19 +355,20 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     ev.wmu = static_cast<const double *>(slot.d_wmu);
     ev.wmu_f = static_cast<const float *>(slot.d_wmu);
     ev.wmu_c = static_cast<const double2 *>(slot.d_wmu);
-    const bool slp = (o.layers & TSQBX_SLP) != 0, dlp = (o.layers & TSQBX_DLP) != 0;
+    // S' is formed only when the call asks for it (an S' output was given)
+    const unsigned layers = ev.out_sp ? o.layers : (o.layers & ~(unsigned)TSQBX_SP);
     if (timed) ck(cudaEventRecord(P->k_begin, s));
     int rc;
-    if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(p, slp, dlp, P->g, ev, s);
-    else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(p, slp, dlp, P->g, ev, s);
-    else if (o.precision == TSQBX_DF64) rc = launch_laplace_df64(p, slp, dlp, P->g, ev, s);
-    else rc = launch_laplace_fp64(p, slp, dlp, P->g, ev, s);
+    if (o.kernel == TSQBX_HELMHOLTZ) rc = launch_helmholtz_fp64(p, layers, P->g, ev, s);
+    else if (o.precision == TSQBX_MIXED) rc = launch_laplace_mixed(p, layers, P->g, ev, s);
+    else if (o.precision == TSQBX_DF64) rc = launch_laplace_df64(p, layers, P->g, ev, s);
+    else rc = launch_laplace_fp64(p, layers, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
     if (P->g.n_combine > 0) {
         const int64_t th = P->g.n_combine * 32;
         const int cb = (int)std::min<int64_t>((th + 255) / 256, (int64_t)P->n_sm * 8);
-        combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp, ev.part_dlp, ev.out_slp, ev.out_dlp,
-                                          o.kernel == TSQBX_HELMHOLTZ ? 2 : 1);
+        combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp, ev.part_dlp, ev.part_sp, ev.out_slp, ev.out_dlp,
+                                          ev.out_sp, o.kernel == TSQBX_HELMHOLTZ ? 2 : 1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return status_of(e);
     }
@@ -429,6 +438,7 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             cudaGetLastError();
         }
         const bool dlp = (o->layers & TSQBX_DLP) != 0;
+        const bool sp = (o->layers & TSQBX_SP) != 0;
         const bool mixed = o->precision == TSQBX_MIXED;
         const int64_t n_src = G->n_src, n_tgt = G->n_tgt, n_group = G->n_group;
 
@@ -471,8 +481,10 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
 
         // target slot records
         std::vector<double4_32a> slot_c(n_tgt), slot_e(n_tgt);
-        std::vector<float4> slot_chi, slot_clo, slot_ef;
+        std::vector<float4> slot_chi, slot_clo, slot_ef, slot_nf;
+        std::vector<double4_32a> slot_n;
         if (mixed) { slot_chi.resize(n_tgt); slot_clo.resize(n_tgt); slot_ef.resize(n_tgt); }
+        if (sp) { slot_n.resize(n_tgt); if (mixed) slot_nf.resize(n_tgt); }
         const int64_t nc = G->n_ctr;
         for (int64_t i = 0; i < n_tgt; ++i) {
             const int64_t t = slot_tgt[i];
@@ -491,6 +503,12 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
                 slot_chi[i] = make_float4(h[0], h[1], h[2], 0.f);
                 slot_clo[i] = make_float4(l[0], l[1], l[2], 0.f);
                 slot_ef[i] = make_float4((float)e[0], (float)e[1], (float)e[2], (float)rho2);
+            }
+            if (sp) {
+                double nt[3];
+                for (int a = 0; a < 3; ++a) nt[a] = G->tgt_normal[a * n_tgt + t];
+                slot_n[i] = make_double4_32a(nt[0], nt[1], nt[2], 0.0);
+                if (mixed) slot_nf[i] = make_float4((float)nt[0], (float)nt[1], (float)nt[2], 0.f);
             }
         }
         // source records
@@ -529,7 +547,9 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             g.slot_chi = P->upload(slot_chi);
             g.slot_clo = P->upload(slot_clo);
             g.slot_ef = P->upload(slot_ef);
+            if (sp) g.slot_nf = P->upload(slot_nf);
         }
+        if (sp) g.slot_n = P->upload(slot_n);
         g.slot_tgt = P->upload(slot_tgt);
         g.slot_c = P->upload(slot_c);
         g.slot_e = P->upload(slot_e);
@@ -547,10 +567,12 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             s.d_wmu = P->dalloc<char>(P->wmu_bytes);
             if (o->layers & TSQBX_SLP) s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            if (o->layers & TSQBX_SP) s.d_out[2] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             s.d_status = P->dalloc<int>(1);
             s.h_density = P->halloc(P->density_bytes);
             s.h_out[0] = P->halloc(P->out_bytes);
             s.h_out[1] = P->halloc(P->out_bytes);
+            if (o->layers & TSQBX_SP) s.h_out[2] = P->halloc(P->out_bytes);
             s.h_status = static_cast<int *>(P->halloc(sizeof(int)));
         }
         ck(cudaEventCreate(&P->k_begin));
@@ -705,7 +727,7 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
             float acc[64];
             const int reps = std::min(repeats, 64);
             for (int r = -1; r < reps; ++r) {
-                int rc = enqueue(P, slot, d_density, slot.d_out[0], slot.d_out[1], slot.stream, true,
+                int rc = enqueue(P, slot, d_density, slot.d_out[0], slot.d_out[1], slot.d_out[2], slot.stream, true,
                                  P->opt.p, P->opt.k);
                 if (rc) return rc;
                 ck(cudaEventSynchronize(P->k_end));
@@ -775,8 +797,8 @@ bool layer_args_ok(tsqbx_plan P, const void *out_slp, const void *out_dlp)
 
 // Stage inputs, enqueue, and (for host outputs) copy back into pinned
 // staging; records slot.done.  Host outputs are delivered by finish().
-int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *out_dlp, bool timed, int p,
-          double k)
+int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *out_dlp, void *out_sp,
+          bool timed, int p, double k)
 {
     const void *d_density = density;
     if (P->g.n_src && !is_device_ptr(density)) {
@@ -785,9 +807,9 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
                            slot.stream));
         d_density = slot.d_density;
     }
-    void *outs[2] = {out_slp, out_dlp};
-    double *d_outs[2] = {nullptr, nullptr};
-    for (int l = 0; l < 2; ++l) {
+    void *outs[3] = {out_slp, out_dlp, out_sp};
+    double *d_outs[3] = {nullptr, nullptr, nullptr};
+    for (int l = 0; l < 3; ++l) {
         slot.user_out[l] = outs[l];
         slot.copy_out[l] = false;
         if (!outs[l] || !slot.d_out[l]) continue;
@@ -795,9 +817,9 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
         else { d_outs[l] = slot.d_out[l]; slot.copy_out[l] = true; }
     }
     ck(cudaMemsetAsync(slot.d_status, 0, sizeof(int), slot.stream));
-    int rc = enqueue(P, slot, d_density, d_outs[0], d_outs[1], slot.stream, timed, p, k);
+    int rc = enqueue(P, slot, d_density, d_outs[0], d_outs[1], d_outs[2], slot.stream, timed, p, k);
     if (rc) return rc;
-    for (int l = 0; l < 2; ++l)
+    for (int l = 0; l < 3; ++l)
         if (slot.copy_out[l] && P->out_bytes)
             ck(cudaMemcpyAsync(slot.h_out[l], slot.d_out[l], P->out_bytes, cudaMemcpyDeviceToHost,
                                slot.stream));
@@ -808,7 +830,7 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
 
 int finish(tsqbx_plan P, Slot &slot)
 {
-    for (int l = 0; l < 2; ++l)
+    for (int l = 0; l < 3; ++l)
         if (slot.copy_out[l]) std::memcpy(slot.user_out[l], slot.h_out[l], P->out_bytes);
     return *slot.h_status ? TSQBX_E_KERNEL : TSQBX_OK;
 }
@@ -817,7 +839,8 @@ int finish(tsqbx_plan P, Slot &slot)
 
 extern "C" {
 
-int tsqbx_eval_pk(tsqbx_plan P, int p, double k, const void *density, void *out_slp, void *out_dlp)
+int tsqbx_eval_pk(tsqbx_plan P, int p, double k, const void *density, void *out_slp, void *out_dlp,
+                  void *out_sp)
 {
     if (!P || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp) || !pk_ok(P, p, k))
         return TSQBX_E_INVAL;
@@ -825,7 +848,7 @@ int tsqbx_eval_pk(tsqbx_plan P, int p, double k, const void *density, void *out_
         DeviceGuard dg(P->opt.device);
         std::lock_guard<std::mutex> lk(P->mu);
         Slot &slot = P->slots[0];
-        int rc = start(P, slot, density, out_slp, out_dlp, true, p, k);
+        int rc = start(P, slot, density, out_slp, out_dlp, out_sp, true, p, k);
         if (rc) return rc;
         ck(cudaEventSynchronize(slot.done));
         return finish(P, slot);
@@ -840,7 +863,7 @@ int tsqbx_eval_pk(tsqbx_plan P, int p, double k, const void *density, void *out_
 int tsqbx_eval(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp)
 {
     if (!P) return TSQBX_E_INVAL;
-    return tsqbx_eval_pk(P, P->opt.p, P->opt.k, density, out_slp, out_dlp);
+    return tsqbx_eval_pk(P, P->opt.p, P->opt.k, density, out_slp, out_dlp, nullptr);
 }
 
 int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void *d_out_dlp, void *stream)
@@ -851,7 +874,7 @@ int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void 
         Slot &slot = P->slots[0];
         cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : slot.stream;
         return enqueue(P, slot, d_density, static_cast<double *>(d_out_slp), static_cast<double *>(d_out_dlp),
-                       s, true, P->opt.p, P->opt.k);
+                       nullptr, s, true, P->opt.p, P->opt.k);
     } catch (const CudaFail &f) {
         cudaGetLastError();
         return status_of(f.err);
@@ -861,7 +884,7 @@ int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void 
 }
 
 int tsqbx_submit_pk(tsqbx_plan P, int p, double k, const void *density, void *out_slp, void *out_dlp,
-                    uint64_t *ticket)
+                    void *out_sp, uint64_t *ticket)
 {
     if (!P || !ticket || (P->g.n_src && !density) || !layer_args_ok(P, out_slp, out_dlp) || !pk_ok(P, p, k))
         return TSQBX_E_INVAL;
@@ -873,7 +896,7 @@ int tsqbx_submit_pk(tsqbx_plan P, int p, double k, const void *density, void *ou
             if (!P->slots[i].busy) { idx = (int)i; break; }
         if (idx < 0) return TSQBX_E_BUSY;
         Slot &slot = P->slots[idx];
-        int rc = start(P, slot, density, out_slp, out_dlp, false, p, k);
+        int rc = start(P, slot, density, out_slp, out_dlp, out_sp, false, p, k);
         if (rc) return rc;
         slot.busy = true;
         slot.ticket = g_next_ticket.fetch_add(1);
@@ -894,7 +917,7 @@ int tsqbx_submit_pk(tsqbx_plan P, int p, double k, const void *density, void *ou
 int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp, uint64_t *ticket)
 {
     if (!P) return TSQBX_E_INVAL;
-    return tsqbx_submit_pk(P, P->opt.p, P->opt.k, density, out_slp, out_dlp, ticket);
+    return tsqbx_submit_pk(P, P->opt.p, P->opt.k, density, out_slp, out_dlp, nullptr, ticket);
 }
 
 int tsqbx_poll(uint64_t ticket, int timeout_us)

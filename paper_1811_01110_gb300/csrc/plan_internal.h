@@ -73,16 +73,16 @@ struct Slot {
     cudaEvent_t done = nullptr;
     void *d_density = nullptr;     // device copy of a host density
     void *d_wmu = nullptr;         // w mu scratch (f64, f32 or c128)
-    double *d_out[2] = {nullptr, nullptr};
-    double *d_part[2] = {nullptr, nullptr};   // partial sums of sliced items
+    double *d_out[3] = {nullptr, nullptr, nullptr};    // single layer, double layer, S'
+    double *d_part[3] = {nullptr, nullptr, nullptr};   // partial sums of sliced items
     int *d_status = nullptr;
     void *h_density = nullptr;     // pinned staging
-    void *h_out[2] = {nullptr, nullptr};
+    void *h_out[3] = {nullptr, nullptr, nullptr};
     int *h_status = nullptr;
     bool busy = false;
     uint64_t ticket = 0;
-    void *user_out[2] = {nullptr, nullptr};
-    bool copy_out[2] = {false, false};
+    void *user_out[3] = {nullptr, nullptr, nullptr};
+    bool copy_out[3] = {false, false, false};
 };
 
 }  // namespace tsqbx
@@ -146,8 +146,9 @@ namespace tsqbx {
 // partial-sum buffers of every slot (frees what the old schedule used).
 void apply_schedule(tsqbx_plan P, Schedule &&s);
 // Enqueue prep + expansion (+ combine) for one evaluation on stream s, with
-// expansion order p and (Helmholtz) wavenumber k.
-int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp,
+// expansion order p and (Helmholtz) wavenumber k; S' is formed only when the
+// plan's mask has it and d_sp is given.
+int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, double *d_dlp, double *d_sp,
             cudaStream_t s, bool timed, int p, double k);
 
 }  // namespace tsqbx

@@ -38,7 +38,7 @@ double seconds_since(Clock::time_point t0) { return std::chrono::duration<double
 
 // Host copy of a registered geometry.
 struct GeomCopy {
-    std::vector<double> src_xyz, src_weight, src_normal, ctr_xyz, ctr_radius, tgt_xyz;
+    std::vector<double> src_xyz, src_weight, src_normal, ctr_xyz, ctr_radius, tgt_xyz, tgt_normal;
     std::vector<int32_t> tgt_center, ctr_group, range_begin, range_end;
     std::vector<int64_t> group_range_start;
     tsqbx_geometry view{};
@@ -62,7 +62,7 @@ struct Request {
     tsqbx_options opt{};
     PlanKey key;
     std::vector<double> density;
-    void *out_slp = nullptr, *out_dlp = nullptr;
+    void *out_slp = nullptr, *out_dlp = nullptr, *out_sp = nullptr;
     Clock::time_point arrive;
     double latency_s = 0;
     RState state = RState::Queued;
@@ -78,6 +78,7 @@ size_t estimate_bytes(const GeomCopy &g, const tsqbx_options &o)
     const bool helm = o.kernel == TSQBX_HELMHOLTZ, mixed = o.precision == TSQBX_MIXED;
     size_t b = ns * 32 + (size_t)g.list_entries * 4 + nt * (4 + 64) + (size_t)g.view.n_group * 8;
     if (o.layers & TSQBX_DLP) b += ns * 32;
+    if (o.layers & TSQBX_SP) b += nt * 32;
     if (mixed) b += ns * 48 + nt * 48;
     const int slots = (o.n_slots ? o.n_slots : 2) + 1;
     b += (size_t)slots * (ns * (helm ? 32 : 16) + nt * 16 * (helm ? 2 : 1));
@@ -165,7 +166,7 @@ bool tsqbx_server_s::admit(Request *r)
     }
     PlanEntry &pe = it->second;
     const int rc = tsqbx_submit_pk(pe.plan, r->opt.p, r->opt.k, r->density.data(), r->out_slp, r->out_dlp,
-                                   &r->ticket);
+                                   r->out_sp, &r->ticket);
     if (rc == TSQBX_E_BUSY) return false;                      // every slot of the plan busy
     if (rc != TSQBX_OK) {
         r->status = rc;
@@ -282,6 +283,7 @@ int tsqbx_server_add_geometry(tsqbx_server S, const tsqbx_geometry *G, int *geom
         cp(G->ctr_xyz, 3 * G->n_ctr, g->ctr_xyz);
         cp(G->ctr_radius, G->n_ctr, g->ctr_radius);
         cp(G->tgt_xyz, 3 * G->n_tgt, g->tgt_xyz);
+        cp(G->tgt_normal, 3 * G->n_tgt, g->tgt_normal);
         cp(G->tgt_center, G->n_tgt, g->tgt_center);
         cp(G->ctr_group, G->n_ctr, g->ctr_group);
         cp(G->group_range_start, G->n_group + 1, g->group_range_start);
@@ -292,7 +294,8 @@ int tsqbx_server_add_geometry(tsqbx_server S, const tsqbx_geometry *G, int *geom
         g->view = tsqbx_geometry{G->n_src, ptr(g->src_xyz), ptr(g->src_weight), ptr(g->src_normal),
                                  G->n_ctr, ptr(g->ctr_xyz), ptr(g->ctr_radius), G->n_tgt, ptr(g->tgt_xyz),
                                  ptr(g->tgt_center), G->n_group, ptr(g->ctr_group),
-                                 g->group_range_start.data(), ptr(g->range_begin), ptr(g->range_end)};
+                                 g->group_range_start.data(), ptr(g->range_begin), ptr(g->range_end),
+                                 ptr(g->tgt_normal)};
         std::lock_guard<std::mutex> lk(S->mu);
         S->geoms.push_back(std::move(g));
         *geom_id = (int)S->geoms.size() - 1;
@@ -303,7 +306,7 @@ int tsqbx_server_add_geometry(tsqbx_server S, const tsqbx_geometry *G, int *geom
 }
 
 int tsqbx_server_submit(tsqbx_server S, int geom_id, const tsqbx_options *opt, const void *density,
-                        void *out_slp, void *out_dlp, uint64_t *request)
+                        void *out_slp, void *out_dlp, void *out_sp, uint64_t *request)
 {
     if (!S || !opt || !request) return TSQBX_E_INVAL;
     try {
@@ -315,7 +318,8 @@ int tsqbx_server_submit(tsqbx_server S, int geom_id, const tsqbx_options *opt, c
         const int64_t width = opt->kernel == TSQBX_HELMHOLTZ ? 2 : 1;
         if (g.view.n_src && !density) return TSQBX_E_INVAL;
         if (((opt->layers & TSQBX_SLP) && g.view.n_tgt && !out_slp) ||
-            ((opt->layers & TSQBX_DLP) && g.view.n_tgt && !out_dlp))
+            ((opt->layers & TSQBX_DLP) && g.view.n_tgt && !out_dlp) ||
+            ((opt->layers & TSQBX_SP) && g.view.n_tgt && !out_sp))
             return TSQBX_E_INVAL;
         r->id = S->next_id++;
         r->geom = geom_id;
@@ -326,6 +330,7 @@ int tsqbx_server_submit(tsqbx_server S, int geom_id, const tsqbx_options *opt, c
         if (d) r->density.assign(d, d + g.view.n_src * width);
         r->out_slp = out_slp;
         r->out_dlp = out_dlp;
+        r->out_sp = out_sp;
         if (!S->span_started) {
             S->t_first = r->arrive;
             S->span_started = true;

@@ -84,7 +84,29 @@ def test_invalid_options_rejected_on_host(L):
     assert _create(g, p=21) == -1
     assert _create(g, kernel="helmholtz", k=0.0) == -1
     assert _create(g, kernel="helmholtz", k=1.0, precision="mixed") == -9
-    assert _create(g, kernel="helmholtz", k=1.0, layers=("dlp",)) == -9
     assert _create(g, lanes_per_target=33) == -1
     g.src_normal = None
     assert _create(g, layers=("slp", "dlp")) == -1
+    assert _create(g, kernel="helmholtz", k=1.0, layers=("dlp",)) == -1
+
+
+def test_sp_needs_finite_target_normals(L):
+    g = _tiny()
+    g.tgt_normal = None
+    assert _create(g, layers=("slp", "sp")) == -1
+    assert _create(g, kernel="helmholtz", k=1.0, layers=("sp",)) == -1
+    g = _tiny()
+    g.tgt_normal[1, 0] = np.inf
+    assert _create(g, layers=("sp",)) == -1
+
+
+def test_unknown_layer_bits_rejected(L):
+    import paper_1811_01110_gb300 as pkg
+    from paper_1811_01110_gb300 import _lib
+    g = _tiny()
+    geo, keep = pkg.marshal_geometry(g)
+    for mask in (0, 8, 1 | 16):
+        opt = pkg.make_options()
+        opt.layers = mask
+        h = ctypes.c_void_p()
+        assert L.tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)) == _lib.TSQBX_E_INVAL
