@@ -40,23 +40,44 @@ PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
-def flops_per_pair(p, precision, dlp=True):
+def flops_per_pair(p, precision, dlp=True, sp=False):
     """Algorithmic flops per (target, source) pair (FMA = 2) of the Laplace
-    kernels: geometry 19 (d, R^2, 1/R, qx, q2), per recurrence step n = 1..p-1
-    6 for the single layer (+4 for the double layer), closing 3 (+29 for the
-    double layer); mixed precision adds 6 for the float-float difference and 4
-    per layer for the Kahan update."""
-    f = 19 + (10 if dlp else 6) * max(p - 1, 0) + (32 if dlp else 3)
+    kernels.  Single layer alone: geometry 19 (d, R^2, 1/R, qx, q2), 6 per
+    Bonnet step n = 1..p-1, closing 3.  With the double layer or S' (one
+    recurrence for Q'_n): geometry 20, 6 per step n = 1..p-1, the top step
+    and sums 7, sum Q_n from the closing identity 7, accumulation 2; the
+    double layer adds 21 (two normal dots, sum (n+1) Q_n, the combination and
+    its accumulation), S' 10 (one dot, the combination, accumulation; +1 for
+    1/R^3 without the double layer).  Mixed precision adds 6 for the
+    float-float difference and 4 per layer for the Kahan update."""
+    if not dlp and not sp:
+        f = 19 + 6 * max(p - 1, 0) + 3
+    else:
+        f = 20 + 6 * max(p - 1, 0) + 16
+        if dlp:
+            f += 21
+        if sp:
+            f += 10 + (0 if dlp else 1)
     if precision == "mixed":
-        f += 6 + (8 if dlp else 4)
+        f += 6 + 4 * (1 + int(dlp) + int(sp))
     return f
 
 
-def helmholtz_flops_per_pair(p):
-    """Helmholtz single layer (FP64): geometry and 1/z 20, 13 per order
-    (Hankel factor 5, Legendre 3, complex accumulation 5), closing with e^{iz}
-    and the complex weight 16, sincos counted as 2."""
-    return 20 + 13 * max(p - 1, 0) + 16 + 2 + 12
+def helmholtz_flops_per_pair(p, dlp=False, sp=False):
+    """Helmholtz kernel (FP64): geometry and 1/z 20, 13 per order for the
+    single layer (Hankel factor 5, Legendre 3, complex accumulation 5),
+    closing with e^{iz} and the complex weight 16, sincos counted as 2, orders
+    0 and 1 12.  The double layer adds 18 per order (h_n' factor and its
+    complex sum 9, the differentiated Legendre recurrence and its sum 9) and
+    about 50 of closing (two normal dots, the combination, a second e^{iz}
+    product and weight); S' adds 5 per order (14 without the double layer,
+    whose Legendre-derivative sum it shares) and about 42 of closing."""
+    f = 20 + 13 * max(p - 1, 0) + 16 + 2 + 12
+    if dlp:
+        f += 18 * max(p - 1, 0) + 50
+    if sp:
+        f += (5 if dlp else 14) * max(p - 1, 0) + 42
+    return f
 
 
 def parse():
@@ -313,22 +334,50 @@ def leg_batched(pkg, torch, dev, steps, warmup, flush):
 
 def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
     """Torus 444 x 166 quads (884,448 sources, 1,768,896 targets), octree
-    lists, Helmholtz single layer k = 10, p = 12, FP64, plane-wave density."""
+    lists, Helmholtz k = 10, p = 12, FP64, plane-wave density: the single
+    layer alone, single + double layer (the combined-field operator's
+    parts, one pass), and all three layers with S'."""
     from tsqbx_inputs import configs
     g, mu, _ = configs.torus_helmholtz()
-    plan = pkg.Plan(g, "helmholtz", ("slp",), p=12, k=10.0, device=dev.index)
-    info = plan.info()
     dmu = torch.from_numpy(mu).to(dev)
-    out = {"slp": torch.empty(g.n_tgt, dtype=torch.complex128, device=dev)}
     stream = torch.cuda.Stream(device=dev)
-    step_ms, kern_ms = time_device(plan, dmu, out, stream, steps, warmup, flush, lambda: None)
-    t = sum(kern_ms) / 1e3 / steps
     res = {"workload": "torus 444x166 quads, 884448 sources, 1768896 targets, octree lists, "
-                       "Helmholtz SLP k=10 p=12", "n_pairs": info["n_pairs"],
-           "value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps), "unit": UNIT, "dtype": "f64",
-           "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
-           "roofline": roofline(helmholtz_flops_per_pair(12) * info["n_pairs"], t, "fp64")}
-    plan.close()
+                       "Helmholtz k=10 p=12", "unit": UNIT, "dtype": "f64"}
+    for name, layers in (("slp", ("slp",)), ("slp+dlp", ("slp", "dlp")), ("slp+dlp+sp", ("slp", "dlp", "sp"))):
+        plan = pkg.Plan(g, "helmholtz", layers, p=12, k=10.0, device=dev.index)
+        info = plan.info()
+        out = {l: torch.empty(g.n_tgt, dtype=torch.complex128, device=dev) for l in layers}
+        step_ms, kern_ms = time_device(plan, dmu, out, stream, steps, warmup, flush, lambda: None)
+        t = sum(kern_ms) / 1e3 / steps
+        fl = helmholtz_flops_per_pair(12, "dlp" in layers, "sp" in layers)
+        res["n_pairs"] = info["n_pairs"]
+        res[name] = {"value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps),
+                     "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
+                     "roofline": dict(roofline(fl * info["n_pairs"], t, "fp64"), flops_per_pair=fl)}
+        plan.close()
+    res["value"] = res["slp"]["value"]
+    return res
+
+
+def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush):
+    """The benchmark torus with S' added: Laplace single + double layer + S'
+    (target-normal derivative) in one pass, p = 9, in every precision."""
+    dmu = torch.from_numpy(mu).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    layers = ("slp", "dlp", "sp")
+    res = {"workload": WORKLOAD.replace("SLP+DLP", "SLP+DLP+S'"), "unit": UNIT}
+    for prec in ("fp64", "mixed", "df64"):
+        plan = pkg.Plan(g, "laplace", layers, p=P, precision=prec, device=dev.index)
+        info = plan.info()
+        out = {l: torch.empty(g.n_tgt, dtype=torch.float64, device=dev) for l in layers}
+        step_ms, kern_ms = time_device(plan, dmu, out, stream, steps, warmup, flush, lambda: None)
+        t = sum(kern_ms) / 1e3 / steps
+        fprec = "fp64" if prec == "df64" else prec
+        fl = flops_per_pair(P, fprec, dlp=True, sp=True)
+        res[prec] = {"value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps),
+                     "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
+                     "roofline": dict(roofline(fl * info["n_pairs"], t, fprec), flops_per_pair=fl)}
+        plan.close()
     return res
 
 
@@ -511,6 +560,8 @@ def main():
     if not args.no_extras and rank == 0:
         for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere)):
             extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush)
+        extras["target_derivative"] = leg_target_derivative(pkg, torch, dev, g, mu, max(3, args.steps // 2),
+                                                            args.warmup, flush)
         extras["serving"] = leg_serving(pkg)
 
     if rank != 0:

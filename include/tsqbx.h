@@ -208,6 +208,11 @@ TSQBX_API int tsqbx_submit_pk(tsqbx_plan plan, int p, double k, const void *dens
  * be ordered on one stream.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_eval_async(tsqbx_plan plan, const void *d_density, void *d_out_slp, void *d_out_dlp,
                      void *stream);
+/* tsqbx_eval_async with the order p and wavenumber k chosen per call (as in
+ * tsqbx_eval_pk) and an S' output (DEVICE pointer, may be NULL: S' is then
+ * not formed).  Errors as tsqbx_eval_async. */
+TSQBX_API int tsqbx_eval_async_pk(tsqbx_plan plan, int p, double k, const void *d_density, void *d_out_slp,
+                                  void *d_out_dlp, void *d_out_sp, void *stream);
 
 /* Submit an evaluation and return at once with a ticket.  Pointers as for
  * tsqbx_eval; host density is copied before return, host outputs are written

@@ -205,16 +205,22 @@ class Plan:
             check(lib().tsqbx_eval_pk(self._h, pp, kk, d, a_slp, a_dlp, a_sp), "tsqbx_eval_pk")
         return outs
 
-    def eval_async(self, density, out, stream=None):
-        """Enqueue on a CUDA stream (tsqbx_eval_async); device tensors only;
-        single and double layers only (an "sp" entry of out is not written).
+    def eval_async(self, density, out, stream=None, p=None, k=None):
+        """Enqueue on a CUDA stream (tsqbx_eval_async; tsqbx_eval_async_pk
+        when p or k is given or out has an "sp" entry); device tensors only.
         stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
         handle = None
         if stream is not None:
             handle = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-        a_slp, a_dlp, _ = self._out_addrs(out)
-        check(lib().tsqbx_eval_async(self._h, self._density_addr(density), a_slp, a_dlp, handle),
-              "tsqbx_eval_async")
+        a_slp, a_dlp, a_sp = self._out_addrs(out)
+        d = self._density_addr(density)
+        if p is None and k is None and a_sp is None:
+            check(lib().tsqbx_eval_async(self._h, d, a_slp, a_dlp, handle), "tsqbx_eval_async")
+        else:
+            pp = self.p if p is None else int(p)
+            kk = self.k if k is None else float(k)
+            check(lib().tsqbx_eval_async_pk(self._h, pp, kk, d, a_slp, a_dlp, a_sp, handle),
+                  "tsqbx_eval_async_pk")
         return out
 
     def submit(self, density, out=None):

@@ -90,4 +90,21 @@ __host__ __device__ constexpr double rec_beta(int n)
     return (1.0 * n * n) / ((2.0 * n + 1.0) * (2.0 * n - 1.0));
 }
 
+// The same for the derivatives alone.  With Q'_n = (rho/R)^{n-1} P_n'(x), the
+// Legendre identities P'_{n+1} - x P'_n = (n+1) P_n and P'_{n+1} - P'_{n-1} =
+// (2n+1) P_n give n Q'_{n+1} = (2n+1) qx Q'_n - (n+1) q2 Q'_{n-1} (the
+// Gegenbauer C^(3/2) recurrence); scaled, Q'_n = lambda_n U_n,
+//   U_{n+1} = qx U_n - gamma_n q2 U_{n-1},  U_0 = 0, U_1 = 1,
+// lambda_{n+1} = lambda_n (2n+1)/n, lambda_1 = 1, gamma_n = (n^2-1)/(4n^2-1).
+__host__ __device__ constexpr double rec_lambda(int n)
+{
+    double l = 1.0;
+    for (int m = 1; m < n; ++m) l *= (2.0 * m + 1.0) / m;
+    return l;
+}
+__host__ __device__ constexpr double rec_gamma(int n)
+{
+    return (1.0 * n * n - 1.0) / (4.0 * n * n - 1.0);
+}
+
 }  // namespace tsqbx

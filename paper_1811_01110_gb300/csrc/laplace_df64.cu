@@ -1,11 +1,10 @@
 // laplace_df64.cu -- Laplace TSQBX kernels with FP64-class accuracy computed
 // in double-float arithmetic (dfloat.cuh) on the FP32 pipes.
 //
-// Same expansion and warp mapping as laplace_fp64.cu (Appendix A; scaled
-// Bonnet recurrence T_{n+1} = qx T_n - beta_n q2 T_{n-1}, Q_n = kappa_n T_n;
-// double layer through Q'_{n+1} = q2 Q'_{n-1} + (2n+1) Q_n; S' through the
-// recurrence differentiated along n_t), every quantity a
-// double-float.  Geometry: each item picks a reference point (its first
+// Same expansion, recurrences and warp mapping as laplace_fp64.cu (Appendix
+// A; the scaled Bonnet recurrence for the single layer alone, the Q'-only
+// recurrence with its closing sums when the double layer or S' is formed),
+// every quantity a double-float.  Geometry: each item picks a reference point (its first
 // target's center) and forms s - ref and c - ref in FP64 before splitting
 // them into double-floats, so d = s - c keeps ~48 significant bits relative
 // to |d| itself.  The recurrence constants are exact double-float splits of

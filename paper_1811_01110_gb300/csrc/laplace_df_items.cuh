@@ -25,57 +25,62 @@ __device__ __forceinline__ df df_dot(const df3 &a, const df3 &b)
     return df_add(df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_mul(a.z, b.z));
 }
 
-// One pair; tn = n_t and f2 = 2 e.n_t (S' only).
+// One pair; tn = n_t and en = e.n_t (S' only).  Same two recurrences and
+// closing sums as pair_fp64 (laplace_items.cuh), in double-float.
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df wm, const df3 &n, const df3 &tn,
-                                        df f2, df &acc_s, df &acc_d, df &acc_p)
+                                        df en, df &acc_s, df &acc_d, df &acc_p)
 {
     const df R2 = df_dot(d, d);
     const df rinv = df_rsqrt(R2);
     const df r2inv = df_mul(rinv, rinv);
     const df qx = df_mul(df_dot(d, e), r2inv);
     const df q2 = df_mul(rho2, r2inv);
-    const df zero{0.f, 0.f};
-    const df qxp = SP ? df_mul(df_dot(d, tn), r2inv) : zero;
-    const df q2p = SP ? df_mul(f2, r2inv) : zero;
-    df S0{1.f, 0.f}, S2{0.f, 0.f}, S3{0.f, 0.f};
-    df Tm{1.f, 0.f}, Tc{1.f, 0.f}, Dm{0.f, 0.f}, Dc{0.f, 0.f}, Pm{0.f, 0.f}, Pc{0.f, 0.f};
-    if (P >= 1) {
-        S0 = df_add(S0, qx); S2 = df{1.f, 0.f}; Tc = qx; Dc = df{1.f, 0.f};
-        Pc = qxp; S3 = qxp;
-    }
+    const df wr = df_mul(wm, rinv);
+    const df one{1.f, 0.f};
+    if constexpr (!DLP && !SP) {
+        df S0 = one, Tm = one, Tc = one;
+        if (P >= 1) { S0 = df_add(S0, qx); Tc = qx; }
 #pragma unroll
-    for (int n = 1; n < P; ++n) {
-        const df beta = df_of(df_const(rec_beta(n)));
-        const df kap = df_of(df_const(rec_kappa(n + 1)));
-        const df bq = df_mul(beta, q2);
-        const df Tn = df_sub(df_mul(qx, Tc), df_mul(bq, Tm));
-        S0 = df_add(S0, df_mul(kap, Tn));
+        for (int n = 1; n < P; ++n) {
+            const df bq = df_mul(df_of(df_const(rec_beta(n))), q2);
+            const df Tn = df_sub(df_mul(qx, Tc), df_mul(bq, Tm));
+            S0 = df_add(S0, df_mul(df_of(df_const(rec_kappa(n + 1))), Tn));
+            Tm = Tc; Tc = Tn;
+        }
+        acc_s = df_add(acc_s, df_mul(wr, S0));
+    } else {
+        df Um{0.f, 0.f}, Uc = one, S2m{0.f, 0.f};
+#pragma unroll
+        for (int n = 1; n < P; ++n) {
+            S2m = df_add(S2m, df_mul(df_of(df_const(rec_lambda(n))), Uc));
+            const df gq = df_mul(df_of(df_const(rec_gamma(n))), q2);
+            const df Un = df_sub(df_mul(qx, Uc), df_mul(gq, Um));
+            Um = Uc; Uc = Un;
+        }
+        df Qp{0.f, 0.f}, Qp1 = one;
+        if (P >= 1) {
+            Qp = df_mul(df_of(df_const(rec_lambda(P))), Uc);
+            const df gq = df_mul(df_of(df_const(rec_gamma(P))), q2);
+            Qp1 = df_mul(df_of(df_const(rec_lambda(P + 1))), df_sub(df_mul(qx, Uc), df_mul(gq, Um)));
+        }
+        const df S2 = df_add(S2m, Qp);
+        // S = (1 - 2 qx + q2) S2 + Q'_{p+1} - q2 Q'_p
+        const df c1 = df_add(df_sub(one, df_mul_f(qx, 2.f)), q2);
+        const df S = df_add(df_mul(c1, S2), df_sub(Qp1, df_mul(q2, Qp)));
+        acc_s = df_add(acc_s, df_mul(wr, S));
+        const df wr3 = df_mul(wr, r2inv);
         if (DLP) {
-            const df Dn = df_add(df_mul(q2, Dm), df_mul(df_of(df_const((2.0 * n + 1.0) * rec_kappa(n))), Tc));
-            S2 = df_add(S2, Dn);
-            Dm = Dc; Dc = Dn;
+            const df S1 = df_add(df_mul(df_sub(one, qx), S2), Qp1);
+            const df a = df_dot(d, n);
+            const df b = df_dot(e, n);
+            const df val = df_sub(df_mul(df_sub(b, df_mul(a, qx)), S2), df_mul(a, S1));
+            acc_d = df_add(acc_d, df_mul(wr3, val));
         }
         if (SP) {
-            // T'_{n+1} = qx' T_n + qx T'_n - beta_n (q2' T_{n-1} + q2 T'_{n-1})
-            const df u = df_add(df_mul(q2p, Tm), df_mul(q2, Pm));
-            const df Pn = df_sub(df_add(df_mul(qxp, Tc), df_mul(qx, Pc)), df_mul(beta, u));
-            S3 = df_add(S3, df_mul(kap, Pn));
-            Pm = Pc; Pc = Pn;
+            const df dn = df_dot(d, tn);
+            acc_p = df_add(acc_p, df_mul(wr3, df_sub(df_mul(dn, S2), df_mul(en, S2m))));
         }
-        Tm = Tc; Tc = Tn;
-    }
-    const df wr = df_mul(wm, rinv);
-    acc_s = df_add(acc_s, df_mul(wr, S0));
-    if (SP) acc_p = df_add(acc_p, df_mul(wr, S3));
-    if (DLP) {
-        const df Dp1 = df_add(df_mul(q2, Dm), df_mul(df_of(df_const((2.0 * P + 1.0) * rec_kappa(P))), Tc));
-        // S1 = sum (n+1) Q_n = ((1 - q2) S2 + Q'_{p+1} + q2 Q'_p + S0) / 2
-        const df S1 = df_mul_f(df_add(df_add(df_sub(S2, df_mul(q2, S2)), Dp1), df_add(df_mul(q2, Dc), S0)), 0.5f);
-        const df a = df_dot(d, n);
-        const df b = df_dot(e, n);
-        const df val = df_sub(df_mul(df_sub(b, df_mul(a, qx)), S2), df_mul(a, S1));
-        acc_d = df_add(acc_d, df_mul(df_mul(wm, df_mul(rinv, r2inv)), val));
     }
 }
 
@@ -95,12 +100,12 @@ __device__ __forceinline__ void write_df_result(const DevGeom &g, const DevEval 
     }
 }
 
-// Per-target target normal and f2 = 2 e.n_t, both as double-floats.
-__device__ __forceinline__ void df_target_normal(const DevGeom &g, int slot, const double4_32a &e4, df3 &tn, df &f2)
+// Per-target target normal and e.n_t, both as double-floats.
+__device__ __forceinline__ void df_target_normal(const DevGeom &g, int slot, const double4_32a &e4, df3 &tn, df &en)
 {
     const double4_32a n = g.slot_n[slot];
     tn = df3_from(n.x, n.y, n.z);
-    f2 = df_from_double(2.0 * fma(e4.x, n.x, fma(e4.y, n.y, e4.z * n.z)));
+    en = df_from_double(fma(e4.x, n.x, fma(e4.y, n.y, e4.z * n.z)));
 }
 
 template <int P, bool DLP, bool SP>
@@ -117,8 +122,8 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
         const df3 e = df3_from(e4.x, e4.y, e4.z);
         const df rho2 = df_from_double(e4.w);
         df3 tn = zero3;
-        df f2{0.f, 0.f};
-        if (SP) df_target_normal(g, it.slot_begin, e4, tn, f2);
+        df ent{0.f, 0.f};
+        if (SP) df_target_normal(g, it.slot_begin, e4, tn, ent);
 #pragma unroll 1
         for (int k = it.src_lo + lane; k < src_hi; k += 32) {
             int s = g.grp_src[s0 + k];
@@ -129,7 +134,7 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
             const df3 d = df3_from(pw.x - c.x, pw.y - c.y, pw.z - c.z);
             df3 n = zero3;
             if (DLP) { const double4_32a nn = g.src_n[s]; n = df3_from(nn.x, nn.y, nn.z); }
-            pair_df<P, DLP, SP>(d, e, rho2, df_from_double(wmd), n, tn, f2, acc_s, acc_d, acc_p);
+            pair_df<P, DLP, SP>(d, e, rho2, df_from_double(wmd), n, tn, ent, acc_s, acc_d, acc_p);
         }
         double vs = df_to_double(acc_s), vd = df_to_double(acc_d), vp = df_to_double(acc_p);
 #pragma unroll
@@ -146,14 +151,14 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
     const bool active = j < it.n_tgt;
     const double4_32a ref = g.slot_c[it.slot_begin];      // item reference point
     df3 crel = zero3, e = zero3, tn = zero3;
-    df rho2{0.f, 0.f}, f2{0.f, 0.f};
+    df rho2{0.f, 0.f}, ent{0.f, 0.f};
     if (active) {
         const double4_32a c = g.slot_c[it.slot_begin + j];
         const double4_32a e4 = g.slot_e[it.slot_begin + j];
         crel = df3_from(c.x - ref.x, c.y - ref.y, c.z - ref.z);
         e = df3_from(e4.x, e4.y, e4.z);
         rho2 = df_from_double(e4.w);
-        if (SP) df_target_normal(g, it.slot_begin + j, e4, tn, f2);
+        if (SP) df_target_normal(g, it.slot_begin + j, e4, tn, ent);
     }
     for (int base = it.src_lo; base < src_hi; base += kTile) {
         const int cnt = min(kTile, src_hi - base);
@@ -185,7 +190,7 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
                     const float4 c = T[2][k], h = T[3][k];
                     n = df3{{c.x, h.x}, {c.y, h.y}, {c.z, h.z}};
                 }
-                pair_df<P, DLP, SP>(d, e, rho2, df{a.w, b.w}, n, tn, f2, acc_s, acc_d, acc_p);
+                pair_df<P, DLP, SP>(d, e, rho2, df{a.w, b.w}, n, tn, ent, acc_s, acc_d, acc_p);
             }
         }
         __syncwarp();

@@ -25,15 +25,30 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
     s = t;
 }
 
-// One (target, source) pair in FP64: d = s - c, e = t - c, wm = w mu, n = n_s.
-// S' (target-normal derivative): the recurrence differentiated along n_t,
-// T'_{n+1} = qx' T_n + qx T'_n - beta_n (q2' T_{n-1} + q2 T'_{n-1}) with
-// qx' = (d.n_t)/R^2 and q2' = 2 (e.n_t)/R^2 (f2 = 2 e.n_t, per target), so
-// n_t.grad_t G^(p) = (1/4pi)(1/R) sum kappa_n T'_n -- no division by rho.
+// One (target, source) pair in FP64: d = s - c, e = t - c, wm = w mu, n = n_s,
+// t = n_t and ent = e.n_t (S').
+//
+// Single layer alone: T_{n+1} = qx T_n - beta_n q2 T_{n-1}, S = sum kappa_n T_n
+// (three operations per order plus the sum).
+//
+// With the double layer or S': everything follows from the derivatives
+// Q'_n = (rho/R)^{n-1} P_n'(x) alone (rec_lambda / rec_gamma recurrence, three
+// operations per order plus one sum).  With S2 = sum_{n<=p} Q'_n and
+// S2m = sum_{n<p} Q'_n, summing P'_{n+1} - x P'_n = (n+1) P_n and
+// P'_{n+1} - P'_{n-1} = (2n+1) P_n over n <= p gives
+//   S  = sum Q_n       = (1 - 2 qx + q2) S2 + Q'_{p+1} - q2 Q'_p,
+//   S1 = sum (n+1) Q_n = (1 - qx) S2 + Q'_{p+1},
+// and since dQ_n/dqx = Q'_n and 2 dQ_n/dq2 = -Q'_{n-1} (the identity
+// x P'_n - P'_{n-1} = n P_n), with grad_s qx = (e - 2 qx d)/R^2,
+// grad_s q2 = -2 q2 d/R^2, grad_t qx = d/R^2 and grad_t q2 = 2 e/R^2:
+//   double layer  n_s.grad_s (S/R) = (1/R^3) [ -a S1 + (b - a qx) S2 ],
+//   S'            n_t.grad_t (S/R) = (1/R^3) [ (d.n_t) S2 - (e.n_t) S2m ],
+// a = d.n_s, b = e.n_s.  The closing sums cancel at most by a factor of a few
+// hundred over rho/R <= 0.9, orders 0..20, a cost of ~2e-14 in FP64.
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, double ex, double ey, double ez,
                                           double rho2, double wm, double nx, double ny, double nz,
-                                          double tx, double ty, double tz, double f2,
+                                          double tx, double ty, double tz, double ent,
                                           double &acc_s, double &acc_d, double &acc_p)
 {
     const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
@@ -41,43 +56,50 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
     const double r2inv = rinv * rinv;
     const double qx = fma(dx, ex, fma(dy, ey, dz * ez)) * r2inv;
     const double q2 = rho2 * r2inv;
-    const double qxp = SP ? fma(dx, tx, fma(dy, ty, dz * tz)) * r2inv : 0.0;
-    const double q2p = SP ? f2 * r2inv : 0.0;
-    // n = 0 (and n = 1 when P >= 1); T_{n-1}, T_n, Q'_{n-1}, Q'_n, T'_{n-1}, T'_n
-    double S0 = 1.0, S2 = 0.0, S3 = 0.0;
-    double Tm = 1.0, Tc = 1.0, Dm = 0.0, Dc = 0.0, Pm = 0.0, Pc = 0.0;
-    if (P >= 1) { S0 += qx; S2 = 1.0; Tc = qx; Dc = 1.0; Pc = qxp; S3 = qxp; }
+    const double wr = wm * rinv;
+    if constexpr (!DLP && !SP) {
+        double S0 = 1.0, Tm = 1.0, Tc = 1.0;
+        if (P >= 1) { S0 += qx; Tc = qx; }
 #pragma unroll
-    for (int n = 1; n < P; ++n) {
-        const double Tn = fma(qx, Tc, -(rec_beta(n) * q2) * Tm);
-        S0 = fma(rec_kappa(n + 1), Tn, S0);
+        for (int n = 1; n < P; ++n) {
+            const double Tn = fma(qx, Tc, -(rec_beta(n) * q2) * Tm);
+            S0 = fma(rec_kappa(n + 1), Tn, S0);
+            Tm = Tc; Tc = Tn;
+        }
+        acc_s = fma(wr, S0, acc_s);
+    } else {
+        // U_{n-1}, U_n starting at n = 1; S2m accumulates Q'_1..Q'_{P-1}
+        double Um = 0.0, Uc = 1.0, S2m = 0.0;
+#pragma unroll
+        for (int n = 1; n < P; ++n) {
+            S2m = fma(rec_lambda(n), Uc, S2m);
+            const double Un = fma(qx, Uc, -(rec_gamma(n) * q2) * Um);
+            Um = Uc; Uc = Un;
+        }
+        // Uc = U_P, Um = U_{P-1} (P >= 1);  P = 0: Q'_0 = 0, Q'_1 = 1
+        const double Qp = P >= 1 ? rec_lambda(P) * Uc : 0.0;
+        const double Qp1 = P >= 1 ? rec_lambda(P + 1) * fma(qx, Uc, -(rec_gamma(P) * q2) * Um) : 1.0;
+        const double S2 = S2m + Qp;
+        const double S = fma(fma(-2.0, qx, 1.0) + q2, S2, fma(-q2, Qp, Qp1));
+        acc_s = fma(wr, S, acc_s);
+        const double wr3 = wr * r2inv;
         if (DLP) {
-            const double Dn = fma(q2, Dm, ((2.0 * n + 1.0) * rec_kappa(n)) * Tc);
-            S2 += Dn;
-            Dm = Dc; Dc = Dn;
+            const double S1 = fma(1.0 - qx, S2, Qp1);
+            const double a = fma(dx, nx, fma(dy, ny, dz * nz));
+            const double b = fma(ex, nx, fma(ey, ny, ez * nz));
+            acc_d = fma(wr3, fma(-a, S1, fma(-a, qx, b) * S2), acc_d);
         }
         if (SP) {
-            const double Pn = fma(qxp, Tc, fma(qx, Pc, -rec_beta(n) * fma(q2p, Tm, q2 * Pm)));
-            S3 = fma(rec_kappa(n + 1), Pn, S3);
-            Pm = Pc; Pc = Pn;
+            const double dn = fma(dx, tx, fma(dy, ty, dz * tz));
+            acc_p = fma(wr3, fma(dn, S2, -ent * S2m), acc_p);
         }
-        Tm = Tc; Tc = Tn;
-    }
-    acc_s = fma(wm * rinv, S0, acc_s);
-    if (SP) acc_p = fma(wm * rinv, S3, acc_p);
-    if (DLP) {
-        const double Dp1 = fma(q2, Dm, ((2.0 * P + 1.0) * rec_kappa(P)) * Tc);
-        const double S1 = 0.5 * (fma(-q2, S2, S2) + Dp1 + fma(q2, Dc, S0));
-        const double a = fma(dx, nx, fma(dy, ny, dz * nz));
-        const double b = fma(ex, nx, fma(ey, ny, ez * nz));
-        const double val = fma(-a, S1, fma(-a, qx, b) * S2);
-        acc_d = fma(wm * rinv * r2inv, val, acc_d);
     }
 }
 
 // One pair in mixed precision: h/l = source hi/lo (h.w = w mu), ch/cl = center
-// hi/lo, e = {t - c, rho^2}, nn = n_s, tn = {n_t, 2 e.n_t}; Kahan-compensated
-// FP32 sums (as/ac single layer, ds/dc double layer, ps/pc S').
+// hi/lo, e = {t - c, rho^2}, nn = n_s, tn = {n_t, e.n_t}; Kahan-compensated
+// FP32 sums (as/ac single layer, ds/dc double layer, ps/pc S').  Same two
+// recurrences and closing sums as pair_fp64, in FP32.
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, const float4 &ch, const float4 &cl,
                                            const float4 &e, const float4 &nn, const float4 &tn, float &as,
@@ -91,36 +113,41 @@ __device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, con
     const float r2inv = rinv * rinv;
     const float qx = fmaf(dx, e.x, fmaf(dy, e.y, dz * e.z)) * r2inv;
     const float q2 = e.w * r2inv;
-    const float qxp = SP ? fmaf(dx, tn.x, fmaf(dy, tn.y, dz * tn.z)) * r2inv : 0.f;
-    const float q2p = SP ? tn.w * r2inv : 0.f;
-    float S0 = 1.f, S2 = 0.f, S3 = 0.f;
-    float Tm = 1.f, Tc = 1.f, Dm = 0.f, Dc = 0.f, Pm = 0.f, Pc = 0.f;
-    if (P >= 1) { S0 += qx; S2 = 1.f; Tc = qx; Dc = 1.f; Pc = qxp; S3 = qxp; }
+    const float wr = h.w * rinv;
+    if constexpr (!DLP && !SP) {
+        float S0 = 1.f, Tm = 1.f, Tc = 1.f;
+        if (P >= 1) { S0 += qx; Tc = qx; }
 #pragma unroll
-    for (int n = 1; n < P; ++n) {
-        const float Tn = fmaf(qx, Tc, -((float)rec_beta(n) * q2) * Tm);
-        S0 = fmaf((float)rec_kappa(n + 1), Tn, S0);
+        for (int n = 1; n < P; ++n) {
+            const float Tn = fmaf(qx, Tc, -((float)rec_beta(n) * q2) * Tm);
+            S0 = fmaf((float)rec_kappa(n + 1), Tn, S0);
+            Tm = Tc; Tc = Tn;
+        }
+        kahan_add(as, ac, wr * S0);
+    } else {
+        float Um = 0.f, Uc = 1.f, S2m = 0.f;
+#pragma unroll
+        for (int n = 1; n < P; ++n) {
+            S2m = fmaf((float)rec_lambda(n), Uc, S2m);
+            const float Un = fmaf(qx, Uc, -((float)rec_gamma(n) * q2) * Um);
+            Um = Uc; Uc = Un;
+        }
+        const float Qp = P >= 1 ? (float)rec_lambda(P) * Uc : 0.f;
+        const float Qp1 = P >= 1 ? (float)rec_lambda(P + 1) * fmaf(qx, Uc, -((float)rec_gamma(P) * q2) * Um) : 1.f;
+        const float S2 = S2m + Qp;
+        const float S = fmaf(fmaf(-2.f, qx, 1.f) + q2, S2, fmaf(-q2, Qp, Qp1));
+        kahan_add(as, ac, wr * S);
+        const float wr3 = wr * r2inv;
         if (DLP) {
-            const float Dn = fmaf(q2, Dm, (float)((2.0 * n + 1.0) * rec_kappa(n)) * Tc);
-            S2 += Dn;
-            Dm = Dc; Dc = Dn;
+            const float S1 = fmaf(1.f - qx, S2, Qp1);
+            const float a = fmaf(dx, nn.x, fmaf(dy, nn.y, dz * nn.z));
+            const float b = fmaf(e.x, nn.x, fmaf(e.y, nn.y, e.z * nn.z));
+            kahan_add(ds, dc, wr3 * fmaf(-a, S1, fmaf(-a, qx, b) * S2));
         }
         if (SP) {
-            const float Pn = fmaf(qxp, Tc, fmaf(qx, Pc, -(float)rec_beta(n) * fmaf(q2p, Tm, q2 * Pm)));
-            S3 = fmaf((float)rec_kappa(n + 1), Pn, S3);
-            Pm = Pc; Pc = Pn;
+            const float dn = fmaf(dx, tn.x, fmaf(dy, tn.y, dz * tn.z));
+            kahan_add(ps, pc, wr3 * fmaf(dn, S2, -tn.w * S2m));
         }
-        Tm = Tc; Tc = Tn;
-    }
-    kahan_add(as, ac, h.w * rinv * S0);
-    if (SP) kahan_add(ps, pc, h.w * rinv * S3);
-    if (DLP) {
-        const float Dp1 = fmaf(q2, Dm, (float)((2.0 * P + 1.0) * rec_kappa(P)) * Tc);
-        const float S1 = 0.5f * (fmaf(-q2, S2, S2) + Dp1 + fmaf(q2, Dc, S0));
-        const float a = fmaf(dx, nn.x, fmaf(dy, nn.y, dz * nn.z));
-        const float b = fmaf(e.x, nn.x, fmaf(e.y, nn.y, e.z * nn.z));
-        const float val = fmaf(-a, S1, fmaf(-a, qx, b) * S2);
-        kahan_add(ds, dc, h.w * rinv * r2inv * val);
     }
 }
 
@@ -169,11 +196,11 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
     if (it.n_tgt == 1) {                                   // direct loads, all 32 lanes
         const double4_32a c = g.slot_c[it.slot_begin];
         const double4_32a e = g.slot_e[it.slot_begin];
-        double tx = 0, ty = 0, tz = 0, f2 = 0;
+        double tx = 0, ty = 0, tz = 0, ent = 0;
         if (SP) {
             const double4_32a tn = g.slot_n[it.slot_begin];
             tx = tn.x; ty = tn.y; tz = tn.z;
-            f2 = 2.0 * fma(e.x, tx, fma(e.y, ty, e.z * tz));
+            ent = fma(e.x, tx, fma(e.y, ty, e.z * tz));                  // e.n_t
         }
 #pragma unroll 2
         for (int k = it.src_lo + lane; k < src_hi; k += 32) {
@@ -185,7 +212,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
             double nx = 0, ny = 0, nz = 0;
             if (DLP) { const double4_32a n = g.src_n[s]; nx = n.x; ny = n.y; nz = n.z; }
             pair_fp64<P, DLP, SP>(pw.x - c.x, pw.y - c.y, pw.z - c.z, e.x, e.y, e.z, e.w, wm, nx, ny, nz,
-                                  tx, ty, tz, f2, acc_s, acc_d, acc_p);
+                                  tx, ty, tz, ent, acc_s, acc_d, acc_p);
         }
         acc_s = warp_sum(acc_s);
         if (DLP) acc_d = warp_sum(acc_d);
@@ -196,7 +223,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
     const int L = it.L;
     const int j = lane / L, sub = lane - j * L;
     const bool active = j < it.n_tgt;
-    double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rho2 = 0, tx = 0, ty = 0, tz = 0, f2 = 0;
+    double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rho2 = 0, tx = 0, ty = 0, tz = 0, ent = 0;
     if (active) {
         const double4_32a c = g.slot_c[it.slot_begin + j];
         const double4_32a e = g.slot_e[it.slot_begin + j];
@@ -205,7 +232,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
         if (SP) {
             const double4_32a tn = g.slot_n[it.slot_begin + j];
             tx = tn.x; ty = tn.y; tz = tn.z;
-            f2 = 2.0 * fma(ex, tx, fma(ey, ty, ez * tz));
+            ent = fma(ex, tx, fma(ey, ty, ez * tz));                      // e.n_t
         }
     }
     for (int base = it.src_lo; base < src_hi; base += kTile) {
@@ -227,7 +254,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
             for (int k = sub; k < cnt; k += L)
                 pair_fp64<P, DLP, SP>(T[0][k] - cx, T[1][k] - cy, T[2][k] - cz, ex, ey, ez, rho2, T[3][k],
                                       DLP ? T[4][k] : 0.0, DLP ? T[5][k] : 0.0, DLP ? T[6][k] : 0.0,
-                                      tx, ty, tz, f2, acc_s, acc_d, acc_p);
+                                      tx, ty, tz, ent, acc_s, acc_d, acc_p);
         }
         __syncwarp();
     }
@@ -252,7 +279,7 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         float4 tn = zero;
         if (SP) {
             tn = g.slot_nf[it.slot_begin];
-            tn.w = 2.f * fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));
+            tn.w = fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));    // e.n_t
         }
 #pragma unroll 2
         for (int k = it.src_lo + lane; k < src_hi; k += 32) {
@@ -282,7 +309,7 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         e = g.slot_ef[it.slot_begin + j];
         if (SP) {
             tn = g.slot_nf[it.slot_begin + j];
-            tn.w = 2.f * fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));
+            tn.w = fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));    // e.n_t
         }
     }
     for (int base = it.src_lo; base < src_hi; base += kTile) {

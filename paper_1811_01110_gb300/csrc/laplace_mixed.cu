@@ -1,7 +1,8 @@
 // laplace_mixed.cu -- Laplace TSQBX kernels in mixed precision.
 //
-// Same expansion and warp mapping as laplace_fp64.cu (Appendix A; scaled
-// Bonnet recurrence Q_n = (rho/R)^n P_n), with the arithmetic split as:
+// Same expansion, recurrences and warp mapping as laplace_fp64.cu (Appendix
+// A; the scaled Bonnet recurrence for the single layer alone, the Q'-only
+// recurrence with its closing sums otherwise), with the arithmetic split as:
 //  * coordinates arrive as float-float pairs (hi + lo, formed from the FP64
 //    inputs when the plan is built); s - c is formed as (s_hi - c_hi) +
 //    (s_lo - c_lo), accurate to FP32 rounding of the difference itself, so

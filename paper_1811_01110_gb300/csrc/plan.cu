@@ -866,21 +866,29 @@ int tsqbx_eval(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp)
     return tsqbx_eval_pk(P, P->opt.p, P->opt.k, density, out_slp, out_dlp, nullptr);
 }
 
-int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void *d_out_dlp, void *stream)
+int tsqbx_eval_async_pk(tsqbx_plan P, int p, double k, const void *d_density, void *d_out_slp, void *d_out_dlp,
+                        void *d_out_sp, void *stream)
 {
-    if (!P || (P->g.n_src && !d_density) || !layer_args_ok(P, d_out_slp, d_out_dlp)) return TSQBX_E_INVAL;
+    if (!P || (P->g.n_src && !d_density) || !layer_args_ok(P, d_out_slp, d_out_dlp) || !pk_ok(P, p, k))
+        return TSQBX_E_INVAL;
     try {
         DeviceGuard dg(P->opt.device);
         Slot &slot = P->slots[0];
         cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : slot.stream;
         return enqueue(P, slot, d_density, static_cast<double *>(d_out_slp), static_cast<double *>(d_out_dlp),
-                       nullptr, s, true, P->opt.p, P->opt.k);
+                       static_cast<double *>(d_out_sp), s, true, p, k);
     } catch (const CudaFail &f) {
         cudaGetLastError();
         return status_of(f.err);
     } catch (...) {
         return TSQBX_E_CUDA;
     }
+}
+
+int tsqbx_eval_async(tsqbx_plan P, const void *d_density, void *d_out_slp, void *d_out_dlp, void *stream)
+{
+    if (!P) return TSQBX_E_INVAL;
+    return tsqbx_eval_async_pk(P, P->opt.p, P->opt.k, d_density, d_out_slp, d_out_dlp, nullptr, stream);
 }
 
 int tsqbx_submit_pk(tsqbx_plan P, int p, double k, const void *density, void *out_slp, void *out_dlp,

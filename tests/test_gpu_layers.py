@@ -150,11 +150,22 @@ def test_sp_submit_and_device_outputs(pkg):
     mu = rng.standard_normal(g.n_src)
     with pkg.Plan(g, "laplace", ("slp", "sp"), p=6, n_slots=2) as plan:
         host = plan.eval(mu)
-        dev = plan.eval(torch.from_numpy(mu).cuda())
+        dmu = torch.from_numpy(mu).cuda()
+        dev = plan.eval(dmu)
         t, outs = plan.submit(mu)
         assert pkg.poll(t, -1)
+        asy = {l: torch.full((g.n_tgt,), 7.0, dtype=torch.float64, device="cuda") for l in ("slp", "sp")}
+        plan.eval_async(dmu, asy, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        asy_p4 = {l: torch.empty(g.n_tgt, dtype=torch.float64, device="cuda") for l in ("slp", "sp")}
+        plan.eval_async(dmu, asy_p4, stream=torch.cuda.current_stream(), p=4)
+        torch.cuda.synchronize()
     assert np.array_equal(dev["sp"].cpu().numpy(), host["sp"])
     assert np.array_equal(outs["sp"], host["sp"])
+    assert np.array_equal(asy["sp"].cpu().numpy(), host["sp"])
+    ref4 = oracle.tsqbx_laplace(g, 4, mu, slp=True, sp=True)
+    for layer in ("slp", "sp"):
+        assert relerr(asy_p4[layer].cpu().numpy(), ref4[layer]) <= 1e-12
 
 
 # ------------------------------------------------- Helmholtz double layer, S'
