@@ -42,8 +42,8 @@ PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 def flops_per_pair(p, precision, dlp=True, sp=False):
     """Algorithmic flops per (target, source) pair (FMA = 2) of the Laplace
-    kernels.  Single layer alone: geometry 19 (d, R^2, 1/R, qx, q2), 6 per
-    Bonnet step n = 1..p-1, closing 3.  With the double layer or S' (one
+    kernels.  Single layer alone: geometry 19 (d, R^2, 1/R, qx, q2), 2 for
+    b_{p-1}, 5 per Clenshaw step k = p-2..0, closing 3.  With the double layer or S' (one
     recurrence for Q'_n): geometry 20, 6 per step n = 1..p-1, the top step
     and sums 7, sum Q_n from the closing identity 7, accumulation 2; the
     double layer adds 21 (two normal dots, sum (n+1) Q_n, the combination and
@@ -51,7 +51,7 @@ def flops_per_pair(p, precision, dlp=True, sp=False):
     1/R^3 without the double layer).  Mixed precision adds 6 for the
     float-float difference and 4 per layer for the Kahan update."""
     if not dlp and not sp:
-        f = 19 + 6 * max(p - 1, 0) + 3
+        f = 19 + (2 + 5 * (p - 1) if p >= 1 else 0) + 3
     else:
         f = 20 + 6 * max(p - 1, 0) + 16
         if dlp:
@@ -92,6 +92,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline workload (no batched / Helmholtz / sphere legs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic schedules")
+    ap.add_argument("--only", choices=["batched", "helmholtz", "sphere", "serving", "target_derivative"],
+                    help="run one secondary workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -263,11 +265,25 @@ def gpu_selector(dev, local_rank):
     return str(local_rank)
 
 
-def roofline(flops_per_launch, kernel_s, precision):
+# DRAM bytes (read + write) per launch of each timed kernel, from one ncu
+# capture of the current kernel versions (summaries in profiles/: the
+# laplace_*_p9_torus256x96.md files and helmholtz_slp_p12_torus444x166.md).
+# A kernel changed since its capture must map to None here.
+TRAFFIC_BYTES = {
+    ("laplace", "fp64", "slp+dlp"): 175.85e6,
+    ("laplace", "mixed", "slp+dlp"): 158.02e6,
+    ("laplace", "df64", "slp+dlp"): 175.63e6,
+    ("helmholtz", "fp64", "slp"): 714.07e6,
+}
+
+
+def roofline(flops_per_launch, kernel_s, precision, traffic_key=None):
     peak = PEAK_FP64_TFLOPS if precision == "fp64" else PEAK_FP32_TFLOPS
     achieved = flops_per_launch / kernel_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "pipe": precision if precision == "fp64" else "fp32",
+            "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(traffic_key),
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "pipe": precision if precision == "fp64" else "fp32",
             "peak_source": "derived: 152 SMs x %d FMA/clk x 2 flop x 2070 MHz"
                            % (2 if precision == "fp64" else 128)}
 
@@ -353,7 +369,8 @@ def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
         res["n_pairs"] = info["n_pairs"]
         res[name] = {"value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps),
                      "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
-                     "roofline": dict(roofline(fl * info["n_pairs"], t, "fp64"), flops_per_pair=fl)}
+                     "roofline": dict(roofline(fl * info["n_pairs"], t, "fp64", ("helmholtz", "fp64", name)),
+                                      flops_per_pair=fl)}
         plan.close()
     res["value"] = res["slp"]["value"]
     return res
@@ -480,6 +497,20 @@ def main():
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     import paper_1811_01110_gb300 as pkg
+    if args.only:
+        flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+        steps = max(3, args.steps // 2)
+        if args.only == "serving":
+            res = leg_serving(pkg)
+        elif args.only == "target_derivative":
+            g, mu = workload()
+            res = leg_target_derivative(pkg, torch, dev, g, mu, steps, args.warmup, flush)
+        else:
+            fn = {"batched": leg_batched, "helmholtz": leg_helmholtz, "sphere": leg_sphere}[args.only]
+            res = fn(pkg, torch, dev, steps, args.warmup, flush)
+        if rank == 0:
+            print(json.dumps({"leg": args.only, **res}), flush=True)
+        return
 
     g, mu = workload()
     if world > 1:    # each rank evaluates its own density (independent matvec)
@@ -529,7 +560,7 @@ def main():
         # df64 runs the FP64 algorithm in double-float on the FP32 pipes: its
         # algorithmic flops are the FP64 ones, set against the FP64 peak
         fprec = "fp64" if prec == "df64" else prec
-        rf = roofline(flops_per_pair(P, fprec) * info["n_pairs"], kavg, fprec)
+        rf = roofline(flops_per_pair(P, fprec) * info["n_pairs"], kavg, fprec, ("laplace", prec, "slp+dlp"))
         rf["flops_per_pair"] = flops_per_pair(P, fprec)
         if prec == "df64":
             rf["note"] = ("FP64-equivalent flops (double-float arithmetic on the FP32 pipes) "

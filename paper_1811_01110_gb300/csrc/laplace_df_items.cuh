@@ -39,16 +39,15 @@ __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df 
     const df wr = df_mul(wm, rinv);
     const df one{1.f, 0.f};
     if constexpr (!DLP && !SP) {
-        df S0 = one, Tm = one, Tc = one;
-        if (P >= 1) { S0 = df_add(S0, qx); Tc = qx; }
+        df b2 = df_of(df_const(rec_kappa(P)));                 // Clenshaw, as in pair_fp64
+        df b1 = P >= 1 ? df_add(df_of(df_const(rec_kappa(P - 1))), df_mul(qx, b2)) : one;
 #pragma unroll
-        for (int n = 1; n < P; ++n) {
-            const df bq = df_mul(df_of(df_const(rec_beta(n))), q2);
-            const df Tn = df_sub(df_mul(qx, Tc), df_mul(bq, Tm));
-            S0 = df_add(S0, df_mul(df_of(df_const(rec_kappa(n + 1))), Tn));
-            Tm = Tc; Tc = Tn;
+        for (int k = P - 2; k >= 0; --k) {
+            const df bq = df_mul(df_of(df_const(rec_beta(k + 1))), q2);
+            const df bk = df_sub(df_add(df_of(df_const(rec_kappa(k))), df_mul(qx, b1)), df_mul(bq, b2));
+            b2 = b1; b1 = bk;
         }
-        acc_s = df_add(acc_s, df_mul(wr, S0));
+        acc_s = df_add(acc_s, df_mul(wr, b1));
     } else {
         df Um{0.f, 0.f}, Uc = one, S2m{0.f, 0.f};
 #pragma unroll

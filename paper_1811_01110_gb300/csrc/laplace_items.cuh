@@ -28,8 +28,10 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 // One (target, source) pair in FP64: d = s - c, e = t - c, wm = w mu, n = n_s,
 // t = n_t and ent = e.n_t (S').
 //
-// Single layer alone: T_{n+1} = qx T_n - beta_n q2 T_{n-1}, S = sum kappa_n T_n
-// (three operations per order plus the sum).
+// Single layer alone: S = sum kappa_n T_n with T_{n+1} = qx T_n - beta_n q2
+// T_{n-1}, summed by Clenshaw's backward recurrence b_k = kappa_k + qx b_{k+1}
+// - beta_{k+1} q2 b_{k+2}, S = b_0 (T_1 = qx T_0): three operations per order
+// with the sum folded in.
 //
 // With the double layer or S': everything follows from the derivatives
 // Q'_n = (rho/R)^{n-1} P_n'(x) alone (rec_lambda / rec_gamma recurrence, three
@@ -58,15 +60,14 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
     const double q2 = rho2 * r2inv;
     const double wr = wm * rinv;
     if constexpr (!DLP && !SP) {
-        double S0 = 1.0, Tm = 1.0, Tc = 1.0;
-        if (P >= 1) { S0 += qx; Tc = qx; }
+        // b_{k+1}, b_{k+2} at k = P - 2 (b_{P+1} = 0 drops out of b_{P-1})
+        double b1 = P >= 1 ? fma(qx, rec_kappa(P), rec_kappa(P - 1)) : 1.0, b2 = rec_kappa(P);
 #pragma unroll
-        for (int n = 1; n < P; ++n) {
-            const double Tn = fma(qx, Tc, -(rec_beta(n) * q2) * Tm);
-            S0 = fma(rec_kappa(n + 1), Tn, S0);
-            Tm = Tc; Tc = Tn;
+        for (int k = P - 2; k >= 0; --k) {
+            const double bk = fma(-(rec_beta(k + 1) * q2), b2, fma(qx, b1, rec_kappa(k)));
+            b2 = b1; b1 = bk;
         }
-        acc_s = fma(wr, S0, acc_s);
+        acc_s = fma(wr, b1, acc_s);
     } else {
         // U_{n-1}, U_n starting at n = 1; S2m accumulates Q'_1..Q'_{P-1}
         double Um = 0.0, Uc = 1.0, S2m = 0.0;
@@ -115,15 +116,14 @@ __device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, con
     const float q2 = e.w * r2inv;
     const float wr = h.w * rinv;
     if constexpr (!DLP && !SP) {
-        float S0 = 1.f, Tm = 1.f, Tc = 1.f;
-        if (P >= 1) { S0 += qx; Tc = qx; }
+        float b1 = P >= 1 ? fmaf(qx, (float)rec_kappa(P), (float)rec_kappa(P - 1)) : 1.f;   // as pair_fp64
+        float b2 = (float)rec_kappa(P);
 #pragma unroll
-        for (int n = 1; n < P; ++n) {
-            const float Tn = fmaf(qx, Tc, -((float)rec_beta(n) * q2) * Tm);
-            S0 = fmaf((float)rec_kappa(n + 1), Tn, S0);
-            Tm = Tc; Tc = Tn;
+        for (int k = P - 2; k >= 0; --k) {
+            const float bk = fmaf(-((float)rec_beta(k + 1) * q2), b2, fmaf(qx, b1, (float)rec_kappa(k)));
+            b2 = b1; b1 = bk;
         }
-        kahan_add(as, ac, wr * S0);
+        kahan_add(as, ac, wr * b1);
     } else {
         float Um = 0.f, Uc = 1.f, S2m = 0.f;
 #pragma unroll
