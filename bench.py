@@ -92,7 +92,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline workload (no batched / Helmholtz / sphere legs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic schedules")
-    ap.add_argument("--only", choices=["batched", "helmholtz", "sphere", "serving", "target_derivative"],
+    ap.add_argument("--only", choices=["batched", "helmholtz", "sphere", "serving", "target_derivative",
+                                       "conventional"],
                     help="run one secondary workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -376,6 +377,37 @@ def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
     return res
 
 
+def leg_conventional(pkg, torch, dev, steps, warmup, flush):
+    """Torus 96 x 36 quads (41,472 sources, 82,944 centers, octree lists) with
+    1, 4, 16 and 64 targets per center, Laplace SLP+DLP p = 9, FP64: the
+    target-specific path alone ("off"), conventional QBX for every center
+    ("all"), and the cost model's per-center choice ("auto")."""
+    from tsqbx_inputs import configs
+    stream = torch.cuda.Stream(device=dev)
+    res = {"workload": "torus 96x36 quads, 41472 sources, 82944 centers, octree lists, targets per center "
+                       "in {1,4,16,64} (uniform in each center's half-radius ball), Laplace SLP+DLP p=9, FP64",
+           "unit": UNIT, "cases": []}
+    for tpc in (1, 4, 16, 64):
+        g, mu, _ = configs.torus_near_targets(96, 36, tpc)
+        dmu = torch.from_numpy(mu).to(dev)
+        case = {"targets_per_center": tpc, "n_targets": g.n_tgt}
+        for mode in ("off", "all", "auto"):
+            plan = pkg.Plan(g, "laplace", ("slp", "dlp"), p=9, conventional=mode, device=dev.index)
+            info = plan.info()
+            outs = {l: torch.empty(g.n_tgt, dtype=torch.float64, device=dev) for l in ("slp", "dlp")}
+            step_ms, kern_ms = time_device(plan, dmu, outs, stream, steps, warmup, flush, lambda: None)
+            t = sum(step_ms) / 1e3 / steps
+            case[mode] = {"ms_per_step": 1e3 * t, "pair_terms_per_s": info["n_pair_terms"] / t,
+                          "conv_centers": info["n_conv_centers"], "conv_targets": info["n_conv_targets"]}
+            case["n_pairs"] = info["n_pairs"]
+            plan.close()
+        case["auto_vs_best"] = case["auto"]["ms_per_step"] / min(case["off"]["ms_per_step"],
+                                                                   case["all"]["ms_per_step"])
+        res["cases"].append(case)
+        del dmu
+    return res
+
+
 def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush):
     """The benchmark torus with S' added: Laplace single + double layer + S'
     (target-normal derivative) in one pass, p = 9, in every precision."""
@@ -506,7 +538,8 @@ def main():
             g, mu = workload()
             res = leg_target_derivative(pkg, torch, dev, g, mu, steps, args.warmup, flush)
         else:
-            fn = {"batched": leg_batched, "helmholtz": leg_helmholtz, "sphere": leg_sphere}[args.only]
+            fn = {"batched": leg_batched, "helmholtz": leg_helmholtz, "sphere": leg_sphere,
+                  "conventional": leg_conventional}[args.only]
             res = fn(pkg, torch, dev, steps, args.warmup, flush)
         if rank == 0:
             print(json.dumps({"leg": args.only, **res}), flush=True)
@@ -589,7 +622,8 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
-        for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere)):
+        for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere),
+                         ("conventional", leg_conventional)):
             extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush)
         extras["target_derivative"] = leg_target_derivative(pkg, torch, dev, g, mu, max(3, args.steps // 2),
                                                             args.warmup, flush)

@@ -97,9 +97,19 @@ typedef enum { TSQBX_FP64 = 0, TSQBX_MIXED = 1, TSQBX_DF64 = 2 } tsqbx_precision
 enum {
     TSQBX_FLAG_ALLOW_DIVERGENT = 1u,  /* accept pairs with |t-c| >= |s-c| (report only) */
     TSQBX_FLAG_SKIP_CHECK = 2u,       /* do not run the per-pair convergence check      */
-    TSQBX_FLAG_USE_TUNED = 4u         /* start from the process-wide tuning cache entry
+    TSQBX_FLAG_USE_TUNED = 4u,        /* start from the process-wide tuning cache entry
                                          matching (kernel, precision, p, layers, list
                                          shape), if tsqbx_plan_autotune stored one      */
+    /* Conventional QBX (Sec. 2.1 eqs. local-coeffs, local-expansion) for chosen
+     * centers: the center's local coefficients L_n^m are formed from its
+     * group's list (P2QBXL, (p+1)^2 per source) and evaluated at each of its
+     * targets (QBXL2P, (p+1)^2 per target), instead of the target-specific
+     * expansion ((p+1) per target and source).  The values are the same
+     * truncated expansion (eq. tsqbx).  Laplace, FP64 only (else
+     * TSQBX_E_UNSUPPORTED); such plans accept per-call orders up to their own p. */
+    TSQBX_FLAG_CONVENTIONAL_AUTO = 8u,  /* per center, whichever the cost model (Table 2
+                                           form, GPU constants) says is cheaper        */
+    TSQBX_FLAG_CONVENTIONAL_ALL = 16u   /* every center takes the conventional path     */
 };
 
 typedef struct {
@@ -159,7 +169,11 @@ typedef struct {
     size_t device_bytes;       /* device memory held by the plan                     */
     int64_t n_sliced;          /* target chunks whose list was cut into slices       */
     int launches_per_eval;     /* kernels one evaluation launches (prep, expansion,
-                                  and the slice combine when n_sliced > 0)          */
+                                  the slice combine when n_sliced > 0, and the two
+                                  conventional kernels when n_conv_centers > 0)     */
+    int64_t n_conv_centers;    /* centers on the conventional path                   */
+    int64_t n_conv_targets;    /* their targets                                      */
+    int64_t n_conv_items;      /* conventional coefficient-formation work items      */
 } tsqbx_plan_stats;
 
 /* Create a plan: validates the geometry and options, counts divergent pairs

@@ -91,7 +91,11 @@ class Plan:
 
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
-                 lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False):
+                 lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False,
+                 conventional="off"):
+        """conventional: "off" (target-specific expansions only), "auto"
+        (conventional QBX for the centers the cost model finds cheaper) or
+        "all" (conventional QBX for every center)."""
         self.kernel = kernel
         self.layers = tuple(layers)
         self.p = int(p)
@@ -102,7 +106,9 @@ class Plan:
         self.n_src, self.n_tgt = int(geo.n_src), int(geo.n_tgt)
         flags = (_lib.TSQBX_FLAG_ALLOW_DIVERGENT if allow_divergent else 0) | \
                 (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0) | \
-                (_lib.TSQBX_FLAG_USE_TUNED if use_tuned else 0)
+                (_lib.TSQBX_FLAG_USE_TUNED if use_tuned else 0) | \
+                {"off": 0, "auto": _lib.TSQBX_FLAG_CONVENTIONAL_AUTO,
+                 "all": _lib.TSQBX_FLAG_CONVENTIONAL_ALL}[conventional]
         opt = make_options(kernel, self.layers, self.p, k, precision, device, flags,
                            lanes_per_target, n_slots, max_item_iters)
         h = ctypes.c_void_p()

@@ -22,6 +22,7 @@ TSQBX_LAPLACE, TSQBX_HELMHOLTZ = 0, 1
 TSQBX_SLP, TSQBX_DLP, TSQBX_SP = 1, 2, 4
 TSQBX_FP64, TSQBX_MIXED, TSQBX_DF64 = 0, 1, 2
 TSQBX_FLAG_ALLOW_DIVERGENT, TSQBX_FLAG_SKIP_CHECK, TSQBX_FLAG_USE_TUNED = 1, 2, 4
+TSQBX_FLAG_CONVENTIONAL_AUTO, TSQBX_FLAG_CONVENTIONAL_ALL = 8, 16
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -55,6 +56,8 @@ class tsqbx_plan_stats(ctypes.Structure):
         ("n_coincident", ctypes.c_int64), ("list_entries", ctypes.c_int64),
         ("lane_utilisation", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
         ("n_sliced", ctypes.c_int64), ("launches_per_eval", ctypes.c_int),
+        ("n_conv_centers", ctypes.c_int64), ("n_conv_targets", ctypes.c_int64),
+        ("n_conv_items", ctypes.c_int64),
     ]
 
 

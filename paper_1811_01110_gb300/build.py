@@ -25,7 +25,8 @@ def _nvcc():
 
 
 def _deps():
-    return glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "tsqbx.h")]
+    return (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+            + [os.path.join(INCLUDE, "tsqbx.h")])
 
 
 def _compile(src, verbose):

@@ -27,6 +27,20 @@ constexpr int kWarpsPerBlock = 4;   // independent warps per CTA
 constexpr int kTile = 64;           // sources staged per warp per tile
 constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;  // 1/(4 pi)
 
+// Conventional-path records.  A center on the conventional path owns the
+// target slots [slot_begin, slot_begin + n_tgt) (contiguous) and n_slices
+// blocks of partial coefficients starting at block part0, one per
+// coefficient-formation item (ConvItem) over its group's list.
+struct __align__(16) ConvCenter {
+    int32_t group, slot_begin, n_tgt, part0, n_slices, pad0, pad1, pad2;
+};
+struct __align__(16) ConvItem {              // P2QBXL: one center, one source slice
+    int32_t center, src_lo, src_hi, part;
+};
+struct __align__(16) ConvEvalItem {          // QBXL2P: one center, <= 32 of its targets
+    int32_t center, slot_begin, n_tgt, pad;
+};
+
 // Everything a kernel needs about a plan's geometry (device pointers).
 struct DevGeom {
     int64_t n_src = 0, n_tgt = 0, n_items = 0, n_combine = 0, n_parts = 0;
@@ -50,6 +64,11 @@ struct DevGeom {
     const float4 *slot_ef = nullptr;    // {ex, ey, ez, rho^2} rounded to FP32
     const double4_32a *slot_n = nullptr;    // target normal {nx, ny, nz, 0} (S')
     const float4 *slot_nf = nullptr;    // target normal rounded to FP32 (mixed S')
+    // conventional path
+    int64_t n_conv_centers = 0, n_conv_items = 0, n_conv_eval = 0;
+    const ConvCenter *conv_centers = nullptr;
+    const ConvItem *conv_items = nullptr;
+    const ConvEvalItem *conv_eval = nullptr;
 };
 
 // Per-evaluation buffers (device pointers).
@@ -65,6 +84,7 @@ struct DevEval {
     double *part_sp = nullptr;
     int *status = nullptr;              // bit 0: out-of-range source index seen
     double k = 0.0;                     // Helmholtz wavenumber
+    double *conv_coef = nullptr;        // conventional partial coefficients (scratch)
 };
 
 // Launchers (one per translation unit).  Return a cudaError_t as int.
@@ -73,6 +93,14 @@ int launch_laplace_fp64(int p, unsigned layers, const DevGeom &g, const DevEval 
 int launch_laplace_mixed(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_laplace_df64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_helmholtz_fp64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
+// Conventional path (conventional.cu): coefficient formation, then evaluation.
+int launch_conventional(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
+// Doubles of one block of partial coefficients: (p+1)^2 per layer formed
+// (single layer when the mask has SLP or SP, double layer when it has DLP).
+inline int conv_coef_doubles(int p, unsigned layers)
+{
+    return (p + 1) * (p + 1) * (((layers & 5u) ? 1 : 0) + ((layers & 2u) ? 1 : 0));
+}
 
 // Legendre three-term recurrence in the scaled form used by every kernel:
 //   Q_n = (rho/R)^n P_n(x) = kappa_n T_n,

@@ -167,6 +167,9 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
         if (o->precision != TSQBX_FP64) return TSQBX_E_UNSUPPORTED;
     }
+    if ((o->flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL)) &&
+        (o->kernel != TSQBX_LAPLACE || o->precision != TSQBX_FP64))
+        return TSQBX_E_UNSUPPORTED;
     if (G->n_src < 0 || G->n_ctr < 0 || G->n_tgt < 0 || G->n_group < 0) return TSQBX_E_INVAL;
     if (G->n_src > INT32_MAX || G->n_ctr > INT32_MAX || G->n_tgt > INT32_MAX || G->n_group > INT32_MAX)
         return TSQBX_E_INVAL;
@@ -207,7 +210,8 @@ void fill_stats(tsqbx_plan P)
     st.lane_utilisation = P->sched.lane_utilisation;
     st.device_bytes = P->device_bytes;
     st.n_sliced = (int64_t)P->sched.combine.size();
-    st.launches_per_eval = (P->g.n_src > 0 ? 1 : 0) + (P->g.n_items > 0 ? 1 : 0) + (st.n_sliced > 0 ? 1 : 0);
+    st.launches_per_eval = (P->g.n_src > 0 ? 1 : 0) + (P->g.n_items > 0 ? 1 : 0) + (st.n_sliced > 0 ? 1 : 0) +
+                           (P->g.n_conv_items > 0 ? 1 : 0) + (P->g.n_conv_eval > 0 ? 1 : 0);
 }
 
 }  // namespace
@@ -221,6 +225,28 @@ static thread_local const char *t_last_error = "no error";
 void note_cuda_error(cudaError_t e) { t_last_error = cudaGetErrorName(e); }
 
 int cost_bucket(double cost) { return cost > 0 ? (int)std::floor(2.0 * std::log2(cost)) : -1; }
+
+bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers)
+{
+    // Cost per unit in FP64-pipe operations (the form of Table 2: c_ts (p+1)
+    // per target-specific pair, c_p2qbxl (p+1)^2 per source and c_qbxl2p
+    // (p+1)^2 per target).  The constants were calibrated on GB300 with the
+    // torus at p = 9, SLP+DLP: 0.144 ns per target-specific pair (~80
+    // operations), 1.8 ns per (center, source) of coefficient formation and
+    // 0.73 ns per target of evaluation.  The split between layers follows the
+    // kernels' operation counts (the double layer's derivatives cost about
+    // twice the single layer's recurrence).
+    const bool slp_only = layers == TSQBX_SLP;
+    const bool cs = (layers & (TSQBX_SLP | TSQBX_SP)) != 0, cd = (layers & TSQBX_DLP) != 0;
+    const bool spd = (layers & TSQBX_SP) != 0;
+    const double parts = (double)(p + 1) * (p + 1);
+    const double f_ts = slp_only ? 3.0 * p + 22.0 : 4.0 * p + 32.0 + (cd ? 12.0 : 0.0) + (spd ? 6.0 : 0.0);
+    const double f_p2l = parts * ((cs ? 3.0 : 0.0) + (cd ? 7.0 : 0.0)) + 16.0;
+    const double f_l2p = parts * ((cs ? 2.5 : 0.0) + (cd ? 1.5 : 0.0) + (spd ? 5.0 : 0.0)) + 10.0;
+    const double conv = (double)ns * f_p2l + (double)nt * f_l2p;
+    const double ts = (double)nt * (double)ns * f_ts;
+    return conv < ts;
+}
 
 int choose_lanes(int64_t nt, int64_t ns)
 {
@@ -326,6 +352,7 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
             cudaStream_t s, bool timed, int p, double k)
 {
     const tsqbx_options &o = P->opt;
+    if (P->g.n_conv_centers > 0 && p > o.p) return TSQBX_E_UNSUPPORTED;   // coefficient scratch sized for o.p
     const int64_t n = P->g.n_src;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, (int64_t)P->n_sm * 16);
@@ -338,6 +365,7 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     ev.part_dlp = slot.d_part[1];
     ev.part_sp = ev.out_sp ? slot.d_part[2] : nullptr;
     ev.k = k;
+    ev.conv_coef = slot.d_conv;
     if (n > 0) {
         if (o.kernel == TSQBX_HELMHOLTZ) {
             prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, static_cast<const double2 *>(d_density), n,
@@ -364,6 +392,10 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     else if (o.precision == TSQBX_DF64) rc = launch_laplace_df64(p, layers, P->g, ev, s);
     else rc = launch_laplace_fp64(p, layers, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
+    if (P->g.n_conv_centers > 0) {
+        rc = launch_conventional(p, layers, P->g, ev, s);
+        if (rc != 0) return status_of((cudaError_t)rc);
+    }
     if (P->g.n_combine > 0) {
         const int64_t th = P->g.n_combine * 32;
         const int cb = (int)std::min<int64_t>((th + 255) / 256, (int64_t)P->n_sm * 8);
@@ -442,15 +474,6 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         const bool mixed = o->precision == TSQBX_MIXED;
         const int64_t n_src = G->n_src, n_tgt = G->n_tgt, n_group = G->n_group;
 
-        // targets grouped by their center's group (stable counting sort)
-        std::vector<int64_t> tcount(n_group + 1, 0);
-        for (int64_t t = 0; t < n_tgt; ++t) ++tcount[G->ctr_group[G->tgt_center[t]] + 1];
-        for (int64_t q = 0; q < n_group; ++q) tcount[q + 1] += tcount[q];
-        std::vector<int32_t> slot_tgt(n_tgt);
-        {
-            std::vector<int64_t> pos(tcount.begin(), tcount.end() - 1);
-            for (int64_t t = 0; t < n_tgt; ++t) slot_tgt[pos[G->ctr_group[G->tgt_center[t]]]++] = (int32_t)t;
-        }
         // flattened source list per group
         std::vector<int64_t> grp_off(n_group + 1, 0);
         for (int64_t q = 0; q < n_group; ++q) {
@@ -466,18 +489,78 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             for (int64_t r = G->group_range_start[q]; r < G->group_range_start[q + 1]; ++r)
                 for (int32_t s = G->range_begin[r]; s < G->range_end[r]; ++s) grp_src[w++] = s;
         }
+        // path of each center: conventional QBX or target-specific
+        const int64_t n_ctr = G->n_ctr;
+        std::vector<int64_t> ctr_nt(n_ctr, 0);
+        for (int64_t t = 0; t < n_tgt; ++t) ++ctr_nt[G->tgt_center[t]];
+        std::vector<char> conv(n_ctr, 0);
+        if (o->flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL)) {
+            const bool all = (o->flags & TSQBX_FLAG_CONVENTIONAL_ALL) != 0;
+            for (int64_t c = 0; c < n_ctr; ++c) {
+                if (ctr_nt[c] == 0) continue;
+                const int64_t q = G->ctr_group[c];
+                conv[c] = all || conventional_cheaper(ctr_nt[c], grp_off[q + 1] - grp_off[q], o->p, o->layers);
+            }
+        }
+        // target slots: by group; within a group the target-specific targets
+        // first (input order), then each conventional center's targets
+        // (center order, then input order), contiguous per center
+        std::vector<int64_t> tcount(n_group + 1, 0), ts_count(n_group, 0);
+        for (int64_t t = 0; t < n_tgt; ++t) {
+            const int64_t c = G->tgt_center[t], q = G->ctr_group[c];
+            ++tcount[q + 1];
+            if (!conv[c]) ++ts_count[q];
+        }
+        for (int64_t q = 0; q < n_group; ++q) tcount[q + 1] += tcount[q];
+        std::vector<int32_t> slot_tgt(n_tgt);
+        std::vector<ConvCenter> conv_centers;
+        std::vector<int64_t> conv_pos(n_ctr, -1);
+        {
+            std::vector<int64_t> pos_ts(tcount.begin(), tcount.end() - 1), pos_cv(n_group);
+            for (int64_t q = 0; q < n_group; ++q) pos_cv[q] = tcount[q] + ts_count[q];
+            for (int64_t c = 0; c < n_ctr; ++c) {
+                if (!conv[c]) continue;
+                const int64_t q = G->ctr_group[c];
+                conv_pos[c] = pos_cv[q];
+                conv_centers.push_back(ConvCenter{(int32_t)q, (int32_t)pos_cv[q], (int32_t)ctr_nt[c], 0, 0, 0, 0, 0});
+                pos_cv[q] += ctr_nt[c];
+            }
+            for (int64_t t = 0; t < n_tgt; ++t) {
+                const int64_t c = G->tgt_center[t];
+                if (conv[c]) slot_tgt[conv_pos[c]++] = (int32_t)t;
+                else slot_tgt[pos_ts[G->ctr_group[c]]++] = (int32_t)t;
+            }
+        }
         int64_t n_pairs = 0, n_busy = 0;
         double sum_ns = 0.0;
+        std::vector<GroupWork> all_groups;              // every target (convergence check)
         for (int64_t q = 0; q < n_group; ++q) {
             const int64_t nt = tcount[q + 1] - tcount[q];
             if (nt == 0) continue;
             const int64_t ns = grp_off[q + 1] - grp_off[q];
-            P->groups.push_back({q, tcount[q], nt, ns});
+            all_groups.push_back({q, tcount[q], nt, ns});
+            if (ts_count[q] > 0) P->groups.push_back({q, tcount[q], ts_count[q], ns});
             n_pairs += nt * ns;
             sum_ns += (double)ns;
             ++n_busy;
         }
         P->list_hist = {n_busy ? sum_ns / n_busy : 0.0, n_busy ? (double)n_tgt / n_busy : 0.0};
+        // conventional work: source slices per center, target chunks per center
+        std::vector<ConvItem> conv_items;
+        std::vector<ConvEvalItem> conv_eval;
+        for (size_t i = 0; i < conv_centers.size(); ++i) {
+            ConvCenter &cc = conv_centers[i];
+            const int64_t ns = grp_off[cc.group + 1] - grp_off[cc.group];
+            cc.part0 = (int32_t)conv_items.size();
+            for (int64_t lo = 0; lo < ns || lo == 0; lo += kConvSlice) {
+                conv_items.push_back(ConvItem{(int32_t)i, (int32_t)lo, (int32_t)std::min<int64_t>(ns, lo + kConvSlice),
+                                              (int32_t)conv_items.size()});
+                if (ns == 0) break;
+            }
+            cc.n_slices = (int32_t)conv_items.size() - cc.part0;
+            for (int32_t j = 0; j < cc.n_tgt; j += 32)
+                conv_eval.push_back(ConvEvalItem{(int32_t)i, cc.slot_begin + j, std::min<int32_t>(32, cc.n_tgt - j), 0});
+        }
 
         // target slot records
         std::vector<double4_32a> slot_c(n_tgt), slot_e(n_tgt);
@@ -551,6 +634,15 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         }
         if (sp) g.slot_n = P->upload(slot_n);
         g.slot_tgt = P->upload(slot_tgt);
+        if (!conv_centers.empty()) {
+            g.n_conv_centers = (int64_t)conv_centers.size();
+            g.n_conv_items = (int64_t)conv_items.size();
+            g.n_conv_eval = (int64_t)conv_eval.size();
+            g.conv_centers = P->upload(conv_centers);
+            g.conv_items = P->upload(conv_items);
+            g.conv_eval = P->upload(conv_eval);
+            P->conv_coef_doubles = (size_t)g.n_conv_items * (size_t)conv_coef_doubles(o->p, o->layers);
+        }
         g.slot_c = P->upload(slot_c);
         g.slot_e = P->upload(slot_e);
 
@@ -569,6 +661,7 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             if (o->layers & TSQBX_SP) s.d_out[2] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             s.d_status = P->dalloc<int>(1);
+            if (P->conv_coef_doubles) s.d_conv = P->dalloc<double>(P->conv_coef_doubles);
             s.h_density = P->halloc(P->density_bytes);
             s.h_out[0] = P->halloc(P->out_bytes);
             s.h_out[1] = P->halloc(P->out_bytes);
@@ -596,17 +689,28 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         }
         apply_schedule(P, std::move(sched));
 
-        // convergence check on the device
+        // convergence check on the device, over every target (both paths)
         int64_t n_div = 0, n_zero = 0;
-        if (!(o->flags & TSQBX_FLAG_SKIP_CHECK) && g.n_items > 0) {
+        if (!(o->flags & TSQBX_FLAG_SKIP_CHECK) && !all_groups.empty()) {
+            Schedule chk;
+            if ((rc = build_schedule(all_groups, 0, 0, P->n_sm, chk)) != TSQBX_OK) {
+                delete P;
+                return rc;
+            }
+            std::vector<Item> chk_items(chk.items.size());
+            for (size_t i = 0; i < chk_items.size(); ++i) chk_items[i] = chk.items[i].it;
+            DevGeom gc = g;
+            gc.items = P->upload(chk_items);
+            gc.n_items = (int64_t)chk_items.size();
             unsigned long long *cnt = P->dalloc<unsigned long long>(2);
             ck(cudaMemset(cnt, 0, 2 * sizeof(unsigned long long)));
-            const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-            check_pairs_kernel<<<(unsigned)blocks, kWarpsPerBlock * 32>>>(g, cnt, cnt + 1);
+            const int64_t blocks = (gc.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+            if (blocks > 0) check_pairs_kernel<<<(unsigned)blocks, kWarpsPerBlock * 32>>>(gc, cnt, cnt + 1);
             ck(cudaGetLastError());
             unsigned long long h[2] = {0, 0};
             ck(cudaMemcpy(h, cnt, sizeof(h), cudaMemcpyDeviceToHost));
             P->dfree(cnt);
+            P->dfree(gc.items);
             n_div = (int64_t)h[0];
             n_zero = (int64_t)h[1];
             if (n_zero > 0 || (n_div > 0 && !(o->flags & TSQBX_FLAG_ALLOW_DIVERGENT))) {
@@ -625,6 +729,9 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         st.n_divergent = n_div;
         st.n_coincident = n_zero;
         st.list_entries = grp_off[n_group];
+        st.n_conv_centers = g.n_conv_centers;
+        st.n_conv_items = g.n_conv_items;
+        for (const ConvCenter &cc : conv_centers) st.n_conv_targets += cc.n_tgt;
         fill_stats(P);
         *out = P;
         return TSQBX_OK;

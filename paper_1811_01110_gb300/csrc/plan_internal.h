@@ -64,6 +64,12 @@ struct Schedule {
 int cost_bucket(double cost);
 // Lanes per target chosen for a group (items * (lane iterations + staging)).
 int choose_lanes(int64_t nt, int64_t ns);
+// Sources per conventional coefficient-formation item.
+constexpr int64_t kConvSlice = 1024;
+// Cost model (the form of the paper's Table 2, with this GPU's constants):
+// whether a center with nt targets and ns listed sources is cheaper on the
+// conventional path than on the target-specific one.
+bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers);
 // Build the schedule; max_iters <= 0 picks the automatic cap.
 int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
                    int n_sm, Schedule &out);
@@ -76,6 +82,7 @@ struct Slot {
     double *d_out[3] = {nullptr, nullptr, nullptr};    // single layer, double layer, S'
     double *d_part[3] = {nullptr, nullptr, nullptr};   // partial sums of sliced items
     int *d_status = nullptr;
+    double *d_conv = nullptr;      // conventional partial coefficients
     void *h_density = nullptr;     // pinned staging
     void *h_out[3] = {nullptr, nullptr, nullptr};
     int *h_status = nullptr;
@@ -97,6 +104,7 @@ struct tsqbx_plan_s {
     std::vector<tsqbx::Slot> slots;
     std::mutex mu;
     size_t density_bytes = 0, out_bytes = 0, wmu_bytes = 0;
+    size_t conv_coef_doubles = 0;                     // per slot, for the plan's p
     cudaEvent_t k_begin = nullptr, k_end = nullptr;   // brackets the expansion (slot 0)
     bool k_timed = false;
     int n_sm = 152;

@@ -110,3 +110,10 @@ def test_unknown_layer_bits_rejected(L):
         opt.layers = mask
         h = ctypes.c_void_p()
         assert L.tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)) == _lib.TSQBX_E_INVAL
+
+
+def test_conventional_needs_laplace_fp64(L):
+    g = _tiny()
+    assert _create(g, conventional="all", precision="mixed") == -9
+    assert _create(g, conventional="auto", precision="df64") == -9
+    assert _create(g, kernel="helmholtz", k=1.0, conventional="all") == -9

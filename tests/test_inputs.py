@@ -117,3 +117,17 @@ def test_octree_sources_sorted_by_box(rng):
         pts = sp[tree.src_begin[b]:tree.src_end[b]]
         if len(pts):
             assert np.all(np.abs(pts - tree.center[:, b]) <= tree.halfwidth[b] + 1e-12)
+
+
+def test_near_targets_stay_convergent():
+    """Extra targets per center lie within the original target's distance of
+    their center, so every listed pair stays convergent."""
+    import oracle
+    from tsqbx_inputs import configs
+    g, mu, _ = configs.torus_near_targets(24, 10, targets_per_center=5)
+    assert g.n_tgt == 5 * g.n_ctr
+    assert np.bincount(g.tgt_center, minlength=g.n_ctr).tolist() == [5] * g.n_ctr
+    rho = np.linalg.norm(g.tgt_xyz - g.ctr_xyz[:, g.tgt_center], axis=0)
+    assert np.all(rho[g.n_ctr:] <= rho[g.tgt_center[g.n_ctr:]] * (1 + 1e-12))
+    nd, nz = oracle.count_divergent(g)
+    assert nd == 0 and nz == 0

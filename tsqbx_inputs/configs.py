@@ -10,6 +10,8 @@
                  884,448 sources), octree lists as above, plane-wave density.
   ellipsoids  -- 64 ellipsoids (semi-axes U(0.5,2)), log-uniform sizes, nearest
                  lists of log-uniform length 50..800, p in {5,7,9}.
+  torus_near_targets -- the torus recipe with many targets per center (the
+                 regime where conventional QBX is cheaper).
 Scaled-down variants (same recipe, fewer quads) serve the parity tests.
 """
 import numpy as np
@@ -78,6 +80,31 @@ def torus(nu=256, nv=96, seed_offset=0, n_max=64):
     g.meta.update(name=f"torus-{nu}x{nv}", kernel="laplace", p=9)
     src = g.src_xyz.T
     return g, dens.harmonic_density(src, rng), tree
+
+
+def torus_near_targets(nu=96, nv=36, targets_per_center=16, seed_offset=0, n_max=64):
+    """The torus recipe with many targets per QBX center (off-surface
+    evaluation near the surface): besides its own target at half the ball
+    radius, each center gets targets_per_center - 1 more, uniform in the ball
+    of that same radius about the center (so |t-c| is never larger than for
+    the original target and every pair stays convergent).  Extra targets
+    carry their center's target normal."""
+    g, mu, tree = torus(nu, nv, seed_offset=seed_offset, n_max=n_max)
+    rng = np.random.default_rng(BASE_SEED + 5 + seed_offset)
+    extra = targets_per_center - 1
+    if extra > 0:
+        n = g.n_ctr
+        c = np.repeat(np.arange(n, dtype=np.int32), extra)
+        rho = np.linalg.norm(g.tgt_xyz - g.ctr_xyz, axis=0)        # one target per center, in order
+        v = rng.standard_normal((len(c), 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        r = rho[c] * rng.uniform(0.0, 1.0, len(c)) ** (1.0 / 3.0)
+        t = g.ctr_xyz[:, c].T + r[:, None] * v
+        g.tgt_xyz = np.ascontiguousarray(np.concatenate([g.tgt_xyz, t.T], axis=1))
+        g.tgt_center = np.concatenate([g.tgt_center, c])
+        g.tgt_normal = np.ascontiguousarray(np.concatenate([g.tgt_normal, g.tgt_normal[:, c]], axis=1))
+    g.meta.update(name=f"torus-{nu}x{nv}-tpc{targets_per_center}", targets_per_center=targets_per_center)
+    return g, mu, tree
 
 
 def torus_helmholtz(nu=444, nv=166, k=10.0, seed_offset=0, n_max=64):
