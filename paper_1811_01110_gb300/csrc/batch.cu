@@ -63,7 +63,7 @@ __device__ __forceinline__ void run_item_fp64(int p, const DevGeom &g, const Dev
 
 template <bool DLP, int... Ps>
 __device__ __forceinline__ void run_item_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
-                                               float4 (*T)[kTile], int lane, std::integer_sequence<int, Ps...>)
+                                               float4 (*T)[kMixedPairs], int lane, std::integer_sequence<int, Ps...>)
 {
     ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, T, lane), 0) : 0), ...);
 }
@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, int64_t n_items,
                      unsigned long long *head)
 {
-    using TileT = typename std::conditional<MIXED, float4, double>::type;
-    constexpr int NF = MIXED ? (DLP ? 3 : 2) : (DLP ? 7 : 4);
-    __shared__ TileT tile[kWarpsPerBlock][NF][kTile];
+    // per-warp tile: mixed, pair records (laplace_items.cuh); FP64, one row per field
+    constexpr int kWarpBytes = MIXED ? mixed_tile_rows(DLP) * kMixedPairs * 16 : (DLP ? 7 : 4) * kTile * 8;
+    __shared__ __align__(16) unsigned char tile_raw[kWarpsPerBlock * kWarpBytes];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         // pop kPopChunk consecutive items (similar cost: the queue is sorted)
@@ -90,11 +90,12 @@ batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *item
             DevEval ev = bp.ev;
             ev.out_slp = io[it.pad].out_slp;
             ev.out_dlp = io[it.pad].out_dlp;
+            unsigned char *mine = tile_raw + warp * kWarpBytes;
             if constexpr (MIXED)
-                run_item_mixed<DLP>(bp.p, bp.g, ev, it, tile[warp], lane,
+                run_item_mixed<DLP>(bp.p, bp.g, ev, it, reinterpret_cast<float4 (*)[kMixedPairs]>(mine), lane,
                                     std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
             else
-                run_item_fp64<DLP>(bp.p, bp.g, ev, it, tile[warp], lane,
+                run_item_fp64<DLP>(bp.p, bp.g, ev, it, reinterpret_cast<double (*)[kTile]>(mine), lane,
                                    std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
             __syncwarp();
         }

@@ -13,17 +13,10 @@
 //    butterfly reduction.
 #pragma once
 
+#include "f32x2.cuh"
 #include "internal.cuh"
 
 namespace tsqbx {
-
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
-{
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
 
 // One (target, source) pair in FP64: d = s - c, e = t - c, wm = w mu, n = n_s,
 // t = n_t and ent = e.n_t (S').
@@ -93,60 +86,6 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
         if (SP) {
             const double dn = fma(dx, tx, fma(dy, ty, dz * tz));
             acc_p = fma(wr3, fma(dn, S2, -ent * S2m), acc_p);
-        }
-    }
-}
-
-// One pair in mixed precision: h/l = source hi/lo (h.w = w mu), ch/cl = center
-// hi/lo, e = {t - c, rho^2}, nn = n_s, tn = {n_t, e.n_t}; Kahan-compensated
-// FP32 sums (as/ac single layer, ds/dc double layer, ps/pc S').  Same two
-// recurrences and closing sums as pair_fp64, in FP32.
-template <int P, bool DLP, bool SP>
-__device__ __forceinline__ void pair_mixed(const float4 &h, const float4 &l, const float4 &ch, const float4 &cl,
-                                           const float4 &e, const float4 &nn, const float4 &tn, float &as,
-                                           float &ac, float &ds, float &dc, float &ps, float &pc)
-{
-    const float dx = __fadd_rn(__fsub_rn(h.x, ch.x), __fsub_rn(l.x, cl.x));
-    const float dy = __fadd_rn(__fsub_rn(h.y, ch.y), __fsub_rn(l.y, cl.y));
-    const float dz = __fadd_rn(__fsub_rn(h.z, ch.z), __fsub_rn(l.z, cl.z));
-    const float R2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float rinv = rsqrtf(R2);
-    const float r2inv = rinv * rinv;
-    const float qx = fmaf(dx, e.x, fmaf(dy, e.y, dz * e.z)) * r2inv;
-    const float q2 = e.w * r2inv;
-    const float wr = h.w * rinv;
-    if constexpr (!DLP && !SP) {
-        float b1 = P >= 1 ? fmaf(qx, (float)rec_kappa(P), (float)rec_kappa(P - 1)) : 1.f;   // as pair_fp64
-        float b2 = (float)rec_kappa(P);
-#pragma unroll
-        for (int k = P - 2; k >= 0; --k) {
-            const float bk = fmaf(-((float)rec_beta(k + 1) * q2), b2, fmaf(qx, b1, (float)rec_kappa(k)));
-            b2 = b1; b1 = bk;
-        }
-        kahan_add(as, ac, wr * b1);
-    } else {
-        float Um = 0.f, Uc = 1.f, S2m = 0.f;
-#pragma unroll
-        for (int n = 1; n < P; ++n) {
-            S2m = fmaf((float)rec_lambda(n), Uc, S2m);
-            const float Un = fmaf(qx, Uc, -((float)rec_gamma(n) * q2) * Um);
-            Um = Uc; Uc = Un;
-        }
-        const float Qp = P >= 1 ? (float)rec_lambda(P) * Uc : 0.f;
-        const float Qp1 = P >= 1 ? (float)rec_lambda(P + 1) * fmaf(qx, Uc, -((float)rec_gamma(P) * q2) * Um) : 1.f;
-        const float S2 = S2m + Qp;
-        const float S = fmaf(fmaf(-2.f, qx, 1.f) + q2, S2, fmaf(-q2, Qp, Qp1));
-        kahan_add(as, ac, wr * S);
-        const float wr3 = wr * r2inv;
-        if (DLP) {
-            const float S1 = fmaf(1.f - qx, S2, Qp1);
-            const float a = fmaf(dx, nn.x, fmaf(dy, nn.y, dz * nn.z));
-            const float b = fmaf(e.x, nn.x, fmaf(e.y, nn.y, e.z * nn.z));
-            kahan_add(ds, dc, wr3 * fmaf(-a, S1, fmaf(-a, qx, b) * S2));
-        }
-        if (SP) {
-            const float dn = fmaf(dx, tn.x, fmaf(dy, tn.y, dz * tn.z));
-            kahan_add(ps, pc, wr3 * fmaf(dn, S2, -tn.w * S2m));
         }
     }
 }
@@ -264,15 +203,121 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
     if (active && sub == 0) write_item_result<DLP, SP>(g, ev, it, j, acc_s, acc_d, acc_p);
 }
 
+// Two (target, source) pairs at once in mixed precision, every FP32 operation
+// packed (f32x2.cuh): the recurrences and closing sums of pair_fp64 in FP32,
+// for the sources in the two halves, with s - c formed as (s_hi - c_hi) +
+// (s_lo - c_lo) from float-float coordinates.  hx.. = source hi coordinates, w = w mu, lx.. = lo parts,
+// nx.. = n_s; ch/cl = center hi/lo, e = {t - c, rho^2}, tn = {n_t, e.n_t}
+// (per target, both halves equal); Kahan pairs per layer, per half.
+template <int P, bool DLP, bool SP>
+__device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2 ly, f2 lz, f2 nx, f2 ny, f2 nz,
+                                            const float4 &ch, const float4 &cl, const float4 &e,
+                                            const float4 &tn, f2 &as, f2 &ac, f2 &ds, f2 &dc, f2 &ps, f2 &pc)
+{
+    const f2 dx = add2(sub2(hx, f2_splat(ch.x)), sub2(lx, f2_splat(cl.x)));
+    const f2 dy = add2(sub2(hy, f2_splat(ch.y)), sub2(ly, f2_splat(cl.y)));
+    const f2 dz = add2(sub2(hz, f2_splat(ch.z)), sub2(lz, f2_splat(cl.z)));
+    const f2 R2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    float r0, r1;
+    f2_split(R2, r0, r1);
+    const f2 rinv = f2_make(rsqrtf(r0), rsqrtf(r1));
+    const f2 r2inv = mul2(rinv, rinv);
+    const f2 qx = mul2(fma2(dx, f2_splat(e.x), fma2(dy, f2_splat(e.y), mul2(dz, f2_splat(e.z)))), r2inv);
+    const f2 q2 = mul2(f2_splat(e.w), r2inv);
+    const f2 wr = mul2(w, rinv);
+    if constexpr (!DLP && !SP) {
+        f2 b1 = P >= 1 ? fma2(qx, f2_splat((float)rec_kappa(P)), f2_splat((float)rec_kappa(P - 1))) : f2_splat(1.f);
+        f2 b2 = f2_splat((float)rec_kappa(P));
+#pragma unroll
+        for (int k = P - 2; k >= 0; --k) {
+            const f2 bq = mul2(f2_splat(-(float)rec_beta(k + 1)), q2);
+            const f2 bk = fma2(bq, b2, fma2(qx, b1, f2_splat((float)rec_kappa(k))));
+            b2 = b1; b1 = bk;
+        }
+        kahan_add2(as, ac, mul2(wr, b1));
+    } else {
+        f2 Um = f2_splat(0.f), Uc = f2_splat(1.f), S2m = f2_splat(0.f);
+#pragma unroll
+        for (int n = 1; n < P; ++n) {
+            S2m = fma2(f2_splat((float)rec_lambda(n)), Uc, S2m);
+            const f2 gq = mul2(f2_splat(-(float)rec_gamma(n)), q2);
+            const f2 Un = fma2(gq, Um, mul2(qx, Uc));
+            Um = Uc; Uc = Un;
+        }
+        f2 Qp = f2_splat(0.f), Qp1 = f2_splat(1.f);
+        if (P >= 1) {
+            Qp = mul2(f2_splat((float)rec_lambda(P)), Uc);
+            const f2 gq = mul2(f2_splat(-(float)rec_gamma(P)), q2);
+            Qp1 = mul2(f2_splat((float)rec_lambda(P + 1)), fma2(gq, Um, mul2(qx, Uc)));
+        }
+        const f2 S2 = add2(S2m, Qp);
+        const f2 c1 = add2(fma2(f2_splat(-2.f), qx, f2_splat(1.f)), q2);
+        const f2 S = fma2(c1, S2, fma2(sub2(f2_splat(0.f), q2), Qp, Qp1));
+        kahan_add2(as, ac, mul2(wr, S));
+        const f2 wr3 = mul2(wr, r2inv);
+        if (DLP) {
+            const f2 S1 = fma2(sub2(f2_splat(1.f), qx), S2, Qp1);
+            const f2 a = fma2(dx, nx, fma2(dy, ny, mul2(dz, nz)));
+            const f2 b = fma2(f2_splat(e.x), nx, fma2(f2_splat(e.y), ny, mul2(f2_splat(e.z), nz)));
+            const f2 na = sub2(f2_splat(0.f), a);
+            kahan_add2(ds, dc, mul2(wr3, fma2(na, S1, mul2(fma2(na, qx, b), S2))));
+        }
+        if (SP) {
+            const f2 dn = fma2(dx, f2_splat(tn.x), fma2(dy, f2_splat(tn.y), mul2(dz, f2_splat(tn.z))));
+            kahan_add2(ps, pc, mul2(wr3, fma2(dn, S2, mul2(f2_splat(-tn.w), S2m))));
+        }
+    }
+}
+
+// Sum of the two halves of a Kahan-compensated packed sum, in FP64.
+__device__ __forceinline__ double kahan2_value(f2 s, f2 c)
+{
+    float s0, s1, c0, c1;
+    f2_split(s, s0, s1);
+    f2_split(c, c0, c1);
+    return ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
+}
+
+// Shared-memory tile of the mixed item, two sources per record (pair j holds
+// sources 2j and 2j+1 of the tile): {hx0, hx1, hy0, hy1}, {hz0, hz1, w0, w1},
+// {lx0, lx1, ly0, ly1}, {lz0, lz1, nx0, nx1} and, for the double layer,
+// {ny0, ny1, nz0, nz1}.  One 16-byte load gives two packed operands.
+constexpr int kMixedPairs = kTile / 2;
+__host__ __device__ constexpr int mixed_tile_rows(bool dlp) { return dlp ? 5 : 4; }
+
+// Load sources k0 and k1 (k1 < 0: a zero-weight copy of k0) of a group's list
+// as packed operands.
+template <bool DLP>
+__device__ __forceinline__ void load_mixed_pair(const DevGeom &g, const DevEval &ev, int64_t s0, int k0, int k1,
+                                                f2 &hx, f2 &hy, f2 &hz, f2 &w, f2 &lx, f2 &ly, f2 &lz, f2 &nx,
+                                                f2 &ny, f2 &nz)
+{
+    int sa = g.grp_src[s0 + k0];
+    int sb = k1 >= 0 ? g.grp_src[s0 + k1] : sa;
+    float wa = 0.f, wb = 0.f;
+    if ((unsigned)sa >= (unsigned)g.n_src) { atomicOr(ev.status, 1); sa = 0; } else wa = ev.wmu_f[sa];
+    if ((unsigned)sb >= (unsigned)g.n_src) { atomicOr(ev.status, 1); sb = 0; } else if (k1 >= 0) wb = ev.wmu_f[sb];
+    const float4 ha = g.src_hi[sa], hb = g.src_hi[sb], la = g.src_lo[sa], lb = g.src_lo[sb];
+    hx = f2_make(ha.x, hb.x); hy = f2_make(ha.y, hb.y); hz = f2_make(ha.z, hb.z); w = f2_make(wa, wb);
+    lx = f2_make(la.x, lb.x); ly = f2_make(la.y, lb.y); lz = f2_make(la.z, lb.z);
+    if (DLP) {
+        const float4 na = g.src_nf[sa], nb = g.src_nf[sb];
+        nx = f2_make(na.x, nb.x); ny = f2_make(na.y, nb.y); nz = f2_make(na.z, nb.z);
+    } else {
+        nx = ny = nz = f2_splat(0.f);
+    }
+}
+
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                   float4 (*T)[kTile], const int lane)
+                                                   float4 (*T)[kMixedPairs], const int lane)
 {
     const int64_t s0 = g.grp_off[it.group];
     const int src_hi = it.src_hi;
-    float as = 0.f, ac = 0.f, ds = 0.f, dc = 0.f, ps = 0.f, pc = 0.f;   // Kahan pairs
+    const f2 z2 = f2_splat(0.f);
+    f2 as = z2, ac = z2, ds = z2, dc = z2, ps = z2, pc = z2;   // Kahan pairs
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (it.n_tgt == 1) {                               // direct loads, all 32 lanes
+    if (it.n_tgt == 1) {                               // direct loads, all 32 lanes, two sources each
         const float4 ch = g.slot_chi[it.slot_begin];
         const float4 cl = g.slot_clo[it.slot_begin];
         const float4 e = g.slot_ef[it.slot_begin];
@@ -281,21 +326,14 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
             tn = g.slot_nf[it.slot_begin];
             tn.w = fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));    // e.n_t
         }
-#pragma unroll 2
-        for (int k = it.src_lo + lane; k < src_hi; k += 32) {
-            int s = g.grp_src[s0 + k];
-            float wm = 0.f;
-            if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
-            else wm = ev.wmu_f[s];
-            float4 h = g.src_hi[s];
-            h.w = wm;
-            const float4 l = g.src_lo[s];
-            const float4 nn = DLP ? g.src_nf[s] : zero;
-            pair_mixed<P, DLP, SP>(h, l, ch, cl, e, nn, tn, as, ac, ds, dc, ps, pc);
+        for (int k = it.src_lo + lane; k < src_hi; k += 64) {
+            f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
+            load_mixed_pair<DLP>(g, ev, s0, k, k + 32 < src_hi ? k + 32 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
+            pair_mixed2<P, DLP, SP>(hx, hy, hz, w, lx, ly, lz, nx, ny, nz, ch, cl, e, tn, as, ac, ds, dc, ps, pc);
         }
-        const double acc_s = warp_sum((double)as - (double)ac);
-        const double acc_d = DLP ? warp_sum((double)ds - (double)dc) : 0.0;
-        const double acc_p = SP ? warp_sum((double)ps - (double)pc) : 0.0;
+        const double acc_s = warp_sum(kahan2_value(as, ac));
+        const double acc_d = DLP ? warp_sum(kahan2_value(ds, dc)) : 0.0;
+        const double acc_p = SP ? warp_sum(kahan2_value(ps, pc)) : 0.0;
         if (lane == 0) write_item_result<DLP, SP>(g, ev, it, 0, acc_s, acc_d, acc_p);
         return;
     }
@@ -314,28 +352,33 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
     }
     for (int base = it.src_lo; base < src_hi; base += kTile) {
         const int cnt = min(kTile, src_hi - base);
-        for (int k = lane; k < cnt; k += 32) {
-            int s = g.grp_src[s0 + base + k];
-            float wm = 0.f;
-            if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
-            else wm = ev.wmu_f[s];
-            float4 h = g.src_hi[s];
-            h.w = wm;
-            T[0][k] = h;
-            T[1][k] = g.src_lo[s];
-            if (DLP) T[2][k] = g.src_nf[s];
+        const int npairs = (cnt + 1) >> 1;
+        if (lane < npairs) {                           // lane stages pair `lane`
+            const int k0 = base + 2 * lane;
+            f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
+            load_mixed_pair<DLP>(g, ev, s0, k0, 2 * lane + 1 < cnt ? k0 + 1 : -1, hx, hy, hz, w, lx, ly, lz, nx,
+                                 ny, nz);
+            float a0, a1, b0, b1;
+            f2_split(hx, a0, a1); f2_split(hy, b0, b1); T[0][lane] = make_float4(a0, a1, b0, b1);
+            f2_split(hz, a0, a1); f2_split(w, b0, b1);  T[1][lane] = make_float4(a0, a1, b0, b1);
+            f2_split(lx, a0, a1); f2_split(ly, b0, b1); T[2][lane] = make_float4(a0, a1, b0, b1);
+            f2_split(lz, a0, a1); f2_split(nx, b0, b1); T[3][lane] = make_float4(a0, a1, b0, b1);
+            if (DLP) { f2_split(ny, a0, a1); f2_split(nz, b0, b1); T[4][lane] = make_float4(a0, a1, b0, b1); }
         }
         __syncwarp();
         if (active) {
-            for (int k = sub; k < cnt; k += L)
-                pair_mixed<P, DLP, SP>(T[0][k], T[1][k], ch, cl, e, DLP ? T[2][k] : zero, tn, as, ac, ds, dc,
-                                       ps, pc);
+            for (int q = sub; q < npairs; q += L) {
+                const float4 A = T[0][q], B = T[1][q], C = T[2][q], D = T[3][q];
+                const float4 E = DLP ? T[4][q] : zero;
+                pair_mixed2<P, DLP, SP>(f2_xy(A), f2_zw(A), f2_xy(B), f2_zw(B), f2_xy(C), f2_zw(C), f2_xy(D),
+                                        f2_zw(D), f2_xy(E), f2_zw(E), ch, cl, e, tn, as, ac, ds, dc, ps, pc);
+            }
         }
         __syncwarp();
     }
-    const double acc_s = segment_sum((double)as - (double)ac, sub, L);
-    const double acc_d = DLP ? segment_sum((double)ds - (double)dc, sub, L) : 0.0;
-    const double acc_p = SP ? segment_sum((double)ps - (double)pc, sub, L) : 0.0;
+    const double acc_s = segment_sum(kahan2_value(as, ac), sub, L);
+    const double acc_d = DLP ? segment_sum(kahan2_value(ds, dc), sub, L) : 0.0;
+    const double acc_p = SP ? segment_sum(kahan2_value(ps, pc), sub, L) : 0.0;
     if (active && sub == 0) write_item_result<DLP, SP>(g, ev, it, j, acc_s, acc_d, acc_p);
 }
 

@@ -28,7 +28,7 @@ template <int P, bool DLP, bool SP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 laplace_mixed_kernel(const DevGeom g, const DevEval ev)
 {
-    __shared__ float4 tile[kWarpsPerBlock][DLP ? 3 : 2][kTile];
+    __shared__ float4 tile[kWarpsPerBlock][mixed_tile_rows(DLP)][kMixedPairs];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
@@ -38,8 +38,8 @@ laplace_mixed_kernel(const DevGeom g, const DevEval ev)
 template <bool MIXED, int P, bool DLP, bool SP>
 void launch_one(unsigned blocks, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
-    if (MIXED) laplace_mixed_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
-    else       laplace_fp64_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    if constexpr (MIXED) laplace_mixed_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    else                 laplace_fp64_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
 }
 
 template <bool MIXED, bool SP, int P>

@@ -10,7 +10,11 @@
 //  * e = t - c and rho^2 are formed in FP64 at plan time and rounded once;
 //  * the geometry ratios, 1/R (rsqrtf) and the recurrence run in FP32;
 //  * each lane keeps Kahan-compensated FP32 sums; the L lanes of a target are
-//    combined in FP64, and the output is FP64.
+//    combined in FP64, and the output is FP64;
+//  * each lane takes two sources at a time and runs every FP32 operation as
+//    a packed f32x2 instruction (f32x2.cuh): the same flops in half the issue
+//    slots.  The staged tile holds sources pairwise, so one 16-byte shared
+//    load gives two packed operands.
 #include "laplace_launch.cuh"
 
 namespace tsqbx {
