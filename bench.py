@@ -93,7 +93,7 @@ def parse():
                     help="only the headline workload (no batched / Helmholtz / sphere legs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic schedules")
     ap.add_argument("--only", choices=["batched", "helmholtz", "sphere", "serving", "target_derivative",
-                                       "conventional"],
+                                       "conventional", "lists"],
                     help="run one secondary workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -408,6 +408,39 @@ def leg_conventional(pkg, torch, dev, steps, warmup, flush):
     return res
 
 
+def leg_lists(pkg, torch, dev, steps, warmup, flush):
+    """Octree + near-field lists (List 1 + List 3 close + List 4 close) on the
+    GPU against the host builder of the input tooling (single-threaded C++),
+    on the benchmark torus, the Helmholtz torus and the urchin gamma_8 (6
+    icosphere subdivisions); n_max = 64, t_f = 0.9, n_mpole = 40.  The GPU
+    time is the wall time of tsqbx_octree_build, host copies in and out
+    included; every array is checked equal to the host builder's."""
+    from tsqbx_inputs import configs, lists as L
+    res = {"unit": "ms", "cases": []}
+    for name, fn in (("torus 256x96", lambda: configs.torus_points(256, 96)),
+                     ("torus 444x166", lambda: configs.torus_points(444, 166)),
+                     ("urchin k=8, 6 subdivisions", lambda: configs.urchin_points(8, 6))):
+        src, ctr, rad = fn()
+        gpu_ms = []
+        for i in range(warmup + steps):
+            t = pkg.Octree(src, ctr, rad, device=dev.index)
+            if i >= warmup:
+                gpu_ms.append(t.stats["build_ms"])
+        t0 = time.perf_counter()
+        ref = L.Octree(src, ctr, rad)
+        host_ms = 1e3 * (time.perf_counter() - t0)
+        same = all(np.array_equal(np.asarray(getattr(t, a)), np.asarray(getattr(ref, a)))
+                   for a in ("level", "parent", "src_perm", "ctr_box", "near_start", "near_begin", "near_end",
+                             "src_begin", "src_end"))
+        res["cases"].append({"workload": name, "n_sources": len(src), "n_centers": len(ctr),
+                             "n_boxes": t.n_boxes, "max_level": t.stats["max_level"],
+                             "near_ranges": t.stats["near_nnz"],
+                             "center_source_pairs": t.stats["center_source_pairs"],
+                             "gpu_ms": statistics.median(gpu_ms), "host_ms": host_ms,
+                             "speedup": host_ms / statistics.median(gpu_ms), "identical_to_host": bool(same)})
+    return res
+
+
 def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush):
     """The benchmark torus with S' added: Laplace single + double layer + S'
     (target-normal derivative) in one pass, p = 9, in every precision."""
@@ -539,7 +572,7 @@ def main():
             res = leg_target_derivative(pkg, torch, dev, g, mu, steps, args.warmup, flush)
         else:
             fn = {"batched": leg_batched, "helmholtz": leg_helmholtz, "sphere": leg_sphere,
-                  "conventional": leg_conventional}[args.only]
+                  "conventional": leg_conventional, "lists": leg_lists}[args.only]
             res = fn(pkg, torch, dev, steps, args.warmup, flush)
         if rank == 0:
             print(json.dumps({"leg": args.only, **res}), flush=True)
@@ -623,7 +656,7 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere),
-                         ("conventional", leg_conventional)):
+                         ("conventional", leg_conventional), ("lists", leg_lists)):
             extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush)
         extras["target_derivative"] = leg_target_derivative(pkg, torch, dev, g, mu, max(3, args.steps // 2),
                                                             args.warmup, flush)

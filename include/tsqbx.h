@@ -401,6 +401,52 @@ TSQBX_API int tsqbx_eval_noalloc(const tsqbx_geometry *d_geometry, int p, uint32
                                  const double *d_density, double *d_out_slp, double *d_out_dlp,
                                  void *stream);
 
+/* ------------------------------------------------------------- octree
+ * The GIGAQBX octree over sources and QBX centers and the near-field pair
+ * lists, built on the GPU (Sec. 3.1-3.2, Defs. 1-9; the list building of
+ * Alg. 1 Stage 1).  Rules: the root is the smallest power-of-two cube holding
+ * every source and QBX ball, centered on the grid of spacing H/1024; a box
+ * with more than n_max owned sources + centers splits, sources moving to their
+ * octant's child and a center only if its ball fits that child's target
+ * confinement region (radius sqrt(3) h (1 + t_f)); empty children are not
+ * created.  Boxes are numbered breadth first (children in octant order),
+ * sources ordered depth first.  For every box owning a center the result is
+ * the sorted, merged source ranges of List 1 + List 3 close + List 4 close
+ * (List 3 boxes separated from the box's confinement region with at least
+ * n_mpole sources are "far" and excluded), in the depth-first source order:
+ * exactly the pair lists tsqbx_geometry takes (groups = boxes owning centers),
+ * so no host preprocessing precedes tsqbx_plan_create. */
+typedef struct tsqbx_octree_s *tsqbx_octree;
+typedef struct {
+    int64_t n_boxes, n_leaves, max_level;
+    int64_t n_target_boxes;     /* boxes owning at least one center                  */
+    int64_t near_nnz;           /* merged near-field ranges over all target boxes    */
+    int64_t center_source_pairs;/* sum over centers of their near-field source count  */
+    double build_ms;            /* wall time of tsqbx_octree_build (host view)        */
+} tsqbx_octree_stats;
+
+/* Build.  src_xyz [3][n_src], ctr_xyz [3][n_ctr] (HOST pointers), ctr_radius
+ * [n_ctr] >= 0, all finite; n_max >= 1, t_f >= 0, n_mpole >= 0.  Errors:
+ * TSQBX_E_INVAL, TSQBX_E_TOO_LARGE (deeper than 30 levels: too many
+ * coincident points), TSQBX_E_NOMEM, TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_octree_build(int64_t n_src, const double *src_xyz, int64_t n_ctr, const double *ctr_xyz,
+                                 const double *ctr_radius, int n_max, double t_f, int n_mpole, int device,
+                                 tsqbx_octree *out);
+TSQBX_API void tsqbx_octree_destroy(tsqbx_octree tree);
+TSQBX_API int tsqbx_octree_info(tsqbx_octree tree, tsqbx_octree_stats *stats);
+/* Host copies (any pointer may be NULL): per box, n_boxes entries (center:
+ * [3][n_boxes]); src_begin/src_end: the box's sources in depth-first order. */
+TSQBX_API int tsqbx_octree_boxes(tsqbx_octree tree, int32_t *level, double *center, double *halfwidth,
+                                 int32_t *parent, int32_t *src_begin, int32_t *src_end, int32_t *n_owned_ctr,
+                                 int32_t *is_leaf);
+/* src_perm[i]: input index of the i-th source in depth-first order;
+ * ctr_box[c]: the box owning center c. */
+TSQBX_API int tsqbx_octree_order(tsqbx_octree tree, int32_t *src_perm, int32_t *ctr_box);
+/* Near-field ranges: box b's are near_begin/near_end[near_start[b] ..
+ * near_start[b+1]) (half-open, depth-first source positions); near_start has
+ * n_boxes + 1 entries, the ranges stats.near_nnz. */
+TSQBX_API int tsqbx_octree_near(tsqbx_octree tree, int64_t *near_start, int32_t *near_begin, int32_t *near_end);
+
 /* Name of the last CUDA runtime error that a libtsqbx call made on the
  * calling thread ran into (the detail behind TSQBX_E_CUDA / TSQBX_E_NOMEM);
  * "no error" if none. */

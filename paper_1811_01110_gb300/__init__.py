@@ -380,6 +380,77 @@ class Server:
         check(lib().tsqbx_server_reset_stats(self._h), "tsqbx_server_reset_stats")
 
 
+class Octree:
+    """The GIGAQBX octree and near-field lists built on the GPU
+    (tsqbx_octree_build).  Attributes mirror the host builder's: per box
+    level, center (3, n_boxes), halfwidth, parent, src_begin, src_end,
+    n_owned_ctr, is_leaf; src_perm, ctr_box; near_start, near_begin,
+    near_end; stats."""
+
+    def __init__(self, src_xyz, ctr_xyz, ctr_radius, n_max=64, t_f=0.9, n_mpole=40, device=0):
+        s = np.ascontiguousarray(np.asarray(src_xyz, dtype=np.float64).T)      # (3, n) from (n, 3)
+        c = np.ascontiguousarray(np.asarray(ctr_xyz, dtype=np.float64).T)
+        r = np.ascontiguousarray(ctr_radius, dtype=np.float64)
+        self.n_src, self.n_ctr = s.shape[1], c.shape[1]
+        h = ctypes.c_void_p()
+        check(lib().tsqbx_octree_build(self.n_src, _ptr(s, ctypes.c_double), self.n_ctr,
+                                       _ptr(c, ctypes.c_double), _ptr(r, ctypes.c_double), int(n_max),
+                                       float(t_f), int(n_mpole), int(device), ctypes.byref(h)),
+              "tsqbx_octree_build")
+        try:
+            st = _lib.tsqbx_octree_stats()
+            check(lib().tsqbx_octree_info(h, ctypes.byref(st)), "tsqbx_octree_info")
+            self.stats = {name: getattr(st, name) for name, _ in st._fields_}
+            nb = int(st.n_boxes)
+            self.n_boxes = nb
+            i32 = lambda n: np.zeros(max(n, 1), np.int32)
+            self.level, self.parent, self.src_begin, self.src_end = i32(nb), i32(nb), i32(nb), i32(nb)
+            self.n_owned_ctr, self.is_leaf = i32(nb), i32(nb)
+            self.center, self.halfwidth = np.zeros(3 * max(nb, 1)), np.zeros(max(nb, 1))
+            check(lib().tsqbx_octree_boxes(h, _ptr(self.level, ctypes.c_int32), _ptr(self.center, ctypes.c_double),
+                                           _ptr(self.halfwidth, ctypes.c_double), _ptr(self.parent, ctypes.c_int32),
+                                           _ptr(self.src_begin, ctypes.c_int32), _ptr(self.src_end, ctypes.c_int32),
+                                           _ptr(self.n_owned_ctr, ctypes.c_int32),
+                                           _ptr(self.is_leaf, ctypes.c_int32)), "tsqbx_octree_boxes")
+            for name in ("level", "parent", "src_begin", "src_end", "n_owned_ctr", "is_leaf", "halfwidth"):
+                setattr(self, name, getattr(self, name)[:nb])
+            self.center = self.center[:3 * nb].reshape(3, nb)
+            self.src_perm, self.ctr_box = i32(self.n_src), i32(self.n_ctr)
+            check(lib().tsqbx_octree_order(h, _ptr(self.src_perm, ctypes.c_int32), _ptr(self.ctr_box, ctypes.c_int32)),
+                  "tsqbx_octree_order")
+            self.src_perm, self.ctr_box = self.src_perm[:self.n_src], self.ctr_box[:self.n_ctr]
+            nnz = int(st.near_nnz)
+            self.near_start = np.zeros(nb + 1, np.int64)
+            self.near_begin, self.near_end = i32(nnz), i32(nnz)
+            check(lib().tsqbx_octree_near(h, _ptr(self.near_start, ctypes.c_int64),
+                                          _ptr(self.near_begin, ctypes.c_int32), _ptr(self.near_end, ctypes.c_int32)),
+                  "tsqbx_octree_near")
+            self.near_begin, self.near_end = self.near_begin[:nnz], self.near_end[:nnz]
+        finally:
+            lib().tsqbx_octree_destroy(h)
+
+
+def octree_lists(src_xyz, ctr_xyz, ctr_radius, n_max=64, t_f=0.9, n_mpole=40, device=0):
+    """GPU-built octree and near-field lists, packaged as pair lists: returns
+    (tree, src_perm, ctr_order, ctr_group, group_range_start, range_begin,
+    range_end).  Sources must be permuted by src_perm and centers by
+    ctr_order (grouped by owning box); the ranges index the permuted sources."""
+    tree = Octree(src_xyz, ctr_xyz, ctr_radius, n_max, t_f, n_mpole, device)
+    target_boxes = np.nonzero(tree.n_owned_ctr > 0)[0]
+    gid = -np.ones(tree.n_boxes, np.int64)
+    gid[target_boxes] = np.arange(len(target_boxes))
+    ctr_g = gid[tree.ctr_box]
+    ctr_order = np.argsort(ctr_g, kind="stable")
+    ctr_group = ctr_g[ctr_order].astype(np.int32)
+    counts = tree.near_start[target_boxes + 1] - tree.near_start[target_boxes]
+    grs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    sel = (np.concatenate([np.arange(tree.near_start[b], tree.near_start[b + 1]) for b in target_boxes])
+           if len(target_boxes) else np.zeros(0, np.int64))
+    rb = tree.near_begin[sel].astype(np.int32)
+    re = tree.near_end[sel].astype(np.int32)
+    return tree, tree.src_perm.astype(np.int64), ctr_order, ctr_group, grs, rb, re
+
+
 def poll(ticket, timeout_us=0):
     """tsqbx_poll: True when done, False while pending (timeout_us == 0)."""
     rc = lib().tsqbx_poll(ctypes.c_uint64(ticket), int(timeout_us))

@@ -80,6 +80,14 @@ class tsqbx_server_stats(ctypes.Structure):
     ]
 
 
+class tsqbx_octree_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("max_level", ctypes.c_int64),
+        ("n_target_boxes", ctypes.c_int64), ("near_nnz", ctypes.c_int64),
+        ("center_source_pairs", ctypes.c_int64), ("build_ms", ctypes.c_double),
+    ]
+
+
 class tsqbx_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_target", ctypes.c_int), ("max_item_iters", ctypes.c_int),
                 ("kernel_ms", ctypes.c_float)]
@@ -137,6 +145,15 @@ _SIGNATURES = [
     ("tsqbx_eval_noalloc", ctypes.c_int,
      [ctypes.POINTER(tsqbx_geometry), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("tsqbx_octree_build", ctypes.c_int,
+     [ctypes.c_int64, _dp, ctypes.c_int64, _dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+      ctypes.POINTER(ctypes.c_void_p)]),
+    ("tsqbx_octree_destroy", None, [ctypes.c_void_p]),
+    ("tsqbx_octree_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_octree_stats)]),
+    ("tsqbx_octree_boxes", ctypes.c_int,
+     [ctypes.c_void_p, _i32p, _dp, _dp, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    ("tsqbx_octree_order", ctypes.c_int, [ctypes.c_void_p, _i32p, _i32p]),
+    ("tsqbx_octree_near", ctypes.c_int, [ctypes.c_void_p, _i64p, _i32p, _i32p]),
     ("tsqbx_last_error", ctypes.c_char_p, []),
     ("tsqbx_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("tsqbx_version", ctypes.c_int, []),

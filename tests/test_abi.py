@@ -117,3 +117,14 @@ def test_conventional_needs_laplace_fp64(L):
     assert _create(g, conventional="all", precision="mixed") == -9
     assert _create(g, conventional="auto", precision="df64") == -9
     assert _create(g, kernel="helmholtz", k=1.0, conventional="all") == -9
+
+
+def test_octree_inputs_rejected_on_host(L):
+    import paper_1811_01110_gb300 as pkg
+    rng = np.random.default_rng(1)
+    src, ctr, rad = rng.uniform(-1, 1, (20, 3)), rng.uniform(-1, 1, (5, 3)), np.full(5, 0.01)
+    for kw, args in ((dict(n_max=0), (src, ctr, rad)), (dict(t_f=-1.0), (src, ctr, rad)),
+                     (dict(), (np.full((20, 3), np.nan), ctr, rad)), (dict(), (src, ctr, -rad))):
+        with pytest.raises(pkg.TsqbxError) as ei:
+            pkg.Octree(*args, **kw)
+        assert ei.value.code == -1

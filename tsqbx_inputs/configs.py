@@ -12,6 +12,8 @@
                  lists of log-uniform length 50..800, p in {5,7,9}.
   torus_near_targets -- the torus recipe with many targets per center (the
                  regime where conventional QBX is cheaper).
+  urchin_points -- list-building inputs on the urchin surfaces gamma_k of
+                 Sec. 5.1 as flat triangles.
 Scaled-down variants (same recipe, fewer quads) serve the parity tests.
 """
 import numpy as np
@@ -105,6 +107,46 @@ def torus_near_targets(nu=96, nv=36, targets_per_center=16, seed_offset=0, n_max
         g.tgt_normal = np.ascontiguousarray(np.concatenate([g.tgt_normal, g.tgt_normal[:, c]], axis=1))
     g.meta.update(name=f"torus-{nu}x{nv}-tpc{targets_per_center}", targets_per_center=targets_per_center)
     return g, mu, tree
+
+
+def torus_points(nu=256, nv=96):
+    """The torus recipe's raw list-building inputs: sources (N, 3), QBX centers
+    (M, 3) and their radii (M,), before the octree orders them."""
+    V, F = mesh.torus(nu, nv, 1.0, 0.35)
+    F = mesh.orient_outward(V, F, _torus_core)
+    xyz, w, nrm, h = _surface_nodes(V, F)
+    one = np.ones(len(xyz))
+    C, Rr, T, Tn, node = mesh.centers_and_targets(xyz, nrm, h, [one, -one])
+    return xyz, C, Rr
+
+
+def urchin_radius(k, dirs):
+    """The urchin gamma_k of Sec. 5.1: r_k = 0.2 + (Re Y_k^{floor(k/2)} - m_k)
+    / (M_k - m_k) at unit directions dirs (N, 3), with M_k, m_k the extrema
+    of Re Y_k^{floor(k/2)} over the sphere (taken on a 1201 x 2400 grid in
+    (theta, phi) and the given directions).  P_k^m is taken without the
+    Condon-Shortley phase; the spherical-harmonic normalisation cancels."""
+    m = k // 2
+    th, ph = np.meshgrid(np.linspace(0.0, np.pi, 1201), np.linspace(0.0, 2 * np.pi, 2400, endpoint=False))
+    grid = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=-1).reshape(-1, 3)
+    yg = dens.real_sph_harm(k, m, grid)
+    y = dens.real_sph_harm(k, m, dirs)
+    hi, lo = max(yg.max(), y.max()), min(yg.min(), y.min())
+    return 0.2 + (y - lo) / (hi - lo)
+
+
+def urchin_points(k=8, subdiv=5):
+    """Raw list-building inputs on the urchin gamma_k as flat triangles: an
+    icosphere subdivided subdiv times, each vertex moved radially to r_k;
+    6 nodes per triangle, two QBX centers per node (one each side)."""
+    V, F = mesh.icosphere(subdiv)
+    dirs = V / np.linalg.norm(V, axis=1, keepdims=True)
+    V = dirs * urchin_radius(k, dirs)[:, None]
+    F = mesh.orient_outward(V, F, lambda c: np.zeros_like(c))
+    xyz, w, nrm, h = _surface_nodes(V, F)
+    one = np.ones(len(xyz))
+    C, Rr, T, Tn, node = mesh.centers_and_targets(xyz, nrm, h, [one, -one])
+    return xyz, C, Rr
 
 
 def torus_helmholtz(nu=444, nv=166, k=10.0, seed_offset=0, n_max=64):
