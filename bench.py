@@ -437,7 +437,9 @@ def leg_lists(pkg, torch, dev, steps, warmup, flush):
                              "near_ranges": t.stats["near_nnz"],
                              "center_source_pairs": t.stats["center_source_pairs"],
                              "gpu_ms": statistics.median(gpu_ms), "host_ms": host_ms,
-                             "speedup": host_ms / statistics.median(gpu_ms), "identical_to_host": bool(same)})
+                             "speedup": host_ms / statistics.median(gpu_ms), "identical_to_host": bool(same),
+                             "gpu_phases_ms": {k: round(t.stats[k], 2) for k in
+                                               ("upload_ms", "tree_ms", "order_ms", "lists_ms", "download_ms")}})
     return res
 
 

@@ -423,6 +423,7 @@ typedef struct {
     int64_t near_nnz;           /* merged near-field ranges over all target boxes    */
     int64_t center_source_pairs;/* sum over centers of their near-field source count  */
     double build_ms;            /* wall time of tsqbx_octree_build (host view)        */
+    double upload_ms, tree_ms, order_ms, lists_ms, download_ms;   /* its phases     */
 } tsqbx_octree_stats;
 
 /* Build.  src_xyz [3][n_src], ctr_xyz [3][n_ctr] (HOST pointers), ctr_radius

@@ -85,6 +85,8 @@ class tsqbx_octree_stats(ctypes.Structure):
         ("n_boxes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("max_level", ctypes.c_int64),
         ("n_target_boxes", ctypes.c_int64), ("near_nnz", ctypes.c_int64),
         ("center_source_pairs", ctypes.c_int64), ("build_ms", ctypes.c_double),
+        ("upload_ms", ctypes.c_double), ("tree_ms", ctypes.c_double), ("order_ms", ctypes.c_double),
+        ("lists_ms", ctypes.c_double), ("download_ms", ctypes.c_double),
     ]
 
 

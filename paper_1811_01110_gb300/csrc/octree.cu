@@ -126,10 +126,49 @@ __device__ int colleagues(const TreeView &T, int b, int *out)
     return n;
 }
 
+// Raw List 4 of box a (a target box or an ancestor of one): leaves coarser
+// than a, adjacent to parent(a) but not to a, and a's non-adjacent colleague
+// leaves (coll: a's colleagues); emit(d) for each.
+template <class Emit>
+__device__ void raw_list4(const TreeView &T, int a, const int *coll, int nc, Emit &emit)
+{
+    const int pa = T.parent[a];
+    if (pa >= 0) {
+        int stack[kStack], sp = 0;
+        stack[sp++] = 0;
+        while (sp > 0) {
+            const int x = stack[--sp];
+            if (T.level[x] >= T.level[a] || !adjacent(T, x, pa)) continue;
+            if (T.leaf[x]) {
+                if (T.nsrc[x] > 0 && !adjacent(T, x, a)) emit(x);
+                continue;
+            }
+            for (int o = 7; o >= 0; --o) {
+                const int c = T.child[8 * x + o];
+                if (c >= 0 && sp < kStack) stack[sp++] = c;
+            }
+        }
+    }
+    for (int i = 0; i < nc; ++i) {
+        const int d = coll[i];
+        if (T.leaf[d] && T.nsrc[d] > 0 && !adjacent(T, d, a)) emit(d);
+    }
+}
+
+// CSR lists per "list box" (target boxes and their ancestors): colleagues
+// and raw List 4; pos[b] = the box's row, -1 if it has none.
+struct BoxLists {
+    const int *pos;
+    const long long *coll_off;
+    const int *coll;
+    const long long *l4_off;
+    const int *l4;
+};
+
 // Every box of the near field of target box w (List 1, List 3 close, List 4
 // close), passed to emit(box).
 template <class Emit>
-__device__ void near_field(const TreeView &T, int w, Emit &emit)
+__device__ void near_field(const TreeView &T, const BoxLists &BL, int w, Emit &emit)
 {
     int stack[kStack], sp;
     // List 1: leaves adjacent to w that hold sources
@@ -144,12 +183,11 @@ __device__ void near_field(const TreeView &T, int w, Emit &emit)
             if (c >= 0 && sp < kStack) stack[sp++] = c;
         }
     }
-    int coll[128];
     // List 3 (close part): below the colleagues' children
-    const int nc = colleagues(T, w, coll);
-    for (int i = 0; i < nc; ++i)
+    const int row = BL.pos[w];
+    for (long long i = BL.coll_off[row]; i < BL.coll_off[row + 1]; ++i)
         for (int o = 0; o < 8; ++o) {
-            const int c0 = T.child[8 * coll[i] + o];
+            const int c0 = T.child[8 * BL.coll[i] + o];
             if (c0 < 0) continue;
             sp = 0;
             stack[sp++] = c0;
@@ -183,29 +221,12 @@ __device__ void near_field(const TreeView &T, int w, Emit &emit)
                 }
             }
         }
-    // List 4 close: the raw List 4 of w and of each ancestor a
+    // List 4 close: raw List 4 of w and of each ancestor, not separated from TCR(w)
     for (int a = w; a >= 0; a = T.parent[a]) {
-        const int pa = T.parent[a];
-        if (pa >= 0) {                   // leaves coarser than a, adjacent to parent(a), not to a
-            sp = 0;
-            stack[sp++] = 0;
-            while (sp > 0) {
-                const int x = stack[--sp];
-                if (T.level[x] >= T.level[a] || !adjacent(T, x, pa)) continue;
-                if (T.leaf[x]) {
-                    if (T.nsrc[x] > 0 && !adjacent(T, x, a) && !sep_tcr_box(T, w, x)) emit(x);
-                    continue;
-                }
-                for (int o = 7; o >= 0; --o) {
-                    const int c = T.child[8 * x + o];
-                    if (c >= 0 && sp < kStack) stack[sp++] = c;
-                }
-            }
-        }
-        const int n = colleagues(T, a, coll);   // non-adjacent colleague leaves of a
-        for (int i = 0; i < n; ++i) {
-            const int d = coll[i];
-            if (T.leaf[d] && T.nsrc[d] > 0 && !adjacent(T, d, a) && !sep_tcr_box(T, w, d)) emit(d);
+        const int r = BL.pos[a];
+        for (long long i = BL.l4_off[r]; i < BL.l4_off[r + 1]; ++i) {
+            const int d = BL.l4[i];
+            if (!sep_tcr_box(T, w, d)) emit(d);
         }
     }
 }
@@ -220,23 +241,58 @@ struct FillEmit {
     int n = 0;
     __device__ void operator()(int b) { out[n++] = make_int2(T->sbeg[b], T->send[b]); }
 };
+struct BoxEmit {
+    int *out;
+    int n = 0;
+    __device__ void operator()(int b) { out[n++] = b; }
+};
 
-__global__ void near_count_kernel(const TreeView T, const int *tboxes, int nt, int *count)
+// Colleagues of each list box (count or fill).
+template <bool FILL>
+__global__ void coll_kernel(const TreeView T, const int *boxes, int n, const long long *off, int *out, int *count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c[128];
+    const int m = colleagues(T, boxes[i], c);
+    if (FILL) for (int k = 0; k < m; ++k) out[off[i] + k] = c[k];
+    else count[i] = m;
+}
+
+// Raw List 4 of each list box (count or fill).
+template <bool FILL>
+__global__ void l4_kernel(const TreeView T, const int *boxes, int n, const long long *coll_off, const int *coll,
+                          const long long *off, int *out, int *count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nc = (int)(coll_off[i + 1] - coll_off[i]);
+    if (FILL) {
+        BoxEmit e{out + off[i]};
+        raw_list4(T, boxes[i], coll + coll_off[i], nc, e);
+    } else {
+        CountEmit e;
+        raw_list4(T, boxes[i], coll + coll_off[i], nc, e);
+        count[i] = e.n;
+    }
+}
+
+__global__ void near_count_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt, int *count)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nt) return;
     CountEmit e;
-    near_field(T, tboxes[i], e);
+    near_field(T, BL, tboxes[i], e);
     count[i] = e.n;
 }
 
-__global__ void near_fill_kernel(const TreeView T, const int *tboxes, int nt, const long long *off, int2 *raw,
-                                 int *merged)
+__global__ void near_fill_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt, const long long *off,
+                                 int2 *raw, int *merged)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nt) return;
     FillEmit e{&T, raw + off[i]};
-    near_field(T, tboxes[i], e);
+    near_field(T, BL, tboxes[i], e);
     // sort by (begin, end), then drop empty ranges and join touching ones
     int2 *r = raw + off[i];
     const int n = e.n;
@@ -298,14 +354,29 @@ struct BuildBuf {
     double *cx, *cy, *cz, *h;
 };
 
-// Count the points of each box of the current level (boxes [lb, le)).
+// Count the points of each box of the current level (boxes [lb, lb + nlev)).
+// Few boxes (the top levels): counted in shared memory first, one global
+// atomic per box and block.
+constexpr int kSmemBoxes = 4096;
 __global__ void count_kernel(int64_t ns, const int *sbox, const char *sact, int64_t nc, const int *cbox,
-                             const char *cact, int lb, int *cnt)
+                             const char *cact, int lb, int nlev, int *cnt)
 {
+    __shared__ int sh[kSmemBoxes];
+    const bool local = nlev <= kSmemBoxes;
+    if (local) {
+        for (int i = threadIdx.x; i < nlev; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+    }
+    int *dst = local ? sh : cnt;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns + nc; i += stride) {
-        if (i < ns) { if (sact[i]) atomicAdd(&cnt[sbox[i] - lb], 1); }
-        else { const int64_t j = i - ns; if (cact[j]) atomicAdd(&cnt[cbox[j] - lb], 1); }
+        if (i < ns) { if (sact[i]) atomicAdd(&dst[sbox[i] - lb], 1); }
+        else { const int64_t j = i - ns; if (cact[j]) atomicAdd(&dst[cbox[j] - lb], 1); }
+    }
+    if (local) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nlev; i += blockDim.x)
+            if (sh[i]) atomicAdd(&cnt[i], sh[i]);
     }
 }
 
@@ -483,6 +554,14 @@ void to_host(std::vector<T> &v, const T *d, size_t n)
 void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const double *hc, const double *hr,
            int n_max, double t_f, int n_mpole, int n_sm)
 {
+    using clk = std::chrono::steady_clock;
+    auto t_mark = clk::now();
+    auto lap = [&](double &dst) {
+        ck(cudaDeviceSynchronize());
+        const auto now = clk::now();
+        dst = std::chrono::duration<double, std::milli>(now - t_mark).count();
+        t_mark = now;
+    };
     DBuf<double> s, c, r;
     s.alloc(3 * ns); c.alloc(3 * nc); r.alloc(nc);
     if (ns) ck(cudaMemcpy(s.p, hs, 3 * ns * sizeof(double), cudaMemcpyHostToDevice));
@@ -492,6 +571,7 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     }
     const int64_t np = ns + nc;
     const int gp = grid_for(np, n_sm);
+    lap(O.stats.upload_ms);
 
     // bounding cube of the sources and QBX balls; root as in the host builder
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
@@ -559,7 +639,7 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
         cnt.alloc(nlev); flag.alloc(8 * (size_t)nlev); off.alloc(8 * (size_t)nlev);
         ck(cudaMemset(cnt.p, 0, nlev * sizeof(int)));
         ck(cudaMemset(flag.p, 0, 8 * (size_t)nlev * sizeof(int)));
-        count_kernel<<<gp, 256>>>(ns, sbox.p, sact.p, nc, cbox.p, cact.p, lb, cnt.p);
+        count_kernel<<<gp, 256>>>(ns, sbox.p, sact.p, nc, cbox.p, cact.p, lb, nlev, cnt.p);
         ck(cudaGetLastError());
         BuildBuf B{level.p, parent.p, child.p, nullptr, nullptr, nullptr, nullptr, leaf.p, cx.p, cy.p, cz.p, hw.p};
         octant_kernel<<<gp, 256>>>(ns, s.p, sbox.p, sact.p, soct.p, nc, c.p, r.p, cbox.p, cact.p, coct.p, B, lb, cnt.p,
@@ -587,6 +667,7 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     }
     const int nb = le;
     const int n_levels = (int)lev_begin.size() - 1;      // lev_begin[L] .. lev_begin[L+1]
+    lap(O.stats.tree_ms);
 
     // subtree source counts (bottom up), depth-first offsets (top down)
     nsrc.alloc(nb); nctr.alloc(nb); sbeg.alloc(nb); send.alloc(nb);
@@ -619,33 +700,66 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
         ck(cub::DeviceRadixSort::SortPairs(tmp.p, tb, key.p, key2.p, val.p, val2.p, (int)ns, 0, bits));
     }
 
+    lap(O.stats.order_ms);
     // near-field lists of the target boxes
     to_host(O.n_owned_ctr, nctr.p, nb);
-    std::vector<int> tboxes;
-    for (int b = 0; b < nb; ++b) if (O.n_owned_ctr[b] > 0) tboxes.push_back(b);
-    const int nt = (int)tboxes.size();
+    std::vector<int> par;
+    to_host(par, parent.p, nb);
+    std::vector<char> toa(nb, 0);                      // target box or ancestor of one
+    std::vector<int> tboxes, lboxes, pos(nb, -1);
+    for (int b = 0; b < nb; ++b) {
+        if (O.n_owned_ctr[b] <= 0) continue;
+        tboxes.push_back(b);
+        for (int a = b; a >= 0 && !toa[a]; a = par[a]) toa[a] = 1;
+    }
+    for (int b = 0; b < nb; ++b)
+        if (toa[b]) { pos[b] = (int)lboxes.size(); lboxes.push_back(b); }
+    const int nt = (int)tboxes.size(), nl = (int)lboxes.size();
     TreeView T{nb, level.p, parent.p, child.p, nsrc.p, sbeg.p, send.p, leaf.p, cx.p, cy.p, cz.p, hw.p, t_f, n_mpole};
     std::vector<long long> hoff(nt + 1, 0);
     std::vector<int> hmerged(nt);
     DBuf<int2> raw;
-    if (nt > 0) {
-        DBuf<int> dt, dcount;
-        DBuf<long long> doff;
-        dt.alloc(nt); dcount.alloc(nt);
-        ck(cudaMemcpy(dt.p, tboxes.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
-        near_count_kernel<<<(nt + 127) / 128, 128>>>(T, dt.p, nt, dcount.p);
-        ck(cudaGetLastError());
+    // CSR from per-row counts (prefix sum on the host: one copy each way)
+    auto csr = [&](DBuf<int> &dcount, int n, DBuf<long long> &doff) {
         std::vector<int> hc;
-        to_host(hc, dcount.p, nt);
-        for (int i = 0; i < nt; ++i) hoff[i + 1] = hoff[i] + hc[i];
+        to_host(hc, dcount.p, n);
+        std::vector<long long> o(n + 1, 0);
+        for (int i = 0; i < n; ++i) o[i + 1] = o[i] + hc[i];
+        doff.alloc(n + 1);
+        ck(cudaMemcpy(doff.p, o.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+        return o;
+    };
+    if (nt > 0) {
+        DBuf<int> dl, dpos, dcount, dcoll, dl4, dt;
+        DBuf<long long> dcoll_off, dl4_off, doff;
+        dl.alloc(nl); dpos.alloc(nb); dcount.alloc(std::max(nl, nt));
+        ck(cudaMemcpy(dl.p, lboxes.data(), nl * sizeof(int), cudaMemcpyHostToDevice));
+        ck(cudaMemcpy(dpos.p, pos.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+        const int gl = (nl + 127) / 128, gt = (nt + 127) / 128;
+        coll_kernel<false><<<gl, 128>>>(T, dl.p, nl, nullptr, nullptr, dcount.p);
+        ck(cudaGetLastError());
+        const std::vector<long long> co = csr(dcount, nl, dcoll_off);
+        dcoll.alloc(std::max<long long>(1, co[nl]));
+        coll_kernel<true><<<gl, 128>>>(T, dl.p, nl, dcoll_off.p, dcoll.p, nullptr);
+        ck(cudaGetLastError());
+        l4_kernel<false><<<gl, 128>>>(T, dl.p, nl, dcoll_off.p, dcoll.p, nullptr, nullptr, dcount.p);
+        ck(cudaGetLastError());
+        const std::vector<long long> lo4 = csr(dcount, nl, dl4_off);
+        dl4.alloc(std::max<long long>(1, lo4[nl]));
+        l4_kernel<true><<<gl, 128>>>(T, dl.p, nl, dcoll_off.p, dcoll.p, dl4_off.p, dl4.p, nullptr);
+        ck(cudaGetLastError());
+        const BoxLists BL{dpos.p, dcoll_off.p, dcoll.p, dl4_off.p, dl4.p};
+        dt.alloc(nt);
+        ck(cudaMemcpy(dt.p, tboxes.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+        near_count_kernel<<<gt, 128>>>(T, BL, dt.p, nt, dcount.p);
+        ck(cudaGetLastError());
+        hoff = csr(dcount, nt, doff);
         raw.alloc(std::max<long long>(1, hoff[nt]));
-        doff.alloc(nt + 1);
-        ck(cudaMemcpy(doff.p, hoff.data(), (nt + 1) * sizeof(long long), cudaMemcpyHostToDevice));
-        near_fill_kernel<<<(nt + 127) / 128, 128>>>(T, dt.p, nt, doff.p, raw.p, dcount.p);
+        near_fill_kernel<<<gt, 128>>>(T, BL, dt.p, nt, doff.p, raw.p, dcount.p);
         ck(cudaGetLastError());
         to_host(hmerged, dcount.p, nt);
     }
-    ck(cudaDeviceSynchronize());
+    lap(O.stats.lists_ms);
 
     // results to the host
     O.n_boxes = nb;
@@ -687,6 +801,7 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     st.n_target_boxes = nt;
     st.near_nnz = (int64_t)O.near_begin.size();
     st.center_source_pairs = pairs;
+    lap(st.download_ms);
 }
 
 }  // namespace
