@@ -165,81 +165,9 @@ struct BoxLists {
     const int *l4;
 };
 
-// Every box of the near field of target box w (List 1, List 3 close, List 4
-// close), passed to emit(box).
-template <class Emit>
-__device__ void near_field(const TreeView &T, const BoxLists &BL, int w, Emit &emit)
-{
-    int stack[kStack], sp;
-    // List 1: leaves adjacent to w that hold sources
-    sp = 0;
-    stack[sp++] = 0;
-    while (sp > 0) {
-        const int x = stack[--sp];
-        if (!adjacent(T, x, w)) continue;
-        if (T.leaf[x]) { if (T.nsrc[x] > 0) emit(x); continue; }
-        for (int o = 7; o >= 0; --o) {
-            const int c = T.child[8 * x + o];
-            if (c >= 0 && sp < kStack) stack[sp++] = c;
-        }
-    }
-    // List 3 (close part): below the colleagues' children
-    const int row = BL.pos[w];
-    for (long long i = BL.coll_off[row]; i < BL.coll_off[row + 1]; ++i)
-        for (int o = 0; o < 8; ++o) {
-            const int c0 = T.child[8 * BL.coll[i] + o];
-            if (c0 < 0) continue;
-            sp = 0;
-            stack[sp++] = c0;
-            while (sp > 0) {
-                const int d = stack[--sp];
-                if (T.nsrc[d] == 0) continue;
-                if (!adjacent(T, d, w)) {
-                    // classify the List 3 box d: close unless separated from
-                    // TCR(w) with at least n_mpole sources
-                    int st2[kStack], sp2 = 0;
-                    st2[sp2++] = d;
-                    while (sp2 > 0) {
-                        const int u = st2[--sp2];
-                        if (T.nsrc[u] == 0) continue;
-                        if (sep_box_tcr(T, u, w)) {
-                            if (T.nsrc[u] < T.n_mpole) emit(u);
-                            continue;
-                        }
-                        if (T.leaf[u]) { emit(u); continue; }
-                        for (int q = 7; q >= 0; --q) {
-                            const int c = T.child[8 * u + q];
-                            if (c >= 0 && sp2 < kStack) st2[sp2++] = c;
-                        }
-                    }
-                    continue;
-                }
-                if (T.leaf[d]) continue;
-                for (int q = 7; q >= 0; --q) {
-                    const int c = T.child[8 * d + q];
-                    if (c >= 0 && sp < kStack) stack[sp++] = c;
-                }
-            }
-        }
-    // List 4 close: raw List 4 of w and of each ancestor, not separated from TCR(w)
-    for (int a = w; a >= 0; a = T.parent[a]) {
-        const int r = BL.pos[a];
-        for (long long i = BL.l4_off[r]; i < BL.l4_off[r + 1]; ++i) {
-            const int d = BL.l4[i];
-            if (!sep_tcr_box(T, w, d)) emit(d);
-        }
-    }
-}
-
 struct CountEmit {
     int n = 0;
     __device__ void operator()(int) { ++n; }
-};
-struct FillEmit {
-    const TreeView *T;
-    int2 *out;
-    int n = 0;
-    __device__ void operator()(int b) { out[n++] = make_int2(T->sbeg[b], T->send[b]); }
 };
 struct BoxEmit {
     int *out;
@@ -277,36 +205,175 @@ __global__ void l4_kernel(const TreeView T, const int *boxes, int n, const long 
     }
 }
 
-__global__ void near_count_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt, int *count)
+// Warp-cooperative near field of target box w: one shared stack of typed
+// entries (box | mode << 29) holds the List 1 walk (from the root), the
+// List 3 walks (from the colleagues' children) and the List 3 classification;
+// each step the lanes pop up to 32 entries, process one each, and push their
+// children at offsets from a warp prefix sum.  List 4 close is a lane-strided
+// filter over the raw List 4 of w and its ancestors.  emit(lane, box) is
+// called by the lane that found the box (any order: the ranges are sorted
+// afterwards).  Returns false if the stack overflowed (never silently).
+constexpr int kWarpStack = 4096;
+constexpr int kNearWarps = 2;
+enum : int { kModeL1 = 0, kModeL3 = 1, kModeCls = 2 };
+
+template <class Emit>
+__device__ bool near_field_warp(const TreeView &T, const BoxLists &BL, int w, int lane, int *stk, Emit &emit)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nt) return;
-    CountEmit e;
-    near_field(T, BL, tboxes[i], e);
-    count[i] = e.n;
+    int top = 0;
+    bool ok = true;
+    // initial entries: the root (List 1) and the colleagues' children (List 3)
+    if (lane == 0) stk[0] = 0 | (kModeL1 << 29);
+    top = 1;
+    const int row = BL.pos[w];
+    const long long c0 = BL.coll_off[row], c1 = BL.coll_off[row + 1];
+    for (long long base = c0 * 8; base < c1 * 8; base += 32) {
+        const long long j = base + lane;
+        int c = -1;
+        if (j < c1 * 8) c = T.child[8 * BL.coll[j / 8] + (int)(j % 8)];
+        const unsigned m = __ballot_sync(0xffffffffu, c >= 0);
+        const int pos = __popc(m & ((1u << lane) - 1));
+        if (c >= 0) {
+            if (top + pos < kWarpStack) stk[top + pos] = c | (kModeL3 << 29);
+        }
+        top += __popc(m);
+        if (top > kWarpStack) ok = false;
+    }
+    __syncwarp();
+    while (top > 0 && ok) {
+        const int take = min(32, top);
+        top -= take;
+        const int e = lane < take ? stk[top + lane] : -1;
+        __syncwarp();
+        int kids[8], nk = 0, mode = 0;
+        if (e >= 0) {
+            const int x = e & ((1 << 29) - 1);
+            mode = e >> 29;
+            bool expand = false;
+            if (mode == kModeL1) {
+                if (adjacent(T, x, w)) {
+                    if (T.leaf[x]) { if (T.nsrc[x] > 0) emit(lane, x); }
+                    else expand = true;
+                }
+            } else if (T.nsrc[x] > 0) {
+                if (mode == kModeL3 && adjacent(T, x, w)) {
+                    expand = !T.leaf[x];
+                } else {                       // a List 3 box, or below one: classify
+                    mode = kModeCls;
+                    if (sep_box_tcr(T, x, w)) { if (T.nsrc[x] < T.n_mpole) emit(lane, x); }
+                    else if (T.leaf[x]) emit(lane, x);
+                    else expand = true;
+                }
+            }
+            if (expand)
+                for (int o = 0; o < 8; ++o) {
+                    const int c = T.child[8 * x + o];
+                    if (c >= 0) kids[nk++] = c;
+                }
+        }
+        // warp prefix sum of the pushes
+        int incl = nk;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (top + total > kWarpStack) { ok = false; break; }
+        const int at = top + incl - nk;
+        for (int i = 0; i < nk; ++i) stk[at + i] = kids[i] | (mode << 29);
+        top += total;
+        __syncwarp();
+    }
+    // List 4 close
+    for (int a = w; a >= 0; a = T.parent[a]) {
+        const int r = BL.pos[a];
+        for (long long i = BL.l4_off[r] + lane; i < BL.l4_off[r + 1]; i += 32) {
+            const int d = BL.l4[i];
+            if (!sep_tcr_box(T, w, d)) emit(lane, d);
+        }
+    }
+    __syncwarp();
+    return ok;
 }
 
-__global__ void near_fill_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt, const long long *off,
-                                 int2 *raw, int *merged)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nt) return;
-    FillEmit e{&T, raw + off[i]};
-    near_field(T, BL, tboxes[i], e);
-    // sort by (begin, end), then drop empty ranges and join touching ones
-    int2 *r = raw + off[i];
-    const int n = e.n;
-    for (int a = 1; a < n; ++a) {
-        const int2 v = r[a];
-        int b = a - 1;
-        while (b >= 0 && (r[b].x > v.x || (r[b].x == v.x && r[b].y > v.y))) { r[b + 1] = r[b]; --b; }
-        r[b + 1] = v;
+struct WarpCount {
+    int n = 0;
+    __device__ void operator()(int, int) { ++n; }
+};
+struct WarpFill {
+    const TreeView *T;
+    int2 *out;
+    int *cursor;             // shared per-warp append position
+    __device__ void operator()(int, int b)
+    {
+        const int k = atomicAdd(cursor, 1);
+        out[k] = make_int2(T->sbeg[b], T->send[b]);
     }
+};
+
+__global__ void __launch_bounds__(kNearWarps * 32)
+near_count_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt, int *count, int *status)
+{
+    __shared__ int stk_all[kNearWarps][kWarpStack];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kNearWarps + warp;
+    if (i >= nt) return;
+    WarpCount e;
+    const bool ok = near_field_warp(T, BL, tboxes[i], lane, stk_all[warp], e);
+    int n = e.n;
+    for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xffffffffu, n, d);
+    if (lane == 0) {
+        count[i] = n;
+        if (!ok) atomicOr(status, 1);
+    }
+}
+
+__global__ void __launch_bounds__(kNearWarps * 32)
+near_fill_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt, const long long *off, int2 *raw,
+                 int2 *sorted, int *merged, int *status)
+{
+    __shared__ int stk_all[kNearWarps][kWarpStack];
+    __shared__ int cursor[kNearWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kNearWarps + warp;
+    if (i >= nt) return;
+    if (lane == 0) cursor[warp] = 0;
+    __syncwarp();
+    WarpFill e{&T, raw + off[i], &cursor[warp]};
+    const bool ok = near_field_warp(T, BL, tboxes[i], lane, stk_all[warp], e);
+    __syncwarp();
+    if (lane == 0 && !ok) atomicOr(status, 1);
+    // rank sort by (begin, end, arrival): element k goes to position rank(k);
+    // staged in the (now free) stack when it fits
+    const int n = cursor[warp];
+    const int2 *r = raw + off[i];
+    int2 *out = sorted + off[i];
+    const int2 *src = r;
+    if (n <= kWarpStack / 2) {
+        int2 *buf = reinterpret_cast<int2 *>(stk_all[warp]);
+        for (int k = lane; k < n; k += 32) buf[k] = r[k];
+        __syncwarp();
+        src = buf;
+    }
+    for (int k = lane; k < n; k += 32) {
+        const int2 v = src[k];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+            const int2 u = src[j];
+            rank += (u.x < v.x) || (u.x == v.x && (u.y < v.y || (u.y == v.y && j < k)));
+        }
+        out[rank] = v;
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    // drop empty ranges and join touching ones (into raw)
+    int2 *m_out = raw + off[i];
     int m = 0;
     for (int a = 0; a < n; ++a) {
-        if (r[a].x == r[a].y) continue;
-        if (m > 0 && r[m - 1].y == r[a].x) r[m - 1].y = r[a].y;
-        else r[m++] = r[a];
+        const int2 v = out[a];
+        if (v.x == v.y) continue;
+        if (m > 0 && m_out[m - 1].y == v.x) m_out[m - 1].y = v.y;
+        else m_out[m++] = v;
     }
     merged[i] = m;
 }
@@ -735,7 +802,7 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
         dl.alloc(nl); dpos.alloc(nb); dcount.alloc(std::max(nl, nt));
         ck(cudaMemcpy(dl.p, lboxes.data(), nl * sizeof(int), cudaMemcpyHostToDevice));
         ck(cudaMemcpy(dpos.p, pos.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
-        const int gl = (nl + 127) / 128, gt = (nt + 127) / 128;
+        const int gl = (nl + 127) / 128;
         coll_kernel<false><<<gl, 128>>>(T, dl.p, nl, nullptr, nullptr, dcount.p);
         ck(cudaGetLastError());
         const std::vector<long long> co = csr(dcount, nl, dcoll_off);
@@ -751,13 +818,22 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
         const BoxLists BL{dpos.p, dcoll_off.p, dcoll.p, dl4_off.p, dl4.p};
         dt.alloc(nt);
         ck(cudaMemcpy(dt.p, tboxes.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
-        near_count_kernel<<<gt, 128>>>(T, BL, dt.p, nt, dcount.p);
+        DBuf<int> dstatus;
+        dstatus.alloc(1);
+        ck(cudaMemset(dstatus.p, 0, sizeof(int)));
+        const int gw = (nt + kNearWarps - 1) / kNearWarps;
+        near_count_kernel<<<gw, kNearWarps * 32>>>(T, BL, dt.p, nt, dcount.p, dstatus.p);
         ck(cudaGetLastError());
         hoff = csr(dcount, nt, doff);
         raw.alloc(std::max<long long>(1, hoff[nt]));
-        near_fill_kernel<<<gt, 128>>>(T, BL, dt.p, nt, doff.p, raw.p, dcount.p);
+        DBuf<int2> sorted;
+        sorted.alloc(std::max<long long>(1, hoff[nt]));
+        near_fill_kernel<<<gw, kNearWarps * 32>>>(T, BL, dt.p, nt, doff.p, raw.p, sorted.p, dcount.p, dstatus.p);
         ck(cudaGetLastError());
         to_host(hmerged, dcount.p, nt);
+        int hstatus = 0;
+        ck(cudaMemcpy(&hstatus, dstatus.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (hstatus) throw std::invalid_argument("near-field walk exceeded its stack");
     }
     lap(O.stats.lists_ms);
 
