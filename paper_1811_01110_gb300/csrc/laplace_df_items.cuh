@@ -69,11 +69,10 @@ __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df 
         const df S = df_add(df_mul(c1, S2), df_sub(Qp1, df_mul(q2, Qp)));
         acc_s = df_add(acc_s, df_mul(wr, S));
         const df wr3 = df_mul(wr, r2inv);
-        if (DLP) {
-            const df S1 = df_add(df_mul(df_sub(one, qx), S2), Qp1);
+        if (DLP) {                     // (b - a) S2 - a Q'_{p+1}, as in pair_fp64
             const df a = df_dot(d, n);
             const df b = df_dot(e, n);
-            const df val = df_sub(df_mul(df_sub(b, df_mul(a, qx)), S2), df_mul(a, S1));
+            const df val = df_sub(df_mul(df_sub(b, a), S2), df_mul(a, Qp1));
             acc_d = df_add(acc_d, df_mul(wr3, val));
         }
         if (SP) {

@@ -36,7 +36,8 @@ namespace tsqbx {
 // and since dQ_n/dqx = Q'_n and 2 dQ_n/dq2 = -Q'_{n-1} (the identity
 // x P'_n - P'_{n-1} = n P_n), with grad_s qx = (e - 2 qx d)/R^2,
 // grad_s q2 = -2 q2 d/R^2, grad_t qx = d/R^2 and grad_t q2 = 2 e/R^2:
-//   double layer  n_s.grad_s (S/R) = (1/R^3) [ -a S1 + (b - a qx) S2 ],
+//   double layer  n_s.grad_s (S/R) = (1/R^3) [ -a S1 + (b - a qx) S2 ]
+//                                  = (1/R^3) [ (b - a) S2 - a Q'_{p+1} ],
 //   S'            n_t.grad_t (S/R) = (1/R^3) [ (d.n_t) S2 - (e.n_t) S2m ],
 // a = d.n_s, b = e.n_s.  The closing sums cancel at most by a factor of a few
 // hundred over rho/R <= 0.9, orders 0..20, a cost of ~2e-14 in FP64.
@@ -78,10 +79,9 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
         acc_s = fma(wr, S, acc_s);
         const double wr3 = wr * r2inv;
         if (DLP) {
-            const double S1 = fma(1.0 - qx, S2, Qp1);
             const double a = fma(dx, nx, fma(dy, ny, dz * nz));
             const double b = fma(ex, nx, fma(ey, ny, ez * nz));
-            acc_d = fma(wr3, fma(-a, S1, fma(-a, qx, b) * S2), acc_d);
+            acc_d = fma(wr3, fma(-a, Qp1, (b - a) * S2), acc_d);
         }
         if (SP) {
             const double dn = fma(dx, tx, fma(dy, ty, dz * tz));
@@ -256,11 +256,10 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
         kahan_add2(as, ac, mul2(wr, S));
         const f2 wr3 = mul2(wr, r2inv);
         if (DLP) {
-            const f2 S1 = fma2(sub2(f2_splat(1.f), qx), S2, Qp1);
             const f2 a = fma2(dx, nx, fma2(dy, ny, mul2(dz, nz)));
             const f2 b = fma2(f2_splat(e.x), nx, fma2(f2_splat(e.y), ny, mul2(f2_splat(e.z), nz)));
             const f2 na = sub2(f2_splat(0.f), a);
-            kahan_add2(ds, dc, mul2(wr3, fma2(na, S1, mul2(fma2(na, qx, b), S2))));
+            kahan_add2(ds, dc, mul2(wr3, fma2(na, Qp1, mul2(sub2(b, a), S2))));
         }
         if (SP) {
             const f2 dn = fma2(dx, f2_splat(tn.x), fma2(dy, f2_splat(tn.y), mul2(dz, f2_splat(tn.z))));
