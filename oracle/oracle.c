@@ -665,7 +665,7 @@ static int qbx_conventional(const oracle_geom *g, int kernel, int p, double k,
         for (int a = 0; a < 3; ++a) v[a] = D(tx[a] - cx[a], ntv[a]);
         dual rho = dsqrt(dadd(dadd(dmul(v[0], v[0]), dmul(v[1], v[1])), dmul(v[2], v[2])));
         int nmax = p;
-        if (rho.v == 0.0) {            /* only n = 0 survives; its Y is constant */
+        if (rho.v == 0.0) {            /* value: only n = 0 survives, its Y constant (S': below) */
             nmax = 0;
             v[0] = D(0.0, 0.0); v[1] = D(0.0, 0.0); v[2] = D(1.0, 0.0);
             rho = D(0.0, 0.0);
@@ -691,6 +691,21 @@ static int qbx_conventional(const oracle_geom *g, int kernel, int p, double k,
                 double complex a0 = Lv * ev, a1 = Ld * ev, a2 = Lv * ed;
                 nsum_add(&acc[0][0], creal(a0)); nsum_add(&acc[0][1], cimag(a0));
                 nsum_add(&acc[1][0], creal(a1)); nsum_add(&acc[1][1], cimag(a1));
+                nsum_add(&acc[2][0], creal(a2)); nsum_add(&acc[2][1], cimag(a2));
+            }
+        }
+        if (out_sp && rho.v == 0.0 && p >= 1) {
+            /* S' at t = c: the limit along n_t.  Only n = 1 has a radial
+             * factor with a nonzero slope at rho = 0 (rho for Laplace, j_1(k rho)
+             * ~ k rho / 3 for Helmholtz), and its angular factor is constant
+             * along the ray, so the derivative is slope * Y_1^m(n_t). */
+            const double slope = kernel == 0 ? 1.0 : k / 3.0;
+            sph_harm_dual(p, D(ntv[0], 0.0), D(ntv[1], 0.0), D(ntv[2], 0.0), Y);
+            for (int m = -1; m <= 1; ++m) {
+                cdual Lc = L[1 + 1 + m];
+                double complex Lv = Lc.re.v + I * Lc.im.v;
+                double complex yv = Y[1 + 1 + m].re.v + I * Y[1 + 1 + m].im.v;
+                double complex a2 = Lv * slope * yv;
                 nsum_add(&acc[2][0], creal(a2)); nsum_add(&acc[2][1], cimag(a2));
             }
         }

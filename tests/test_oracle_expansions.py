@@ -54,6 +54,13 @@ def test_target_at_center_paths_agree(rng):
     a = oracle.tsqbx_helmholtz(g, 7, 3.0, mz, slp=True, dlp=True)
     b = oracle.qbx_helmholtz(g, 7, 3.0, mz, slp=True, dlp=True)
     assert rel(a["slp"], b["slp"]) < 1e-12 and rel(a["dlp"], b["dlp"]) < 1e-12
+    # S' at t = c: both paths take the limit along n_t
+    a = oracle.tsqbx_laplace(g, 7, mu, sp=True)["sp"]
+    b = oracle.qbx_laplace(g, 7, mu, sp=True)["sp"]
+    assert rel(a, b) < 1e-12
+    a = oracle.tsqbx_helmholtz(g, 7, 3.0, mz, sp=True)["sp"]
+    b = oracle.qbx_helmholtz(g, 7, 3.0, mz, sp=True)["sp"]
+    assert rel(a, b) < 1e-12
 
 
 # ------------------------------------------------------ special geometries
@@ -206,6 +213,26 @@ def test_target_normal_derivative_at_center_by_finite_differences():
             uh = oracle.tsqbx_helmholtz(g, p, k, np.array([1.0 + 0j]), sp=True)["sp"][0]
             fh = lambda tt: oracle.tsqbx_helmholtz(single_pair(tt, c, s), p, k,
                                                    np.array([1.0 + 0j]))["slp"][0]
+            fd = (fh(c + h * nt) - fh(c - h * nt)) / (2 * h)
+            assert abs(uh - fd) <= 1e-8 * abs(fd)
+
+
+def test_conventional_path_target_derivative_at_center_by_finite_differences():
+    """Path B on its own: S' at t = c equals the central difference of path
+    B's single layer through the center along n_t (Laplace and Helmholtz)."""
+    c = np.array([-0.2, 0.4, 0.1])
+    s = c + np.array([-0.4, 0.5, 0.6])
+    nt = np.array([0.6, 0.3, -0.7]); nt /= np.linalg.norm(nt)
+    h = 1e-5
+    for p in (1, 3, 8):
+        g = single_pair(c, c, s, n_t=nt)
+        u = oracle.qbx_laplace(g, p, np.array([1.0]), slp=True, sp=True)["sp"][0]
+        f = lambda tt: oracle.qbx_laplace(single_pair(tt, c, s), p, np.array([1.0]))["slp"][0]
+        assert u == pytest.approx((f(c + h * nt) - f(c - h * nt)) / (2 * h), rel=1e-8)
+        for k in (0.7, 5.0):
+            uh = oracle.qbx_helmholtz(g, p, k, np.array([1.0 + 0j]), sp=True)["sp"][0]
+            fh = lambda tt: oracle.qbx_helmholtz(single_pair(tt, c, s), p, k,
+                                                 np.array([1.0 + 0j]))["slp"][0]
             fd = (fh(c + h * nt) - fh(c - h * nt)) / (2 * h)
             assert abs(uh - fd) <= 1e-8 * abs(fd)
 
