@@ -105,8 +105,11 @@ enum {
      * group's list (P2QBXL, (p+1)^2 per source) and evaluated at each of its
      * targets (QBXL2P, (p+1)^2 per target), instead of the target-specific
      * expansion ((p+1) per target and source).  The values are the same
-     * truncated expansion (eq. tsqbx).  Laplace, FP64 only (else
-     * TSQBX_E_UNSUPPORTED); such plans accept per-call orders up to their own p. */
+     * truncated expansion (eq. tsqbx; Appendix A's addition theorem for
+     * Helmholtz).  FP64 only (else TSQBX_E_UNSUPPORTED); such plans accept
+     * per-call orders up to their own p.  Helmholtz: p <= 12 (with
+     * CONVENTIONAL_ALL a larger p is TSQBX_E_UNSUPPORTED; CONVENTIONAL_AUTO
+     * keeps every center target-specific). */
     TSQBX_FLAG_CONVENTIONAL_AUTO = 8u,  /* per center, whichever the cost model (Table 2
                                            form, GPU constants) says is cheaper        */
     TSQBX_FLAG_CONVENTIONAL_ALL = 16u   /* every center takes the conventional path     */

@@ -27,10 +27,10 @@
 // target-specific kernels evaluate (eq. tsqbx).  S' differentiates K along n_t.
 //
 // Mapping.  P2QBXL: one warp per (center, source slice); lane l takes every
-// 32nd source, walks its whole (n, m) triangle in registers, and the warp sums
-// each run of 32 coefficient parts with a reduce-scatter (lane l receives
-// part l of the run), adding it to a per-warp shared accumulator; the slice's
-// coefficients go to a partial block.  QBXL2P: one warp per (center, up to 32
+// 32nd source and walks its whole (n, m) triangle in registers, storing each
+// coefficient part to its row of a padded shared buffer; every 32 parts, lane
+// l adds up column l (the 32 sources' contributions to one part) into the
+// slice's partial block.  QBXL2P: one warp per (center, up to 32
 // targets); the center's partial blocks are summed in slice order into shared
 // memory, one lane per target.  Every sum runs in a fixed order, so results
 // are deterministic.
@@ -67,40 +67,31 @@ __host__ __device__ constexpr double conv_weight(int n, int m)
     return (m == 0 ? 1.0 : 2.0) * df * t * kInv4Pi;
 }
 
-// Lane l returns the warp-wide sum of v[l] (v is overwritten): 31 shuffles and
-// adds per lane, in a fixed pattern.
-__device__ __forceinline__ double reduce_scatter32(double (&v)[32], int lane)
-{
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const bool hi = (lane & s) != 0;
-#pragma unroll
-        for (int i = 0; i < s; ++i) {
-            const double send = hi ? v[i] : v[i + s];
-            const double keep = hi ? v[i + s] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-        }
-    }
-    return v[0];
-}
-
-// Receives the coefficient parts of one source in order; every 32 parts
-// (and at the end) the warp's parts are summed into the shared accumulator.
+// Receives the coefficient parts of one source per lane, in order: part k of
+// lane l goes to row l, column k mod 32 of the warp's padded 32 x 33 buffer;
+// after every 32 parts (and at the end) lane l adds up column l over the 32
+// rows (a fixed order) into the item's partial block, dst[32 (k / 32) + l].
+// One shared store per part keeps the unrolled (n, m) triangles short.
 template <int NC>
 struct PartSink {
-    double v[32];
-    double *acc;
+    double *buf;     // the warp's 32 x 33 doubles
+    double *dst;     // the item's NC partial coefficients (zeroed)
     int lane;
     __device__ __forceinline__ void put(int k, double x)
     {
-        v[k & 31] = x;
+        buf[33 * lane + (k & 31)] = x;
         if ((k & 31) == 31 || k == NC - 1) {
             if (k == NC - 1) {
 #pragma unroll
-                for (int i = (k & 31) + 1; i < 32; ++i) v[i] = 0.0;
+                for (int i = (k & 31) + 1; i < 32; ++i) buf[33 * lane + i] = 0.0;
             }
-            const double r = reduce_scatter32(v, lane);
-            acc[(k & ~31) + lane] += r;
+            __syncwarp();
+            double sum = 0.0;
+#pragma unroll 1
+            for (int r = 0; r < 32; ++r) sum += buf[33 * r + lane];
+            const int at = (k & ~31) + lane;
+            if (at < NC) dst[at] += sum;
+            __syncwarp();
         }
     }
 };
@@ -191,20 +182,18 @@ __global__ void __launch_bounds__(kConvWarps * 32)
 p2qbxl_kernel(const DevGeom g, const DevEval ev)
 {
     constexpr int NC = (P + 1) * (P + 1) * (int(CS) + int(CD));
-    constexpr int NPAD = (NC + 31) / 32 * 32;
-    __shared__ double acc_all[kConvWarps][NPAD];
+    __shared__ double buf_all[kConvWarps][32 * 33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kConvWarps + warp;
     if (item >= g.n_conv_items) return;                  // whole warp leaves together
     const ConvItem it = g.conv_items[item];
     const ConvCenter cc = g.conv_centers[it.center];
     const double4_32a c = g.slot_c[cc.slot_begin];
-    double *acc = acc_all[warp];
-    for (int i = lane; i < NPAD; i += 32) acc[i] = 0.0;
+    double *dst = ev.conv_coef + (int64_t)it.part * NC;
+    for (int i = lane; i < NC; i += 32) dst[i] = 0.0;
+    __syncwarp();
     const int64_t s0 = g.grp_off[cc.group];
-    PartSink<NC> sink;
-    sink.acc = acc;
-    sink.lane = lane;
+    PartSink<NC> sink{buf_all[warp], dst, lane};
     for (int base = it.src_lo; base < it.src_hi; base += 32) {
         const int k = base + lane;
         double x = 1.0, y = 0.0, z = 0.0, wm = 0.0, nx = 0.0, ny = 0.0, nz = 0.0;
@@ -221,9 +210,6 @@ p2qbxl_kernel(const DevGeom g, const DevEval ev)
         }
         conv_source<P, CS, CD>(x, y, z, wm, nx, ny, nz, sink);
     }
-    __syncwarp();
-    double *dst = ev.conv_coef + (int64_t)it.part * NC;
-    for (int i = lane; i < NC; i += 32) dst[i] = acc[i];
 }
 
 template <int P, bool CS, bool CD, bool SP>

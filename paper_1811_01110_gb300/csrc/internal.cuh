@@ -93,13 +93,20 @@ int launch_laplace_fp64(int p, unsigned layers, const DevGeom &g, const DevEval 
 int launch_laplace_mixed(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_laplace_df64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_helmholtz_fp64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
-// Conventional path (conventional.cu): coefficient formation, then evaluation.
+// Conventional path: coefficient formation, then evaluation (Laplace in
+// conventional.cu, Helmholtz in conventional_helm.cu).
 int launch_conventional(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
-// Doubles of one block of partial coefficients: (p+1)^2 per layer formed
-// (single layer when the mask has SLP or SP, double layer when it has DLP).
-inline int conv_coef_doubles(int p, unsigned layers)
+int launch_conventional_helm(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
+// Orders the Helmholtz conventional path is compiled for (its unrolled complex
+// triangles make higher orders slow to compile; the paper's Helmholtz
+// computations use p <= 12).
+constexpr int kConvHelmMaxP = 12;
+// Doubles of one block of partial coefficients: (p+1)^2 real parts per layer
+// formed (single layer when the mask has SLP or SP, double layer when it has
+// DLP), twice that for the complex Helmholtz coefficients.
+inline int conv_coef_doubles(int p, unsigned layers, bool helmholtz)
 {
-    return (p + 1) * (p + 1) * (((layers & 5u) ? 1 : 0) + ((layers & 2u) ? 1 : 0));
+    return (helmholtz ? 2 : 1) * (p + 1) * (p + 1) * (((layers & 5u) ? 1 : 0) + ((layers & 2u) ? 1 : 0));
 }
 
 // Legendre three-term recurrence in the scaled form used by every kernel:

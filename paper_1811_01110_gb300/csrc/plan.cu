@@ -167,8 +167,9 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
         if (o->precision != TSQBX_FP64) return TSQBX_E_UNSUPPORTED;
     }
-    if ((o->flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL)) &&
-        (o->kernel != TSQBX_LAPLACE || o->precision != TSQBX_FP64))
+    if ((o->flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL)) && o->precision != TSQBX_FP64)
+        return TSQBX_E_UNSUPPORTED;
+    if ((o->flags & TSQBX_FLAG_CONVENTIONAL_ALL) && o->kernel == TSQBX_HELMHOLTZ && o->p > kConvHelmMaxP)
         return TSQBX_E_UNSUPPORTED;
     if (G->n_src < 0 || G->n_ctr < 0 || G->n_tgt < 0 || G->n_group < 0) return TSQBX_E_INVAL;
     if (G->n_src > INT32_MAX || G->n_ctr > INT32_MAX || G->n_tgt > INT32_MAX || G->n_group > INT32_MAX)
@@ -226,8 +227,22 @@ void note_cuda_error(cudaError_t e) { t_last_error = cudaGetErrorName(e); }
 
 int cost_bucket(double cost) { return cost > 0 ? (int)std::floor(2.0 * std::log2(cost)) : -1; }
 
-bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers)
+bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool helmholtz)
 {
+    if (helmholtz) {
+        // FP64 operations per unit: target-specific ~13 per order per pair
+        // (plus ~18 / ~5 for the double layer / S'); conventional ~12 per
+        // real coefficient part per source (two complex products and the
+        // reduction; 2 (p+1)^2 parts per layer) plus the Hankel recurrence,
+        // ~8 per part per target plus the Bessel recurrence
+        const bool cs = (layers & (TSQBX_SLP | TSQBX_SP)) != 0, cd = (layers & TSQBX_DLP) != 0;
+        const bool spd = (layers & TSQBX_SP) != 0;
+        const double parts = 2.0 * (p + 1) * (p + 1);
+        const double f_ts = 50.0 + (p + 1) * (13.0 + (cd ? 18.0 : 0.0) + (spd ? 5.0 : 0.0));
+        const double f_p2l = parts * ((cs ? 6.0 : 0.0) + (cd ? 10.0 : 0.0)) + 40.0 * (p + 1);
+        const double f_l2p = parts * ((cs ? 4.0 : 0.0) + (cd ? 2.0 : 0.0) + (spd ? 6.0 : 0.0)) + 30.0 * (p + 20);
+        return (double)ns * f_p2l + (double)nt * f_l2p < (double)nt * (double)ns * f_ts;
+    }
     // Cost per unit in FP64-pipe operations (the form of Table 2: c_ts (p+1)
     // per target-specific pair, c_p2qbxl (p+1)^2 per source and c_qbxl2p
     // (p+1)^2 per target).  The constants were calibrated on GB300 with the
@@ -393,7 +408,8 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     else rc = launch_laplace_fp64(p, layers, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
     if (P->g.n_conv_centers > 0) {
-        rc = launch_conventional(p, layers, P->g, ev, s);
+        rc = o.kernel == TSQBX_HELMHOLTZ ? launch_conventional_helm(p, layers, P->g, ev, s)
+                                         : launch_conventional(p, layers, P->g, ev, s);
         if (rc != 0) return status_of((cudaError_t)rc);
     }
     if (P->g.n_combine > 0) {
@@ -494,12 +510,14 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         std::vector<int64_t> ctr_nt(n_ctr, 0);
         for (int64_t t = 0; t < n_tgt; ++t) ++ctr_nt[G->tgt_center[t]];
         std::vector<char> conv(n_ctr, 0);
-        if (o->flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL)) {
+        const bool conv_ok = o->kernel != TSQBX_HELMHOLTZ || o->p <= kConvHelmMaxP;
+        if ((o->flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL)) && conv_ok) {
             const bool all = (o->flags & TSQBX_FLAG_CONVENTIONAL_ALL) != 0;
             for (int64_t c = 0; c < n_ctr; ++c) {
                 if (ctr_nt[c] == 0) continue;
                 const int64_t q = G->ctr_group[c];
-                conv[c] = all || conventional_cheaper(ctr_nt[c], grp_off[q + 1] - grp_off[q], o->p, o->layers);
+                conv[c] = all || conventional_cheaper(ctr_nt[c], grp_off[q + 1] - grp_off[q], o->p, o->layers,
+                                                      o->kernel == TSQBX_HELMHOLTZ);
             }
         }
         // target slots: by group; within a group the target-specific targets
@@ -641,7 +659,8 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             g.conv_centers = P->upload(conv_centers);
             g.conv_items = P->upload(conv_items);
             g.conv_eval = P->upload(conv_eval);
-            P->conv_coef_doubles = (size_t)g.n_conv_items * (size_t)conv_coef_doubles(o->p, o->layers);
+            P->conv_coef_doubles = (size_t)g.n_conv_items *
+                                   (size_t)conv_coef_doubles(o->p, o->layers, o->kernel == TSQBX_HELMHOLTZ);
         }
         g.slot_c = P->upload(slot_c);
         g.slot_e = P->upload(slot_e);

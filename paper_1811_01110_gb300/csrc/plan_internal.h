@@ -69,7 +69,7 @@ constexpr int64_t kConvSlice = 1024;
 // Cost model (the form of the paper's Table 2, with this GPU's constants):
 // whether a center with nt targets and ns listed sources is cheaper on the
 // conventional path than on the target-specific one.
-bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers);
+bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool helmholtz);
 // Build the schedule; max_iters <= 0 picks the automatic cap.
 int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
                    int n_sm, Schedule &out);

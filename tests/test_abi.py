@@ -116,7 +116,7 @@ def test_conventional_needs_laplace_fp64(L):
     g = _tiny()
     assert _create(g, conventional="all", precision="mixed") == -9
     assert _create(g, conventional="auto", precision="df64") == -9
-    assert _create(g, kernel="helmholtz", k=1.0, conventional="all") == -9
+    assert _create(g, kernel="helmholtz", k=1.0, conventional="all", p=13) == -9
 
 
 def test_octree_inputs_rejected_on_host(L):

@@ -142,8 +142,73 @@ def test_deterministic_and_per_call_order(pkg):
 def test_unsupported_combinations(pkg):
     rng = np.random.default_rng(97)
     g = cloud_geometry(rng, n_ctr=2, n_src=30, tgt_per_ctr=3)
-    for kw in (dict(precision="mixed"), dict(precision="df64"), dict(kernel="helmholtz", k=1.0)):
+    for kw in (dict(precision="mixed"), dict(precision="df64")):
         with pytest.raises(pkg.TsqbxError) as ei:
             kernel = kw.pop("kernel", "laplace")
             pkg.Plan(g, kernel, ("slp",), p=4, conventional="all", **kw)
         assert ei.value.code == -9
+
+
+# ------------------------------------------------------------------ Helmholtz
+
+@pytest.mark.parametrize("p,k", [(0, 1.0), (1, 2.0), (4, 5.0), (8, 0.5), (10, 3.0), (12, 10.0)])
+def test_helmholtz_all_conventional(pkg, p, k):
+    rng = np.random.default_rng(600 + p)
+    g = cloud_geometry(rng, n_ctr=6, n_src=90, q_max=0.6, tgt_per_ctr=5, list_frac=0.8, rho_zero=True)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    with pkg.Plan(g, "helmholtz", ("slp", "dlp", "sp"), p=p, k=k, conventional="all") as plan:
+        out = plan.eval(mu)
+        assert plan.info()["n_conv_centers"] == 6
+    ref_a = oracle.tsqbx_helmholtz(g, p, k, mu, slp=True, dlp=True, sp=True)
+    ref_b = oracle.qbx_helmholtz(g, p, k, mu, slp=True, dlp=True, sp=True)
+    for layer in ("slp", "dlp", "sp"):
+        assert relerr(out[layer], ref_a[layer]) <= TOL, (layer, p)
+        assert relerr(out[layer], ref_b[layer]) <= TOL, (layer, p)
+
+
+@pytest.mark.parametrize("layers", [("slp",), ("dlp",), ("sp",), ("slp", "dlp"), ("dlp", "sp")])
+def test_helmholtz_layer_subsets(pkg, layers):
+    rng = np.random.default_rng(611)
+    g = cloud_geometry(rng, n_ctr=5, n_src=120, q_max=0.5, tgt_per_ctr=7, list_frac=0.9)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    with pkg.Plan(g, "helmholtz", layers, p=7, k=4.0, conventional="all") as plan:
+        out = plan.eval(mu)
+    ref = oracle.tsqbx_helmholtz(g, 7, 4.0, mu, slp=True, dlp="dlp" in layers, sp="sp" in layers)
+    for layer in layers:
+        assert relerr(out[layer], ref[layer]) <= TOL, layer
+
+
+def test_helmholtz_long_lists_and_targets(pkg):
+    rng = np.random.default_rng(613)
+    g = cloud_geometry(rng, n_ctr=3, n_src=2200, q_max=0.5, tgt_per_ctr=45, list_frac=0.95)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    with pkg.Plan(g, "helmholtz", ("slp", "dlp"), p=9, k=6.0, conventional="all") as plan:
+        out = plan.eval(mu)
+        assert plan.info()["n_conv_items"] >= 6
+    ref = oracle.tsqbx_helmholtz(g, 9, 6.0, mu, slp=True, dlp=True)
+    for layer in ("slp", "dlp"):
+        assert relerr(out[layer], ref[layer]) <= TOL, layer
+
+
+def test_helmholtz_order_cap(pkg):
+    rng = np.random.default_rng(617)
+    g = cloud_geometry(rng, n_ctr=3, n_src=60, tgt_per_ctr=20)
+    with pytest.raises(pkg.TsqbxError) as ei:
+        pkg.Plan(g, "helmholtz", ("slp",), p=13, k=2.0, conventional="all")
+    assert ei.value.code == -9
+    with pkg.Plan(g, "helmholtz", ("slp",), p=13, k=2.0, conventional="auto") as plan:
+        assert plan.info()["n_conv_centers"] == 0
+
+
+def test_helmholtz_auto_and_per_call(pkg):
+    """Many targets per center: the cost model takes the conventional path;
+    per-call order and wavenumber below the plan's."""
+    rng = np.random.default_rng(619)
+    g = cloud_geometry(rng, n_ctr=4, n_src=500, q_max=0.5, tgt_per_ctr=120, list_frac=0.9)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    with pkg.Plan(g, "helmholtz", ("slp",), p=10, k=3.0, conventional="auto") as plan:
+        assert plan.info()["n_conv_centers"] == 4
+        out = plan.eval(mu)
+        out2 = plan.eval(mu, p=6, k=1.5)
+    assert relerr(out["slp"], oracle.tsqbx_helmholtz(g, 10, 3.0, mu)["slp"]) <= TOL
+    assert relerr(out2["slp"], oracle.tsqbx_helmholtz(g, 6, 1.5, mu)["slp"]) <= TOL
