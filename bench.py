@@ -379,32 +379,41 @@ def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
 
 def leg_conventional(pkg, torch, dev, steps, warmup, flush):
     """Torus 96 x 36 quads (41,472 sources, 82,944 centers, octree lists) with
-    1, 4, 16 and 64 targets per center, Laplace SLP+DLP p = 9, FP64: the
-    target-specific path alone ("off"), conventional QBX for every center
-    ("all"), and the cost model's per-center choice ("auto")."""
+    1, 4, 16 and 64 targets per center, SLP+DLP FP64, Laplace at p = 9 and
+    Helmholtz (k = 10, plane-wave density) at p = 12: the target-specific path
+    alone ("off"), conventional QBX for every center ("all"), and the cost
+    model's per-center choice ("auto")."""
     from tsqbx_inputs import configs
     stream = torch.cuda.Stream(device=dev)
-    res = {"workload": "torus 96x36 quads, 41472 sources, 82944 centers, octree lists, targets per center "
-                       "in {1,4,16,64} (uniform in each center's half-radius ball), Laplace SLP+DLP p=9, FP64",
-           "unit": UNIT, "cases": []}
+    base = "torus 96x36 quads, 41472 sources, 82944 centers, octree lists, targets per center in {1,4,16,64} " \
+           "(uniform in each center's half-radius ball), SLP+DLP FP64, "
+    res = {"workload": base + "Laplace p=9", "unit": UNIT, "cases": []}
+    hel = {"workload": base + "Helmholtz k=10 p=12", "unit": UNIT, "cases": []}
     for tpc in (1, 4, 16, 64):
         g, mu, _ = configs.torus_near_targets(96, 36, tpc)
-        dmu = torch.from_numpy(mu).to(dev)
-        case = {"targets_per_center": tpc, "n_targets": g.n_tgt}
-        for mode in ("off", "all", "auto"):
-            plan = pkg.Plan(g, "laplace", ("slp", "dlp"), p=9, conventional=mode, device=dev.index)
-            info = plan.info()
-            outs = {l: torch.empty(g.n_tgt, dtype=torch.float64, device=dev) for l in ("slp", "dlp")}
-            step_ms, kern_ms = time_device(plan, dmu, outs, stream, steps, warmup, flush, lambda: None)
-            t = sum(step_ms) / 1e3 / steps
-            case[mode] = {"ms_per_step": 1e3 * t, "pair_terms_per_s": info["n_pair_terms"] / t,
-                          "conv_centers": info["n_conv_centers"], "conv_targets": info["n_conv_targets"]}
-            case["n_pairs"] = info["n_pairs"]
-            plan.close()
-        case["auto_vs_best"] = case["auto"]["ms_per_step"] / min(case["off"]["ms_per_step"],
-                                                                   case["all"]["ms_per_step"])
-        res["cases"].append(case)
-        del dmu
+        for kernel, p, dest in (("laplace", 9, res), ("helmholtz", 12, hel)):
+            if kernel == "helmholtz":
+                dmu = torch.from_numpy(np.ascontiguousarray(mu * np.exp(1j * 10.0 * g.src_xyz[0]))).to(dev)
+                dt, kw = torch.complex128, {"k": 10.0}
+            else:
+                dmu = torch.from_numpy(mu).to(dev)
+                dt, kw = torch.float64, {}
+            case = {"targets_per_center": tpc, "n_targets": g.n_tgt}
+            for mode in ("off", "all", "auto"):
+                plan = pkg.Plan(g, kernel, ("slp", "dlp"), p=p, conventional=mode, device=dev.index, **kw)
+                info = plan.info()
+                outs = {l: torch.empty(g.n_tgt, dtype=dt, device=dev) for l in ("slp", "dlp")}
+                step_ms, kern_ms = time_device(plan, dmu, outs, stream, steps, warmup, flush, lambda: None)
+                t = sum(step_ms) / 1e3 / steps
+                case[mode] = {"ms_per_step": 1e3 * t, "pair_terms_per_s": info["n_pair_terms"] / t,
+                              "conv_centers": info["n_conv_centers"], "conv_targets": info["n_conv_targets"]}
+                case["n_pairs"] = info["n_pairs"]
+                plan.close()
+            case["auto_vs_best"] = case["auto"]["ms_per_step"] / min(case["off"]["ms_per_step"],
+                                                                       case["all"]["ms_per_step"])
+            dest["cases"].append(case)
+            del dmu
+    res["helmholtz"] = hel
     return res
 
 

@@ -67,6 +67,20 @@ __host__ __device__ constexpr double conv_weight(int n, int m)
     return (m == 0 ? 1.0 : 2.0) * df * t * kInv4Pi;
 }
 
+// The weights as a constant-bank table, filled at compile time: indexed by the
+// (n, m) of the unrolled triangles, each is an immediate constant-bank operand.
+struct ConvWeightTable {
+    double w[21][21];
+};
+constexpr ConvWeightTable conv_weight_table()
+{
+    ConvWeightTable t{};
+    for (int n = 0; n <= 20; ++n)
+        for (int m = 0; m <= n; ++m) t.w[n][m] = conv_weight(n, m);
+    return t;
+}
+__constant__ ConvWeightTable c_conv_weight = conv_weight_table();
+
 // Receives the coefficient parts of one source per lane, in order: part k of
 // lane l goes to row l, column k mod 32 of the warp's padded 32 x 33 buffer;
 // after every 32 parts (and at the end) lane l adds up column l over the 32
@@ -243,7 +257,7 @@ qbxl2p_kernel(const DevGeom g, const DevEval ev)
     double us = 0.0, ud = 0.0, up = 0.0;
     int k = 0;
     auto take = [&](int n, int m, double kr, double ki, double k1r, double k1i) {
-        const double w = conv_weight(n, m);
+        const double w = c_conv_weight.w[n][m];
         if (CS) {
             const double mr = M[k++], mi = m > 0 ? M[k++] : 0.0;
             us = fma(w, fma(kr, mr, ki * mi), us);

@@ -43,6 +43,20 @@ __host__ __device__ constexpr double conv_helm_weight(int n, int m)
     return (m == 0 ? 1.0 : 2.0) * df * df / (fp * fm) * kInv4Pi / rec_kappa(n);
 }
 
+// The weights as a constant-bank table, filled at compile time (see
+// c_conv_weight in the Laplace path).
+struct ConvHelmWeightTable {
+    double w[kConvHelmMaxP + 1][kConvHelmMaxP + 1];
+};
+constexpr ConvHelmWeightTable conv_helm_weight_table()
+{
+    ConvHelmWeightTable t{};
+    for (int n = 0; n <= kConvHelmMaxP; ++n)
+        for (int m = 0; m <= n; ++m) t.w[n][m] = conv_helm_weight(n, m);
+    return t;
+}
+__constant__ ConvHelmWeightTable c_conv_helm_weight = conv_helm_weight_table();
+
 // The (n, m) triangle of one source: parts per (n, m) in column order:
 // single layer Re(B Jr), Im(B Jr) [, Re(B Ji), Im(B Ji) if m > 0], then the
 // double layer's four (or two) in the same pattern.
@@ -244,7 +258,7 @@ qbxl2p_helm_kernel(const DevGeom g, const DevEval ev)
     double usr = 0.0, usi = 0.0, udr = 0.0, udi = 0.0, upr = 0.0, upi = 0.0;
     int kk = 0;
     auto take = [&](int n, int m, double jr, double ji, double tr, double ti) {
-        const double wgt = conv_helm_weight(n, m);
+        const double wgt = c_conv_helm_weight.w[n][m];
         const double a = wgt * cj[n];
         if (CS) {
             const double m0r = M[kk++], m0i = M[kk++];                 // M(r)

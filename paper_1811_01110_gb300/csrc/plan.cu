@@ -227,40 +227,46 @@ void note_cuda_error(cudaError_t e) { t_last_error = cudaGetErrorName(e); }
 
 int cost_bucket(double cost) { return cost > 0 ? (int)std::floor(2.0 * std::log2(cost)) : -1; }
 
+// Cost per unit in ns, measured on GB300 (torus 96 x 36, every center on one
+// path, kernel time of whole evaluations; orders 2..20 for Laplace, 2..12 for
+// Helmholtz k = 10) and fitted in q = p + 1, the form of Table 2:
+//   target-specific, per (target, source) pair:      ts0 + ts1 q
+//   P2QBXL, per (center, source):                    c0 + c1 q + c2 q^2
+//   QBXL2P, per warp item (a center's <= 32 targets): w0 + w1 q + w2 q^2
+// Indexed by the layer bits (SLP 1, DLP 2, S' 4); S' alone costs as SLP + S'.
+struct ConvCostFit {
+    double ts[2], p2l[3], l2p[3];
+};
+constexpr ConvCostFit kLaplaceCost[8] = {
+    {{0, 0}, {0, 0, 0}, {0, 0, 0}},
+    {{0.02604, 0.005689}, {0.1122, -0.02055, 0.007475}, {0.1807, -0.2473, 0.2366}},     // slp
+    {{0.0534, 0.007602}, {0.1749, -0.04791, 0.01721}, {0.2934, -0.3058, 0.2418}},       // dlp
+    {{0.05343, 0.007597}, {0.0906, -0.01624, 0.01806}, {-0.13, -0.1184, 0.3189}},       // slp+dlp
+    {{0.04471, 0.007716}, {0.1123, -0.02061, 0.007484}, {-1.655, 0.2953, 0.5637}},      // sp
+    {{0.04471, 0.007716}, {0.1123, -0.02061, 0.007484}, {-1.655, 0.2953, 0.5637}},      // slp+sp
+    {{0.06253, 0.007715}, {0.09266, -0.01707, 0.01811}, {-1.418, 0.1222, 0.675}},       // dlp+sp
+    {{0.06249, 0.007722}, {0.09095, -0.01642, 0.01806}, {-0.8973, -0.09392, 0.6941}},   // slp+dlp+sp
+};
+constexpr ConvCostFit kHelmholtzCost[8] = {
+    {{0, 0}, {0, 0, 0}, {0, 0, 0}},
+    {{0.08178, 0.01458}, {0.08981, 0.01622, 0.01129}, {9.758, 2.279, 0.2306}},   // slp
+    {{0.1037, 0.03277}, {0.1014, 0.03242, 0.02055}, {10.16, 2.145, 0.2431}},     // dlp
+    {{0.1036, 0.03279}, {0.1264, 0.03291, 0.02829}, {10.99, 1.983, 0.4262}},     // slp+dlp
+    {{0.1012, 0.02863}, {0.08737, 0.01723, 0.01122}, {11.05, 2.606, 0.7122}},    // sp
+    {{0.1012, 0.02863}, {0.08737, 0.01723, 0.01122}, {11.05, 2.606, 0.7122}},    // slp+sp
+    {{0.139, 0.03773}, {0.1284, 0.03217, 0.02833}, {10.61, 2.948, 0.8605}},      // dlp+sp
+    {{0.1391, 0.03774}, {0.1285, 0.0325, 0.02831}, {10.79, 2.812, 0.872}},       // slp+dlp+sp
+};
+
 bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool helmholtz)
 {
-    if (helmholtz) {
-        // FP64 operations per unit: target-specific ~13 per order per pair
-        // (plus ~18 / ~5 for the double layer / S'); conventional ~12 per
-        // real coefficient part per source (two complex products and the
-        // reduction; 2 (p+1)^2 parts per layer) plus the Hankel recurrence,
-        // ~8 per part per target plus the Bessel recurrence
-        const bool cs = (layers & (TSQBX_SLP | TSQBX_SP)) != 0, cd = (layers & TSQBX_DLP) != 0;
-        const bool spd = (layers & TSQBX_SP) != 0;
-        const double parts = 2.0 * (p + 1) * (p + 1);
-        const double f_ts = 50.0 + (p + 1) * (13.0 + (cd ? 18.0 : 0.0) + (spd ? 5.0 : 0.0));
-        const double f_p2l = parts * ((cs ? 6.0 : 0.0) + (cd ? 10.0 : 0.0)) + 40.0 * (p + 1);
-        const double f_l2p = parts * ((cs ? 4.0 : 0.0) + (cd ? 2.0 : 0.0) + (spd ? 6.0 : 0.0)) + 30.0 * (p + 20);
-        return (double)ns * f_p2l + (double)nt * f_l2p < (double)nt * (double)ns * f_ts;
-    }
-    // Cost per unit in FP64-pipe operations (the form of Table 2: c_ts (p+1)
-    // per target-specific pair, c_p2qbxl (p+1)^2 per source and c_qbxl2p
-    // (p+1)^2 per target).  The constants were calibrated on GB300 with the
-    // torus at p = 9, SLP+DLP: 0.144 ns per target-specific pair (~80
-    // operations), 1.8 ns per (center, source) of coefficient formation and
-    // 0.73 ns per target of evaluation.  The split between layers follows the
-    // kernels' operation counts (the double layer's derivatives cost about
-    // twice the single layer's recurrence).
-    const bool slp_only = layers == TSQBX_SLP;
-    const bool cs = (layers & (TSQBX_SLP | TSQBX_SP)) != 0, cd = (layers & TSQBX_DLP) != 0;
-    const bool spd = (layers & TSQBX_SP) != 0;
-    const double parts = (double)(p + 1) * (p + 1);
-    const double f_ts = slp_only ? 3.0 * p + 22.0 : 4.0 * p + 32.0 + (cd ? 12.0 : 0.0) + (spd ? 6.0 : 0.0);
-    const double f_p2l = parts * ((cs ? 3.0 : 0.0) + (cd ? 7.0 : 0.0)) + 16.0;
-    const double f_l2p = parts * ((cs ? 2.5 : 0.0) + (cd ? 1.5 : 0.0) + (spd ? 5.0 : 0.0)) + 10.0;
-    const double conv = (double)ns * f_p2l + (double)nt * f_l2p;
-    const double ts = (double)nt * (double)ns * f_ts;
-    return conv < ts;
+    const ConvCostFit &f = (helmholtz ? kHelmholtzCost : kLaplaceCost)[layers & 7u];
+    const double q = p + 1.0;
+    const double ts = f.ts[0] + f.ts[1] * q;
+    const double p2l = f.p2l[0] + q * (f.p2l[1] + q * f.p2l[2]);
+    const double l2p = f.l2p[0] + q * (f.l2p[1] + q * f.l2p[2]);
+    const double warps = (double)((nt + 31) / 32);
+    return (double)ns * p2l + warps * l2p < (double)nt * (double)ns * ts;
 }
 
 int choose_lanes(int64_t nt, int64_t ns)
