@@ -271,10 +271,10 @@ def gpu_selector(dev, local_rank):
 # laplace_*_p9_torus256x96.md files and helmholtz_slp_p12_torus444x166.md).
 # A kernel changed since its capture must map to None here.
 TRAFFIC_BYTES = {
-    ("laplace", "fp64", "slp+dlp"): None,      # changed since the last capture
-    ("laplace", "mixed", "slp+dlp"): None,
-    ("laplace", "df64", "slp+dlp"): None,
-    ("helmholtz", "fp64", "slp"): 714.07e6,
+    ("laplace", "fp64", "slp+dlp"): 175.95e6,
+    ("laplace", "mixed", "slp+dlp"): 157.78e6,
+    ("laplace", "df64", "slp+dlp"): 176.06e6,
+    ("helmholtz", "fp64", "slp"): 714.85e6,
 }
 
 

@@ -54,24 +54,36 @@ __global__ void batch_prep_kernel(const BatchPlan *plans, const BatchIO *io, int
     }
 }
 
+// Where each queued item's slice starts in its plan's run lists.
+__global__ void batch_walk_kernel(const BatchPlan *plans, const Item *items, int64_t n_items, WalkStart *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_items) {
+        const Item it = items[i];
+        out[i] = walk_start_of(plans[it.pad].g, it);
+    }
+}
+
 template <bool DLP, int... Ps>
 __device__ __forceinline__ void run_item_fp64(int p, const DevGeom &g, const DevEval &ev, const Item &it,
-                                              double (*T)[kTile], int lane, std::integer_sequence<int, Ps...>)
+                                              const WalkStart &ws, double (*T)[kTile], int lane,
+                                              std::integer_sequence<int, Ps...>)
 {
-    ((p == Ps ? (laplace_fp64_item<Ps, DLP, false>(g, ev, it, T, lane), 0) : 0), ...);
+    ((p == Ps ? (laplace_fp64_item<Ps, DLP, false>(g, ev, it, ws, T, lane), 0) : 0), ...);
 }
 
 template <bool DLP, int... Ps>
 __device__ __forceinline__ void run_item_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
-                                               float4 (*T)[kMixedPairs], int lane, std::integer_sequence<int, Ps...>)
+                                               const WalkStart &ws, float4 (*T)[kMixedPairs], int lane,
+                                               std::integer_sequence<int, Ps...>)
 {
-    ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, T, lane), 0) : 0), ...);
+    ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, ws, T, lane), 0) : 0), ...);
 }
 
 template <bool MIXED, bool DLP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, int64_t n_items,
-                     unsigned long long *head)
+batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, const WalkStart *walks,
+                     int64_t n_items, unsigned long long *head)
 {
     // per-warp tile: mixed, pair records (laplace_items.cuh); FP64, one row per field
     constexpr int kWarpBytes = MIXED ? mixed_tile_rows(DLP) * kMixedPairs * 16 : (DLP ? 7 : 4) * kTile * 8;
@@ -86,16 +98,17 @@ batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *item
         const unsigned long long last = min(first + kPopChunk, (unsigned long long)n_items);
         for (unsigned long long idx = first; idx < last; ++idx) {
             const Item it = items[idx];
+            const WalkStart ws = walks[idx];
             const BatchPlan &bp = plans[it.pad];
             DevEval ev = bp.ev;
             ev.out_slp = io[it.pad].out_slp;
             ev.out_dlp = io[it.pad].out_dlp;
             unsigned char *mine = tile_raw + warp * kWarpBytes;
             if constexpr (MIXED)
-                run_item_mixed<DLP>(bp.p, bp.g, ev, it, reinterpret_cast<float4 (*)[kMixedPairs]>(mine), lane,
+                run_item_mixed<DLP>(bp.p, bp.g, ev, it, ws, reinterpret_cast<float4 (*)[kMixedPairs]>(mine), lane,
                                     std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
             else
-                run_item_fp64<DLP>(bp.p, bp.g, ev, it, reinterpret_cast<double (*)[kTile]>(mine), lane,
+                run_item_fp64<DLP>(bp.p, bp.g, ev, it, ws, reinterpret_cast<double (*)[kTile]>(mine), lane,
                                    std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
             __syncwarp();
         }
@@ -138,6 +151,7 @@ struct tsqbx_batch_s {
     BatchIO *d_io = nullptr;
     BatchIO *h_io = nullptr;               // pinned
     Item *d_items = nullptr;
+    WalkStart *d_walks = nullptr;
     BatchCombine *d_combine = nullptr;
     unsigned long long *d_head = nullptr;
     int *d_status = nullptr;
@@ -195,11 +209,11 @@ int issue(tsqbx_batch B, cudaStream_t s, bool capturing)
     if (B->n_items > 0) {
         const unsigned g = (unsigned)B->grid;
         if (B->mixed) {
-            if (B->dlp) batch_laplace_kernel<true, true><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->n_items, B->d_head);
-            else batch_laplace_kernel<true, false><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->n_items, B->d_head);
+            if (B->dlp) batch_laplace_kernel<true, true><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->d_walks, B->n_items, B->d_head);
+            else batch_laplace_kernel<true, false><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->d_walks, B->n_items, B->d_head);
         } else {
-            if (B->dlp) batch_laplace_kernel<false, true><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->n_items, B->d_head);
-            else batch_laplace_kernel<false, false><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->n_items, B->d_head);
+            if (B->dlp) batch_laplace_kernel<false, true><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->d_walks, B->n_items, B->d_head);
+            else batch_laplace_kernel<false, false><<<g, kWarpsPerBlock * 32, 0, s>>>(B->d_plans, B->d_io, B->d_items, B->d_walks, B->n_items, B->d_head);
         }
         ck(cudaGetLastError());
     }
@@ -286,8 +300,14 @@ int tsqbx_batch_create(const tsqbx_plan *plans, int n_plans, int use_graph, tsqb
         B->d_plans = B->dalloc<BatchPlan>(n_plans);
         ck(cudaMemcpy(B->d_plans, bp.data(), sizeof(BatchPlan) * n_plans, cudaMemcpyHostToDevice));
         B->d_items = B->dalloc<Item>(item_v.size());
-        if (!item_v.empty())
+        B->d_walks = B->dalloc<WalkStart>(item_v.size());
+        if (!item_v.empty()) {
             ck(cudaMemcpy(B->d_items, item_v.data(), sizeof(Item) * item_v.size(), cudaMemcpyHostToDevice));
+            const int64_t wb = ((int64_t)item_v.size() + 255) / 256;
+            batch_walk_kernel<<<(unsigned)wb, 256>>>(B->d_plans, B->d_items, B->n_items, B->d_walks);
+            ck(cudaGetLastError());
+            ck(cudaStreamSynchronize(0));
+        }
         B->d_combine = B->dalloc<BatchCombine>(comb.size());
         if (!comb.empty())
             ck(cudaMemcpy(B->d_combine, comb.data(), sizeof(BatchCombine) * comb.size(), cudaMemcpyHostToDevice));

@@ -195,14 +195,14 @@ p2qbxl_helm_kernel(const DevGeom g, const DevEval ev)
     double *dst = ev.conv_coef + (int64_t)it.part * NC;
     for (int i = lane; i < NC; i += 32) dst[i] = 0.0;
     __syncwarp();
-    const int64_t s0 = g.grp_off[cc.group];
+    ListWalk walk(g, cc.group);
     PartSink<NC> sink{buf_all[warp], dst, lane};
     for (int base = it.src_lo; base < it.src_hi; base += 32) {
         const int kq = base + lane;
         double x = 1.0, y = 0.0, z = 0.0, nx = 0.0, ny = 0.0, nz = 0.0;
         double2 wm = make_double2(0.0, 0.0);
         if (kq < it.src_hi) {
-            const int s = g.grp_src[s0 + kq];
+            const int s = walk.at(kq);
             if ((unsigned)s >= (unsigned)g.n_src) {
                 atomicOr(ev.status, 1);
             } else {

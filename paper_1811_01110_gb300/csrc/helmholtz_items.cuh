@@ -10,71 +10,63 @@
 namespace tsqbx {
 namespace {
 
-// Per-target radial factors, orders 0..p (z = k rho):
+// Per-target radial factors, orders 0..P (z = k rho):
 //   cj[n]  = (2n+1) kappa_n j_n(z)
 //   caj[n] = (2n+1) kappa_n k j_n'(z) (that.n_t)        (S' only)
 // j_n by Miller's downward recurrence (f_{n-1} = (2n+1)/z f_n - f_{n+1}),
-// started p + 20 + ceil(z) orders up and normalised against j_0 = sin z / z
+// started P + 20 + ceil(z) orders up and normalised against j_0 = sin z / z
 // or j_1 = sin z / z^2 - cos z / z, whichever is larger; j_n' = (n/z) j_n -
-// j_{n+1} (the run also yields j_{p+1}).  z = 0: j_0 = 1, j_1' = 1/3, rest 0.
-// Once per target, so it runs as a plain loop (not unrolled) over local
-// arrays: p + 2 <= 22 entries.
-__device__ __noinline__ void helmholtz_bessel(int p, double k, double rho, double tdot, bool sp, double *cj,
-                                              double *caj)
+// j_{n+1} (the run also yields j_{P+1}).  z = 0: j_0 = 1, j_1' = 1/3, rest 0.
+// The run above P keeps two scalars; orders P+1..0 are unrolled, so every
+// array here stays in registers.
+template <int P, bool SP>
+__device__ __forceinline__ void helmholtz_target_factors(double k, double rho, double tdot, double (&cj)[P + 1],
+                                                         double (&caj)[SP ? P + 1 : 1])
 {
     const double z = k * rho;
-    double jn[22];
+    double jn[P + 2];
     if (z == 0.0) {
-        jn[0] = 1.0;
-        for (int n = 1; n <= p + 1; ++n) jn[n] = 0.0;
+#pragma unroll
+        for (int n = 0; n <= P + 1; ++n) jn[n] = n == 0 ? 1.0 : 0.0;
     } else {
         const double zinv = 1.0 / z;
-        const int N = p + 20 + (int)fmin(ceil(z), 1.0e6);   // no int overflow for huge k rho
+        const int N = P + 20 + (int)fmin(ceil(z), 1.0e6);   // no int overflow for huge k rho
         double fa = 0.0, fb = 1e-30;           // f_{n+1}, f_n
-        for (int n = N; n > p; --n) {
+        for (int n = N; n > P; --n) {
             const double fnew = (2.0 * n + 1.0) * zinv * fb - fa;
             fa = fb;
             fb = fnew;
             if (fabs(fb) > 1e200) { fa *= 1e-200; fb *= 1e-200; }
         }
-        jn[p + 1] = fa;
-        jn[p] = fb;
-        for (int n = p; n >= 1; --n) {
+        jn[P + 1] = fa;
+        jn[P] = fb;
+#pragma unroll
+        for (int n = P; n >= 1; --n) {
             jn[n - 1] = (2.0 * n + 1.0) * zinv * jn[n] - jn[n + 1];
-            if (fabs(jn[n - 1]) > 1e200)
-                for (int m = n - 1; m <= p + 1; ++m) jn[m] *= 1e-200;
+            if (fabs(jn[n - 1]) > 1e200) {
+#pragma unroll
+                for (int m = n - 1; m <= P + 1; ++m) jn[m] *= 1e-200;
+            }
         }
         double sn, cs;
         sincos(z, &sn, &cs);
         const double j0 = sn * zinv;
         const double j1 = (sn * zinv - cs) * zinv;
         const double scale = fabs(j1) > fabs(j0) ? j1 / jn[1] : j0 / jn[0];
-        for (int n = 0; n <= p + 1; ++n) jn[n] *= scale;
+#pragma unroll
+        for (int n = 0; n <= P + 1; ++n) jn[n] *= scale;
     }
     double kap = 1.0;                                   // kappa_n
     const double zinv = z == 0.0 ? 0.0 : 1.0 / z;
-    for (int n = 0; n <= p; ++n) {
+#pragma unroll
+    for (int n = 0; n <= P; ++n) {
         const double f = (2.0 * n + 1.0) * kap;
         cj[n] = f * jn[n];
-        if (sp) {
+        if (SP) {
             const double jd = z == 0.0 ? (n == 1 ? 1.0 / 3.0 : 0.0) : fma(n * zinv, jn[n], -jn[n + 1]);
-            caj[n] = f * k * jd * tdot;
+            caj[SP ? n : 0] = f * k * jd * tdot;
         }
         kap *= (2.0 * n + 1.0) / (n + 1.0);
-    }
-}
-
-template <int P, bool SP>
-__device__ __forceinline__ void helmholtz_target_factors(double k, double rho, double tdot, double (&cj)[P + 1],
-                                                         double (&caj)[SP ? P + 1 : 1])
-{
-    double lc[P + 1], la[P + 1];
-    helmholtz_bessel(P, k, rho, tdot, SP, lc, la);
-#pragma unroll
-    for (int n = 0; n <= P; ++n) cj[n] = lc[n];
-    if (SP) {
-#pragma unroll
-        for (int n = 0; n <= P; ++n) caj[SP ? n : 0] = la[n];
     }
 }
 
@@ -122,7 +114,7 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
         }
         helmholtz_target_factors<P, SP>(k, rho, tdot, cj, caj);
     }
-    const int64_t s0 = g.grp_off[it.group];
+    ListWalk walk(g, g.item_walk[item]);
     const int src_hi = it.src_hi;
     double (*T)[kTile] = tile[warp];
     double acc_re = 0.0, acc_im = 0.0, dacc_re = 0.0, dacc_im = 0.0, pacc_re = 0.0, pacc_im = 0.0;
@@ -130,7 +122,7 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
     for (int base = it.src_lo; base < src_hi; base += kTile) {
         const int cnt = min(kTile, src_hi - base);
         for (int kk = lane; kk < cnt; kk += 32) {
-            int s = g.grp_src[s0 + base + kk];
+            int s = walk.at(base + kk);
             double2 wm = make_double2(0.0, 0.0);
             if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
             else wm = ev.wmu_c[s];

@@ -41,13 +41,29 @@ struct __align__(16) ConvEvalItem {          // QBXL2P: one center, <= 32 of its
     int32_t center, slot_begin, n_tgt, pad;
 };
 
+// Where an item's slice [src_lo, src_hi) of its group's list starts: run r,
+// which covers the positions [p0, p1) and starts at source s0.  Computed once
+// per schedule on the device, so an item's first sources load straight after
+// the item record.
+struct __align__(16) WalkStart {
+    int32_t r, p0, p1, s0;
+};
+
 // Everything a kernel needs about a plan's geometry (device pointers).
 struct DevGeom {
     int64_t n_src = 0, n_tgt = 0, n_items = 0, n_combine = 0, n_parts = 0;
     const Item *items = nullptr;
     const Combine *combine = nullptr;
-    const int64_t *grp_off = nullptr;   // [n_group+1] offsets into grp_src
-    const int32_t *grp_src = nullptr;   // flattened source indices of each group
+    // Each group's source list as merged runs of consecutive sources: run r
+    // (grp_run[q] <= r < grp_run[q+1]) holds the list positions up to
+    // run_end[r] (exclusive; the group's previous run, or 0, gives its first)
+    // and the sources run_src[r], run_src[r] + 1, ...  See ListWalk.
+    const int64_t *grp_off = nullptr;   // [n_group+1] prefix sums of the list lengths
+    const int32_t *grp_run = nullptr;   // [n_group+1] offsets into the run arrays
+    const int32_t *run_end = nullptr;   // [n_runs] end of each run, as a list position
+    const int32_t *run_src = nullptr;   // [n_runs] first source of each run
+    int32_t n_runs = 0;
+    const WalkStart *item_walk = nullptr;  // [n_items] where each item's slice starts
     // FP64 source records
     const double4_32a *src_pw = nullptr;    // {x, y, z, w}
     const double4_32a *src_n = nullptr;     // {nx, ny, nz, 0}
@@ -70,6 +86,58 @@ struct DevGeom {
     const ConvItem *conv_items = nullptr;
     const ConvEvalItem *conv_eval = nullptr;
 };
+
+// Source index at position k of one group's list, for positions that never
+// decrease from one call to the next (each lane walks its own positions).
+// Moving to the next run costs two loads from the small run arrays, which
+// stay in cache; the list itself is never stored one entry per source.
+// Positions must lie in the group's list; the walk never leaves the run arrays.
+struct ListWalk {
+    const int32_t *src, *end;
+    int r, p0, p1, s0, r_last;
+    __device__ __forceinline__ ListWalk(const DevGeom &g, const WalkStart &w)
+        : src(g.run_src), end(g.run_end), r(w.r), p0(w.p0), p1(w.p1), s0(w.s0), r_last(g.n_runs - 1)
+    {
+    }
+    // from the start of the group's list
+    __device__ __forceinline__ ListWalk(const DevGeom &g, int group)
+        : src(g.run_src), end(g.run_end), r(g.grp_run[group]), p0(0), r_last(g.n_runs - 1)
+    {
+        if (r < g.grp_run[group + 1]) {
+            s0 = src[r];
+            p1 = end[r];
+        } else {
+            s0 = 0;
+            p1 = 0;
+        }
+    }
+    __device__ __forceinline__ int at(int k)
+    {
+        while (k >= p1 && r < r_last) {
+            ++r;
+            p0 = p1;
+            s0 = src[r];
+            p1 = end[r];
+        }
+        return s0 + (k - p0);
+    }
+};
+
+// The WalkStart of an item: the run of its group's list that holds position
+// src_lo (a scan from the group's first run; an empty list gives p1 = 0).
+__device__ __forceinline__ WalkStart walk_start_of(const DevGeom &g, const Item &it)
+{
+    int r = g.grp_run[it.group];
+    const int r_end = g.grp_run[it.group + 1];
+    if (r >= r_end) return WalkStart{r, 0, 0, 0};
+    int p0 = 0, p1 = g.run_end[r];
+    while (it.src_lo >= p1 && r + 1 < r_end) {
+        p0 = p1;
+        ++r;
+        p1 = g.run_end[r];
+    }
+    return WalkStart{r, p0, p1, g.run_src[r]};
+}
 
 // Per-evaluation buffers (device pointers).
 struct DevEval {

@@ -108,9 +108,9 @@ __device__ __forceinline__ void df_target_normal(const DevGeom &g, int slot, con
 
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                float4 (*T)[kTile], const int lane)
+                                                const WalkStart &ws, float4 (*T)[kTile], const int lane)
 {
-    const int64_t s0 = g.grp_off[it.group];
+    ListWalk walk(g, ws);
     const int src_hi = it.src_hi;
     df acc_s{0.f, 0.f}, acc_d{0.f, 0.f}, acc_p{0.f, 0.f};
     const df3 zero3{{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -124,7 +124,7 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
         if (SP) df_target_normal(g, it.slot_begin, e4, tn, ent);
 #pragma unroll 1
         for (int k = it.src_lo + lane; k < src_hi; k += 32) {
-            int s = g.grp_src[s0 + k];
+            int s = walk.at(k);
             double wmd = 0.0;
             if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
             else wmd = ev.wmu[s];
@@ -161,7 +161,7 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
     for (int base = it.src_lo; base < src_hi; base += kTile) {
         const int cnt = min(kTile, src_hi - base);
         for (int k = lane; k < cnt; k += 32) {
-            int s = g.grp_src[s0 + base + k];
+            int s = walk.at(base + k);
             double wmd = 0.0;
             if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
             else wmd = ev.wmu[s];
@@ -211,7 +211,7 @@ laplace_df_kernel(const DevGeom g, const DevEval ev)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
-    laplace_df_item<P, DLP, SP>(g, ev, g.items[item], tile[warp], lane);
+    laplace_df_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], tile[warp], lane);
 }
 
 template <bool SP, int P>

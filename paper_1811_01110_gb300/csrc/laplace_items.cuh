@@ -127,9 +127,9 @@ __device__ __forceinline__ double warp_sum(double v)
 
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                  double (*T)[kTile], const int lane)
+                                                  const WalkStart &ws, double (*T)[kTile], const int lane)
 {
-    const int64_t s0 = g.grp_off[it.group];
+    ListWalk walk(g, ws);
     const int src_hi = it.src_hi;
     double acc_s = 0.0, acc_d = 0.0, acc_p = 0.0;
     if (it.n_tgt == 1) {                                   // direct loads, all 32 lanes
@@ -143,7 +143,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
         }
 #pragma unroll 2
         for (int k = it.src_lo + lane; k < src_hi; k += 32) {
-            int s = g.grp_src[s0 + k];
+            int s = walk.at(k);
             double wm = 0.0;
             if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
             else wm = ev.wmu[s];
@@ -177,7 +177,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
     for (int base = it.src_lo; base < src_hi; base += kTile) {
         const int cnt = min(kTile, src_hi - base);
         for (int k = lane; k < cnt; k += 32) {
-            int s = g.grp_src[s0 + base + k];
+            int s = walk.at(base + k);
             double wm = 0.0;
             if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
             else wm = ev.wmu[s];
@@ -284,15 +284,15 @@ __device__ __forceinline__ double kahan2_value(f2 s, f2 c)
 constexpr int kMixedPairs = kTile / 2;
 __host__ __device__ constexpr int mixed_tile_rows(bool dlp) { return dlp ? 5 : 4; }
 
-// Load sources k0 and k1 (k1 < 0: a zero-weight copy of k0) of a group's list
-// as packed operands.
+// Load the list positions k0 and k1 (k1 < 0: a zero-weight copy of k0) of a
+// group's list as packed operands; k0 < k1, neither before the walk's last call.
 template <bool DLP>
-__device__ __forceinline__ void load_mixed_pair(const DevGeom &g, const DevEval &ev, int64_t s0, int k0, int k1,
+__device__ __forceinline__ void load_mixed_pair(const DevGeom &g, const DevEval &ev, ListWalk &walk, int k0, int k1,
                                                 f2 &hx, f2 &hy, f2 &hz, f2 &w, f2 &lx, f2 &ly, f2 &lz, f2 &nx,
                                                 f2 &ny, f2 &nz)
 {
-    int sa = g.grp_src[s0 + k0];
-    int sb = k1 >= 0 ? g.grp_src[s0 + k1] : sa;
+    int sa = walk.at(k0);
+    int sb = k1 >= 0 ? walk.at(k1) : sa;
     float wa = 0.f, wb = 0.f;
     if ((unsigned)sa >= (unsigned)g.n_src) { atomicOr(ev.status, 1); sa = 0; } else wa = ev.wmu_f[sa];
     if ((unsigned)sb >= (unsigned)g.n_src) { atomicOr(ev.status, 1); sb = 0; } else if (k1 >= 0) wb = ev.wmu_f[sb];
@@ -309,9 +309,9 @@ __device__ __forceinline__ void load_mixed_pair(const DevGeom &g, const DevEval 
 
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                   float4 (*T)[kMixedPairs], const int lane)
+                                                   const WalkStart &ws, float4 (*T)[kMixedPairs], const int lane)
 {
-    const int64_t s0 = g.grp_off[it.group];
+    ListWalk walk(g, ws);
     const int src_hi = it.src_hi;
     const f2 z2 = f2_splat(0.f);
     f2 as = z2, ac = z2, ds = z2, dc = z2, ps = z2, pc = z2;   // Kahan pairs
@@ -327,7 +327,7 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         }
         for (int k = it.src_lo + lane; k < src_hi; k += 64) {
             f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
-            load_mixed_pair<DLP>(g, ev, s0, k, k + 32 < src_hi ? k + 32 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
+            load_mixed_pair<DLP>(g, ev, walk, k, k + 32 < src_hi ? k + 32 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
             pair_mixed2<P, DLP, SP>(hx, hy, hz, w, lx, ly, lz, nx, ny, nz, ch, cl, e, tn, as, ac, ds, dc, ps, pc);
         }
         const double acc_s = warp_sum(kahan2_value(as, ac));
@@ -355,7 +355,7 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         if (lane < npairs) {                           // lane stages pair `lane`
             const int k0 = base + 2 * lane;
             f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
-            load_mixed_pair<DLP>(g, ev, s0, k0, 2 * lane + 1 < cnt ? k0 + 1 : -1, hx, hy, hz, w, lx, ly, lz, nx,
+            load_mixed_pair<DLP>(g, ev, walk, k0, 2 * lane + 1 < cnt ? k0 + 1 : -1, hx, hy, hz, w, lx, ly, lz, nx,
                                  ny, nz);
             float a0, a1, b0, b1;
             f2_split(hx, a0, a1); f2_split(hy, b0, b1); T[0][lane] = make_float4(a0, a1, b0, b1);

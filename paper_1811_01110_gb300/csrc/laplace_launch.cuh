@@ -21,7 +21,7 @@ laplace_fp64_kernel(const DevGeom g, const DevEval ev)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;                       // whole warp leaves together
-    laplace_fp64_item<P, DLP, SP>(g, ev, g.items[item], tile[warp], lane);
+    laplace_fp64_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], tile[warp], lane);
 }
 
 template <int P, bool DLP, bool SP>
@@ -32,7 +32,7 @@ laplace_mixed_kernel(const DevGeom g, const DevEval ev)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
-    laplace_mixed_item<P, DLP, SP>(g, ev, g.items[item], tile[warp], lane);
+    laplace_mixed_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], tile[warp], lane);
 }
 
 template <bool MIXED, int P, bool DLP, bool SP>

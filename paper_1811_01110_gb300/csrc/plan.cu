@@ -52,6 +52,13 @@ __global__ void prep_wmu_c128(const double4_32a *src_pw, const double2 *mu, int6
 }
 
 // Convergence check over every listed pair (same item walk as the kernels):
+// Where each item's slice starts in its group's run list (WalkStart).
+__global__ void walk_start_kernel(const DevGeom g, WalkStart *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < g.n_items) out[i] = walk_start_of(g, g.items[i]);
+}
+
 // counts |t-c|^2 >= |s-c|^2 (outside the expansion's region of convergence,
 // Appendix A) and s == c.
 __global__ void check_pairs_kernel(const DevGeom g, unsigned long long *n_div,
@@ -61,13 +68,13 @@ __global__ void check_pairs_kernel(const DevGeom g, unsigned long long *n_div,
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
     const Item it = g.items[item];
-    const int64_t s0 = g.grp_off[it.group];
     unsigned long long nd = 0, nz = 0;
     for (int j = 0; j < it.n_tgt; ++j) {
         const double4_32a c = g.slot_c[it.slot_begin + j];
         const double rho2 = g.slot_e[it.slot_begin + j].w;
+        ListWalk walk(g, it.group);
         for (int k = it.src_lo + lane; k < it.src_hi; k += 32) {
-            const int s = g.grp_src[s0 + k];
+            const int s = walk.at(k);
             if ((unsigned)s >= (unsigned)g.n_src) continue;
             const double4_32a p = g.src_pw[s];
             const double dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
@@ -357,6 +364,15 @@ void apply_schedule(tsqbx_plan P, Schedule &&s)
     P->g.items = P->upload(items);
     P->g.combine = P->upload(s.combine);
     P->g.n_items = (int64_t)items.size();
+    if (P->g.item_walk) P->dfree(P->g.item_walk);
+    WalkStart *walks = P->dalloc<WalkStart>(items.size());
+    P->g.item_walk = walks;
+    if (!items.empty()) {
+        const int64_t blocks = ((int64_t)items.size() + 255) / 256;
+        walk_start_kernel<<<(unsigned)blocks, 256>>>(P->g, walks);
+        ck(cudaGetLastError());
+        ck(cudaStreamSynchronize(0));
+    }
     P->g.n_combine = (int64_t)s.combine.size();
     P->g.n_parts = s.n_parts;
     const size_t part_doubles = (size_t)s.n_parts * (helm ? 2 : 1);
@@ -505,11 +521,25 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
             if (ns > INT32_MAX) { delete P; return TSQBX_E_INVAL; }
             grp_off[q + 1] = grp_off[q] + ns;
         }
-        std::vector<int32_t> grp_src((size_t)grp_off[n_group]);
+        // the lists as merged runs: a range that continues the previous one
+        // extends its run; empty ranges add nothing
+        std::vector<int32_t> grp_run(n_group + 1, 0), run_end, run_src;
         for (int64_t q = 0; q < n_group; ++q) {
-            int64_t w = grp_off[q];
-            for (int64_t r = G->group_range_start[q]; r < G->group_range_start[q + 1]; ++r)
-                for (int32_t s = G->range_begin[r]; s < G->range_end[r]; ++s) grp_src[w++] = s;
+            int32_t at = 0, prev_end = -1;
+            for (int64_t r = G->group_range_start[q]; r < G->group_range_start[q + 1]; ++r) {
+                const int32_t b = G->range_begin[r], e = G->range_end[r];
+                if (e <= b) continue;
+                at += e - b;
+                if (b == prev_end) {
+                    run_end.back() = at;
+                } else {
+                    run_end.push_back(at);
+                    run_src.push_back(b);
+                }
+                prev_end = e;
+            }
+            if (run_end.size() > (size_t)INT32_MAX - 1) { delete P; return TSQBX_E_INVAL; }
+            grp_run[q + 1] = (int32_t)run_end.size();
         }
         // path of each center: conventional QBX or target-specific
         const int64_t n_ctr = G->n_ctr;
@@ -644,7 +674,10 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         g.n_src = n_src;
         g.n_tgt = n_tgt;
         g.grp_off = P->upload(grp_off);
-        g.grp_src = P->upload(grp_src);
+        g.grp_run = P->upload(grp_run);
+        g.run_end = P->upload(run_end);
+        g.run_src = P->upload(run_src);
+        g.n_runs = (int32_t)run_end.size();
         g.src_pw = P->upload(src_pw);
         if (dlp) g.src_n = P->upload(src_n);
         if (mixed) {

@@ -42,7 +42,6 @@ struct GeomCopy {
     std::vector<int32_t> tgt_center, ctr_group, range_begin, range_end;
     std::vector<int64_t> group_range_start;
     tsqbx_geometry view{};
-    int64_t list_entries = 0;
 };
 
 using PlanKey = std::tuple<int, int, unsigned, int>;   // geom, kernel, layers, precision
@@ -73,10 +72,11 @@ struct Request {
 
 size_t estimate_bytes(const GeomCopy &g, const tsqbx_options &o)
 {
-    // the larger device arrays of a plan (sources, lists, target slots, slot buffers)
+    // the larger device arrays of a plan (sources, list runs, target slots,
+    // slot buffers); the ranges bound the merged runs (8 bytes each)
     const size_t ns = (size_t)g.view.n_src, nt = (size_t)g.view.n_tgt;
     const bool helm = o.kernel == TSQBX_HELMHOLTZ, mixed = o.precision == TSQBX_MIXED;
-    size_t b = ns * 32 + (size_t)g.list_entries * 4 + nt * (4 + 64) + (size_t)g.view.n_group * 8;
+    size_t b = ns * 32 + g.range_begin.size() * 8 + nt * (4 + 64) + (size_t)g.view.n_group * 12;
     if (o.layers & TSQBX_DLP) b += ns * 32;
     if (o.layers & TSQBX_SP) b += nt * 32;
     if (mixed) b += ns * 48 + nt * 48;
@@ -289,7 +289,6 @@ int tsqbx_server_add_geometry(tsqbx_server S, const tsqbx_geometry *G, int *geom
         cp(G->group_range_start, G->n_group + 1, g->group_range_start);
         cp(G->range_begin, nnz, g->range_begin);
         cp(G->range_end, nnz, g->range_end);
-        for (int64_t i = 0; i < nnz; ++i) g->list_entries += (int64_t)G->range_end[i] - G->range_begin[i];
         auto ptr = [](auto &v) { return v.empty() ? nullptr : v.data(); };
         g->view = tsqbx_geometry{G->n_src, ptr(g->src_xyz), ptr(g->src_weight), ptr(g->src_normal),
                                  G->n_ctr, ptr(g->ctr_xyz), ptr(g->ctr_radius), G->n_tgt, ptr(g->tgt_xyz),

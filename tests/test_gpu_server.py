@@ -97,10 +97,14 @@ def test_results_same_alone_and_in_the_mix(pkg):
 def test_admission_eviction_and_rejection(pkg):
     geoms = _geoms()
     rng = np.random.default_rng(83)
-    # a budget that holds about one of the larger plans at a time
-    with pkg.Plan(geoms[2], "laplace", ("slp",), p=5) as probe:
-        one = probe.footprint()
-    with pkg.Server(hbm_budget=int(1.6 * one), max_inflight=8) as srv:
+    # a budget that holds the largest plan but never all three at once
+    fps = []
+    for g in geoms[:3]:
+        with pkg.Plan(g, "laplace", ("slp",), p=5) as probe:
+            fps.append(probe.footprint())
+    budget = max(fps) + min(fps) // 2
+    assert budget < sum(fps)
+    with pkg.Server(hbm_budget=budget, max_inflight=8) as srv:
         gids = [srv.add_geometry(g) for g in geoms]
         rids = []
         for i in range(12):
@@ -111,7 +115,7 @@ def test_admission_eviction_and_rejection(pkg):
             assert srv.poll(rid, timeout_us=-1)
         st = srv.stats()
         assert st["completed"] == 12 and st["plans_evicted"] > 0
-        assert st["resident_bytes"] <= int(1.6 * one)
+        assert st["resident_bytes"] <= budget
     # a plan that can never fit the budget is rejected, not queued forever
     with pkg.Server(hbm_budget=1 << 10, max_inflight=4) as srv:
         gid = srv.add_geometry(geoms[0])
