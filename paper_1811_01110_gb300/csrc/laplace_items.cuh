@@ -13,6 +13,7 @@
 //    butterfly reduction.
 #pragma once
 
+#include "dfloat.cuh"
 #include "f32x2.cuh"
 #include "internal.cuh"
 
@@ -268,13 +269,39 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
     }
 }
 
-// Sum of the two halves of a Kahan-compensated packed sum, in FP64.
-__device__ __forceinline__ double kahan2_value(f2 s, f2 c)
+// A lane's Kahan-compensated packed sums (two halves, each s - c) as one
+// double-float value, and its sums across lanes in double-float: the lanes'
+// partial sums meet on the FP32 pipes, and only the writing lane converts the
+// total to FP64.  (An FP64 reduction per item costs ~12 FP64 operations per
+// lane, which on a 2-DFMA/clk/SM part rivals the pair work of short lists.)
+__device__ __forceinline__ df kahan2_df(f2 s, f2 c)
 {
     float s0, s1, c0, c1;
     f2_split(s, s0, s1);
     f2_split(c, c0, c1);
-    return ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
+    return df_add(two_sum(s0, -c0), two_sum(s1, -c1));
+}
+
+__device__ __forceinline__ df df_shfl_xor(df v, int off)
+{
+    return df{__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+
+__device__ __forceinline__ df warp_sum_df(df v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
+    return v;
+}
+
+// Sum over the L lanes of each target's segment (sub = 0 holds the total).
+__device__ __forceinline__ df segment_sum_df(df v, int sub, int L)
+{
+    for (int off = 1; off < L; off <<= 1) {
+        const df u{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+        if (sub + off < L) v = df_add(v, u);
+    }
+    return v;
 }
 
 // Shared-memory tile of the mixed item, two sources per record (pair j holds
@@ -330,10 +357,11 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
             load_mixed_pair<DLP>(g, ev, walk, k, k + 32 < src_hi ? k + 32 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
             pair_mixed2<P, DLP, SP>(hx, hy, hz, w, lx, ly, lz, nx, ny, nz, ch, cl, e, tn, as, ac, ds, dc, ps, pc);
         }
-        const double acc_s = warp_sum(kahan2_value(as, ac));
-        const double acc_d = DLP ? warp_sum(kahan2_value(ds, dc)) : 0.0;
-        const double acc_p = SP ? warp_sum(kahan2_value(ps, pc)) : 0.0;
-        if (lane == 0) write_item_result<DLP, SP>(g, ev, it, 0, acc_s, acc_d, acc_p);
+        const df acc_s = warp_sum_df(kahan2_df(as, ac));
+        const df acc_d = DLP ? warp_sum_df(kahan2_df(ds, dc)) : df{0.f, 0.f};
+        const df acc_p = SP ? warp_sum_df(kahan2_df(ps, pc)) : df{0.f, 0.f};
+        if (lane == 0)
+            write_item_result<DLP, SP>(g, ev, it, 0, df_to_double(acc_s), df_to_double(acc_d), df_to_double(acc_p));
         return;
     }
     const int L = it.L;
@@ -375,10 +403,11 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         }
         __syncwarp();
     }
-    const double acc_s = segment_sum(kahan2_value(as, ac), sub, L);
-    const double acc_d = DLP ? segment_sum(kahan2_value(ds, dc), sub, L) : 0.0;
-    const double acc_p = SP ? segment_sum(kahan2_value(ps, pc), sub, L) : 0.0;
-    if (active && sub == 0) write_item_result<DLP, SP>(g, ev, it, j, acc_s, acc_d, acc_p);
+    const df acc_s = segment_sum_df(kahan2_df(as, ac), sub, L);
+    const df acc_d = DLP ? segment_sum_df(kahan2_df(ds, dc), sub, L) : df{0.f, 0.f};
+    const df acc_p = SP ? segment_sum_df(kahan2_df(ps, pc), sub, L) : df{0.f, 0.f};
+    if (active && sub == 0)
+        write_item_result<DLP, SP>(g, ev, it, j, df_to_double(acc_s), df_to_double(acc_d), df_to_double(acc_p));
 }
 
 }  // namespace tsqbx
