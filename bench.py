@@ -268,13 +268,15 @@ def gpu_selector(dev, local_rank):
 
 # DRAM bytes (read + write) per launch of each timed kernel, from one ncu
 # capture of the current kernel versions (summaries in profiles/: the
-# laplace_*_p9_torus256x96.md files and helmholtz_slp_p12_torus444x166.md).
+# laplace_*_p9_torus256x96.md files, helmholtz_slp_p12_torus444x166.md and
+# batch_laplace_mixed_ellipsoids64.md).
 # A kernel changed since its capture must map to None here.
 TRAFFIC_BYTES = {
-    ("laplace", "fp64", "slp+dlp"): 175.95e6,
-    ("laplace", "mixed", "slp+dlp"): 157.78e6,
-    ("laplace", "df64", "slp+dlp"): 176.06e6,
-    ("helmholtz", "fp64", "slp"): 714.85e6,
+    ("laplace", "fp64", "slp+dlp"): 75.37e6,
+    ("laplace", "mixed", "slp+dlp"): 56.68e6,
+    ("laplace", "df64", "slp+dlp"): 75.21e6,
+    ("helmholtz", "fp64", "slp"): 322.75e6,
+    ("batched", "mixed", "slp"): 1129.56e6,
 }
 
 
@@ -343,7 +345,7 @@ def leg_batched(pkg, torch, dev, steps, warmup, flush):
            "persistent_ctas": info["grid_blocks"], "graph": bool(info["graph"]),
            "sequential_ms_per_step": sum(seq) / steps,
            "speedup_vs_sequential": (sum(seq) / steps) / (1e3 * t),
-           "roofline": roofline(fl, sum(kms) / steps / 1e3, "mixed")}
+           "roofline": roofline(fl, sum(kms) / steps / 1e3, "mixed", ("batched", "mixed", "slp"))}
     for pl in plans:
         pl.close()
     return res
