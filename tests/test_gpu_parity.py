@@ -236,3 +236,78 @@ def test_submit_slots_and_busy(pkg):
         for mu, o in zip(mus[:2], (o1, o2)):
             ref = oracle.tsqbx_laplace(g, 5, mu)["slp"]
             assert relerr(o["slp"], ref) <= 1e-12
+
+
+def ragged_range_geometry(rng, n_src=600, n_ctr=9, tgt_per_ctr=(1, 5, 17)):
+    """Groups whose ranges abut (so they merge into one run), include empty
+    ranges, run backwards through the source order, repeat a source range,
+    or are empty altogether; targets as in cloud_geometry (convergent).
+    Sources lie in a shell with outward normals, so that with a positive
+    density the layers are as well conditioned as on a surface."""
+    from tsqbx_inputs.geometry import Geometry
+    src = rng.uniform(-2, 2, (4 * n_src, 3))
+    src = src[np.linalg.norm(src, axis=1) >= 0.9][:n_src]     # >= 0.2 from every center
+    w = rng.uniform(0.5, 1.5, n_src)
+    nrm = src / np.linalg.norm(src, axis=1, keepdims=True)     # outward, like a closed surface's
+    ctr = rng.uniform(-0.4, 0.4, (n_ctr, 3))
+    rb, re, grs = [], [], [0]
+    for c in range(n_ctr):
+        kind = c % 5
+        if kind == 0:          # one long run cut into abutting pieces, with empty ranges between
+            a = int(rng.integers(0, 100))
+            cuts = np.sort(rng.choice(np.arange(a + 1, a + 450), size=12, replace=False))
+            edges = [a] + list(cuts) + [a + 450]
+            for lo, hi in zip(edges[:-1], edges[1:]):
+                rb.append(lo); re.append(hi)
+                rb.append(hi); re.append(hi)                     # empty
+        elif kind == 1:        # runs in decreasing source order
+            for lo in range(540, 0, -60):
+                rb.append(lo); re.append(lo + int(rng.integers(1, 40)))
+        elif kind == 2:        # the same range twice, and a single source
+            rb += [10, 10, 333]; re += [210, 210, 334]
+        elif kind == 3:        # nothing but empty ranges
+            rb += [5, 70]; re += [5, 70]
+        else:                  # many one-source runs
+            sel = np.sort(rng.choice(n_src, size=120, replace=False))
+            rb += list(sel); re += list(sel + 1)
+        grs.append(len(rb))
+    rb, re, grs = np.array(rb, np.int32), np.array(re, np.int32), np.array(grs, np.int64)
+    tgt, tc, tn = [], [], []
+    for c in range(n_ctr):
+        members = [np.arange(rb[i], re[i]) for i in range(grs[c], grs[c + 1])]
+        members = np.concatenate(members) if members else np.zeros(0, int)
+        Rmin = np.linalg.norm(src[members] - ctr[c], axis=1).min() if len(members) else 1.0
+        for j in range(tgt_per_ctr[c % len(tgt_per_ctr)]):
+            d = rng.standard_normal(3)
+            tgt.append(ctr[c] + rng.uniform(0.05, 0.6) * Rmin * d / np.linalg.norm(d))
+            tc.append(c)
+            tn.append(d / np.linalg.norm(d))
+    tgt = np.array(tgt)
+    return Geometry(np.ascontiguousarray(src.T), w, np.ascontiguousarray(nrm.T), np.ascontiguousarray(ctr.T),
+                    np.full(n_ctr, 0.1), np.ascontiguousarray(tgt.T), np.array(tc, np.int32),
+                    np.ascontiguousarray(np.array(tn).T), np.arange(n_ctr, dtype=np.int32), grs, rb, re)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "df64"])
+@pytest.mark.parametrize("max_iters,lanes", [(0, 0), (1, 0), (2, 3), (3, 32), (0, 1)])
+def test_laplace_ragged_range_lists(pkg, precision, max_iters, lanes):
+    """Source lists read as merged runs: abutting, empty, backwards, repeated
+    and single-source ranges, slices that start inside a run, every path."""
+    rng = np.random.default_rng(2024 + max_iters)
+    g = ragged_range_geometry(rng)
+    mu = 1.0 + 0.5 * rng.uniform(-1, 1, g.n_src)
+    out = check_laplace(pkg, g, mu, 7, precision, max_item_iters=max_iters, lanes_per_target=lanes)
+    empty = g.tgt_center % 5 == 3
+    assert np.all(out["slp"][empty] == 0.0) and np.all(out["dlp"][empty] == 0.0)
+
+
+def test_helmholtz_ragged_range_lists(pkg):
+    rng = np.random.default_rng(77)
+    g = ragged_range_geometry(rng)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    ref = oracle.tsqbx_helmholtz(g, 8, 4.0, mu, slp=True, dlp=True)
+    for max_iters in (0, 2):
+        with pkg.Plan(g, "helmholtz", ("slp", "dlp"), p=8, k=4.0, max_item_iters=max_iters) as plan:
+            out = plan.eval(mu)
+        for layer in ("slp", "dlp"):
+            assert relerr(out[layer], ref[layer]) <= 1e-12, (layer, max_iters)
