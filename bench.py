@@ -280,15 +280,32 @@ TRAFFIC_BYTES = {
 }
 
 
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json), else the
+    fallback figure of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def roofline(flops_per_launch, kernel_s, precision, traffic_key=None):
     peak = PEAK_FP64_TFLOPS if precision == "fp64" else PEAK_FP32_TFLOPS
     achieved = flops_per_launch / kernel_s / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_BYTES.get(traffic_key),
-            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "pipe": precision if precision == "fp64" else "fp32",
-            "peak_source": "derived: 152 SMs x %d FMA/clk x 2 flop x 2070 MHz"
-                           % (2 if precision == "fp64" else 128)}
+    traffic = TRAFFIC_BYTES.get(traffic_key)
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": traffic,
+           "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+           "pipe": precision if precision == "fp64" else "fp32",
+           "peak_source": "derived: 152 SMs x %d FMA/clk x 2 flop x 2070 MHz"
+                          % (2 if precision == "fp64" else 128)}
+    if traffic is not None:
+        # the DRAM side of the same launch: ncu bytes over this run's kernel time
+        hbm, src = measured_hbm_gbs()
+        out["hbm"] = {"achieved_gbs": traffic / kernel_s / 1e9, "peak_gbs": hbm,
+                      "frac": traffic / kernel_s / 1e9 / hbm, "peak_source": src}
+    return out
 
 
 def leg_batched(pkg, torch, dev, steps, warmup, flush):
@@ -645,7 +662,8 @@ def main():
             rf["note"] = ("FP64-equivalent flops (double-float arithmetic on the FP32 pipes) "
                           "against the FP64 peak; above 1 means faster than native FP64 could be")
         summary[prec] = {"value": value, "ms_per_step": 1e3 * t_step / args.steps,
-                         "kernel_ms": 1e3 * kavg, "roofline": rf}
+                         "kernel_ms": 1e3 * kavg, "roofline": rf,
+                         "pairs_per_s": info["n_pairs"] * args.steps * world / t_step}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -706,14 +724,15 @@ def main():
                    "timing": "CUDA events on the launching stream per step"},
         "roofline": f["roofline"],
         "kernel_ms": f["kernel_ms"],
+        "pairs_per_s": f["pairs_per_s"],
         "mixed": {"value": summary["mixed"]["value"], "unit": UNIT, "dtype": "f32 recurrence, f64 sums",
                   "ms_per_step": summary["mixed"]["ms_per_step"], "kernel_ms": summary["mixed"]["kernel_ms"],
-                  "roofline": summary["mixed"]["roofline"],
+                  "roofline": summary["mixed"]["roofline"], "pairs_per_s": summary["mixed"]["pairs_per_s"],
                   "speedup_vs_fp64": summary["mixed"]["value"] / f["value"]},
         "df64": {"value": summary["df64"]["value"], "unit": UNIT,
                  "dtype": "double-float (f32 pairs), f64 geometry offsets and sums",
                  "ms_per_step": summary["df64"]["ms_per_step"], "kernel_ms": summary["df64"]["kernel_ms"],
-                 "roofline": summary["df64"]["roofline"],
+                 "roofline": summary["df64"]["roofline"], "pairs_per_s": summary["df64"]["pairs_per_s"],
                  "speedup_vs_fp64": summary["df64"]["value"] / f["value"]},
         "error_vs_oracle": err or None,
         "e2e": e2e,
