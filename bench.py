@@ -398,17 +398,18 @@ def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
 
 def leg_conventional(pkg, torch, dev, steps, warmup, flush):
     """Torus 96 x 36 quads (41,472 sources, 82,944 centers, octree lists) with
-    1, 4, 16 and 64 targets per center, SLP+DLP FP64, Laplace at p = 9 and
-    Helmholtz (k = 10, plane-wave density) at p = 12: the target-specific path
-    alone ("off"), conventional QBX for every center ("all"), and the cost
-    model's per-center choice ("auto")."""
+    1, 4, 16 and 64 targets per center, and with a mix (each center 1..64,
+    log-uniform), SLP+DLP FP64, Laplace at p = 9 and Helmholtz (k = 10,
+    plane-wave density) at p = 12: the target-specific path alone ("off"),
+    conventional QBX for every center ("all"), and the cost model's
+    per-center choice ("auto")."""
     from tsqbx_inputs import configs
     stream = torch.cuda.Stream(device=dev)
     base = "torus 96x36 quads, 41472 sources, 82944 centers, octree lists, targets per center in {1,4,16,64} " \
-           "(uniform in each center's half-radius ball), SLP+DLP FP64, "
+           "or mixed 1..64 log-uniform (uniform in each center's half-radius ball), SLP+DLP FP64, "
     res = {"workload": base + "Laplace p=9", "unit": UNIT, "cases": []}
     hel = {"workload": base + "Helmholtz k=10 p=12", "unit": UNIT, "cases": []}
-    for tpc in (1, 4, 16, 64):
+    for tpc in (1, 4, 16, 64, "mixed:64"):
         g, mu, _ = configs.torus_near_targets(96, 36, tpc)
         for kernel, p, dest in (("laplace", 9, res), ("helmholtz", 12, hel)):
             if kernel == "helmholtz":

@@ -212,3 +212,34 @@ def test_helmholtz_auto_and_per_call(pkg):
         out2 = plan.eval(mu, p=6, k=1.5)
     assert relerr(out["slp"], oracle.tsqbx_helmholtz(g, 10, 3.0, mu)["slp"]) <= TOL
     assert relerr(out2["slp"], oracle.tsqbx_helmholtz(g, 6, 1.5, mu)["slp"]) <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["laplace", "helmholtz"])
+def test_auto_on_torus_with_mixed_target_counts(pkg, kernel):
+    """Octree groups whose centers hold 1..64 targets: the cost model splits
+    the centers of one group between the two paths; the result matches the
+    target-specific path everywhere and the oracle on sampled targets."""
+    from tsqbx_inputs import configs
+    g, mu, _ = configs.torus_near_targets(32, 12, "mixed:64")
+    kw = {}
+    if kernel == "helmholtz":
+        mu = mu * np.exp(1j * 4.0 * g.src_xyz[0])
+        kw = {"k": 4.0}
+    layers = ("slp", "dlp", "sp")
+    with pkg.Plan(g, kernel, layers, p=8, conventional="auto", **kw) as plan:
+        out = plan.eval(mu)
+        info = plan.info()
+    assert 0 < info["n_conv_centers"] < g.n_ctr
+    cnt = np.bincount(g.tgt_center, minlength=g.n_ctr)
+    assert info["n_conv_targets"] > np.sum(cnt[cnt < 4])     # the conventional centers are the busy ones
+    with pkg.Plan(g, kernel, layers, p=8, conventional="off", **kw) as plan:
+        ts = plan.eval(mu)
+    for layer in layers:
+        assert relerr(out[layer], ts[layer]) <= TOL, layer
+    idx = np.sort(np.random.default_rng(5).choice(g.n_tgt, 300, replace=False))
+    if kernel == "laplace":
+        ref = oracle.tsqbx_laplace(g, 8, mu, subset=idx, slp=True, dlp=True, sp=True)
+    else:
+        ref = oracle.tsqbx_helmholtz(g, 8, 4.0, mu, subset=idx, slp=True, dlp=True, sp=True)
+    for layer in layers:
+        assert relerr(out[layer][idx], ref[layer]) <= TOL, layer

@@ -90,12 +90,19 @@ def torus_near_targets(nu=96, nv=36, targets_per_center=16, seed_offset=0, n_max
     radius, each center gets targets_per_center - 1 more, uniform in the ball
     of that same radius about the center (so |t-c| is never larger than for
     the original target and every pair stays convergent).  Extra targets
-    carry their center's target normal."""
+    carry their center's target normal.  targets_per_center = "mixed:M"
+    draws each center's count log-uniformly from 1..M (a mix of centers
+    on both sides of the conventional path's break-even)."""
     g, mu, tree = torus(nu, nv, seed_offset=seed_offset, n_max=n_max)
     rng = np.random.default_rng(BASE_SEED + 5 + seed_offset)
-    extra = targets_per_center - 1
-    if extra > 0:
-        n = g.n_ctr
+    n = g.n_ctr
+    if isinstance(targets_per_center, str) and targets_per_center.startswith("mixed:"):
+        top = int(targets_per_center.split(":")[1])
+        counts = np.clip(np.round(np.exp(rng.uniform(0.0, np.log(top), n))), 1, top).astype(np.int64)
+    else:
+        counts = np.full(n, int(targets_per_center), np.int64)
+    extra = counts - 1
+    if extra.sum() > 0:
         c = np.repeat(np.arange(n, dtype=np.int32), extra)
         rho = np.linalg.norm(g.tgt_xyz - g.ctr_xyz, axis=0)        # one target per center, in order
         v = rng.standard_normal((len(c), 3))
