@@ -513,18 +513,19 @@ def leg_sphere(pkg, torch, dev, steps, warmup, flush):
     return res
 
 
-def leg_serving(pkg, duration_s=6.0, rate=200.0, seed=20191114):
+def leg_serving(pkg, duration_s=6.0, rate=200.0, seed=20191114, size_priority=False):
     """Serving: Poisson arrivals over 16 resident geometries (5k-300k sources);
     each request a Laplace FP64, Laplace mixed or Helmholtz (k in {1,5,10})
     single-layer evaluation with p in {5,9,12} and a new seeded density.
     Plans are built first (warm start); if the offered rate exceeds capacity
-    a second phase runs at 80 % of the measured capacity."""
+    a second phase runs at 80 % of the measured capacity.  size_priority:
+    the server's size-priority policy (short requests overtake long ones)."""
     import threading
     from tsqbx_inputs import configs
     geoms = configs.serving_geometries()
     kinds = [("laplace", "fp64", 0.0), ("laplace", "mixed", 0.0), ("helmholtz", "fp64", 1.0),
              ("helmholtz", "fp64", 5.0), ("helmholtz", "fp64", 10.0)]
-    srv = pkg.Server(hbm_budget=96 << 30, max_inflight=64)
+    srv = pkg.Server(hbm_budget=96 << 30, max_inflight=64, size_priority=size_priority)
     gids = [srv.add_geometry(g, with_normals=False) for g in geoms]
     for gid in gids:
         for kernel, prec, k in (("laplace", "fp64", 0.0), ("laplace", "mixed", 0.0), ("helmholtz", "fp64", 1.0)):
@@ -567,7 +568,7 @@ def leg_serving(pkg, duration_s=6.0, rate=200.0, seed=20191114):
     res = {"workload": "16 resident geometries (spheres, ellipsoids, tori; %d-%d sources), Poisson "
                        "arrivals, Laplace FP64 / mixed or Helmholtz k in {1,5,10}, SLP, p in {5,9,12}"
                        % (min(g.n_src for g in geoms), max(g.n_src for g in geoms)),
-           "offered": first}
+           "policy": "size priority" if size_priority else "fifo", "offered": first}
     capacity = first["achieved_req_per_s"]
     saturated = first["span_s"] > 1.15 * first["submit_s"]
     res["saturated_at_offered_rate"] = bool(saturated)
@@ -597,7 +598,7 @@ def main():
         flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
         steps = max(3, args.steps // 2)
         if args.only == "serving":
-            res = leg_serving(pkg)
+            res = {"fifo": leg_serving(pkg), "size_priority": leg_serving(pkg, size_priority=True)}
         elif args.only == "target_derivative":
             g, mu = workload()
             res = leg_target_derivative(pkg, torch, dev, g, mu, steps, args.warmup, flush)
@@ -693,6 +694,7 @@ def main():
         extras["target_derivative"] = leg_target_derivative(pkg, torch, dev, g, mu, max(3, args.steps // 2),
                                                             args.warmup, flush)
         extras["serving"] = leg_serving(pkg)
+        extras["serving_size_priority"] = leg_serving(pkg, size_priority=True)
 
     if rank != 0:
         return

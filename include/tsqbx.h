@@ -112,7 +112,14 @@ enum {
      * keeps every center target-specific). */
     TSQBX_FLAG_CONVENTIONAL_AUTO = 8u,  /* per center, whichever the cost model (Table 2
                                            form, GPU constants) says is cheaper        */
-    TSQBX_FLAG_CONVENTIONAL_ALL = 16u   /* every center takes the conventional path     */
+    TSQBX_FLAG_CONVENTIONAL_ALL = 16u,  /* every center takes the conventional path     */
+    /* The plan's streams get a CUDA stream priority from the plan's work: the
+     * listed pairs times a per-kernel/precision cost, one priority level per
+     * decade above 1e5 pair-equivalents, the highest for the smallest plans.
+     * When several plans run at once, pending thread blocks of short
+     * evaluations are then dispatched before those of long ones.  Results
+     * are unchanged.  See tsqbx_server_set_size_priority. */
+    TSQBX_FLAG_SIZE_PRIORITY = 32u
 };
 
 typedef struct {
@@ -344,6 +351,15 @@ TSQBX_API int tsqbx_server_poll(tsqbx_server server, uint64_t request, int timeo
 TSQBX_API int tsqbx_server_get_stats(tsqbx_server server, tsqbx_server_stats *stats);
 /* Clears latency samples and counters (e.g. after a warm-up phase). */
 TSQBX_API int tsqbx_server_reset_stats(tsqbx_server server);
+/* Scheduling policy for the plans the server builds from now on (plans that
+ * are already resident keep theirs; build them with tsqbx_server_prepare
+ * after this call).  on = 0 (the default): every plan's streams have the
+ * default priority, so the GPU dispatches the blocks of concurrent requests
+ * roughly in launch order.  on != 0: plans are built with
+ * TSQBX_FLAG_SIZE_PRIORITY, so short evaluations overtake long ones -- a much
+ * lower median latency for mixes of small and large requests, at the cost of
+ * the largest requests' latency.  Errors: TSQBX_E_INVAL. */
+TSQBX_API int tsqbx_server_set_size_priority(tsqbx_server server, int on);
 
 /* ------------------------------------------------------------- tuning
  * Work decomposition of a plan: lanes per target (0 = chosen per group from

@@ -92,10 +92,11 @@ class Plan:
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
                  lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False,
-                 conventional="off"):
+                 conventional="off", size_priority=False):
         """conventional: "off" (target-specific expansions only), "auto"
         (conventional QBX for the centers the cost model finds cheaper) or
-        "all" (conventional QBX for every center)."""
+        "all" (conventional QBX for every center).  size_priority: stream
+        priority from the plan's work (TSQBX_FLAG_SIZE_PRIORITY)."""
         self.kernel = kernel
         self.layers = tuple(layers)
         self.p = int(p)
@@ -108,7 +109,8 @@ class Plan:
                 (_lib.TSQBX_FLAG_SKIP_CHECK if skip_check else 0) | \
                 (_lib.TSQBX_FLAG_USE_TUNED if use_tuned else 0) | \
                 {"off": 0, "auto": _lib.TSQBX_FLAG_CONVENTIONAL_AUTO,
-                 "all": _lib.TSQBX_FLAG_CONVENTIONAL_ALL}[conventional]
+                 "all": _lib.TSQBX_FLAG_CONVENTIONAL_ALL}[conventional] | \
+                (_lib.TSQBX_FLAG_SIZE_PRIORITY if size_priority else 0)
         opt = make_options(kernel, self.layers, self.p, k, precision, device, flags,
                            lanes_per_target, n_slots, max_item_iters)
         h = ctypes.c_void_p()
@@ -303,13 +305,17 @@ class Server:
     """Request-serving runtime (tsqbx_server_*): register geometries, submit
     evaluations as they arrive, poll for completion, read p50/p99 latency."""
 
-    def __init__(self, device=0, hbm_budget=16 << 30, max_inflight=64):
+    def __init__(self, device=0, hbm_budget=16 << 30, max_inflight=64, size_priority=False):
+        """size_priority: build plans whose streams are prioritised by size
+        (tsqbx_server_set_size_priority): short evaluations overtake long ones."""
         h = ctypes.c_void_p()
         check(lib().tsqbx_server_create(int(device), int(hbm_budget), int(max_inflight), ctypes.byref(h)),
               "tsqbx_server_create")
         self._h = h
         self._geoms = {}
         self._pending = {}
+        if size_priority:
+            check(lib().tsqbx_server_set_size_priority(self._h, 1), "tsqbx_server_set_size_priority")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

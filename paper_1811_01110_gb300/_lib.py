@@ -23,6 +23,7 @@ TSQBX_SLP, TSQBX_DLP, TSQBX_SP = 1, 2, 4
 TSQBX_FP64, TSQBX_MIXED, TSQBX_DF64 = 0, 1, 2
 TSQBX_FLAG_ALLOW_DIVERGENT, TSQBX_FLAG_SKIP_CHECK, TSQBX_FLAG_USE_TUNED = 1, 2, 4
 TSQBX_FLAG_CONVENTIONAL_AUTO, TSQBX_FLAG_CONVENTIONAL_ALL = 8, 16
+TSQBX_FLAG_SIZE_PRIORITY = 32
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -144,6 +145,7 @@ _SIGNATURES = [
     ("tsqbx_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int]),
     ("tsqbx_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_server_stats)]),
     ("tsqbx_server_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
+    ("tsqbx_server_set_size_priority", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("tsqbx_eval_noalloc", ctypes.c_int,
      [ctypes.POINTER(tsqbx_geometry), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

@@ -276,6 +276,26 @@ bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool h
     return (double)ns * p2l + warps * l2p < (double)nt * (double)ns * ts;
 }
 
+// Stream priority of a plan under TSQBX_FLAG_SIZE_PRIORITY: one level per
+// decade of work (pairs times a cost per pair relative to Laplace FP64) above
+// 1e5, from the device's highest priority for the smallest plans down to its
+// lowest.
+int size_priority(int64_t n_pairs, const tsqbx_options &o)
+{
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const double cost = o.kernel == TSQBX_HELMHOLTZ ? 4.0
+                        : o.precision == TSQBX_MIXED ? 0.03
+                        : o.precision == TSQBX_DF64  ? 0.25
+                                                     : 1.0;
+    const double work = std::max(1.0, (double)n_pairs * cost);
+    const int level = std::min(std::max((int)std::floor(std::log10(work)) - 5, 0), least - greatest);
+    return greatest + level;
+}
+
 int choose_lanes(int64_t nt, int64_t ns)
 {
     int best = 1;
@@ -710,8 +730,9 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         P->out_bytes = (size_t)n_tgt * (helm ? 2 : 1) * sizeof(double);
         P->wmu_bytes = (size_t)n_src * (helm ? sizeof(double2) : mixed ? sizeof(float) : sizeof(double));
         P->slots.resize(P->opt.n_slots + 1);
+        const int prio = (o->flags & TSQBX_FLAG_SIZE_PRIORITY) ? size_priority(n_pairs, *o) : 0;
         for (auto &s : P->slots) {
-            ck(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+            ck(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio));
             ck(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
             s.d_density = P->dalloc<char>(P->density_bytes);
             s.d_wmu = P->dalloc<char>(P->wmu_bytes);

@@ -70,6 +70,7 @@ constexpr int64_t kConvSlice = 1024;
 // whether a center with nt targets and ns listed sources is cheaper on the
 // conventional path than on the target-specific one.
 bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool helmholtz);
+int size_priority(int64_t n_pairs, const tsqbx_options &o);
 // Build the schedule; max_iters <= 0 picks the automatic cap.
 int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
                    int n_sm, Schedule &out);

@@ -90,6 +90,7 @@ size_t estimate_bytes(const GeomCopy &g, const tsqbx_options &o)
 struct tsqbx_server_s {
     int device = 0;
     size_t budget = 0;
+    bool size_priority = false;              // plans built with TSQBX_FLAG_SIZE_PRIORITY
     int max_inflight = 64;
     std::mutex mu;
     std::condition_variable cv;
@@ -323,6 +324,7 @@ int tsqbx_server_submit(tsqbx_server S, int geom_id, const tsqbx_options *opt, c
         r->id = S->next_id++;
         r->geom = geom_id;
         r->opt = *opt;
+        if (S->size_priority) r->opt.flags |= TSQBX_FLAG_SIZE_PRIORITY;
         r->opt.device = S->device;
         r->key = PlanKey{geom_id, (int)opt->kernel, opt->layers, (int)opt->precision};
         const double *d = static_cast<const double *>(density);
@@ -402,12 +404,21 @@ int tsqbx_server_reset_stats(tsqbx_server S)
     return TSQBX_OK;
 }
 
+int tsqbx_server_set_size_priority(tsqbx_server S, int on)
+{
+    if (!S) return TSQBX_E_INVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->size_priority = on != 0;
+    return TSQBX_OK;
+}
+
 int tsqbx_server_prepare(tsqbx_server S, int geom_id, const tsqbx_options *opt)
 {
     if (!S || !opt) return TSQBX_E_INVAL;
     std::lock_guard<std::mutex> lk(S->mu);
     if (geom_id < 0 || geom_id >= (int)S->geoms.size()) return TSQBX_E_INVAL;
     tsqbx_options o = *opt;
+    if (S->size_priority) o.flags |= TSQBX_FLAG_SIZE_PRIORITY;
     o.device = S->device;
     const PlanKey key{geom_id, (int)o.kernel, o.layers, (int)o.precision};
     auto it = S->plans.find(key);

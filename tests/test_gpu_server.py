@@ -137,3 +137,35 @@ def test_poll_timeout(pkg):
         assert srv.poll(rid, timeout_us=-1)
         assert time.perf_counter() - t0 < 60
         assert pkg.lib().tsqbx_server_poll(srv._h, ctypes.c_uint64(rid), 0) == -7   # retired
+
+
+def test_size_priority_leaves_results_unchanged(pkg):
+    """TSQBX_FLAG_SIZE_PRIORITY only changes the streams' priority: the same
+    plan with and without it gives bit-identical results."""
+    g = _geoms()[1]
+    mu = np.random.default_rng(5).standard_normal(g.n_src)
+    with pkg.Plan(g, "laplace", ("slp", "dlp"), p=9) as a, \
+            pkg.Plan(g, "laplace", ("slp", "dlp"), p=9, size_priority=True) as b:
+        ra, rb = a.eval(mu), b.eval(mu)
+    for layer in ("slp", "dlp"):
+        assert np.array_equal(ra[layer], rb[layer])
+
+
+def test_size_priority_server_matches_fifo_server(pkg):
+    """The server's size-priority policy changes only the order in which
+    concurrent work is dispatched: every request's result equals the FIFO
+    server's bit for bit."""
+    geoms = _geoms()
+    rng = np.random.default_rng(19)
+    reqs = [(i % 3, rng.standard_normal(geoms[i % 3].n_src)) for i in range(9)]
+    results = []
+    for prio in (False, True):
+        with pkg.Server(hbm_budget=4 << 30, max_inflight=8, size_priority=prio) as srv:
+            gids = [srv.add_geometry(g) for g in geoms]
+            subs = [srv.submit(gids[gi], mu, "laplace", ("slp", "dlp"), 7) for gi, mu in reqs]
+            for rid, _ in subs:
+                assert srv.poll(rid, timeout_us=-1)
+            results.append([outs for _, outs in subs])
+    for a, b in zip(*results):
+        for layer in ("slp", "dlp"):
+            assert np.array_equal(a[layer], b[layer])

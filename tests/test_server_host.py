@@ -25,6 +25,7 @@ def test_server_argument_checks(pkg):
     assert L.tsqbx_server_create(0, 1 << 20, 0, ctypes.byref(h)) == -1    # no in-flight slots
     assert L.tsqbx_server_create(-1, 1 << 20, 4, ctypes.byref(h)) == -1
     assert L.tsqbx_server_poll(None, ctypes.c_uint64(1), 0) == -1
+    assert L.tsqbx_server_set_size_priority(None, 1) == -1
 
 
 def test_request_failure_is_reported_without_gpu(pkg):
