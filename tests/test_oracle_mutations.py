@@ -29,6 +29,8 @@ MUTATIONS = {
                 "nsum_add(&us, wmu * nsum_get(&acc) / (2.0 * ORACLE_PI));"),
     "sp_rho0_limit": ("acc = k * (js[1] + I * ys[1]) * dot3(pg.shat, nt_);",
                       "acc = (js[1] + I * ys[1]) * dot3(pg.shat, nt_);"),
+    "pathB_sp_rho0_slope": ("const double slope = kernel == 0 ? 1.0 : k / 3.0;",
+                            "const double slope = kernel == 0 ? 1.0 : k / 2.0;"),
 }
 
 
