@@ -9,7 +9,7 @@ namespace tsqbx {
 
 // Warp work item: the targets [slot_begin, slot_begin + n_tgt) of one group
 // (all sharing that group's source list), L lanes per target, over the slice
-// [src_lo, src_hi) of the group's flattened source list.  part < 0: the item
+// [src_lo, src_hi) of the group's source list (list positions).  part < 0: the item
 // owns the whole list and writes the outputs; part >= 0: it writes partial
 // sums to partial[part + j] (j < n_tgt), combined later in slice order.
 struct __align__(16) Item {

@@ -532,7 +532,7 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         const bool mixed = o->precision == TSQBX_MIXED;
         const int64_t n_src = G->n_src, n_tgt = G->n_tgt, n_group = G->n_group;
 
-        // flattened source list per group
+        // list length of each group (prefix sums)
         std::vector<int64_t> grp_off(n_group + 1, 0);
         for (int64_t q = 0; q < n_group; ++q) {
             int64_t ns = 0;
