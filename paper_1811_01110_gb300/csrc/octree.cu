@@ -36,6 +36,7 @@
 // thread per target box walking the tree with an explicit stack, in two
 // passes (count, fill), then a per-box sort and merge of the ranges.
 #include <algorithm>
+#include <climits>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -328,11 +329,33 @@ near_count_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt
     }
 }
 
+// Ascending sort of a[0, P) by (x, y) in shared memory by one warp (bitonic
+// network; P a power of two).  Equal ranges may change places, which the
+// merge that follows cannot tell apart.
+__device__ void bitonic_sort_warp(int2 *a, int P, int lane)
+{
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < P / 2; t += 32) {
+                const int i = 2 * t - (t & (j - 1));        // the t-th index with bit j clear
+                const int l = i + j;
+                const bool up = (i & k) == 0;
+                const int2 x = a[i], y = a[l];
+                const bool gt = x.x > y.x || (x.x == y.x && x.y > y.y);
+                if (gt == up) {
+                    a[i] = y;
+                    a[l] = x;
+                }
+            }
+            __syncwarp();
+        }
+}
+
 __global__ void __launch_bounds__(kNearWarps * 32)
 near_fill_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt, const long long *off, int2 *raw,
                  int2 *sorted, int *merged, int *status)
 {
-    __shared__ int stk_all[kNearWarps][kWarpStack];
+    __shared__ __align__(16) int stk_all[kNearWarps][kWarpStack];
     __shared__ int cursor[kNearWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kNearWarps + warp;
@@ -343,28 +366,49 @@ near_fill_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt,
     const bool ok = near_field_warp(T, BL, tboxes[i], lane, stk_all[warp], e);
     __syncwarp();
     if (lane == 0 && !ok) atomicOr(status, 1);
-    // rank sort by (begin, end, arrival): element k goes to position rank(k);
-    // staged in the (now free) stack when it fits
+    // sort by (begin, end): chunks of up to kChunk ranges in the (now free)
+    // stack by a bitonic network; with several chunks, each range then goes
+    // to its index in its chunk plus the number of ranges before it in the
+    // other chunks (binary searches; equal ranges of earlier chunks first)
+    constexpr int kChunk = kWarpStack / 2;
     const int n = cursor[warp];
-    const int2 *r = raw + off[i];
+    int2 *r = raw + off[i];
     int2 *out = sorted + off[i];
-    const int2 *src = r;
-    if (n <= kWarpStack / 2) {
-        int2 *buf = reinterpret_cast<int2 *>(stk_all[warp]);
-        for (int k = lane; k < n; k += 32) buf[k] = r[k];
+    int2 *buf = reinterpret_cast<int2 *>(stk_all[warp]);
+    for (int c0 = 0; c0 < n; c0 += kChunk) {
+        const int m = min(kChunk, n - c0);
+        int P = 1;
+        while (P < m) P <<= 1;
+        for (int k = lane; k < P; k += 32) buf[k] = k < m ? r[c0 + k] : make_int2(INT_MAX, INT_MAX);
         __syncwarp();
-        src = buf;
+        bitonic_sort_warp(buf, P, lane);
+        int2 *dst = n <= kChunk ? out : r;
+        for (int k = lane; k < m; k += 32) dst[c0 + k] = buf[k];
+        __syncwarp();
     }
-    for (int k = lane; k < n; k += 32) {
-        const int2 v = src[k];
-        int rank = 0;
-        for (int j = 0; j < n; ++j) {
-            const int2 u = src[j];
-            rank += (u.x < v.x) || (u.x == v.x && (u.y < v.y || (u.y == v.y && j < k)));
+    if (n > kChunk) {
+        const int nch = (n + kChunk - 1) / kChunk;
+        for (int k = lane; k < n; k += 32) {
+            const int a = k / kChunk;
+            const int2 v = r[k];
+            int pos = k - a * kChunk;
+            for (int b = 0; b < nch; ++b) {
+                if (b == a) continue;
+                const int lo0 = b * kChunk;
+                int lo = lo0, hi = min(n, lo0 + kChunk);
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int2 u = r[mid];
+                    const bool before = u.x < v.x || (u.x == v.x && (u.y < v.y || (u.y == v.y && b < a)));
+                    if (before) lo = mid + 1;
+                    else hi = mid;
+                }
+                pos += lo - lo0;
+            }
+            out[pos] = v;
         }
-        out[rank] = v;
+        __syncwarp();
     }
-    __syncwarp();
     if (lane != 0) return;
     // drop empty ranges and join touching ones (into raw)
     int2 *m_out = raw + off[i];
