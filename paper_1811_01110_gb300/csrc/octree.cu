@@ -422,6 +422,24 @@ near_fill_kernel(const TreeView T, const BoxLists BL, const int *tboxes, int nt,
     merged[i] = m;
 }
 
+// Gathers each target box's merged ranges (the first merged[i] of its raw
+// block at off[i]) into the contiguous near_begin / near_end arrays at moff[i];
+// one warp per box.
+__global__ void compact_near_kernel(const int2 *raw, const long long *off, const int *merged,
+                                    const long long *moff, int nt, int *near_begin, int *near_end)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nt; i += (gridDim.x * blockDim.x) >> 5) {
+        const int2 *src = raw + off[i];
+        const long long at = moff[i];
+        for (int k = lane; k < merged[i]; k += 32) {
+            const int2 v = src[k];
+            near_begin[at + k] = v.x;
+            near_end[at + k] = v.y;
+        }
+    }
+}
+
 // ------------------------------------------------------------- tree building
 
 __global__ void bbox_kernel(int64_t ns, const double *s, int64_t nc, const double *c, const double *r,
@@ -830,6 +848,8 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     std::vector<long long> hoff(nt + 1, 0);
     std::vector<int> hmerged(nt);
     DBuf<int2> raw;
+    DBuf<int> near_b, near_e;
+    long long n_near = 0;
     // CSR from per-row counts (prefix sum on the host: one copy each way)
     auto csr = [&](DBuf<int> &dcount, int n, DBuf<long long> &doff) {
         std::vector<int> hc;
@@ -875,6 +895,18 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
         near_fill_kernel<<<gw, kNearWarps * 32>>>(T, BL, dt.p, nt, doff.p, raw.p, sorted.p, dcount.p, dstatus.p);
         ck(cudaGetLastError());
         to_host(hmerged, dcount.p, nt);
+        // the merged ranges, contiguous in target-box order
+        std::vector<long long> hmoff(nt + 1, 0);
+        for (int i = 0; i < nt; ++i) hmoff[i + 1] = hmoff[i] + hmerged[i];
+        DBuf<long long> dmoff;
+        dmoff.alloc(nt + 1);
+        ck(cudaMemcpy(dmoff.p, hmoff.data(), (nt + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+        near_b.alloc(std::max<long long>(1, hmoff[nt]));
+        near_e.alloc(std::max<long long>(1, hmoff[nt]));
+        compact_near_kernel<<<grid_for((int64_t)nt * 32, n_sm), 256>>>(raw.p, doff.p, dcount.p, dmoff.p, nt,
+                                                                       near_b.p, near_e.p);
+        ck(cudaGetLastError());
+        n_near = hmoff[nt];
         int hstatus = 0;
         ck(cudaMemcpy(&hstatus, dstatus.p, sizeof(int), cudaMemcpyDeviceToHost));
         if (hstatus) throw std::invalid_argument("near-field walk exceeded its stack");
@@ -897,22 +929,18 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     to_host(O.halfwidth, hw.p, nb);
     to_host(O.src_perm, val2.p, ns);
     to_host(O.ctr_box, cbox.p, nc);
-    std::vector<int2> hraw;
-    if (nt > 0) to_host(hraw, raw.p, (size_t)hoff[nt]);
+    to_host(O.near_begin, near_b.p, (size_t)n_near);
+    to_host(O.near_end, near_e.p, (size_t)n_near);
     O.near_start.assign(nb + 1, 0);
     for (int i = 0; i < nt; ++i) O.near_start[tboxes[i] + 1] = hmerged[i];
     for (int b = 0; b < nb; ++b) O.near_start[b + 1] += O.near_start[b];
-    O.near_begin.clear(); O.near_end.clear();
+    // target boxes are in box order, so their blocks follow near_start
     int64_t pairs = 0;
     for (int i = 0; i < nt; ++i) {
         int64_t len = 0;
-        for (int k = 0; k < hmerged[i]; ++k) {
-            const int2 v = hraw[hoff[i] + k];
-            O.near_begin.push_back(v.x);
-            O.near_end.push_back(v.y);
-            len += v.y - v.x;
-        }
-        pairs += len * O.n_owned_ctr[tboxes[i]];
+        const int b = tboxes[i];
+        for (int64_t k = O.near_start[b]; k < O.near_start[b + 1]; ++k) len += O.near_end[k] - O.near_begin[k];
+        pairs += len * O.n_owned_ctr[b];
     }
     tsqbx_octree_stats &st = O.stats;
     st.n_boxes = nb;
