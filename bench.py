@@ -64,14 +64,22 @@ def flops_per_pair(p, precision, dlp=True, sp=False):
 
 
 def helmholtz_flops_per_pair(p, dlp=False, sp=False):
-    """Helmholtz kernel (FP64): geometry and 1/z 20, 13 per order for the
-    single layer (Hankel factor 5, Legendre 3, complex accumulation 5),
-    closing with e^{iz} and the complex weight 16, sincos counted as 2, orders
-    0 and 1 12.  The double layer adds 18 per order (h_n' factor and its
-    complex sum 9, the differentiated Legendre recurrence and its sum 9) and
-    about 50 of closing (two normal dots, the combination, a second e^{iz}
-    product and weight); S' adds 5 per order (14 without the double layer,
-    whose Legendre-derivative sum it shares) and about 42 of closing."""
+    """Helmholtz kernel (FP64), flops per pair (FMA = 2).
+    * Single layer alone (Clenshaw over the Hankel factors): geometry and 1/z
+      20, the Legendre recurrence forward 3 per order, the backward sum 5 per
+      order, the combination with g_0, g_1 5, and the closing with e^{iz} and
+      the complex weight 16, with sincos counted as 2.  That is 8 p + 40.
+    * With the double layer or S', the forward form: 13 per order for the
+      single layer (Hankel factor 5, Legendre 3, complex accumulation 5), 12
+      for orders 0 and 1, plus the same geometry and closing.
+      * The double layer adds 18 per order (h_n' factor and its complex sum 9,
+        the differentiated Legendre recurrence and its sum 9) and about 50 of
+        closing (two normal dots, the combination, a second e^{iz} product
+        and weight).
+      * S' adds 5 per order, or 14 without the double layer, whose
+        Legendre-derivative sum it shares, and about 42 of closing."""
+    if not dlp and not sp:
+        return 8 * p + 40
     f = 20 + 13 * max(p - 1, 0) + 16 + 2 + 12
     if dlp:
         f += 18 * max(p - 1, 0) + 50

@@ -20,6 +20,12 @@
 //    j_{n+1} (DLMF 10.51.2); the 1/rho of the angular part multiplies
 //    j_n(k rho), whose n = 1 term tends to k/3 as rho -> 0 (taken exactly).
 // The sum of cj_n T'_n g_n serves both the double layer and S'.
+// Single layer alone: since the g_n recurrence has real coefficients
+// (2n+1)/z, sum_n a_n g_n with real a_n = cj_n T_n is summed by Clenshaw's
+// backward recurrence b_n = a_n + (2n+1)/z b_{n+1} - b_{n+2} (b_{p+1} =
+// b_{p+2} = 0), sum = (a_0 - b_2) g_0 + b_1 g_1: three real operations per
+// order instead of the complex Hankel step and complex accumulation.  The
+// T_n go forward first and stay in registers.
 // All of it -- Bessel and Hankel recurrences and the sums -- in FP64.
 #include "helmholtz_items.cuh"
 

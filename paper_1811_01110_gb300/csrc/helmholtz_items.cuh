@@ -150,42 +150,64 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
                 //   D2: cj T'_n           (angular part, shared by double layer and S')
                 //   Pa: caj T_n           (S', radial part)
                 double Ar, Ai, D1r = 0, D1i = 0, D2r = 0, D2i = 0, Par = 0, Pai = 0;
-                double gmr = 0.0, gmi = -w;                 // g_0
-                double gr = -w, gi = -w * w;                // g_1
-                Ar = 0.0; Ai = -cj[0] * w;
-                if (DLP) cfma(-cj[0], gr, gi, D1r, D1i);
-                if (SP) Pai = -caj[0] * w;
-                double Tm = 1.0, Tc = x;                    // T_{n-1}, T_n
-                double Um = 0.0, Uc = 1.0;                  // T'_{n-1}, T'_n
-                if (P >= 1) {
-                    const double c1 = cj[1] * x;
-                    cfma(c1, gr, gi, Ar, Ai);
-                    if (DLP) {
-                        const double t = 2.0 * w;
-                        cfma(c1, fma(-t, gr, gmr), fma(-t, gi, gmi), D1r, D1i);
-                    }
-                    if (DLP || SP) cfma(cj[1], gr, gi, D2r, D2i);
-                    if (SP) cfma(caj[SP ? 1 : 0] * x, gr, gi, Par, Pai);
-                }
+                if constexpr (!DLP && !SP) {
+                    // Single layer alone: the g_n obey g_{n+1} = (2n+1) w g_n -
+                    // g_{n-1} with real coefficients, so sum_n a_n g_n (a_n =
+                    // cj_n T_n) goes by Clenshaw's backward recurrence in real
+                    // arithmetic: b_n = a_n + (2n+1) w b_{n+1} - b_{n+2},
+                    // sum = (a_0 - b_2) g_0 + b_1 g_1, with g_0 = -i w and
+                    // g_1 = -w - i w^2.  T_n forward first (kept in registers).
+                    double Tv[P + 1];
+                    Tv[0] = 1.0;
+                    if (P >= 1) Tv[1] = x;
 #pragma unroll
-                for (int n = 1; n < P; ++n) {
-                    const double t = (2.0 * n + 1.0) * w;
-                    const double nr = fma(t, gr, -gmr), ni = fma(t, gi, -gmi);
-                    gmr = gr; gmi = gi; gr = nr; gi = ni;
-                    const double Tn = fma(x, Tc, -rec_beta(n) * Tm);
-                    if (DLP || SP) {
-                        const double Un = fma(-rec_beta(n), Um, fma(x, Uc, Tc));
-                        Um = Uc; Uc = Un;
-                        cfma(cj[n + 1] * Un, gr, gi, D2r, D2i);
+                    for (int n = 1; n < P; ++n) Tv[n + 1] = fma(x, Tv[n], -rec_beta(n) * Tv[n - 1]);
+                    double b1 = 0.0, b2 = 0.0;
+#pragma unroll
+                    for (int n = P; n >= 1; --n) {
+                        const double bn = fma((2.0 * n + 1.0) * w, b1, fma(cj[n], Tv[n], -b2));
+                        b2 = b1; b1 = bn;
                     }
-                    Tm = Tc; Tc = Tn;
-                    const double c = cj[n + 1] * Tn;
-                    cfma(c, gr, gi, Ar, Ai);
-                    if (DLP) {
-                        const double tt = (n + 2.0) * w;
-                        cfma(c, fma(-tt, gr, gmr), fma(-tt, gi, gmi), D1r, D1i);
+                    Ar = -w * b1;
+                    Ai = -w * fma(w, b1, cj[0] - b2);
+                } else {
+                    double gmr = 0.0, gmi = -w;                 // g_0
+                    double gr = -w, gi = -w * w;                // g_1
+                    Ar = 0.0; Ai = -cj[0] * w;
+                    if (DLP) cfma(-cj[0], gr, gi, D1r, D1i);
+                    if (SP) Pai = -caj[0] * w;
+                    double Tm = 1.0, Tc = x;                    // T_{n-1}, T_n
+                    double Um = 0.0, Uc = 1.0;                  // T'_{n-1}, T'_n
+                    if (P >= 1) {
+                        const double c1 = cj[1] * x;
+                        cfma(c1, gr, gi, Ar, Ai);
+                        if (DLP) {
+                            const double t = 2.0 * w;
+                            cfma(c1, fma(-t, gr, gmr), fma(-t, gi, gmi), D1r, D1i);
+                        }
+                        if (DLP || SP) cfma(cj[1], gr, gi, D2r, D2i);
+                        if (SP) cfma(caj[SP ? 1 : 0] * x, gr, gi, Par, Pai);
                     }
-                    if (SP) cfma(caj[SP ? n + 1 : 0] * Tn, gr, gi, Par, Pai);
+#pragma unroll
+                    for (int n = 1; n < P; ++n) {
+                        const double t = (2.0 * n + 1.0) * w;
+                        const double nr = fma(t, gr, -gmr), ni = fma(t, gi, -gmi);
+                        gmr = gr; gmi = gi; gr = nr; gi = ni;
+                        const double Tn = fma(x, Tc, -rec_beta(n) * Tm);
+                        if (DLP || SP) {
+                            const double Un = fma(-rec_beta(n), Um, fma(x, Uc, Tc));
+                            Um = Uc; Uc = Un;
+                            cfma(cj[n + 1] * Un, gr, gi, D2r, D2i);
+                        }
+                        Tm = Tc; Tc = Tn;
+                        const double c = cj[n + 1] * Tn;
+                        cfma(c, gr, gi, Ar, Ai);
+                        if (DLP) {
+                            const double tt = (n + 2.0) * w;
+                            cfma(c, fma(-tt, gr, gmr), fma(-tt, gi, gmi), D1r, D1i);
+                        }
+                        if (SP) cfma(caj[SP ? n + 1 : 0] * Tn, gr, gi, Par, Pai);
+                    }
                 }
                 double sn, cs;
                 sincos(z, &sn, &cs);
