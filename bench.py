@@ -64,27 +64,25 @@ def flops_per_pair(p, precision, dlp=True, sp=False):
 
 
 def helmholtz_flops_per_pair(p, dlp=False, sp=False):
-    """Helmholtz kernel (FP64), flops per pair (FMA = 2).
-    * Single layer alone (Clenshaw over the Hankel factors): geometry and 1/z
-      20, the Legendre recurrence forward 3 per order, the backward sum 5 per
-      order, the combination with g_0, g_1 5, and the closing with e^{iz} and
-      the complex weight 16, with sincos counted as 2.  That is 8 p + 40.
-    * With the double layer or S', the forward form: 13 per order for the
-      single layer (Hankel factor 5, Legendre 3, complex accumulation 5), 12
-      for orders 0 and 1, plus the same geometry and closing.
-      * The double layer adds 18 per order (h_n' factor and its complex sum 9,
-        the differentiated Legendre recurrence and its sum 9) and about 50 of
-        closing (two normal dots, the combination, a second e^{iz} product
-        and weight).
-      * S' adds 5 per order, or 14 without the double layer, whose
-        Legendre-derivative sum it shares, and about 42 of closing."""
-    if not dlp and not sp:
-        return 8 * p + 40
-    f = 20 + 13 * max(p - 1, 0) + 16 + 2 + 12
-    if dlp:
-        f += 18 * max(p - 1, 0) + 50
+    """Helmholtz kernel (FP64), flops per pair (FMA = 2).  Every layer is a
+    Clenshaw sum over the Hankel factors in real arithmetic.
+    * Common to all: geometry and 1/z 20, sincos counted as 2, the Legendre
+      recurrence forward 3 per order step, (2n+1)/z 1 per order, and for the
+      single layer the combination with g_0, g_1 5 plus the closing with
+      e^{iz} and the complex weight 16.
+    * Single layer alone: 4 per order backward (the product folded into an
+      FMA).  That is 8 p + 40 in all.
+    * With the double layer: T'_n forward 4 per step, and 14 per order
+      backward for both sums (a_n, the single layer's step, e_n, the double
+      layer's coefficient and step).  Closing: normal dots 17, combination 11,
+      e^{iz} and weight 16.
+    * S': T'_n forward 4 per step (unless the double layer has it), 7 per
+      order backward, normal dot 10, combination 5, e^{iz} and weight 16."""
+    q = max(p - 1, 0)
+    f = 20 + 2 + 3 * q + p + 5 + 16
+    f += 14 * p + 4 * q + 17 + 11 + 16 if dlp else 4 * p
     if sp:
-        f += (5 if dlp else 14) * max(p - 1, 0) + 42
+        f += 7 * p + (0 if dlp else 4 * q) + 10 + 5 + 16
     return f
 
 
@@ -296,7 +294,7 @@ TRAFFIC_BYTES = {
     ("laplace", "fp64", "slp+dlp"): 75.37e6,
     ("laplace", "mixed", "slp+dlp"): 56.68e6,
     ("laplace", "df64", "slp+dlp"): 75.21e6,
-    ("helmholtz", "fp64", "slp"): 322.75e6,
+    ("helmholtz", "fp64", "slp"): None,       # changed since the last capture
     ("batched", "mixed", "slp"): 1129.56e6,
 }
 

@@ -143,72 +143,75 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
                 const double x = fma(dx, ex, fma(dy, ey, dz * ez)) * rinv * rhoinv;
                 const double w = rinv * kinv;               // 1/z
                 const double z = k * (R2 * rinv);
-                // Sums over n of g_n (h_n = e^{iz} g_n) times
-                //   A : cj T_n            (single layer)
-                //   D1: cj T_n g'_n-part  (double layer, radial: h_n' = e^{iz} gd_n,
-                //                          gd_n = g_{n-1} - (n+1) w g_n, gd_0 = -g_1)
-                //   D2: cj T'_n           (angular part, shared by double layer and S')
-                //   Pa: caj T_n           (S', radial part)
-                double Ar, Ai, D1r = 0, D1i = 0, D2r = 0, D2i = 0, Par = 0, Pai = 0;
-                if constexpr (!DLP && !SP) {
-                    // Single layer alone: the g_n obey g_{n+1} = (2n+1) w g_n -
-                    // g_{n-1} with real coefficients, so sum_n a_n g_n (a_n =
-                    // cj_n T_n) goes by Clenshaw's backward recurrence in real
-                    // arithmetic: b_n = a_n + (2n+1) w b_{n+1} - b_{n+2},
-                    // sum = (a_0 - b_2) g_0 + b_1 g_1, with g_0 = -i w and
-                    // g_1 = -w - i w^2.  T_n forward first (kept in registers).
-                    double Tv[P + 1];
-                    Tv[0] = 1.0;
-                    if (P >= 1) Tv[1] = x;
+                // Every layer is a sum over n of g_n (h_n = e^{iz} g_n) with real
+                // coefficients c_n.  The g_n obey g_{n+1} = (2n+1) w g_n - g_{n-1}
+                // (g_{-1} = w, g_0 = -i w, g_1 = -w - i w^2), so each sum goes by
+                // Clenshaw's backward recurrence b_n = c_n + (2n+1) w b_{n+1} -
+                // b_{n+2}: sum = (c_0 - b_2) g_0 + b_1 g_1, in real arithmetic.
+                //  * single layer: c_n = a_n = cj_n T_n;
+                //  * double layer, kah D1 + u D2 with D1 = sum a_n h_n'/e^{iz} and
+                //    h_n' = e^{iz} (g_{n-1} - (n+1) w g_n):  D1 = a_0 w + sum e_n g_n,
+                //    e_n = a_{n+1} - (n+1) w a_n (a_{P+1} = 0);  c_n = kah e_n +
+                //    u cj_n T'_n, and kah a_0 w adds to the real part;
+                //  * S', C B + Pa:  c_n = (C/rho) cj_n T'_n + caj_n T_n, plus C b1 on
+                //    g_1 (the rho = 0 limit of the n = 1 term).
+                // T_n and T'_n go forward first and stay in registers.
+                double kah = 0.0, u = 0.0, Cr = 0.0, Cl = 0.0;
+                if (DLP) {
+                    // n_s.grad_s: R' = a/R, x' = (1/R) ((e.n_s)/rho - (a/R) x), a = d.n_s
+                    const double nx = T[kRows - 3][kk], ny = T[kRows - 2][kk], nz = T[kRows - 1][kk];
+                    const double ah = fma(dx, nx, fma(dy, ny, dz * nz)) * rinv;
+                    u = (fma(ex, nx, fma(ey, ny, ez * nz)) * rhoinv - ah * x) * rinv;
+                    kah = k * ah;
+                }
+                if (SP) {
+                    // n_t.grad_t: rho' = that.n_t, x' = (1/rho) ((d.n_t)/R - (that.n_t) x)
+                    const double C = fma(dx, tx, fma(dy, ty, dz * tz)) * rinv - tdot * x;
+                    Cr = C * rhoinv;
+                    Cl = C * b1;
+                }
+                double Tv[P + 1], Uv[(DLP || SP) ? P + 1 : 1];
+                Tv[0] = 1.0;
+                if (P >= 1) Tv[1] = x;
+                if (DLP || SP) {
+                    Uv[0] = 0.0;
+                    if (P >= 1) Uv[(DLP || SP) ? 1 : 0] = 1.0;
+                }
 #pragma unroll
-                    for (int n = 1; n < P; ++n) Tv[n + 1] = fma(x, Tv[n], -rec_beta(n) * Tv[n - 1]);
-                    double b1 = 0.0, b2 = 0.0;
+                for (int n = 1; n < P; ++n) {
+                    Tv[n + 1] = fma(x, Tv[n], -rec_beta(n) * Tv[n - 1]);
+                    if (DLP || SP) Uv[n + 1] = fma(-rec_beta(n), Uv[n - 1], fma(x, Uv[n], Tv[n]));
+                }
+                double bA1 = 0.0, bA2 = 0.0, bD1 = 0.0, bD2 = 0.0, bS1 = 0.0, bS2 = 0.0, a_next = 0.0;
 #pragma unroll
-                    for (int n = P; n >= 1; --n) {
-                        const double bn = fma((2.0 * n + 1.0) * w, b1, fma(cj[n], Tv[n], -b2));
-                        b2 = b1; b1 = bn;
+                for (int n = P; n >= 1; --n) {
+                    const double t = (2.0 * n + 1.0) * w;
+                    if (DLP) {
+                        const double an = cj[n] * Tv[n];
+                        const double bA = fma(t, bA1, an - bA2);
+                        bA2 = bA1; bA1 = bA;
+                        const double en = fma(-(n + 1.0) * w, an, a_next);
+                        const double bD = fma(t, bD1, fma(kah, en, u * (cj[n] * Uv[n])) - bD2);
+                        bD2 = bD1; bD1 = bD;
+                        a_next = an;
+                    } else {
+                        const double bA = fma(t, bA1, fma(cj[n], Tv[n], -bA2));
+                        bA2 = bA1; bA1 = bA;
                     }
-                    Ar = -w * b1;
-                    Ai = -w * fma(w, b1, cj[0] - b2);
-                } else {
-                    double gmr = 0.0, gmi = -w;                 // g_0
-                    double gr = -w, gi = -w * w;                // g_1
-                    Ar = 0.0; Ai = -cj[0] * w;
-                    if (DLP) cfma(-cj[0], gr, gi, D1r, D1i);
-                    if (SP) Pai = -caj[0] * w;
-                    double Tm = 1.0, Tc = x;                    // T_{n-1}, T_n
-                    double Um = 0.0, Uc = 1.0;                  // T'_{n-1}, T'_n
-                    if (P >= 1) {
-                        const double c1 = cj[1] * x;
-                        cfma(c1, gr, gi, Ar, Ai);
-                        if (DLP) {
-                            const double t = 2.0 * w;
-                            cfma(c1, fma(-t, gr, gmr), fma(-t, gi, gmi), D1r, D1i);
-                        }
-                        if (DLP || SP) cfma(cj[1], gr, gi, D2r, D2i);
-                        if (SP) cfma(caj[SP ? 1 : 0] * x, gr, gi, Par, Pai);
-                    }
-#pragma unroll
-                    for (int n = 1; n < P; ++n) {
-                        const double t = (2.0 * n + 1.0) * w;
-                        const double nr = fma(t, gr, -gmr), ni = fma(t, gi, -gmi);
-                        gmr = gr; gmi = gi; gr = nr; gi = ni;
-                        const double Tn = fma(x, Tc, -rec_beta(n) * Tm);
-                        if (DLP || SP) {
-                            const double Un = fma(-rec_beta(n), Um, fma(x, Uc, Tc));
-                            Um = Uc; Uc = Un;
-                            cfma(cj[n + 1] * Un, gr, gi, D2r, D2i);
-                        }
-                        Tm = Tc; Tc = Tn;
-                        const double c = cj[n + 1] * Tn;
-                        cfma(c, gr, gi, Ar, Ai);
-                        if (DLP) {
-                            const double tt = (n + 2.0) * w;
-                            cfma(c, fma(-tt, gr, gmr), fma(-tt, gi, gmi), D1r, D1i);
-                        }
-                        if (SP) cfma(caj[SP ? n + 1 : 0] * Tn, gr, gi, Par, Pai);
+                    if (SP) {
+                        double hn = fma(Cr, cj[n] * Uv[(DLP || SP) ? n : 0], caj[SP ? n : 0] * Tv[n]);
+                        if (n == 1) hn += Cl;
+                        const double bS = fma(t, bS1, hn - bS2);
+                        bS2 = bS1; bS1 = bS;
                     }
                 }
+                // (c_0 - b_2) g_0 + b_1 g_1 = (-w b_1, -w (c_0 - b_2 + w b_1))
+                auto close = [&](double c0, double bb1, double bb2, double &re, double &im) {
+                    re = -w * bb1;
+                    im = -w * fma(w, bb1, c0 - bb2);
+                };
+                double Ar, Ai;
+                close(cj[0], bA1, bA2, Ar, Ai);
                 double sn, cs;
                 sincos(z, &sn, &cs);
                 const double wr = T[3][kk], wi = T[4][kk];
@@ -221,20 +224,14 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
                 };
                 accumulate(Ar, Ai, acc_re, acc_im);
                 if (DLP) {
-                    // n_s.grad_s: R' = a/R, x' = (1/R) ((e.n_s)/rho - (a/R) x), a = d.n_s
-                    const double nx = T[kRows - 3][kk], ny = T[kRows - 2][kk], nz = T[kRows - 1][kk];
-                    const double ah = fma(dx, nx, fma(dy, ny, dz * nz)) * rinv;
-                    const double u = (fma(ex, nx, fma(ey, ny, ez * nz)) * rhoinv - ah * x) * rinv;
-                    const double kah = k * ah;
-                    accumulate(fma(kah, D1r, u * D2r), fma(kah, D1i, u * D2i), dacc_re, dacc_im);
+                    double Dr, Di;
+                    close(kah * fma(-w, cj[0], a_next), bD1, bD2, Dr, Di);     // a_next = a_1 (0 if P = 0)
+                    accumulate(fma(kah * cj[0], w, Dr), Di, dacc_re, dacc_im);
                 }
                 if (SP) {
-                    // n_t.grad_t: rho' = that.n_t, x' = (1/rho) ((d.n_t)/R - (that.n_t) x)
-                    const double C = fma(dx, tx, fma(dy, ty, dz * tz)) * rinv - tdot * x;
-                    // (1/rho) sum cj T'_n g_n, plus the rho = 0 limit of the n = 1 term
-                    const double Br = fma(rhoinv, D2r, b1 * (P >= 1 ? -w : 0.0));
-                    const double Bi = fma(rhoinv, D2i, b1 * (P >= 1 ? -w * w : 0.0));
-                    accumulate(fma(C, Br, Par), fma(C, Bi, Pai), pacc_re, pacc_im);
+                    double Sr, Si;
+                    close(caj[0], bS1, bS2, Sr, Si);                           // c_0 = caj_0 (T'_0 = 0)
+                    accumulate(Sr, Si, pacc_re, pacc_im);
                 }
             }
         }
