@@ -294,7 +294,7 @@ TRAFFIC_BYTES = {
     ("laplace", "fp64", "slp+dlp"): 75.37e6,
     ("laplace", "mixed", "slp+dlp"): 56.68e6,
     ("laplace", "df64", "slp+dlp"): 75.21e6,
-    ("helmholtz", "fp64", "slp"): None,       # changed since the last capture
+    ("helmholtz", "fp64", "slp"): 324.34e6,
     ("batched", "mixed", "slp"): 1129.56e6,
 }
 
