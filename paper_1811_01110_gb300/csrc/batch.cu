@@ -81,7 +81,7 @@ __device__ __forceinline__ void run_item_mixed(int p, const DevGeom &g, const De
 }
 
 template <bool MIXED, bool DLP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, DLP ? 1 : 8)
 batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, const WalkStart *walks,
                      int64_t n_items, unsigned long long *head)
 {
