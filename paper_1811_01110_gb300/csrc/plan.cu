@@ -236,7 +236,8 @@ int cost_bucket(double cost) { return cost > 0 ? (int)std::floor(2.0 * std::log2
 
 // Cost per unit in ns, measured on GB300 (torus 96 x 36, every center on one
 // path, kernel time of whole evaluations; orders 2..20 for Laplace, 2..12 for
-// Helmholtz k = 10) and fitted in q = p + 1, the form of Table 2:
+// Helmholtz k = 10, whose target-specific sums are Clenshaw's) and fitted in
+// q = p + 1, the form of Table 2:
 //   target-specific, per (target, source) pair:      ts0 + ts1 q
 //   P2QBXL, per (center, source):                    c0 + c1 q + c2 q^2
 //   QBXL2P, per warp item (a center's <= 32 targets): w0 + w1 q + w2 q^2
@@ -256,13 +257,13 @@ constexpr ConvCostFit kLaplaceCost[8] = {
 };
 constexpr ConvCostFit kHelmholtzCost[8] = {
     {{0, 0}, {0, 0, 0}, {0, 0, 0}},
-    {{0.08178, 0.01458}, {0.08981, 0.01622, 0.01129}, {9.758, 2.279, 0.2306}},   // slp
-    {{0.1037, 0.03277}, {0.1014, 0.03242, 0.02055}, {10.16, 2.145, 0.2431}},     // dlp
-    {{0.1036, 0.03279}, {0.1264, 0.03291, 0.02829}, {10.99, 1.983, 0.4262}},     // slp+dlp
-    {{0.1012, 0.02863}, {0.08737, 0.01723, 0.01122}, {11.05, 2.606, 0.7122}},    // sp
-    {{0.1012, 0.02863}, {0.08737, 0.01723, 0.01122}, {11.05, 2.606, 0.7122}},    // slp+sp
-    {{0.139, 0.03773}, {0.1284, 0.03217, 0.02833}, {10.61, 2.948, 0.8605}},      // dlp+sp
-    {{0.1391, 0.03774}, {0.1285, 0.0325, 0.02831}, {10.79, 2.812, 0.872}},       // slp+dlp+sp
+    {{0.09568, 0.009309}, {0.08981, 0.01622, 0.01129}, {9.758, 2.279, 0.2306}},  // slp
+    {{0.1096, 0.02873}, {0.1014, 0.03242, 0.02055}, {10.16, 2.145, 0.2431}},     // dlp
+    {{0.1096, 0.02874}, {0.1264, 0.03291, 0.02829}, {10.99, 1.983, 0.4262}},     // slp+dlp
+    {{0.1106, 0.02201}, {0.08737, 0.01723, 0.01122}, {11.05, 2.606, 0.7122}},    // sp
+    {{0.1106, 0.02201}, {0.08737, 0.01723, 0.01122}, {11.05, 2.606, 0.7122}},    // slp+sp
+    {{0.1388, 0.03545}, {0.1284, 0.03217, 0.02833}, {10.61, 2.948, 0.8605}},     // dlp+sp
+    {{0.1389, 0.03545}, {0.1285, 0.0325, 0.02831}, {10.79, 2.812, 0.872}},       // slp+dlp+sp
 };
 
 bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool helmholtz)
