@@ -185,6 +185,22 @@ def test_helmholtz_slp(pkg, p, k):
     assert relerr(out, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("p,k", [(6, 0.01), (16, 0.01), (6, 30.0), (16, 30.0), (20, 60.0)])
+def test_helmholtz_extreme_wavenumbers_all_layers(pkg, p, k):
+    """The Clenshaw sums over the Hankel factors where they grow fastest (kR
+    ~ 1e-2: g_n ~ (2n-1)!!/(kR)^(n+1)) and where they oscillate (kR up to
+    ~100, beyond the order), for every layer combination."""
+    rng = np.random.default_rng(int(10 * k) + p)
+    g = cloud_geometry(rng, n_ctr=10, n_src=120, q_max=0.6, tgt_per_ctr=3, rho_zero=True)
+    mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+    ref = oracle.tsqbx_helmholtz(g, p, k, mu, slp=True, dlp=True, sp=True)
+    for layers in (("slp",), ("dlp",), ("slp", "dlp"), ("slp", "sp"), ("slp", "dlp", "sp")):
+        with pkg.Plan(g, "helmholtz", layers, p=p, k=k) as plan:
+            out = plan.eval(mu)
+        for layer in layers:
+            assert relerr(out[layer], ref[layer]) <= 1e-12, (layers, layer)
+
+
 def test_helmholtz_small_torus(pkg):
     g, mu, _ = configs.torus_helmholtz(40, 16, k=10.0)
     ref = oracle.tsqbx_helmholtz(g, 12, 10.0, mu)["slp"]
