@@ -210,7 +210,15 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
 // (s_lo - c_lo) from float-float coordinates.  hx.. = source hi coordinates, w = w mu, lx.. = lo parts,
 // nx.. = n_s; ch/cl = center hi/lo, e = {t - c, rho^2}, tn = {n_t, e.n_t}
 // (per target, both halves equal); Kahan pairs per layer, per half.
-template <int P, bool DLP, bool SP>
+// Adds x to the packed sum s: Kahan-compensated (c the compensation) or plain.
+template <bool KAHAN>
+__device__ __forceinline__ void sum_add2(f2 &s, f2 &c, f2 x)
+{
+    if constexpr (KAHAN) kahan_add2(s, c, x);
+    else s = add2(s, x);
+}
+
+template <int P, bool DLP, bool SP, bool KAHAN = true>
 __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2 ly, f2 lz, f2 nx, f2 ny, f2 nz,
                                             const float4 &ch, const float4 &cl, const float4 &e,
                                             const float4 &tn, f2 &as, f2 &ac, f2 &ds, f2 &dc, f2 &ps, f2 &pc)
@@ -235,7 +243,7 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
             const f2 bk = fma2(bq, b2, fma2(qx, b1, f2_splat((float)rec_kappa(k))));
             b2 = b1; b1 = bk;
         }
-        kahan_add2(as, ac, mul2(wr, b1));
+        sum_add2<KAHAN>(as, ac, mul2(wr, b1));
     } else {
         f2 Um = f2_splat(0.f), Uc = f2_splat(1.f), S2m = f2_splat(0.f);
 #pragma unroll
@@ -254,17 +262,17 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
         const f2 S2 = add2(S2m, Qp);
         const f2 c1 = add2(fma2(f2_splat(-2.f), qx, f2_splat(1.f)), q2);
         const f2 S = fma2(c1, S2, fma2(sub2(f2_splat(0.f), q2), Qp, Qp1));
-        kahan_add2(as, ac, mul2(wr, S));
+        sum_add2<KAHAN>(as, ac, mul2(wr, S));
         const f2 wr3 = mul2(wr, r2inv);
         if (DLP) {
             const f2 a = fma2(dx, nx, fma2(dy, ny, mul2(dz, nz)));
             const f2 b = fma2(f2_splat(e.x), nx, fma2(f2_splat(e.y), ny, mul2(f2_splat(e.z), nz)));
             const f2 na = sub2(f2_splat(0.f), a);
-            kahan_add2(ds, dc, mul2(wr3, fma2(na, Qp1, mul2(sub2(b, a), S2))));
+            sum_add2<KAHAN>(ds, dc, mul2(wr3, fma2(na, Qp1, mul2(sub2(b, a), S2))));
         }
         if (SP) {
             const f2 dn = fma2(dx, f2_splat(tn.x), fma2(dy, f2_splat(tn.y), mul2(dz, f2_splat(tn.z))));
-            kahan_add2(ps, pc, mul2(wr3, fma2(dn, S2, mul2(f2_splat(-tn.w), S2m))));
+            sum_add2<KAHAN>(ps, pc, mul2(wr3, fma2(dn, S2, mul2(f2_splat(-tn.w), S2m))));
         }
     }
 }
@@ -394,12 +402,19 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         }
         __syncwarp();
         if (active) {
+            // plain FP32 sums over the tile (at most 32 source pairs per lane),
+            // added to the compensated sums once per tile
+            f2 ts = z2, td = z2, tp = z2, unused = z2;
             for (int q = sub; q < npairs; q += L) {
                 const float4 A = T[0][q], B = T[1][q], C = T[2][q], D = T[3][q];
                 const float4 E = DLP ? T[4][q] : zero;
-                pair_mixed2<P, DLP, SP>(f2_xy(A), f2_zw(A), f2_xy(B), f2_zw(B), f2_xy(C), f2_zw(C), f2_xy(D),
-                                        f2_zw(D), f2_xy(E), f2_zw(E), ch, cl, e, tn, as, ac, ds, dc, ps, pc);
+                pair_mixed2<P, DLP, SP, false>(f2_xy(A), f2_zw(A), f2_xy(B), f2_zw(B), f2_xy(C), f2_zw(C),
+                                               f2_xy(D), f2_zw(D), f2_xy(E), f2_zw(E), ch, cl, e, tn, ts, unused,
+                                               td, unused, tp, unused);
             }
+            kahan_add2(as, ac, ts);
+            if (DLP) kahan_add2(ds, dc, td);
+            if (SP) kahan_add2(ps, pc, tp);
         }
         __syncwarp();
     }
