@@ -293,10 +293,10 @@ def gpu_selector(dev, local_rank):
 # A kernel changed since its capture must map to None here.
 TRAFFIC_BYTES = {
     ("laplace", "fp64", "slp+dlp"): 75.37e6,
-    ("laplace", "mixed", "slp+dlp"): None,       # changed since the last capture
+    ("laplace", "mixed", "slp+dlp"): 56.91e6,
     ("laplace", "df64", "slp+dlp"): 75.21e6,
     ("helmholtz", "fp64", "slp"): 324.34e6,
-    ("batched", "mixed", "slp"): None,           # changed since the last capture
+    ("batched", "mixed", "slp"): 1147.67e6,
 }
 
 
