@@ -209,7 +209,10 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
 // for the sources in the two halves, with s - c formed as (s_hi - c_hi) +
 // (s_lo - c_lo) from float-float coordinates.  hx.. = source hi coordinates, w = w mu, lx.. = lo parts,
 // nx.. = n_s; ch/cl = center hi/lo, e = {t - c, rho^2}, tn = {n_t, e.n_t}
-// (per target, both halves equal); Kahan pairs per layer, per half.
+// (per target, both halves equal); one sum per layer, per half, added with
+// sum_add2 (KAHAN: compensated per pair; else plain, the caller compensating
+// per tile).
+
 // Adds x to the packed sum s: Kahan-compensated (c the compensation) or plain.
 template <bool KAHAN>
 __device__ __forceinline__ void sum_add2(f2 &s, f2 &c, f2 x)

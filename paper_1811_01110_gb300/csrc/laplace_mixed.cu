@@ -9,8 +9,10 @@
 //    nearby sources lose no digits to cancellation;
 //  * e = t - c and rho^2 are formed in FP64 at plan time and rounded once;
 //  * the geometry ratios, 1/R (rsqrtf) and the recurrence run in FP32;
-//  * each lane keeps Kahan-compensated FP32 sums; the L lanes of a target are
-//    combined in FP64, and the output is FP64;
+//  * each lane sums a shared-memory tile's pairs in plain FP32 and adds the
+//    tile sum to Kahan-compensated FP32 sums (single-target items compensate
+//    every pair); the L lanes of a target are combined in double-float on the
+//    FP32 pipes, and the output is FP64;
 //  * each lane takes two sources at a time and runs every FP32 operation as
 //    a packed f32x2 instruction (f32x2.cuh): the same flops in half the issue
 //    slots.  The staged tile holds sources pairwise, so one 16-byte shared
