@@ -6,7 +6,9 @@
 // independent warps pops items from the queue with an atomic counter, so a
 // warp that finishes a light item immediately takes the next one; each item
 // carries its plan index, and the order p may differ between plans (the item
-// body is instantiated per p and selected per item).  The whole sequence --
+// body is instantiated per p and selected per item).  In single-layer mixed
+// batches two consecutive single-target items of one plan run together, one
+// per half-warp, so that their dependent loads overlap.  The whole sequence --
 // copy of the per-evaluation pointer table, w mu preparation for every plan,
 // queue reset, persistent kernel, slice combine -- is captured once into a
 // CUDA graph and replayed per evaluation.
@@ -80,6 +82,13 @@ __device__ __forceinline__ void run_item_mixed(int p, const DevGeom &g, const De
     ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, ws, T, lane), 0) : 0), ...);
 }
 
+template <int... Ps>
+__device__ __forceinline__ void run_half_item_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
+                                                    const WalkStart &ws, int hl, std::integer_sequence<int, Ps...>)
+{
+    ((p == Ps ? (laplace_mixed_half_item<Ps>(g, ev, it, ws, hl), 0) : 0), ...);
+}
+
 template <bool MIXED, bool DLP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, DLP ? 1 : 8)
 batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, const WalkStart *walks,
@@ -103,6 +112,20 @@ batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *item
             DevEval ev = bp.ev;
             ev.out_slp = io[it.pad].out_slp;
             ev.out_dlp = io[it.pad].out_dlp;
+            if constexpr (MIXED && !DLP) {
+                // two single-target items of one plan: one per half-warp
+                if (it.n_tgt == 1 && idx + 1 < last) {
+                    const Item it2 = items[idx + 1];
+                    if (it2.n_tgt == 1 && it2.pad == it.pad) {
+                        const bool upper = lane >= 16;
+                        run_half_item_mixed(bp.p, bp.g, ev, upper ? it2 : it, upper ? walks[idx + 1] : ws,
+                                            lane & 15, std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
+                        __syncwarp();
+                        ++idx;
+                        continue;
+                    }
+                }
+            }
             unsigned char *mine = tile_raw + warp * kWarpBytes;
             if constexpr (MIXED)
                 run_item_mixed<DLP>(bp.p, bp.g, ev, it, ws, reinterpret_cast<float4 (*)[kMixedPairs]>(mine), lane,

@@ -345,6 +345,35 @@ __device__ __forceinline__ void load_mixed_pair(const DevGeom &g, const DevEval 
     }
 }
 
+// A single-target item of the single layer on one half of a warp (hl =
+// lane within the half, 0..15), so that a warp works two such items at once
+// and their dependent loads overlap: each lane takes sources k and k + 16 of
+// every 32, and the half reduces over its 16 lanes (xor offsets below 16
+// stay within a half).  Both halves must run the same P.
+template <int P>
+__device__ __forceinline__ void laplace_mixed_half_item(const DevGeom &g, const DevEval &ev, const Item &it,
+                                                        const WalkStart &ws, const int hl)
+{
+    ListWalk walk(g, ws);
+    const int src_hi = it.src_hi;
+    const f2 z2 = f2_splat(0.f);
+    f2 as = z2, ac = z2, unused = z2;
+    const float4 ch = g.slot_chi[it.slot_begin];
+    const float4 cl = g.slot_clo[it.slot_begin];
+    const float4 e = g.slot_ef[it.slot_begin];
+    const float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = it.src_lo + hl; k < src_hi; k += 32) {
+        f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
+        load_mixed_pair<false>(g, ev, walk, k, k + 16 < src_hi ? k + 16 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
+        pair_mixed2<P, false, false>(hx, hy, hz, w, lx, ly, lz, nx, ny, nz, ch, cl, e, tn, as, ac, unused, unused,
+                                     unused, unused);
+    }
+    df v = kahan2_df(as, ac);
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
+    if (hl == 0) write_item_result<false, false>(g, ev, it, 0, df_to_double(v), 0.0, 0.0);
+}
+
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEval &ev, const Item &it,
                                                    const WalkStart &ws, float4 (*T)[kMixedPairs], const int lane)

@@ -79,3 +79,35 @@ def test_batch_rejects_mixed_kinds(env):
     finally:
         for p_ in (a, b, h):
             p_.close()
+
+
+def test_single_layer_mixed_batch_half_warp_items(env):
+    """Single-target items of one plan run two per warp (one per half-warp)
+    in single-layer mixed batches: results within 1e-6 of the oracle and of
+    each plan alone (the half reduces in another order), and bit-identical
+    from one replay to the next."""
+    torch, pkg = env
+    from tsqbx_inputs import configs
+    items = configs.ellipsoid_batch(n_surfaces=6, max_src=20000)
+    plans = [pkg.Plan(g, "laplace", ("slp",), p=g.meta["p"], precision="mixed") for g, mu in items]
+    try:
+        with pkg.Batch(plans) as batch:
+            runs = []
+            for rep in range(2):
+                dens = [torch.from_numpy(mu).cuda() for g, mu in items]
+                outs = [{"slp": torch.full((g.n_tgt,), np.nan, dtype=torch.float64, device="cuda")}
+                        for g, mu in items]
+                batch.eval_async(dens, outs, stream=torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                runs.append([o["slp"].cpu().numpy() for o in outs])
+            for a, b in zip(*runs):
+                assert np.array_equal(a, b)
+            for (g, mu), plan, got in zip(items, plans, runs[0]):
+                single = plan.eval(mu)["slp"]
+                assert np.max(np.abs(got - single)) / np.max(np.abs(single)) <= 1e-6
+                idx = np.sort(np.random.default_rng(1).choice(g.n_tgt, min(300, g.n_tgt), replace=False))
+                ref = oracle.tsqbx_laplace(g, g.meta["p"], mu, subset=idx)["slp"]
+                assert np.max(np.abs(got[idx] - ref)) / np.max(np.abs(ref)) <= 1e-6
+    finally:
+        for p_ in plans:
+            p_.close()
