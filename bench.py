@@ -718,10 +718,11 @@ def main():
 
     if rank != 0:
         return
-    # ---- CPU baseline (oracle on a bounded sample) + error of both GPU paths there
+    # ---- CPU baseline (oracle on a bounded sample) + error of both GPU paths
+    # there; on rank 0 of a one-GPU run only
     cpu = None
     err = {}
-    if not args.no_cpu:
+    if not args.no_cpu and world == 1:
         cs = cpu_sample(g, mu, args.cpu_seconds)
         cpu = {"value": cs["value"], "unit": UNIT, "cores": cs["cores"], "kind": "oracle",
                "sample": f"{len(cs['idx'])} random targets ({cs['pairs']} pairs, "
