@@ -7,8 +7,9 @@
 // warp that finishes a light item immediately takes the next one; each item
 // carries its plan index, and the order p may differ between plans (the item
 // body is instantiated per p and selected per item).  In single-layer mixed
-// batches two consecutive single-target items of one plan run together, one
-// per half-warp, so that their dependent loads overlap.  The whole sequence --
+// batches up to four consecutive single-target items of one plan run
+// together (8 or 16 lanes each), so that their dependent loads overlap.  The
+// whole sequence --
 // copy of the per-evaluation pointer table, w mu preparation for every plan,
 // queue reset, persistent kernel, slice combine -- is captured once into a
 // CUDA graph and replayed per evaluation.
@@ -82,11 +83,11 @@ __device__ __forceinline__ void run_item_mixed(int p, const DevGeom &g, const De
     ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, ws, T, lane), 0) : 0), ...);
 }
 
-template <int... Ps>
-__device__ __forceinline__ void run_half_item_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
-                                                    const WalkStart &ws, int hl, std::integer_sequence<int, Ps...>)
+template <int W, int... Ps>
+__device__ __forceinline__ void run_part_item_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
+                                                    const WalkStart &ws, int sl, std::integer_sequence<int, Ps...>)
 {
-    ((p == Ps ? (laplace_mixed_half_item<Ps>(g, ev, it, ws, hl), 0) : 0), ...);
+    ((p == Ps ? (laplace_mixed_part_item<Ps, W>(g, ev, it, ws, sl), 0) : 0), ...);
 }
 
 template <bool MIXED, bool DLP>
@@ -113,17 +114,27 @@ batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *item
             ev.out_slp = io[it.pad].out_slp;
             ev.out_dlp = io[it.pad].out_dlp;
             if constexpr (MIXED && !DLP) {
-                // two single-target items of one plan: one per half-warp
-                if (it.n_tgt == 1 && idx + 1 < last) {
-                    const Item it2 = items[idx + 1];
-                    if (it2.n_tgt == 1 && it2.pad == it.pad) {
-                        const bool upper = lane >= 16;
-                        run_half_item_mixed(bp.p, bp.g, ev, upper ? it2 : it, upper ? walks[idx + 1] : ws,
-                                            lane & 15, std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
-                        __syncwarp();
-                        ++idx;
-                        continue;
+                // up to four single-target items of one plan: 8 or 16 lanes each
+                int m = 0;
+                if (it.n_tgt == 1)
+                    for (m = 1; m < 4 && idx + m < last; ++m) {
+                        const Item o = items[idx + m];
+                        if (o.n_tgt != 1 || o.pad != it.pad) break;
                     }
+                if (m >= 2) {
+                    const int W = m >= 4 ? 8 : 16;
+                    const int q = lane / W;
+                    const Item mine_it = items[idx + q];
+                    const WalkStart mine_ws = walks[idx + q];
+                    if (W == 8)
+                        run_part_item_mixed<8>(bp.p, bp.g, ev, mine_it, mine_ws, lane & 7,
+                                               std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
+                    else
+                        run_part_item_mixed<16>(bp.p, bp.g, ev, mine_it, mine_ws, lane & 15,
+                                                std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
+                    __syncwarp();
+                    idx += 32 / W - 1;
+                    continue;
                 }
             }
             unsigned char *mine = tile_raw + warp * kWarpBytes;

@@ -345,14 +345,14 @@ __device__ __forceinline__ void load_mixed_pair(const DevGeom &g, const DevEval 
     }
 }
 
-// A single-target item of the single layer on one half of a warp (hl =
-// lane within the half, 0..15), so that a warp works two such items at once
-// and their dependent loads overlap: each lane takes sources k and k + 16 of
-// every 32, and the half reduces over its 16 lanes (xor offsets below 16
-// stay within a half).  Both halves must run the same P.
-template <int P>
-__device__ __forceinline__ void laplace_mixed_half_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                        const WalkStart &ws, const int hl)
+// A single-target item of the single layer on W lanes of a warp (W = 16 or
+// 8; sl = lane within the group), so that a warp works 32/W such items at
+// once and their dependent loads overlap: each lane takes sources k and k + W
+// of every 2W, and the group reduces over its W lanes (xor offsets below W
+// stay within a group).  Every group must run the same P.
+template <int P, int W>
+__device__ __forceinline__ void laplace_mixed_part_item(const DevGeom &g, const DevEval &ev, const Item &it,
+                                                        const WalkStart &ws, const int sl)
 {
     ListWalk walk(g, ws);
     const int src_hi = it.src_hi;
@@ -362,16 +362,16 @@ __device__ __forceinline__ void laplace_mixed_half_item(const DevGeom &g, const 
     const float4 cl = g.slot_clo[it.slot_begin];
     const float4 e = g.slot_ef[it.slot_begin];
     const float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = it.src_lo + hl; k < src_hi; k += 32) {
+    for (int k = it.src_lo + sl; k < src_hi; k += 2 * W) {
         f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
-        load_mixed_pair<false>(g, ev, walk, k, k + 16 < src_hi ? k + 16 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
+        load_mixed_pair<false>(g, ev, walk, k, k + W < src_hi ? k + W : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
         pair_mixed2<P, false, false>(hx, hy, hz, w, lx, ly, lz, nx, ny, nz, ch, cl, e, tn, as, ac, unused, unused,
                                      unused, unused);
     }
     df v = kahan2_df(as, ac);
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
-    if (hl == 0) write_item_result<false, false>(g, ev, it, 0, df_to_double(v), 0.0, 0.0);
+    for (int off = W / 2; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
+    if (sl == 0) write_item_result<false, false>(g, ev, it, 0, df_to_double(v), 0.0, 0.0);
 }
 
 template <int P, bool DLP, bool SP>

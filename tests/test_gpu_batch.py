@@ -81,11 +81,11 @@ def test_batch_rejects_mixed_kinds(env):
             p_.close()
 
 
-def test_single_layer_mixed_batch_half_warp_items(env):
-    """Single-target items of one plan run two per warp (one per half-warp)
-    in single-layer mixed batches: results within 1e-6 of the oracle and of
-    each plan alone (the half reduces in another order), and bit-identical
-    from one replay to the next."""
+def test_single_layer_mixed_batch_shared_warp_items(env):
+    """Single-target items of one plan run up to four per warp (8 or 16 lanes
+    each) in single-layer mixed batches: results within 1e-6 of the oracle
+    and of each plan alone (the lanes reduce in another order), and
+    bit-identical from one replay to the next."""
     torch, pkg = env
     from tsqbx_inputs import configs
     items = configs.ellipsoid_batch(n_surfaces=6, max_src=20000)
