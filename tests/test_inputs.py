@@ -131,3 +131,23 @@ def test_near_targets_stay_convergent():
     assert np.all(rho[g.n_ctr:] <= rho[g.tgt_center[g.n_ctr:]] * (1 + 1e-12))
     nd, nz = oracle.count_divergent(g)
     assert nd == 0 and nz == 0
+
+
+def test_near_targets_mixed_counts():
+    """targets_per_center = "mixed:M": each center gets 1..M targets,
+    log-uniformly (both sides of the conventional path's break-even), every
+    extra target inside its center's convergence radius, seeded."""
+    import oracle
+    from tsqbx_inputs import configs
+    g, mu, _ = configs.torus_near_targets(24, 10, targets_per_center="mixed:64")
+    cnt = np.bincount(g.tgt_center, minlength=g.n_ctr)
+    assert cnt.min() >= 1 and cnt.max() <= 64
+    assert (cnt == 1).any() and (cnt >= 32).any()
+    # log-uniform on [1, 64]: about half the centers have at most 8 targets
+    assert 0.35 < np.mean(cnt <= 8) < 0.65
+    rho = np.linalg.norm(g.tgt_xyz - g.ctr_xyz[:, g.tgt_center], axis=0)
+    assert np.all(rho[g.n_ctr:] <= rho[g.tgt_center[g.n_ctr:]] * (1 + 1e-12))
+    nd, nz = oracle.count_divergent(g)
+    assert nd == 0 and nz == 0
+    g2, _, _ = configs.torus_near_targets(24, 10, targets_per_center="mixed:64")
+    assert np.array_equal(g.tgt_xyz, g2.tgt_xyz)
