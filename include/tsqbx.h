@@ -269,7 +269,12 @@ TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
  * snapshots the plans' schedules at creation and uses the plans' device
  * geometry, so the plans must outlive it; its scratch (w mu per plan, partial
  * sums, queue head) is its own, so batch and plan evaluations may interleave
- * on different streams. */
+ * on different streams.  Results are deterministic.  In single-layer mixed
+ * batches up to four single-target items of one plan share a warp (8 or 16
+ * lanes each), so their lane sums are reduced in another order than the plan
+ * alone reduces them: the two agree to rounding (within the mixed error bar),
+ * not bit for bit.  Otherwise a batch reproduces each plan's results bit for
+ * bit. */
 typedef struct tsqbx_batch_s *tsqbx_batch;
 
 typedef struct {
@@ -291,8 +296,9 @@ TSQBX_API void tsqbx_batch_destroy(tsqbx_batch batch);
 /* Enqueue one evaluation of every plan on `stream` (NULL = the batch's own
  * stream).  d_density[i], d_out_slp[i], d_out_dlp[i]: DEVICE pointers for
  * plan i (layouts as tsqbx_eval; out arrays may be NULL for absent layers;
- * a batch forms the single and double layers only, never S').  Waits only until the previous evaluation of this batch has read its pointer
- * table.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA. */
+ * a batch forms the single and double layers only, never S').  Waits only
+ * until the previous evaluation of this batch has read its pointer table.
+ * Errors: TSQBX_E_INVAL, TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_batch_eval_async(tsqbx_batch batch, const void *const *d_density,
                                      void *const *d_out_slp, void *const *d_out_dlp, void *stream);
 
