@@ -54,13 +54,15 @@ def nearest_lists(src_xyz, ctr_xyz, counts):
 LIST_KINDS = {"L1": 0, "L3close": 1, "L3far": 2, "L4close": 3, "L2": 4, "L4far": 5,
               "L3": 6, "L4": 7}
 
-_lib = None
+_libs = {}
 
 
-def _octlib():
-    global _lib
-    if _lib is None:
-        L = ctypes.CDLL(_build.build())
+def _octlib(path=None):
+    """The builder library, compiled on first use; `path` loads another build of
+    the same source (the tests load copies with planted mistakes)."""
+    key = path or ""
+    if key not in _libs:
+        L = ctypes.CDLL(path or _build.build())
         dp = ctypes.POINTER(ctypes.c_double)
         i32 = ctypes.POINTER(ctypes.c_int32)
         i64 = ctypes.POINTER(ctypes.c_int64)
@@ -80,8 +82,8 @@ def _octlib():
         L.oct_near_nnz.restype = ctypes.c_int64
         L.oct_near_nnz.argtypes = [ctypes.c_void_p]
         L.oct_near_ranges.argtypes = [ctypes.c_void_p, i64, i32, i32]
-        _lib = L
-    return _lib
+        _libs[key] = L
+    return _libs[key]
 
 
 def _ptr(a, t):
@@ -94,8 +96,9 @@ class Octree:
     box's sources form one contiguous range; `src_perm[i]` is the original
     index of sorted source i."""
 
-    def __init__(self, src_xyz, ctr_xyz, ctr_radius, n_max=64, t_f=0.9, n_mpole=40):
-        L = _octlib()
+    def __init__(self, src_xyz, ctr_xyz, ctr_radius, n_max=64, t_f=0.9, n_mpole=40, lib_path=None):
+        L = _octlib(lib_path)
+        self.t_f, self.n_mpole = float(t_f), int(n_mpole)
         s = np.ascontiguousarray(np.asarray(src_xyz, dtype=np.float64).T)
         c = np.ascontiguousarray(np.asarray(ctr_xyz, dtype=np.float64).T)
         r = np.ascontiguousarray(ctr_radius, dtype=np.float64)
