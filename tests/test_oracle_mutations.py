@@ -1,6 +1,7 @@
 """The pins are sensitive: plausible mistakes planted in copies of oracle.c
 (a wrong sign, a dropped factor, an index off by one, transposed operands, the
-wrong Hankel kind) each make at least one pin test fail."""
+wrong Hankel kind, a wrong derivative rule, a too-short recurrence) each make at
+least one pin test fail."""
 import os
 import subprocess
 import sys
@@ -31,6 +32,22 @@ MUTATIONS = {
                       "acc = (js[1] + I * ys[1]) * dot3(pg.shat, nt_);"),
     "pathB_sp_rho0_slope": ("const double slope = kernel == 0 ? 1.0 : k / 3.0;",
                             "const double slope = kernel == 0 ? 1.0 : k / 2.0;"),
+    "helm_sp_no_derivative": ("(k * tcn * djt[n] * P[n] + stn * jt[n] * dP[n])",
+                              "(k * tcn * jt[n] * P[n] + stn * jt[n] * dP[n])"),
+    "helm_sp_transposed": ("dot3(pg.shat, nt_) - dot3(pg.that_, nt_) * pg.x",
+                           "dot3(pg.that_, nt_) - dot3(pg.shat, nt_) * pg.x"),
+    "pathB_helm_missing_i": ("double complex a = I * k * h, b", "double complex a = k * h, b"),
+    "pathB_dual_chain": ("b = I * k * (k * R.d) * dh;", "b = I * k * R.d * dh;"),
+    "pathB_laplace_2n1": ("dscale(Rpow, 2.0 * n + 1.0)", "dscale(Rpow, 2.0 * n + 2.0)"),
+    "sph_harm_dual_recurrence": ("dual t2 = dscale(A[n - 1][m], (double)(n + m));",
+                                 "dual t2 = dscale(A[n - 1][m], (double)(n - m));"),
+    "dual_quotient_sign": ("(a.d * b.v - a.v * b.d) / (b.v * b.v)", "(a.d * b.v + a.v * b.d) / (b.v * b.v)"),
+    "bessel_deriv_index": ("df[n] = f[n - 1] - (n + 1.0) / z * f[n];", "df[n] = f[n - 1] - n / z * f[n];"),
+    "miller_short_start": ("int N = nmax + 20 + (int)ceil(z);", "int N = nmax + 1;"),
+    "point_dlp_sign": ("wmu * dG * dot3(ns, ts), -wmu", "-wmu * dG * dot3(ns, ts), -wmu"),
+    "point_helm_outgoing": ("e * (1.0 - I * k * rr)", "e * (1.0 + I * k * rr)"),
+    "pathB_laplace_sp_slope": ("const double slope = kernel == 0 ? 1.0 : k / 3.0;",
+                               "const double slope = kernel == 0 ? 0.5 : k / 3.0;"),
 }
 
 
