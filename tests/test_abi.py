@@ -112,7 +112,9 @@ def test_unknown_layer_bits_rejected(L):
         assert L.tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)) == _lib.TSQBX_E_INVAL
 
 
-def test_conventional_needs_laplace_fp64(L):
+def test_conventional_needs_fp64_within_its_orders(L):
+    """The conventional path runs in FP64 only, for Laplace p <= 20 and
+    Helmholtz p <= 12; other requests are refused on the host."""
     g = _tiny()
     assert _create(g, conventional="all", precision="mixed") == -9
     assert _create(g, conventional="auto", precision="df64") == -9
