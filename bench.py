@@ -212,6 +212,35 @@ def cpu_sample(g, mu, seconds, rng_seed=7):
                             "seconds": dt1}}
 
 
+def oracle_sample(g, run, seconds, terms_per_pair, seed=7, cal=200):
+    """Time the FP64 oracle, `run(subset) -> {layer: values}`, on a random
+    sample of targets sized to about `seconds` after a calibration run on
+    `cal` targets.  Returns the sample, its reference values and the rate."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    tgt_pairs = g.group_source_counts()[g.ctr_group[g.tgt_center]]
+    order = rng.permutation(g.n_tgt)
+    n0 = min(cal, g.n_tgt)
+    c = np.sort(order[:n0])
+    t0 = time.perf_counter()
+    run(c)
+    rate = tgt_pairs[c].sum() / max(time.perf_counter() - t0, 1e-6)
+    csum = np.cumsum(tgt_pairs[order])
+    n = int(min(max(np.searchsorted(csum, rate * seconds) + 1, n0), g.n_tgt))
+    idx = np.sort(order[:n])
+    t0 = time.perf_counter()
+    ref = run(idx)
+    dt = time.perf_counter() - t0
+    pairs = int(tgt_pairs[idx].sum())
+    return {"idx": idx, "ref": ref, "seconds": dt, "pairs": pairs,
+            "value": pairs * terms_per_pair / dt, "cores": oracle.num_threads()}
+
+
+def max_rel_err(got, ref):
+    """max_t |got - ref| / max_t |ref| over one output array."""
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
 def reference_arm(args):
     """--impl reference: the FP64 CPU oracle on a bounded sample per step."""
     rank, _, world = dist_env()
@@ -388,11 +417,13 @@ def leg_batched(pkg, torch, dev, steps, warmup, flush):
     return res
 
 
-def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
+def leg_helmholtz(pkg, torch, dev, steps, warmup, flush, cpu_seconds=0.0):
     """Torus 444 x 166 quads (884,448 sources, 1,768,896 targets), octree
     lists, Helmholtz k = 10, p = 12, FP64, plane-wave density: the single
     layer alone, single + double layer (the combined-field operator's
-    parts, one pass), and all three layers with S'."""
+    parts, one pass), and all three layers with S'.  With cpu_seconds > 0
+    the FP64 oracle is timed on a random target sample of the single layer
+    (about that long), and every layer's GPU result is compared with it."""
     from tsqbx_inputs import configs
     g, mu, _ = configs.torus_helmholtz()
     dmu = torch.from_numpy(mu).to(dev)
@@ -411,9 +442,36 @@ def leg_helmholtz(pkg, torch, dev, steps, warmup, flush):
                      "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
                      "roofline": dict(roofline(fl * info["n_pairs"], t, "fp64", ("helmholtz", "fp64", name)),
                                       flops_per_pair=fl)}
+        if cpu_seconds > 0:
+            res[name]["error_vs_oracle"] = _helmholtz_oracle_check(res, g, mu, layers, out, cpu_seconds)
         plan.close()
     res["value"] = res["slp"]["value"]
     return res
+
+
+def _helmholtz_oracle_check(res, g, mu, layers, out, cpu_seconds):
+    """The oracle on target samples of the Helmholtz workload: the timed
+    single-layer sample (which also gives the CPU baseline), and for the plans
+    with more layers 200 targets of it, all their layers."""
+    import oracle
+    try:
+        if layers == ("slp",):
+            cs = oracle_sample(g, lambda s: oracle.tsqbx_helmholtz(g, 12, 10.0, mu, subset=s, slp=True),
+                               cpu_seconds, 13)
+            res["_sample"] = cs["idx"]
+            res["cpu_baseline"] = {"value": cs["value"], "unit": UNIT, "cores": cs["cores"], "kind": "oracle",
+                                   "sample": f"{len(cs['idx'])} random targets ({cs['pairs']} pairs, "
+                                             f"{cs['seconds']:.1f} s), single layer"}
+            return {"slp": max_rel_err(out["slp"].cpu().numpy()[cs["idx"]], cs["ref"]["slp"]),
+                    "targets": int(len(cs["idx"]))}
+        sub = res["_sample"][:200]
+        ref = oracle.tsqbx_helmholtz(g, 12, 10.0, mu, subset=sub, slp=True, dlp="dlp" in layers,
+                                     sp="sp" in layers)
+        e = {l: max_rel_err(out[l].cpu().numpy()[sub], ref[l]) for l in layers}
+        e["targets"] = int(len(sub))
+        return e
+    except Exception as exc:          # the GPU numbers stand without the check
+        return {"unavailable": repr(exc)[:200]}
 
 
 def leg_conventional(pkg, torch, dev, steps, warmup, flush):
@@ -514,8 +572,10 @@ def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush):
     return res
 
 
-def leg_sphere(pkg, torch, dev, steps, warmup, flush):
-    """Icosphere (3 subdivisions, 7,680 sources), radius-4h lists, Laplace SLP p = 5, FP64."""
+def leg_sphere(pkg, torch, dev, steps, warmup, flush, cpu_seconds=0.0):
+    """Icosphere (3 subdivisions, 7,680 sources), radius-4h lists, Laplace SLP
+    p = 5, FP64.  With cpu_seconds > 0 the FP64 oracle is timed on (up to)
+    the whole workload and the GPU result compared with it."""
     from tsqbx_inputs import configs
     g, mu = configs.sphere()
     plan = pkg.Plan(g, "laplace", ("slp",), p=5, device=dev.index)
@@ -529,6 +589,17 @@ def leg_sphere(pkg, torch, dev, steps, warmup, flush):
            "n_pairs": info["n_pairs"], "value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps),
            "unit": UNIT, "dtype": "f64", "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
            "roofline": roofline(flops_per_pair(5, "fp64", dlp=False) * info["n_pairs"], t, "fp64")}
+    if cpu_seconds > 0:
+        import oracle
+        try:
+            cs = oracle_sample(g, lambda s: oracle.tsqbx_laplace(g, 5, mu, subset=s, slp=True), cpu_seconds, 6)
+            res["cpu_baseline"] = {"value": cs["value"], "unit": UNIT, "cores": cs["cores"], "kind": "oracle",
+                                   "sample": f"{len(cs['idx'])} of {g.n_tgt} targets ({cs['pairs']} pairs, "
+                                             f"{cs['seconds']:.2f} s)"}
+            res["error_vs_oracle"] = {"slp": max_rel_err(out["slp"].cpu().numpy()[cs["idx"]], cs["ref"]["slp"]),
+                                      "targets": int(len(cs["idx"]))}
+        except Exception as exc:      # the GPU numbers stand without the check
+            res["error_vs_oracle"] = {"unavailable": repr(exc)[:200]}
     plan.close()
     return res
 
@@ -708,9 +779,13 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
+        # the oracle beside the Helmholtz and sphere legs: one-GPU runs only
+        leg_cpu_s = 0.0 if (args.no_cpu or world != 1) else min(5.0, args.cpu_seconds)
         for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere),
                          ("conventional", leg_conventional), ("lists", leg_lists)):
-            extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush)
+            kw = {"cpu_seconds": leg_cpu_s} if name in ("helmholtz", "sphere") else {}
+            extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush, **kw)
+        extras["helmholtz"].pop("_sample", None)
         extras["target_derivative"] = leg_target_derivative(pkg, torch, dev, g, mu, max(3, args.steps // 2),
                                                             args.warmup, flush)
         extras["serving"] = leg_serving(pkg)
