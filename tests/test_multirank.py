@@ -1,13 +1,14 @@
 """World-size-2 CPU (gloo) test of the sharded evaluation: each rank evaluates
 its shard of targets, the outputs are all-gathered and reassembled, and the
-result equals the single-rank evaluation exactly."""
+result equals the single-rank evaluation exactly.  The per-rank evaluator is
+the oracle here (no GPU); on GPUs it is a Plan over the rank's shard."""
 import os
 import socket
 
 import numpy as np
 import pytest
 
-from paper_1811_01110_gb300.sharding import gather_outputs, shard_targets
+from paper_1811_01110_gb300.sharding import distributed_eval, gather_outputs, shard_geometry, shard_targets
 
 
 def _free_port():
@@ -40,6 +41,18 @@ def _worker(rank, world, port, result_path):
         counts = [int(g.group_source_counts()[g.ctr_group[g.tgt_center[s]]].sum()) for s in shards]
         with open(result_path, "w") as f:
             f.write(f"{int(ok)} {counts[0]} {counts[1]}")
+    # the package's driver, Helmholtz with all three layers on the oracle
+    gh, muh, _ = configs.torus_helmholtz(16, 6, k=5.0)
+
+    def evaluate(shard):
+        return oracle.tsqbx_helmholtz(shard, 6, 5.0, muh, slp=True, dlp=True, sp=True)
+
+    got = distributed_eval(gh, evaluate, rank, world, dist.all_gather_object)
+    if rank == 0:
+        ref = oracle.tsqbx_helmholtz(gh, 6, 5.0, muh, slp=True, dlp=True, sp=True)
+        ok = all(np.array_equal(got[k], ref[k]) and got[k].dtype == np.complex128 for k in ref)
+        with open(result_path, "a") as f:
+            f.write(f" {int(ok)}")
     dist.barrier()
     dist.destroy_process_group()
 
@@ -60,6 +73,45 @@ def test_gloo_world2_sharded_equals_full(tmp_path):
     port = _free_port()
     res = tmp_path / "res.txt"
     mp.start_processes(_worker, args=(2, port, str(res)), nprocs=2, join=True, start_method="spawn")
-    ok, c0, c1 = map(int, res.read_text().split())
+    ok, c0, c1, ok_driver = map(int, res.read_text().split())
     assert ok == 1
     assert abs(c0 - c1) <= 0.1 * (c0 + c1)
+    assert ok_driver == 1
+
+
+def test_shard_geometry_keeps_sources_and_lists():
+    from tsqbx_inputs import configs
+    g, mu, _ = configs.torus(24, 10)
+    idx = shard_targets(g, 3)[1]
+    sub = shard_geometry(g, idx)
+    assert sub.tgt_xyz.shape == (3, len(idx)) and np.array_equal(sub.tgt_center, g.tgt_center[idx])
+    assert sub.src_xyz is g.src_xyz and sub.range_begin is g.range_begin
+    assert sub.tgt_normal is None or np.array_equal(sub.tgt_normal, g.tgt_normal[:, idx])
+
+
+def test_distributed_eval_single_process_world3():
+    """The driver with a fake all-gather over three ranks run in turn."""
+    import oracle
+    from tsqbx_inputs import configs
+    g, mu, _ = configs.torus(20, 8)
+    world = 3
+    mine = {}
+
+    def evaluate_for(r):
+        return lambda shard: oracle.tsqbx_laplace(shard, 5, mu, slp=True, dlp=True)
+
+    # collect every rank's part first, then let each rank's gather see them all
+    shards = shard_targets(g, world)
+    for r in range(world):
+        mine[r] = evaluate_for(r)(shard_geometry(g, shards[r]))
+
+    def gather_for(r):
+        def all_gather_object(parts, obj):
+            for q in range(world):
+                parts[q] = obj if q == r else mine[q]
+        return all_gather_object
+
+    ref = oracle.tsqbx_laplace(g, 5, mu, slp=True, dlp=True)
+    for r in range(world):
+        got = distributed_eval(g, evaluate_for(r), r, world, gather_for(r))
+        assert all(np.array_equal(got[k], ref[k]) for k in ("slp", "dlp"))
