@@ -1,4 +1,6 @@
 import os
+import re
+import shutil
 import sys
 
 import numpy as np
@@ -23,3 +25,15 @@ def pytest_collection_modifyitems(config, items):
 @pytest.fixture(scope="session")
 def rng():
     return np.random.default_rng(12345)
+
+
+@pytest.fixture
+def scratch(request):
+    """A fresh working directory inside the repository (git-ignored), removed
+    after the test: builds of planted-mistake copies and result files."""
+    name = re.sub(r"[^A-Za-z0-9_.-]+", "_", request.node.nodeid)[-120:]
+    d = os.path.join(ROOT, "tests", "native", "_build", "scratch", name)
+    shutil.rmtree(d, ignore_errors=True)
+    os.makedirs(d)
+    yield __import__("pathlib").Path(d)
+    shutil.rmtree(d, ignore_errors=True)

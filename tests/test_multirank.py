@@ -68,10 +68,10 @@ def test_shards_cover_targets_once():
         assert max(pairs) <= 1.25 * (sum(pairs) / world) + 2000
 
 
-def test_gloo_world2_sharded_equals_full(tmp_path):
+def test_gloo_world2_sharded_equals_full(scratch):
     mp = pytest.importorskip("torch.multiprocessing")
     port = _free_port()
-    res = tmp_path / "res.txt"
+    res = scratch / "res.txt"
     mp.start_processes(_worker, args=(2, port, str(res)), nprocs=2, join=True, start_method="spawn")
     ok, c0, c1, ok_driver = map(int, res.read_text().split())
     assert ok == 1

@@ -253,15 +253,15 @@ BUILDER_MUTATIONS = {
 
 
 @pytest.mark.parametrize("name", sorted(BUILDER_MUTATIONS))
-def test_definitions_catch_planted_builder_mistake(tmp_path, name):
+def test_definitions_catch_planted_builder_mistake(scratch, name):
     if shutil.which("g++") is None:
         pytest.skip("no g++")
     old, new = BUILDER_MUTATIONS[name]
     src = open(os.path.join(ROOT, "tsqbx_inputs", "octree.cpp")).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not unique"
-    mut = tmp_path / "octree_mut.cpp"
+    mut = scratch / "octree_mut.cpp"
     mut.write_text(src.replace(old, new))
-    lib = tmp_path / "liboctree_mut.so"
+    lib = scratch / "liboctree_mut.so"
     subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", str(mut),
                     "-o", str(lib)], check=True, capture_output=True)
     caught = False

@@ -52,13 +52,13 @@ MUTATIONS = {
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_planted_mistake(tmp_path, name):
+def test_pins_catch_planted_mistake(scratch, name):
     old, new = MUTATIONS[name]
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation anchor for {name} not unique"
-    mut = tmp_path / "oracle_mut.c"
+    mut = scratch / "oracle_mut.c"
     mut.write_text(src.replace(old, new))
-    lib = tmp_path / "liboracle_mut.so"
+    lib = scratch / "liboracle_mut.so"
     subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", str(mut), "-o", str(lib), "-lm"],
                    check=True, capture_output=True)
     env = dict(os.environ, ORACLE_LIB=str(lib))
