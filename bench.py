@@ -604,12 +604,13 @@ def leg_sphere(pkg, torch, dev, steps, warmup, flush, cpu_seconds=0.0):
     return res
 
 
-def leg_serving(pkg, duration_s=6.0, rate=200.0, seed=20191114, size_priority=False):
+def leg_serving(pkg, duration_s=10.0, rate=200.0, seed=20191114, size_priority=False):
     """Serving: Poisson arrivals over 16 resident geometries (5k-300k sources);
     each request a Laplace FP64, Laplace mixed or Helmholtz (k in {1,5,10})
     single-layer evaluation with p in {5,9,12} and a new seeded density.
-    Plans are built first (warm start); if the offered rate exceeds capacity
-    a second phase runs at 80 % of the measured capacity.  size_priority:
+    Plans are built first (warm start); each phase offers `duration_s` of
+    arrivals; if the offered rate exceeds capacity a second phase runs at
+    80 % of the measured capacity.  size_priority:
     the server's size-priority policy (short requests overtake long ones)."""
     import threading
     from tsqbx_inputs import configs
