@@ -151,3 +151,33 @@ def test_near_targets_mixed_counts():
     assert nd == 0 and nz == 0
     g2, _, _ = configs.torus_near_targets(24, 10, targets_per_center="mixed:64")
     assert np.array_equal(g.tgt_xyz, g2.tgt_xyz)
+
+
+def _max_rho_over_R(g):
+    """max over listed pairs of |t - c| / |s - c| (each center is its own
+    group with one window of sources)."""
+    C, S = g.ctr_xyz.T, g.src_xyz.T
+    rho = np.linalg.norm(g.tgt_xyz.T - C[g.tgt_center], axis=1)
+    L = (g.range_end - g.range_begin).astype(np.int64)
+    mind = np.empty(len(C))
+    for Lv in np.unique(L):
+        idx = np.nonzero(L == Lv)[0]
+        step = max(1, 2_000_000 // int(Lv))
+        for a in range(0, len(idx), step):
+            ii = idx[a:a + step]
+            d = S[g.range_begin[ii][:, None] + np.arange(Lv)[None, :]] - C[ii][:, None, :]
+            mind[ii] = np.sqrt(np.min(np.einsum("ijk,ijk->ij", d, d), axis=1))
+    return float(np.max(rho / mind[g.tgt_center]))
+
+
+def test_batched_surfaces_stay_well_inside_convergence():
+    """The batched ellipsoids: the coarse, strongly curved ones (frequency
+    <= 12, where a window of sources comes closest to a center relative to
+    its target) keep every listed pair at rho/R <= 0.9.  Over the whole
+    batch the maximum is 0.58."""
+    from tsqbx_inputs import configs
+    surfaces = configs.ellipsoid_batch()
+    small = [g for g, _ in surfaces if g.n_src <= 120 * 12 ** 2]
+    assert len(small) >= 10
+    for g in small:
+        assert _max_rho_over_R(g) <= 0.9, g.meta["name"]
