@@ -236,6 +236,20 @@ def oracle_sample(g, run, seconds, terms_per_pair, seed=7, cal=200):
             "value": pairs * terms_per_pair / dt, "cores": oracle.num_threads()}
 
 
+def host_cpu():
+    """The host's CPU model (lscpu 'Model name') and logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
 def max_rel_err(got, ref):
     """max_t |got - ref| / max_t |ref| over one output array."""
     return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
@@ -800,7 +814,7 @@ def main():
     err = {}
     if not args.no_cpu and world == 1:
         cs = cpu_sample(g, mu, args.cpu_seconds)
-        cpu = {"value": cs["value"], "unit": UNIT, "cores": cs["cores"], "kind": "oracle",
+        cpu = {"value": cs["value"], "unit": UNIT, "cores": cs["cores"], "kind": "oracle", **host_cpu(),
                "sample": f"{len(cs['idx'])} random targets ({cs['pairs']} pairs, "
                          f"{cs['seconds']:.1f} s) of the benchmark workload, SLP+DLP p=9",
                "single_core": {"value": cs["single_core"]["value"], "unit": UNIT,
