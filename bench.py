@@ -644,6 +644,7 @@ def leg_serving(pkg, duration_s=10.0, rate=200.0, seed=20191114, size_priority=F
         n = int(rate_hz * seconds)
         gaps = rng.exponential(1.0 / rate_hz, n)
         reqs = []
+        peak_queued = peak_running = 0
         t0 = time.perf_counter()
         due = t0
         for i in range(n):
@@ -659,6 +660,10 @@ def leg_serving(pkg, duration_s=10.0, rate=200.0, seed=20191114, size_priority=F
                 mu = mu * np.exp(1j * 0.1 * i)
             rid, _ = srv.submit(gids[gi], mu, kernel, ("slp",), p, k, prec)
             reqs.append(rid)
+            if i % 25 == 0:                       # queue depth seen by arrivals
+                live = srv.stats()
+                peak_queued = max(peak_queued, live["queued"])
+                peak_running = max(peak_running, live["running"])
         t_submit = time.perf_counter() - t0
         for rid in reqs:
             srv.poll(rid, timeout_us=-1)
@@ -666,6 +671,7 @@ def leg_serving(pkg, duration_s=10.0, rate=200.0, seed=20191114, size_priority=F
         return {"offered_req_per_s": rate_hz, "requests": n, "submit_s": t_submit,
                 "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                 "completed": st["completed"], "failed": st["failed"], "rejected": st["rejected"],
+                "peak_queued": int(peak_queued), "peak_running": int(peak_running),
                 "achieved_req_per_s": st["completed"] / max(st["span_s"], 1e-9),
                 "pair_terms_per_s": st["pair_terms_completed"] / max(st["span_s"], 1e-9),
                 "span_s": st["span_s"]}
