@@ -243,13 +243,7 @@ int size_priority(int64_t n_pairs, const tsqbx_options &o)
         cudaGetLastError();
         return 0;
     }
-    const double cost = o.kernel == TSQBX_HELMHOLTZ ? 4.0
-                        : o.precision == TSQBX_MIXED ? 0.03
-                        : o.precision == TSQBX_DF64  ? 0.25
-                                                     : 1.0;
-    const double work = std::max(1.0, (double)n_pairs * cost);
-    const int level = std::min(std::max((int)std::floor(std::log10(work)) - 5, 0), least - greatest);
-    return greatest + level;
+    return priority_for_work(n_pairs, o.kernel, o.precision, least, greatest);
 }
 
 void apply_schedule(tsqbx_plan P, Schedule &&s)

@@ -71,6 +71,10 @@ constexpr int64_t kConvSlice = 1024;
 // conventional path than on the target-specific one.
 bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool helmholtz);
 int size_priority(int64_t n_pairs, const tsqbx_options &o);
+// The arithmetic of size_priority for a device priority range [greatest, least]
+// (numerically greatest <= least): the pairs times a per-pair cost relative to
+// Laplace FP64, one level per decade above 1e5, clamped to the range.
+int priority_for_work(int64_t n_pairs, int kernel, int precision, int least, int greatest);
 // Build the schedule; max_iters <= 0 picks the automatic cap.
 int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
                    int n_sm, Schedule &out);

@@ -57,6 +57,17 @@ bool conventional_cheaper(int64_t nt, int64_t ns, int p, unsigned layers, bool h
     return (double)ns * p2l + warps * l2p < (double)nt * (double)ns * ts;
 }
 
+int priority_for_work(int64_t n_pairs, int kernel, int precision, int least, int greatest)
+{
+    const double cost = kernel == TSQBX_HELMHOLTZ ? 4.0
+                        : precision == TSQBX_MIXED ? 0.03
+                        : precision == TSQBX_DF64  ? 0.25
+                                                   : 1.0;
+    const double work = std::max(1.0, (double)n_pairs * cost);
+    const int level = std::min(std::max((int)std::floor(std::log10(work)) - 5, 0), least - greatest);
+    return greatest + level;
+}
+
 int choose_lanes(int64_t nt, int64_t ns)
 {
     int best = 1;

@@ -10,6 +10,12 @@ __attribute__((visibility("default"))) int shim_choose_lanes(int64_t nt, int64_t
     return tsqbx::choose_lanes(nt, ns);
 }
 
+__attribute__((visibility("default"))) int shim_priority_for_work(int64_t n_pairs, int kernel, int precision,
+                                                                   int least, int greatest)
+{
+    return tsqbx::priority_for_work(n_pairs, kernel, precision, least, greatest);
+}
+
 __attribute__((visibility("default"))) int shim_cost_bucket(double cost) { return tsqbx::cost_bucket(cost); }
 
 __attribute__((visibility("default"))) int shim_conventional_cheaper(int64_t nt, int64_t ns, int p,

@@ -9,6 +9,8 @@ test shim and checked without a GPU:
   and cover [0, n_parts);
 * the queue runs in half-octave cost buckets, heaviest first, keeping list
   order within a bucket;
+* the size-priority levels: one per decade of work above 1e5 Laplace-FP64
+  pair equivalents, smallest plans highest, clamped to the device's range;
 * the cost model's choice between the target-specific and the conventional
   path matches the measured faster path on the torus 96 x 36 cases
   (1/4/16/64 targets per center; Laplace SLP+DLP p = 9, Helmholtz SLP+DLP
@@ -51,6 +53,7 @@ def shim():
                                       ctypes.c_int, i64p, i32p, f64p, i64p, i32p, i64p, i64p, f64p]
     L.shim_choose_lanes.argtypes = [ctypes.c_int64, ctypes.c_int64]
     L.shim_cost_bucket.argtypes = [ctypes.c_double]
+    L.shim_priority_for_work.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.shim_conventional_cheaper.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint,
                                             ctypes.c_int]
     return L
@@ -183,3 +186,23 @@ def test_cost_model_picks_the_measured_faster_path(shim, helmholtz, p):
     # more targets per center never turn the choice back
     picks = [shim.shim_conventional_cheaper(nt, 650, p, layers, helmholtz) for nt in range(1, 200)]
     assert picks == sorted(picks)
+
+
+def test_size_priority_levels(shim):
+    """Priority range as CUDA reports it: greatest (highest priority) is the
+    numerically smaller value, e.g. [-5, 0]."""
+    least, greatest = 0, -5
+    lap, helm = 0, 1
+    fp64, mixed, df64 = 0, 1, 2
+    f = lambda n, k=lap, pr=fp64: shim.shim_priority_for_work(n, k, pr, least, greatest)
+    assert f(0) == greatest and f(10 ** 5) == greatest and f(999_999) == greatest
+    assert f(10 ** 6) == greatest + 1 and f(10 ** 8) == greatest + 3
+    assert f(10 ** 12) == least                                   # clamped to the lowest priority
+    levels = [f(int(10 ** e)) for e in np.arange(0, 13, 0.5)]
+    assert levels == sorted(levels)                               # more work, never a higher priority
+    # per-pair costs: Helmholtz 4x, mixed 0.03x, df64 0.25x of Laplace FP64
+    assert f(2_500_000, helm) == f(10 ** 7)
+    assert f(10 ** 8, lap, mixed) == f(3 * 10 ** 6)
+    assert f(4 * 10 ** 6, lap, df64) == f(10 ** 6)
+    # a device with a single priority puts everything at it
+    assert shim.shim_priority_for_work(10 ** 9, lap, fp64, 0, 0) == 0
