@@ -203,7 +203,18 @@ def _trees():
     yield "torus 24x8", dict(src=src3, ctr=ctr3, rad=rad3, n_max=24, t_f=0.9, n_mpole=40)
 
 
-TREES = list(_trees())
+TREE_NAMES = ["cloud, large balls", "clustered", "no confinement, no threshold",
+              "cloud, threshold at a candidate's count", "torus 24x8"]
+_TREES = None
+
+
+def trees():
+    """The cases, built on first use (not at collection)."""
+    global _TREES
+    if _TREES is None:
+        _TREES = list(_trees())
+        assert [n for n, _ in _TREES] == TREE_NAMES
+    return _TREES
 
 
 def _build(case, lib_path=None):
@@ -211,8 +222,9 @@ def _build(case, lib_path=None):
                     n_mpole=case["n_mpole"], lib_path=lib_path)
 
 
-@pytest.mark.parametrize("name,case", TREES, ids=[t[0] for t in TREES])
-def test_builder_matches_definitions(name, case):
+@pytest.mark.parametrize("name", TREE_NAMES)
+def test_builder_matches_definitions(name):
+    case = dict(trees())[name]
     tree = _build(case)
     B = Boxes(tree)
     # the cases reach every list: non-leaf target boxes, List 3 far and close,
@@ -224,7 +236,7 @@ def test_builder_matches_definitions(name, case):
 def test_cases_exercise_every_list():
     seen = {k: 0 for k in ("L2", "L3far", "L3close", "L4close", "L4far")}
     nonleaf_targets = 0
-    for _, case in TREES:
+    for _, case in trees():
         tree = _build(case)
         for k in seen:
             seen[k] += len(tree.lists[k][1])
@@ -265,7 +277,7 @@ def test_definitions_catch_planted_builder_mistake(scratch, name):
     subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", str(mut),
                     "-o", str(lib)], check=True, capture_output=True)
     caught = False
-    for _, case in TREES:
+    for _, case in trees():
         try:
             tree = _build(case, lib_path=str(lib))
         except ValueError:
