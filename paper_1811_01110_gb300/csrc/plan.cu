@@ -224,7 +224,8 @@ void fill_stats(tsqbx_plan P)
 
 }  // namespace
 
-// ------------------------------------------------------------- schedules
+// ---------------------------- errors, stream priority, schedule upload
+// (the schedule itself is built in schedule.cu)
 
 namespace tsqbx {
 
