@@ -71,11 +71,35 @@ def _create(g, **kw):
     (lambda g: setattr(g, "group_range_start", g.group_range_start[::-1].copy()), -1),
     (lambda g: setattr(g, "ctr_group", np.full_like(g.ctr_group, -1)), -1),
     (lambda g: g.src_xyz.__setitem__((0, 0), np.nan), -1),
+    (lambda g: g.tgt_xyz.__setitem__((2, 1), np.inf), -1),
+    (lambda g: g.ctr_xyz.__setitem__((1, 0), np.nan), -1),
+    (lambda g: g.src_weight.__setitem__(3, np.nan), -1),
+    (lambda g: setattr(g, "group_range_start", g.group_range_start + 1), -1),
+    (lambda g: setattr(g, "ctr_group", np.full_like(g.ctr_group, 99)), -1),
+    (lambda g: setattr(g, "range_begin", np.full_like(g.range_begin, -1)), -1),
 ])
 def test_invalid_geometry_rejected_on_host(L, mutate, code):
     g = _tiny()
     mutate(g)
     assert _create(g) == code
+
+
+def test_nonfinite_normal_rejected_only_with_the_double_layer(L):
+    g = _tiny()
+    g.src_normal = g.src_normal.copy()
+    g.src_normal[0, 2] = np.nan
+    assert _create(g, layers=("slp", "dlp")) == -1
+    assert _create(g, kernel="helmholtz", k=2.0, layers=("dlp",)) == -1
+
+
+def test_more_invalid_options_rejected_on_host(L):
+    g = _tiny()
+    assert _create(g, n_slots=65) == -1
+    assert _create(g, max_item_iters=-1) == -1
+    assert _create(g, lanes_per_target=-1) == -1
+    assert _create(g, kernel="helmholtz", k=float("inf")) == -1
+    assert _create(g, kernel="helmholtz", k=float("nan")) == -1
+    assert _create(g, kernel="helmholtz", k=-1.0) == -1
 
 
 def test_invalid_options_rejected_on_host(L):
