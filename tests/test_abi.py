@@ -154,3 +154,50 @@ def test_octree_inputs_rejected_on_host(L):
         with pytest.raises(pkg.TsqbxError) as ei:
             pkg.Octree(*args, **kw)
         assert ei.value.code == -1
+
+
+def test_null_handles_rejected_on_host(L):
+    """Every entry point that takes a plan or batch handle rejects NULL (and
+    NULL outputs) with TSQBX_E_INVAL before any CUDA call; destroy accepts NULL."""
+    from paper_1811_01110_gb300 import _lib
+    inval = _lib.TSQBX_E_INVAL
+    ms = ctypes.c_float()
+    nbytes = ctypes.c_size_t()
+    assert L.tsqbx_plan_info(None, ctypes.byref(_lib.tsqbx_plan_stats())) == inval
+    assert L.tsqbx_plan_footprint(None, ctypes.byref(nbytes)) == inval
+    assert L.tsqbx_plan_kernel_ms(None, ctypes.byref(ms)) == inval
+    assert L.tsqbx_plan_get_tuning(None, ctypes.byref(_lib.tsqbx_tuning())) == inval
+    assert L.tsqbx_plan_set_tuning(None, ctypes.byref(_lib.tsqbx_tuning())) == inval
+    assert L.tsqbx_plan_autotune(None, None, 3, None) == inval
+    L.tsqbx_plan_destroy(None)
+    # batches
+    out = ctypes.c_void_p()
+    assert L.tsqbx_batch_create(None, 1, 1, ctypes.byref(out)) == inval
+    plans = (ctypes.c_void_p * 2)(None, None)
+    assert L.tsqbx_batch_create(plans, 2, 1, ctypes.byref(out)) == inval
+    assert L.tsqbx_batch_create(plans, 0, 1, ctypes.byref(out)) == inval
+    assert L.tsqbx_batch_create(plans, 2, 1, None) == inval
+    assert L.tsqbx_batch_eval_async(None, None, None, None, None) == inval
+    assert L.tsqbx_batch_kernel_ms(None, ctypes.byref(ms)) == inval
+    assert L.tsqbx_batch_info(None, ctypes.byref(_lib.tsqbx_batch_stats())) == inval
+    L.tsqbx_batch_destroy(None)
+
+
+def test_noalloc_arguments_rejected_on_host(L):
+    """tsqbx_eval_noalloc checks its counts, order, layer mask and pointers on
+    the host; more sources than its scratch holds is TSQBX_E_TOO_LARGE."""
+    from paper_1811_01110_gb300 import _lib
+    inval = _lib.TSQBX_E_INVAL
+    fake = ctypes.c_void_p(16)             # never dereferenced: every call below returns first
+    geo = _lib.tsqbx_geometry()
+    geo.n_src, geo.n_ctr, geo.n_tgt, geo.n_group = 10, 1, 1, 1
+    assert L.tsqbx_eval_noalloc(None, 3, 1, fake, fake, None, None) == inval
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), -1, 1, fake, fake, None, None) == inval
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 21, 1, fake, fake, None, None) == inval
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 0, fake, fake, None, None) == inval
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 4, fake, fake, fake, None) == inval   # S' not offered
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval   # NULL arrays
+    geo.n_src = 1048544 + 1
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == _lib.TSQBX_E_TOO_LARGE
+    geo.n_src = -1
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval
