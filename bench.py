@@ -373,10 +373,12 @@ def roofline(flops_per_launch, kernel_s, precision, traffic_key=None):
     return out
 
 
-def leg_batched(pkg, torch, dev, steps, warmup, flush):
+def leg_batched(pkg, torch, dev, steps, warmup, flush, check_targets=0):
     """64 ellipsoids (1k-200k sources, Laplace SLP, p in {5,7,9}, mixed) in one
     persistent launch replayed from a CUDA graph, against the same 64 plans
-    evaluated one after another."""
+    evaluated one after another.  With check_targets > 0 the batched results
+    of every eighth surface are compared with the FP64 oracle on that many
+    seeded random targets each."""
     from tsqbx_inputs import configs
     surfaces = configs.ellipsoid_batch()
     plans = [pkg.Plan(g, "laplace", ("slp",), p=g.meta["p"], precision="mixed", device=dev.index)
@@ -403,6 +405,8 @@ def leg_batched(pkg, torch, dev, steps, warmup, flush):
             ms.append(e0.elapsed_time(e1))
             kms.append(batch.kernel_ms())
         torch.cuda.synchronize()
+    checked = list(range(0, len(surfaces), 8)) if check_targets > 0 else []
+    batch_vals = {i: outs[i]["slp"].cpu().numpy().copy() for i in checked}
     # the same work as 64 separate evaluations on one stream
     seq = []
     for i in range(warmup + steps):
@@ -428,6 +432,19 @@ def leg_batched(pkg, torch, dev, steps, warmup, flush):
            "sequential_ms_per_step": sum(seq) / steps,
            "speedup_vs_sequential": (sum(seq) / steps) / (1e3 * t),
            "roofline": roofline(fl, sum(kms) / steps / 1e3, "mixed", ("batched", "mixed", "slp"))}
+    if checked:
+        try:
+            import oracle
+            worst = 0.0
+            rng = np.random.default_rng(17)
+            for i in checked:
+                g, mu = surfaces[i]
+                idx = np.sort(rng.choice(g.n_tgt, min(check_targets, g.n_tgt), replace=False))
+                ref = oracle.tsqbx_laplace(g, g.meta["p"], mu, subset=idx, slp=True)["slp"]
+                worst = max(worst, max_rel_err(batch_vals[i][idx], ref))
+            res["error_vs_oracle"] = {"slp": worst, "surfaces": len(checked), "targets_each": int(check_targets)}
+        except Exception as exc:      # the GPU numbers stand without the check
+            res["error_vs_oracle"] = {"unavailable": repr(exc)[:200]}
     for pl in plans:
         pl.close()
     return res
@@ -566,13 +583,23 @@ def leg_lists(pkg, torch, dev, steps, warmup, flush):
     return res
 
 
-def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush):
+def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush, check_targets=0):
     """The benchmark torus with S' added: Laplace single + double layer + S'
-    (target-normal derivative) in one pass, p = 9, in every precision."""
+    (target-normal derivative) in one pass, p = 9, in every precision.  With
+    check_targets > 0, every layer of every precision is compared with the
+    FP64 oracle on that many seeded random targets."""
     dmu = torch.from_numpy(mu).to(dev)
     stream = torch.cuda.Stream(device=dev)
     layers = ("slp", "dlp", "sp")
     res = {"workload": WORKLOAD.replace("SLP+DLP", "SLP+DLP+S'"), "unit": UNIT}
+    ref = idx = None
+    if check_targets > 0:
+        try:
+            import oracle
+            idx = np.sort(np.random.default_rng(13).choice(g.n_tgt, min(check_targets, g.n_tgt), replace=False))
+            ref = oracle.tsqbx_laplace(g, P, mu, subset=idx, slp=True, dlp=True, sp=True)
+        except Exception as exc:      # the GPU numbers stand without the check
+            res["error_vs_oracle"] = {"unavailable": repr(exc)[:200]}
     for prec in ("fp64", "mixed", "df64"):
         plan = pkg.Plan(g, "laplace", layers, p=P, precision=prec, device=dev.index)
         info = plan.info()
@@ -584,6 +611,9 @@ def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush):
         res[prec] = {"value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps),
                      "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
                      "roofline": dict(roofline(fl * info["n_pairs"], t, fprec), flops_per_pair=fl)}
+        if ref is not None:
+            res[prec]["error_vs_oracle"] = {l: max_rel_err(out[l].cpu().numpy()[idx], ref[l]) for l in layers}
+            res[prec]["error_vs_oracle"]["targets"] = int(len(idx))
         plan.close()
     return res
 
@@ -806,11 +836,13 @@ def main():
         leg_cpu_s = 0.0 if (args.no_cpu or world != 1) else min(5.0, args.cpu_seconds)
         for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere),
                          ("conventional", leg_conventional), ("lists", leg_lists)):
-            kw = {"cpu_seconds": leg_cpu_s} if name in ("helmholtz", "sphere") else {}
+            kw = ({"cpu_seconds": leg_cpu_s} if name in ("helmholtz", "sphere")
+                  else {"check_targets": 300 if leg_cpu_s > 0 else 0} if name == "batched" else {})
             extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush, **kw)
         extras["helmholtz"].pop("_sample", None)
         extras["target_derivative"] = leg_target_derivative(pkg, torch, dev, g, mu, max(3, args.steps // 2),
-                                                            args.warmup, flush)
+                                                            args.warmup, flush,
+                                                            check_targets=600 if leg_cpu_s > 0 else 0)
         extras["serving"] = leg_serving(pkg)
         extras["serving_size_priority"] = leg_serving(pkg, size_priority=True)
 
