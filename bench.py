@@ -507,13 +507,14 @@ def _helmholtz_oracle_check(res, g, mu, layers, out, cpu_seconds):
         return {"unavailable": repr(exc)[:200]}
 
 
-def leg_conventional(pkg, torch, dev, steps, warmup, flush):
+def leg_conventional(pkg, torch, dev, steps, warmup, flush, check_targets=0):
     """Torus 96 x 36 quads (41,472 sources, 82,944 centers, octree lists) with
     1, 4, 16 and 64 targets per center, and with a mix (each center 1..64,
     log-uniform), SLP+DLP FP64, Laplace at p = 9 and Helmholtz (k = 10,
     plane-wave density) at p = 12: the target-specific path alone ("off"),
     conventional QBX for every center ("all"), and the cost model's
-    per-center choice ("auto")."""
+    per-center choice ("auto").  With check_targets > 0 every mode's result is
+    compared with the FP64 oracle on that many seeded random targets."""
     from tsqbx_inputs import configs
     stream = torch.cuda.Stream(device=dev)
     base = "torus 96x36 quads, 41472 sources, 82944 centers, octree lists, targets per center in {1,4,16,64} " \
@@ -524,12 +525,24 @@ def leg_conventional(pkg, torch, dev, steps, warmup, flush):
         g, mu, _ = configs.torus_near_targets(96, 36, tpc)
         for kernel, p, dest in (("laplace", 9, res), ("helmholtz", 12, hel)):
             if kernel == "helmholtz":
-                dmu = torch.from_numpy(np.ascontiguousarray(mu * np.exp(1j * 10.0 * g.src_xyz[0]))).to(dev)
+                hmu = np.ascontiguousarray(mu * np.exp(1j * 10.0 * g.src_xyz[0]))
+                dmu = torch.from_numpy(hmu).to(dev)
                 dt, kw = torch.complex128, {"k": 10.0}
             else:
                 dmu = torch.from_numpy(mu).to(dev)
                 dt, kw = torch.float64, {}
             case = {"targets_per_center": tpc, "n_targets": g.n_tgt}
+            ref = idx = None
+            if check_targets > 0:
+                try:
+                    import oracle
+                    idx = np.sort(np.random.default_rng(19).choice(g.n_tgt, min(check_targets, g.n_tgt),
+                                                                   replace=False))
+                    ref = (oracle.tsqbx_helmholtz(g, p, 10.0, hmu, subset=idx, slp=True, dlp=True)
+                           if kernel == "helmholtz" else
+                           oracle.tsqbx_laplace(g, p, mu, subset=idx, slp=True, dlp=True))
+                except Exception as exc:      # the GPU numbers stand without the check
+                    case["error_vs_oracle"] = {"unavailable": repr(exc)[:200]}
             for mode in ("off", "all", "auto"):
                 plan = pkg.Plan(g, kernel, ("slp", "dlp"), p=p, conventional=mode, device=dev.index, **kw)
                 info = plan.info()
@@ -538,6 +551,9 @@ def leg_conventional(pkg, torch, dev, steps, warmup, flush):
                 t = sum(step_ms) / 1e3 / steps
                 case[mode] = {"ms_per_step": 1e3 * t, "pair_terms_per_s": info["n_pair_terms"] / t,
                               "conv_centers": info["n_conv_centers"], "conv_targets": info["n_conv_targets"]}
+                if ref is not None:
+                    case[mode]["error_vs_oracle"] = {l: max_rel_err(outs[l].cpu().numpy()[idx], ref[l])
+                                                     for l in ("slp", "dlp")}
                 case["n_pairs"] = info["n_pairs"]
                 plan.close()
             case["auto_vs_best"] = case["auto"]["ms_per_step"] / min(case["off"]["ms_per_step"],
@@ -837,7 +853,8 @@ def main():
         for name, fn in (("batched", leg_batched), ("helmholtz", leg_helmholtz), ("sphere", leg_sphere),
                          ("conventional", leg_conventional), ("lists", leg_lists)):
             kw = ({"cpu_seconds": leg_cpu_s} if name in ("helmholtz", "sphere")
-                  else {"check_targets": 300 if leg_cpu_s > 0 else 0} if name == "batched" else {})
+                  else {"check_targets": 300 if leg_cpu_s > 0 else 0} if name in ("batched", "conventional")
+                  else {})
             extras[name] = fn(pkg, torch, dev, max(3, args.steps // 2), args.warmup, flush, **kw)
         extras["helmholtz"].pop("_sample", None)
         extras["target_derivative"] = leg_target_derivative(pkg, torch, dev, g, mu, max(3, args.steps // 2),
