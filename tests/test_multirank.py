@@ -115,3 +115,27 @@ def test_distributed_eval_single_process_world3():
     for r in range(world):
         got = distributed_eval(g, evaluate_for(r), r, world, gather_for(r))
         assert all(np.array_equal(got[k], ref[k]) for k in ("slp", "dlp"))
+
+
+def test_more_ranks_than_targets():
+    """Ranks beyond the target count get empty shards; the reassembled result
+    is still the single-rank one."""
+    import oracle
+    from helpers import cloud_geometry
+    g = cloud_geometry(np.random.default_rng(3), n_ctr=2, n_src=40, tgt_per_ctr=1)
+    mu = np.random.default_rng(4).standard_normal(g.n_src)
+    world = 5
+    shards = shard_targets(g, world)
+    assert sum(len(s) for s in shards) == g.n_tgt and sum(len(s) == 0 for s in shards) >= world - g.n_tgt
+    parts = {r: oracle.tsqbx_laplace(shard_geometry(g, shards[r]), 4, mu, slp=True) for r in range(world)}
+
+    def gather_for(r):
+        def all_gather_object(out, obj):
+            for q in range(world):
+                out[q] = obj if q == r else parts[q]
+        return all_gather_object
+
+    ref = oracle.tsqbx_laplace(g, 4, mu, slp=True)["slp"]
+    for r in range(world):
+        got = distributed_eval(g, lambda sh: oracle.tsqbx_laplace(sh, 4, mu, slp=True), r, world, gather_for(r))
+        assert np.array_equal(got["slp"], ref)
