@@ -1,4 +1,7 @@
-"""Small hand-built geometries for the oracle pins and parity tests."""
+"""Small hand-built geometries for the oracle pins and parity tests, and the
+builder of the test-only native shims."""
+import os
+
 import numpy as np
 
 from tsqbx_inputs.geometry import Geometry
@@ -63,3 +66,27 @@ def single_pair(t, c, s, n_s=None, n_t=None, w=1.0):
     return Geometry(col(s), np.array([w]), col(n_s), col(c), np.array([0.1]), col(t),
                     np.array([0], np.int32), col(n_t), np.array([0], np.int32),
                     np.array([0, 1], np.int64), np.array([0], np.int32), np.array([1], np.int32))
+
+
+def native_shim(name, deps=()):
+    """Build tests/native/<name>.cu (a test-only C shim around library headers)
+    into tests/native/_build/lib<name>.so when it is older than its sources;
+    return the path, or None without nvcc."""
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        return None
+    src = os.path.join(root, "tests", "native", name + ".cu")
+    out = os.path.join(root, "tests", "native", "_build", "lib" + name + ".so")
+    csrc = os.path.join(root, "paper_1811_01110_gb300", "csrc")
+    allsrc = [src, os.path.join(root, "include", "tsqbx.h")] + [os.path.join(csrc, f) for f in os.listdir(csrc)]
+    if not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(d) for d in allsrc):
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                        "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-shared",
+                        "-I", os.path.join(root, "include"), src, "-o", out + ".tmp"],
+                       check=True, capture_output=True)
+        os.replace(out + ".tmp", out)
+    return out

@@ -18,16 +18,11 @@ test shim and checked without a GPU:
 """
 import ctypes
 import os
-import shutil
-import subprocess
 
 import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SHIM = os.path.join(ROOT, "tests", "native", "schedule_shim.cu")
-SCHED = os.path.join(ROOT, "paper_1811_01110_gb300", "csrc", "schedule.cu")
-OUT = os.path.join(ROOT, "tests", "native", "_build", "libschedule_shim.so")
 
 i64p = ctypes.POINTER(ctypes.c_int64)
 i32p = ctypes.POINTER(ctypes.c_int32)
@@ -36,19 +31,11 @@ f64p = ctypes.POINTER(ctypes.c_double)
 
 @pytest.fixture(scope="module")
 def shim():
-    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
-    if nvcc is None:
+    from helpers import native_shim
+    path = native_shim("schedule_shim")
+    if path is None:
         pytest.skip("no nvcc")
-    deps = [SHIM, SCHED] + [os.path.join(ROOT, "paper_1811_01110_gb300", "csrc", f)
-                            for f in ("plan_internal.h", "internal.cuh")] + [os.path.join(ROOT, "include", "tsqbx.h")]
-    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(d) for d in deps):
-        os.makedirs(os.path.dirname(OUT), exist_ok=True)
-        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
-                        "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-shared",
-                        "-I", os.path.join(ROOT, "include"), SHIM, "-o", OUT + ".tmp"],
-                       check=True, capture_output=True)
-        os.replace(OUT + ".tmp", OUT)
-    L = ctypes.CDLL(OUT)
+    L = ctypes.CDLL(path)
     L.shim_build_schedule.argtypes = [ctypes.c_int64, i64p, i64p, i64p, i64p, ctypes.c_int, ctypes.c_int64,
                                       ctypes.c_int, i64p, i32p, f64p, i64p, i32p, i64p, i64p, f64p]
     L.shim_choose_lanes.argtypes = [ctypes.c_int64, ctypes.c_int64]
