@@ -130,3 +130,20 @@ def test_helmholtz_conventional_weights_give_the_addition_theorem(K, seed):
         s = sum(omega[m] * (mpmath.re(Jv[(n, m)]) * mpmath.re(Ju[(n, m)])
                             + mpmath.im(Jv[(n, m)]) * mpmath.im(Ju[(n, m)])) for m in range(n + 1))
         assert abs(s - mpmath.legendre(n, cosg)) < 1e-12, n
+
+
+def test_double_float_constants(K):
+    """df_const splits a double constant into floats hi + lo with hi the
+    nearest float and |lo| <= ulp(hi)/2, so that hi + lo carries it to about
+    2^-48 relative: the form the double-float kernel takes kappa_n, beta_n,
+    the Gegenbauer constants and 1/(4 pi) in."""
+    K.shim_df_const.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+    hi, lo = ctypes.c_float(), ctypes.c_float()
+    values = [K.shim_inv_4pi()] + [K.shim_rec_kappa(n) for n in range(21)] + \
+             [K.shim_rec_beta(n) for n in range(1, 22)] + [K.shim_rec_gamma(n) for n in range(2, 22)] + \
+             [K.shim_rec_lambda(n) for n in range(1, 22)]
+    for v in values:
+        K.shim_df_const(v, ctypes.byref(hi), ctypes.byref(lo))
+        assert hi.value == float(np.float32(v))
+        assert abs(lo.value) <= np.spacing(np.float32(abs(hi.value))) / 2
+        assert abs((float(hi.value) + float(lo.value)) - v) <= 2.0 ** -48 * abs(v)
