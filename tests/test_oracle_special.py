@@ -101,3 +101,27 @@ def test_legendre_addition_identity(rng):
             s = sum(Ya[n * n + n + m] * Yb[n * n + n - m] for m in range(-n, n + 1))
             assert s.imag == pytest.approx(0.0, abs=1e-13)
             assert 4 * np.pi / (2 * n + 1) * s.real == pytest.approx(sp.eval_legendre(n, x), abs=1e-13)
+
+
+def test_oracle_rejects_invalid_lists_and_orders():
+    """The oracle checks its inputs instead of reading out of bounds: ranges
+    past the sources, targets mapped to missing centers, orders out of range
+    and a non-positive wavenumber are refused."""
+    from helpers import cloud_geometry
+    rng = np.random.default_rng(21)
+    g = cloud_geometry(rng, n_ctr=3, n_src=30)
+    mu = rng.standard_normal(g.n_src)
+    oracle.tsqbx_laplace(g, 4, mu)                       # valid input runs
+    for mutate in (lambda h: setattr(h, "range_end", h.range_end + 100),
+                   lambda h: setattr(h, "tgt_center", np.full_like(h.tgt_center, 7)),
+                   lambda h: setattr(h, "ctr_group", np.full_like(h.ctr_group, -1))):
+        h = cloud_geometry(np.random.default_rng(21), n_ctr=3, n_src=30)
+        mutate(h)
+        with pytest.raises(ValueError):
+            oracle.tsqbx_laplace(h, 4, mu)
+    with pytest.raises(ValueError):
+        oracle.tsqbx_laplace(g, -1, mu)
+    with pytest.raises(ValueError):
+        oracle.tsqbx_laplace(g, 41, mu)
+    with pytest.raises(ValueError):
+        oracle.tsqbx_helmholtz(g, 4, 0.0, mu.astype(complex))
