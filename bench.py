@@ -32,12 +32,56 @@ METRIC = "TSQBX pair-terms/s at Laplace p=9 (single+double layer), FP64 vs mixed
 UNIT = "pair-terms/s"
 WORKLOAD = "torus 256x96 quads, 294912 sources, 589824 targets, octree lists n_max=64, Laplace SLP+DLP p=9"
 
-# Peaks (ALU-bound kernels): derived from unit counts and the maximum SM clock
-# (152 SMs x FMA lanes/clock/SM x 2 flop x 2070 MHz); FP64 at 2 FMA/clk/SM
-# (the GB300 nominal 1.25 TFLOP/s), FP32 at 128 FMA/clk/SM.
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# Fallback peaks of the ALU-bound kernels, used only when the register-only
+# probe (tsqbx_measure_pipe_peaks) cannot run: the device's SM count x FMA
+# lanes per clock per SM (FP64 2, FP32 128) x 2 flop x the maximum SM clock.
+SM_MAX_MHZ = 2070.0
+HEADLINE_MAX_BYTES = 2000       # the last stdout line stays well inside a 3-4 KB tail
+
+
+def derived_peaks(sm_count):
+    return {"fp64": sm_count * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12,
+            "fp32": sm_count * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12,
+            "source": f"derived: {sm_count} SMs x (2 | 128) FMA/clk x 2 flop x {SM_MAX_MHZ:.0f} MHz"}
+
+
+def survey_flops_per_pair(p, dlp=True):
+    """The a priori count of the Laplace kernel's work per pair (FMA = 2):
+    6p + 20 for the single layer (geometry about 20, about 6 per order), plus
+    4 per pair-term (p + 1 of them) and 20 per pair for the double layer.
+    134 at p = 9 with both layers."""
+    return 6 * p + 20 + ((4 * (p + 1) + 20) if dlp else 0)
+
+
+# FP32 flops (FMA = 2) of the double-float building blocks (csrc/dfloat.cuh):
+# TwoSum 6, FastTwoSum 3, TwoProd 3; DWPlusDW 11, DWTimesDW 10, DWTimesFP 8;
+# a 3-vector dot product 52; 1/sqrt with two Newton steps 81.
+_DF_ADD, _DF_MUL, _DF_MULF, _DF_DOT, _DF_RSQRT = 11, 10, 8, 52, 81
+
+
+def df64_fp32_flops_per_pair(p, dlp=True, sp=False):
+    """FP32 flops per pair (FMA = 2) of the double-float Laplace kernel
+    (laplace_df_items.cuh, multi-target items): geometry (s - c as three
+    double-float differences, R^2, 1/R, 1/R^2, qx, q2, w/R) 258; the Clenshaw
+    single layer 21 + 52 per order step + 21; with the double layer or S'
+    the Q' recurrence 62 per step, its top 61, the closing sums 83, the
+    single layer's accumulation 21 and w/R^3 10; the double layer 167 (two
+    dots, the combination, accumulation), S' 104.  1096 at p = 9 with both
+    layers."""
+    geo = 3 * _DF_ADD + _DF_DOT + _DF_RSQRT + _DF_MUL + (_DF_DOT + _DF_MUL) + 2 * _DF_MUL
+    q = max(p - 1, 0)
+    if not dlp and not sp:
+        return geo + (_DF_ADD + _DF_MUL) + (3 * _DF_MUL + 2 * _DF_ADD) * q + (_DF_ADD + _DF_MUL)
+    f = geo + (2 * _DF_ADD + 4 * _DF_MUL) * q
+    if p >= 1:
+        f += 5 * _DF_MUL + _DF_ADD                                            # Q'_p, Q'_{p+1}
+    f += _DF_ADD + (_DF_MULF + 2 * _DF_ADD) + (2 * _DF_MUL + 2 * _DF_ADD)     # S2, c1, S
+    f += _DF_MUL + _DF_ADD + _DF_MUL                                          # acc_s, w/R^3
+    if dlp:
+        f += 2 * _DF_DOT + 3 * _DF_MUL + 3 * _DF_ADD
+    if sp:
+        f += _DF_DOT + 3 * _DF_MUL + 2 * _DF_ADD
+    return f
 
 
 def flops_per_pair(p, precision, dlp=True, sp=False):
@@ -99,6 +143,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline workload (no batched / Helmholtz / sphere legs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the automatic schedules")
+    ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
+                    help="file for the full result (every workload); stdout gets the headline line only")
     ap.add_argument("--only", choices=["batched", "helmholtz", "sphere", "serving", "target_derivative",
                                        "conventional", "lists"],
                     help="run one secondary workload alone and print its JSON (for profiling)")
@@ -355,16 +401,36 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
-def roofline(flops_per_launch, kernel_s, precision, traffic_key=None):
-    peak = PEAK_FP64_TFLOPS if precision == "fp64" else PEAK_FP32_TFLOPS
+PEAKS = None     # set once per run by measure_peaks()
+
+
+def measure_peaks(pkg, dev_index, sm_count):
+    """FP64 and FP32 pipe peaks for the rooflines: the library's register-only
+    FMA probe on this device (the packed-FP32 figure when it is higher, since
+    the mixed kernel issues packed instructions), else the derived figures."""
+    global PEAKS
+    try:
+        m = pkg.measure_pipe_peaks(dev_index)
+        PEAKS = {"fp64": m["fp64_tflops"], "fp32": max(m["fp32_tflops"], m["fp32x2_tflops"]),
+                 "source": "measured: register-only FMA probe (tsqbx_measure_pipe_peaks), %d SMs, best of 3 "
+                           "launches of ~150 ms" % m["sm_count"], "probe": m}
+    except Exception as exc:             # the kernels' numbers stand against the derived peaks
+        PEAKS = dict(derived_peaks(sm_count), probe_error=repr(exc)[:200])
+    PEAKS["derived"] = derived_peaks(sm_count)
+    return PEAKS
+
+
+def roofline(flops_per_launch, kernel_s, pipe, traffic_key=None):
+    """ALU roofline of one launch: algorithmic flops over the kernel's CUDA-event
+    time, against the FP64 or FP32 pipe peak (measured when the probe ran)."""
+    peaks = PEAKS or derived_peaks(152)
+    peak = peaks[pipe]
     achieved = flops_per_launch / kernel_s / 1e12
     traffic = TRAFFIC_BYTES.get(traffic_key)
     out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": achieved / peak, "traffic": traffic,
            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-           "pipe": precision if precision == "fp64" else "fp32",
-           "peak_source": "derived: 152 SMs x %d FMA/clk x 2 flop x 2070 MHz"
-                          % (2 if precision == "fp64" else 128)}
+           "pipe": pipe, "peak_source": peaks["source"]}
     if traffic is not None:
         # the DRAM side of the same launch: ncu bytes over this run's kernel time
         hbm, src = measured_hbm_gbs()
@@ -431,7 +497,7 @@ def leg_batched(pkg, torch, dev, steps, warmup, flush, check_targets=0):
            "persistent_ctas": info["grid_blocks"], "graph": bool(info["graph"]),
            "sequential_ms_per_step": sum(seq) / steps,
            "speedup_vs_sequential": (sum(seq) / steps) / (1e3 * t),
-           "roofline": roofline(fl, sum(kms) / steps / 1e3, "mixed", ("batched", "mixed", "slp"))}
+           "roofline": roofline(fl, sum(kms) / steps / 1e3, "fp32", ("batched", "mixed", "slp"))}
     if checked:
         try:
             import oracle
@@ -622,11 +688,12 @@ def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush, check_ta
         out = {l: torch.empty(g.n_tgt, dtype=torch.float64, device=dev) for l in layers}
         step_ms, kern_ms = time_device(plan, dmu, out, stream, steps, warmup, flush, lambda: None)
         t = sum(kern_ms) / 1e3 / steps
-        fprec = "fp64" if prec == "df64" else prec
-        fl = flops_per_pair(P, fprec, dlp=True, sp=True)
+        fl = (df64_fp32_flops_per_pair(P, dlp=True, sp=True) if prec == "df64"
+              else flops_per_pair(P, prec, dlp=True, sp=True))
         res[prec] = {"value": info["n_pair_terms"] / (sum(step_ms) / 1e3 / steps),
                      "ms_per_step": sum(step_ms) / steps, "kernel_ms": 1e3 * t,
-                     "roofline": dict(roofline(fl * info["n_pairs"], t, fprec), flops_per_pair=fl)}
+                     "roofline": dict(roofline(fl * info["n_pairs"], t, "fp64" if prec == "fp64" else "fp32"),
+                                      flops_per_pair=fl)}
         if ref is not None:
             res[prec]["error_vs_oracle"] = {l: max_rel_err(out[l].cpu().numpy()[idx], ref[l]) for l in layers}
             res[prec]["error_vs_oracle"]["targets"] = int(len(idx))
@@ -754,6 +821,7 @@ def main():
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     import paper_1811_01110_gb300 as pkg
+    measure_peaks(pkg, local_rank, torch.cuda.get_device_properties(dev).multi_processor_count)
     if args.only:
         flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
         steps = max(3, args.steps // 2)
@@ -815,14 +883,23 @@ def main():
         t_kern = agg(kern_ms)
         value = pair_terms * args.steps * world / t_step
         kavg = t_kern / args.steps
-        # df64 runs the FP64 algorithm in double-float on the FP32 pipes: its
-        # algorithmic flops are the FP64 ones, set against the FP64 peak
-        fprec = "fp64" if prec == "df64" else prec
-        rf = roofline(flops_per_pair(P, fprec) * info["n_pairs"], kavg, fprec, ("laplace", prec, "slp+dlp"))
-        rf["flops_per_pair"] = flops_per_pair(P, fprec)
         if prec == "df64":
-            rf["note"] = ("FP64-equivalent flops (double-float arithmetic on the FP32 pipes) "
-                          "against the FP64 peak; above 1 means faster than native FP64 could be")
+            # double-float on the FP32 pipes: its own FP32 flops against the
+            # FP32 peak; the FP64-equivalent rate is kept beside it
+            fl = df64_fp32_flops_per_pair(P)
+            rf = roofline(fl * info["n_pairs"], kavg, "fp32", ("laplace", prec, "slp+dlp"))
+            fe = flops_per_pair(P, "fp64") * info["n_pairs"] / kavg / 1e12
+            rf["fp64_equivalent"] = {"flops_per_pair": flops_per_pair(P, "fp64"), "achieved": fe,
+                                     "frac_of_fp64_peak": fe / (PEAKS or derived_peaks(152))["fp64"]}
+        else:
+            fl = flops_per_pair(P, prec)
+            rf = roofline(fl * info["n_pairs"], kavg, "fp64" if prec == "fp64" else "fp32",
+                          ("laplace", prec, "slp+dlp"))
+            # the same launch counted with the a priori per-pair estimate
+            sf = survey_flops_per_pair(P) + (flops_per_pair(P, prec) - flops_per_pair(P, "fp64"))
+            sa = sf * info["n_pairs"] / kavg / 1e12
+            rf["a_priori_count"] = {"flops_per_pair": sf, "achieved": sa, "frac": sa / rf["peak"]}
+        rf["flops_per_pair"] = fl
         summary[prec] = {"value": value, "ms_per_step": 1e3 * t_step / args.steps,
                          "kernel_ms": 1e3 * kavg, "roofline": rf,
                          "pairs_per_s": info["n_pairs"] * args.steps * world / t_step}
@@ -887,7 +964,7 @@ def main():
             err[f"e2e_fp64_{l}"] = float(np.max(np.abs(host_out[l][cs["idx"]] - ref)) / np.max(np.abs(ref)))
 
     f = summary["fp64"]
-    line = {
+    full = {
         "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -915,11 +992,112 @@ def main():
         "clocks": clocks,
         "wall_s_timed_region": wall_s,
         "cpu_baseline": cpu,
+        "peaks": PEAKS,
     }
-    line.update(extras)
-    print(json.dumps(line), flush=True)
+    full.update(extras)
+    emit(full, args.detail)
     for p_ in plans.values():
         p_.close()
+
+
+def _sig(x, digits=4):
+    """x rounded to `digits` significant digits (numbers only)."""
+    if isinstance(x, bool) or not isinstance(x, float):
+        return x
+    if x == 0.0 or x != x or x in (float("inf"), float("-inf")):
+        return x
+    return float(f"{x:.{digits - 1}e}")
+
+
+def _pick(d, *keys):
+    """The listed keys of dict d that exist, floats rounded."""
+    return {k: _sig(d[k]) for k in keys if isinstance(d, dict) and k in d}
+
+
+def _short_roofline(rf):
+    out = _pick(rf, "bound", "achieved", "peak", "unit", "frac", "traffic", "pipe", "flops_per_pair")
+    src = str(rf.get("peak_source", ""))
+    out["peak_source"] = "measured" if src.startswith("measured") else "derived"
+    if "a_priori_count" in rf:
+        out["a_priori"] = _pick(rf["a_priori_count"], "flops_per_pair", "frac")
+    if "fp64_equivalent" in rf:
+        out["fp64_equiv"] = _pick(rf["fp64_equivalent"], "achieved", "frac_of_fp64_peak")
+    return out
+
+
+def headline(full, detail_path=None):
+    """The last stdout line: the contract's keys with the headline workload's
+    numbers, one short block per precision and per secondary workload, all
+    floats to four significant digits; everything else goes to the detail
+    file.  Kept under HEADLINE_MAX_BYTES."""
+    err = full.get("error_vs_oracle") or {}
+    line = {k: _sig(full[k]) for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                                       "higher_is_better", "scaling", "vs_baseline", "dtype", "data")}
+    cfg = full.get("config", {})
+    line["config"] = {"workload": cfg.get("workload"), "n_pairs": cfg.get("n_pairs"),
+                      "l2": "flushed between steps"}
+    line["roofline"] = _short_roofline(full["roofline"])
+    line["kernel_ms"] = _sig(full["kernel_ms"])
+    line["error_vs_oracle"] = {k: _sig(v, 2) for k, v in err.items() if k.startswith("fp64")} or None
+    for prec in ("mixed", "df64"):
+        if prec in full:
+            b = full[prec]
+            line[prec] = dict(_pick(b, "value", "ms_per_step", "kernel_ms"),
+                              frac=_sig(b["roofline"]["frac"]),
+                              error={k[len(prec) + 1:]: _sig(v, 2) for k, v in err.items()
+                                     if k.startswith(prec + "_")} or None)
+    if full.get("e2e"):
+        line["e2e"] = _pick(full["e2e"], "value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")
+    if full.get("cpu_baseline"):
+        line["cpu_baseline"] = _pick(full["cpu_baseline"], "value", "unit", "cores", "kind")
+        line["cpu_baseline"]["sample"] = str(full["cpu_baseline"].get("sample", ""))[:60]
+    line["gpu_launches"] = full.get("gpu_launches")
+    if full.get("clocks"):
+        line["clocks"] = _pick(full["clocks"], "sm_mhz", "sm_max_mhz", "reasons")
+    legs = {}
+    for name in ("helmholtz", "batched", "sphere"):
+        if name in full and isinstance(full[name], dict):
+            b = full[name]
+            sub = b.get("slp", b)                  # Helmholtz: its single-layer plan
+            legs[name] = dict(_pick(b, "value"), **_pick(sub, "ms_per_step"),
+                              frac=_sig(sub.get("roofline", {}).get("frac")))
+            e = sub.get("error_vs_oracle", b.get("error_vs_oracle"))
+            if isinstance(e, dict) and "slp" in e:
+                legs[name]["err"] = _sig(e["slp"], 2)
+    td = full.get("target_derivative")
+    if isinstance(td, dict) and isinstance(td.get("mixed"), dict):
+        e = td["mixed"].get("error_vs_oracle") or {}
+        legs["sp_mixed"] = dict(_pick(td["mixed"], "value"), err=_sig(e.get("sp"), 2))
+    srv = full.get("serving")
+    if isinstance(srv, dict) and "offered" in srv:
+        o = srv["offered"]
+        legs["serving"] = dict(_pick(o, "offered_req_per_s", "achieved_req_per_s", "p50_ms", "p99_ms"),
+                               saturated=srv.get("saturated_at_offered_rate"))
+        if "sustainable" in srv:
+            legs["serving"]["at80"] = _pick(srv["sustainable"], "offered_req_per_s", "p50_ms", "p99_ms")
+    if legs:
+        line["legs"] = legs
+    if detail_path:
+        line["detail"] = os.path.basename(detail_path)
+    text = json.dumps(line, separators=(",", ":"))
+    if len(text) > HEADLINE_MAX_BYTES:          # drop the secondary blocks first
+        for k in ("legs", "df64", "clocks"):
+            line.pop(k, None)
+            text = json.dumps(line, separators=(",", ":"))
+            if len(text) <= HEADLINE_MAX_BYTES:
+                break
+    return text
+
+
+def emit(full, detail_path):
+    """Write every number to the detail file, then print the headline as the
+    only stdout line."""
+    if detail_path:
+        d = os.path.dirname(os.path.abspath(detail_path))
+        os.makedirs(d, exist_ok=True)
+        with open(detail_path, "w") as fh:
+            json.dump(full, fh, indent=1)
+    print(headline(full, detail_path), flush=True)
 
 
 if __name__ == "__main__":

@@ -402,12 +402,16 @@ TSQBX_API int tsqbx_plan_get_tuning(tsqbx_plan plan, tsqbx_tuning *tuning);
  * lives in one fixed __device__ array of 8 MiB inside the library, which every
  * GPU that loads the library holds until the process exits.
  *
- * Computes the Laplace single and/or double layer (FP64) exactly as
- * tsqbx_eval does for a plan with the same geometry, p and layers.
+ * Computes the same quantities as tsqbx_eval for a plan with the same
+ * geometry, p and layers (the Laplace single and/or double layer, FP64), to
+ * FP64 roundoff (about 1e-12 relative): its recurrence and lane reduction are
+ * its own, so the two agree to rounding, not bit for bit.
  *  d_geometry: a HOST struct whose counts are sizes and whose pointer fields
  *              are all DEVICE pointers in the tsqbx_geometry layout;
- *              group_range_start must hold n_group + 1 entries; ctr_radius is
- *              ignored; src_normal is required for TSQBX_DLP.
+ *              group_range_start must hold n_group + 1 entries, and
+ *              range_begin / range_end must be non-NULL when n_group > 0
+ *              (even if every list is empty); ctr_radius is ignored;
+ *              src_normal is required for TSQBX_DLP.
  *  d_density:  n_src doubles (device).  d_out_slp / d_out_dlp: n_tgt doubles
  *              (device) for the requested layers.
  *  stream:     cudaStream_t (NULL = legacy default stream); the call blocks
@@ -419,8 +423,13 @@ TSQBX_API int tsqbx_plan_get_tuning(tsqbx_plan plan, tsqbx_tuning *tuning);
  * first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Index ranges are checked on the device: an
- * out-of-range index is skipped and reported as TSQBX_E_KERNEL.  Errors:
- * TSQBX_E_INVAL, TSQBX_E_TOO_LARGE, TSQBX_E_KERNEL, TSQBX_E_CUDA. */
+ * out-of-range index is skipped and reported as TSQBX_E_KERNEL, and so is a
+ * listed source that sits exactly on its center (|s-c| = 0, where the
+ * expansion does not exist): that pair is skipped.  Unlike
+ * tsqbx_plan_create, this entry point does NOT look for divergent pairs
+ * (|t-c| >= |s-c|); such a pair is summed like any other and its terms grow
+ * with p.  Errors: TSQBX_E_INVAL, TSQBX_E_TOO_LARGE, TSQBX_E_KERNEL,
+ * TSQBX_E_CUDA. */
 #define TSQBX_NOALLOC_MAX_SRC 1048544
 TSQBX_API int tsqbx_eval_noalloc(const tsqbx_geometry *d_geometry, int p, uint32_t layers,
                                  const double *d_density, double *d_out_slp, double *d_out_dlp,
@@ -472,6 +481,26 @@ TSQBX_API int tsqbx_octree_order(tsqbx_octree tree, int32_t *src_perm, int32_t *
  * near_start[b+1]) (half-open, depth-first source positions); near_start has
  * n_boxes + 1 entries, the ranges stats.near_nnz. */
 TSQBX_API int tsqbx_octree_near(tsqbx_octree tree, int64_t *near_start, int32_t *near_begin, int32_t *near_end);
+
+/* ------------------------------------------------------- measurement aid
+ * The paper has no counterpart (its timings are CPU process times, Sec. 4):
+ * the expansion kernels are bound by the FP64 pipe (FP64 and Helmholtz) or
+ * the FP32 pipe (mixed and df64), so their rooflines divide by these pipes'
+ * throughput, measured here on the device itself.  Register-only fused
+ * multiply-add chains (no memory traffic); per pipe, nine launch shapes (4, 8
+ * or 16 chains per thread, 2, 4 or 8 blocks of 256 threads per SM) are timed
+ * briefly and the fastest again at about 150 ms per launch, with CUDA events
+ * (best of 3); an FMA counts as two flops.  Runs a few seconds in all and
+ * changes no setting of the GPU.  Errors: TSQBX_E_INVAL (bad device or NULL),
+ * TSQBX_E_CUDA. */
+typedef struct {
+    double fp64_tflops;         /* DFMA                                               */
+    double fp32_tflops;         /* scalar FFMA                                        */
+    double fp32x2_tflops;       /* packed fma.rn.f32x2 (two FMAs per instruction)     */
+    int sm_count;               /* the device's multiprocessors                       */
+    float ms_fp64, ms_fp32, ms_fp32x2;   /* duration of the best timed launch        */
+} tsqbx_pipe_peaks;
+TSQBX_API int tsqbx_measure_pipe_peaks(int device, tsqbx_pipe_peaks *out);
 
 /* Name of the last CUDA runtime error that a libtsqbx call made on the
  * calling thread ran into (the detail behind TSQBX_E_CUDA / TSQBX_E_NOMEM);

@@ -464,3 +464,12 @@ def poll(ticket, timeout_us=0):
         return False
     check(rc, "tsqbx_poll")
     return True
+
+
+def measure_pipe_peaks(device=0):
+    """tsqbx_measure_pipe_peaks: measured FP64 / FP32 / packed-FP32 FMA
+    throughput (TFLOP/s, FMA = 2 flops) and the device's SM count."""
+    r = _lib.tsqbx_pipe_peaks()
+    check(lib().tsqbx_measure_pipe_peaks(int(device), ctypes.byref(r)), "tsqbx_measure_pipe_peaks")
+    return {"fp64_tflops": r.fp64_tflops, "fp32_tflops": r.fp32_tflops, "fp32x2_tflops": r.fp32x2_tflops,
+            "sm_count": r.sm_count, "ms": {"fp64": r.ms_fp64, "fp32": r.ms_fp32, "fp32x2": r.ms_fp32x2}}

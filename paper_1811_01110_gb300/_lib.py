@@ -91,6 +91,12 @@ class tsqbx_octree_stats(ctypes.Structure):
     ]
 
 
+class tsqbx_pipe_peaks(ctypes.Structure):
+    _fields_ = [("fp64_tflops", ctypes.c_double), ("fp32_tflops", ctypes.c_double),
+                ("fp32x2_tflops", ctypes.c_double), ("sm_count", ctypes.c_int),
+                ("ms_fp64", ctypes.c_float), ("ms_fp32", ctypes.c_float), ("ms_fp32x2", ctypes.c_float)]
+
+
 class tsqbx_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_target", ctypes.c_int), ("max_item_iters", ctypes.c_int),
                 ("kernel_ms", ctypes.c_float)]
@@ -158,6 +164,7 @@ _SIGNATURES = [
      [ctypes.c_void_p, _i32p, _dp, _dp, _i32p, _i32p, _i32p, _i32p, _i32p]),
     ("tsqbx_octree_order", ctypes.c_int, [ctypes.c_void_p, _i32p, _i32p]),
     ("tsqbx_octree_near", ctypes.c_int, [ctypes.c_void_p, _i64p, _i32p, _i32p]),
+    ("tsqbx_measure_pipe_peaks", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tsqbx_pipe_peaks)]),
     ("tsqbx_last_error", ctypes.c_char_p, []),
     ("tsqbx_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("tsqbx_version", ctypes.c_int, []),
