@@ -52,8 +52,13 @@ __global__ void noalloc_prep(const double *w, const double *mu, int64_t n, doubl
 }
 
 // One warp per target; lanes stride through the sources of each listed range
-// (coalesced structure-of-arrays loads) and run the same scaled Legendre
-// recurrence as laplace_fp64.cu; a butterfly shuffle combines the lanes.
+// (coalesced structure-of-arrays loads) and run the scaled Legendre recurrence
+// forward (Q_n = kappa_n T_n, eq. tsqbx), with the double layer from the
+// derivative recurrence and its closing sums (Appendix A); a butterfly shuffle
+// combines the lanes.  Status bits: 1 = an index out of range (the access is
+// skipped), 2 = a source on its center (R = 0, where the expansion does not
+// exist; the pair is skipped).  Divergent pairs (|t-c| >= |s-c|) are not
+// looked for: such a pair is summed like any other.
 template <int P, bool DLP>
 __global__ void __launch_bounds__(128)
 noalloc_laplace_fp64(const RawGeom g, const double *wmu, unsigned long long *status,
@@ -94,6 +99,10 @@ noalloc_laplace_fp64(const RawGeom g, const double *wmu, unsigned long long *sta
                          dz = g.src_xyz[2 * g.n_src + s] - cz;
             const double wm = wmu[s];
             const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            if (!(R2 > 0.0)) {              // source on the center: the expansion does not exist
+                atomicOr(status, 2ull);
+                continue;
+            }
             const double rinv = rsqrt(R2);
             const double r2inv = rinv * rinv;
             const double qx = fma(dx, ex, fma(dy, ey, dz * ez)) * r2inv;
@@ -189,6 +198,7 @@ extern "C" int tsqbx_eval_noalloc(const tsqbx_geometry *d_geometry, int p, uint3
     if ((G->n_src && (!G->src_xyz || !G->src_weight || !d_density)) ||
         (dlp && G->n_src && !G->src_normal) || (G->n_ctr && (!G->ctr_xyz || !G->ctr_group)) ||
         (G->n_tgt && (!G->tgt_xyz || !G->tgt_center)) || !G->group_range_start ||
+        (G->n_group && (!G->range_begin || !G->range_end)) ||
         ((layers & TSQBX_SLP) && G->n_tgt && !d_out_slp) || (dlp && G->n_tgt && !d_out_dlp))
         return TSQBX_E_INVAL;
     int dev = 0;

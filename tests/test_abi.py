@@ -197,7 +197,24 @@ def test_noalloc_arguments_rejected_on_host(L):
     assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 0, fake, fake, None, None) == inval
     assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 4, fake, fake, fake, None) == inval   # S' not offered
     assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval   # NULL arrays
+    # every array present except the range arrays, with n_group > 0
+    dp = ctypes.cast(fake, ctypes.POINTER(ctypes.c_double))
+    ip = ctypes.cast(fake, ctypes.POINTER(ctypes.c_int32))
+    geo.src_xyz = geo.src_weight = geo.ctr_xyz = geo.tgt_xyz = dp
+    geo.tgt_center = geo.ctr_group = ip
+    geo.group_range_start = ctypes.cast(fake, ctypes.POINTER(ctypes.c_int64))
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval   # NULL ranges
+    geo.range_begin = ip
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval   # NULL range_end
+    geo.range_begin, geo.range_end = None, ip
+    assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval   # NULL range_begin
     geo.n_src = 1048544 + 1
     assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == _lib.TSQBX_E_TOO_LARGE
     geo.n_src = -1
     assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval
+
+
+def test_pipe_peak_probe_rejects_null_on_host(L):
+    """tsqbx_measure_pipe_peaks checks its output pointer before any CUDA call."""
+    from paper_1811_01110_gb300 import _lib
+    assert L.tsqbx_measure_pipe_peaks(0, None) == _lib.TSQBX_E_INVAL
