@@ -2,11 +2,9 @@
 single layer, Laplace and Helmholtz) and the Helmholtz double layer, through
 the C ABI, against the FP64 CPU oracle (Appendix A).
 
-Tolerances (max-norm relative, per layer): FP64 and df64 1e-12; mixed 2e-6
-for S' (its per-pair terms carry one more factor |d|/R^2 than the single
-layer, so FP32 rounding of d and of the differentiated recurrence adds about
-one FP32 ulp per order on top of the single layer's error) and 1e-6 for the
-other layers.
+Tolerances (max-norm relative, per layer): FP64 and df64 1e-12; mixed 1e-6
+for every layer, S' included (measured on a GB300 over every test case below:
+at most 5.5e-7 for S', 9.4e-7 for the double layer).
 """
 import numpy as np
 import pytest
@@ -18,7 +16,7 @@ from tsqbx_inputs import configs
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-6, "df64": 1e-12}
-TOL_SP = {"fp64": 1e-12, "mixed": 2e-6, "df64": 1e-12}
+TOL_SP = {"fp64": 1e-12, "mixed": 1e-6, "df64": 1e-12}
 
 
 @pytest.fixture(scope="module")
