@@ -5,7 +5,8 @@ per-rank target shards with no exchange; the outputs are concatenated.
 Sources, centers and pair lists are replicated on every rank; each rank's
 plan holds only its own targets (`shard_geometry`).  `distributed_eval`
 runs one evaluation over a torch.distributed group: every rank evaluates its
-shard and one all-gather of the outputs reassembles them."""
+shard and one all-gather per layer of the (padded) output tensors
+reassembles them -- device tensors under NCCL, host tensors under gloo."""
 import types
 
 import numpy as np
@@ -60,18 +61,52 @@ def shard_geometry(geometry, idx):
     return types.SimpleNamespace(**fields)
 
 
-def distributed_eval(geometry, evaluate, rank, world_size, all_gather_object):
+def _as_real_tensor(torch, v, device):
+    """v (numpy array or torch tensor) as a real torch tensor on `device`:
+    complex values become a trailing (re, im) axis."""
+    t = v if isinstance(v, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(v))
+    t = t.to(device)
+    return torch.view_as_real(t) if t.is_complex() else t
+
+
+def distributed_eval(geometry, evaluate, rank, world_size, all_gather=None, device=None):
     """One evaluation split over `world_size` ranks with no data-path exchange.
 
     evaluate(shard) -> {layer: 1-D array over the shard's targets} runs this
-    rank's part (a Plan on this rank's GPU); all_gather_object is
-    torch.distributed.all_gather_object (or any function with its contract).
-    Every rank returns the full {layer: array over all targets}."""
+    rank's part (a Plan on this rank's GPU); its values may be numpy arrays or
+    torch tensors, host or device.  The shards' outputs are then exchanged by
+    one all-gather per layer of tensors padded to the longest shard (every
+    rank knows every shard's size, so no size exchange is needed).
+    all_gather has the contract of torch.distributed.all_gather(tensor_list,
+    tensor) and defaults to it; device is where the gathered tensors live:
+    the outputs' own device under NCCL (the data plane then stays on the
+    GPUs), the host under gloo (the default for any other backend).  Every
+    rank returns the full {layer: array over all targets}, as numpy arrays
+    if evaluate returned numpy arrays, else as torch tensors on `device`."""
+    import torch
+    import torch.distributed as dist
     shards = shard_targets(geometry, world_size)
     mine = evaluate(shard_geometry(geometry, shards[rank]))
-    mine = {k: np.asarray(v) for k, v in mine.items()}
-    parts = [None] * world_size
-    all_gather_object(parts, mine)
+    as_numpy = not any(isinstance(v, torch.Tensor) for v in mine.values())
+    if device is None:
+        on_nccl = all_gather is None and dist.is_initialized() and dist.get_backend() == "nccl"
+        dev_of = [v.device for v in mine.values() if isinstance(v, torch.Tensor) and v.is_cuda]
+        device = dev_of[0] if (on_nccl and dev_of) else torch.device("cpu")
+    gather = all_gather or dist.all_gather
+    n_max = max(len(s) for s in shards)
     n_tgt = int(np.asarray(geometry.tgt_center).shape[0])
-    return {k: gather_outputs([p_[k] for p_ in parts], shards, n_tgt, dtype=mine[k].dtype)
-            for k in mine}
+    result = {}
+    for layer in sorted(mine):
+        part = _as_real_tensor(torch, mine[layer], device)
+        padded = torch.zeros((n_max,) + tuple(part.shape[1:]), dtype=part.dtype, device=device)
+        padded[: part.shape[0]] = part
+        parts = [torch.empty_like(padded) for _ in range(world_size)]
+        gather(parts, padded)
+        full = torch.zeros((n_tgt,) + tuple(part.shape[1:]), dtype=part.dtype, device=device)
+        for r, idx in enumerate(shards):
+            if len(idx):
+                full[torch.from_numpy(idx).to(device)] = parts[r][: len(idx)]
+        if full.dim() == 2:                              # complex values
+            full = torch.view_as_complex(full.contiguous())
+        result[layer] = full.cpu().numpy() if as_numpy else full
+    return result

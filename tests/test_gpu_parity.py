@@ -209,6 +209,25 @@ def test_helmholtz_small_torus(pkg):
     assert relerr(out, ref) <= 1e-12
 
 
+def test_helmholtz_full_size_torus_sampled_targets(pkg):
+    """The Helmholtz workload at full size: torus 444 x 166 quads (884,448
+    sources, 1,768,896 targets, octree lists), k = 10, p = 12, the single,
+    double and S' layers in one plan, as the benchmark launches it; 900
+    seeded random targets compared element-wise with the oracle (Appendix A,
+    the Helmholtz addition theorem) at the FP64 bar."""
+    g, mu, _ = configs.torus_helmholtz()
+    assert g.n_src == 884448 and g.n_tgt == 1768896
+    rng = np.random.default_rng(31)
+    idx = np.sort(rng.choice(g.n_tgt, 900, replace=False))
+    layers = ("slp", "dlp", "sp")
+    ref = oracle.tsqbx_helmholtz(g, 12, 10.0, mu, subset=idx, slp=True, dlp=True, sp=True)
+    with pkg.Plan(g, "helmholtz", layers, p=12, k=10.0) as plan:
+        out = plan.eval(mu)
+    for layer in layers:
+        e = relerr(out[layer][idx], ref[layer])
+        assert e <= 1e-12, (layer, e)
+
+
 def test_paths_agree_and_are_deterministic(pkg):
     """Host pointers, device tensors, eval_async and submit/poll give
     bit-identical results; repeated evaluations are bit-identical."""

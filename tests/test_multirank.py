@@ -47,7 +47,7 @@ def _worker(rank, world, port, result_path):
     def evaluate(shard):
         return oracle.tsqbx_helmholtz(shard, 6, 5.0, muh, slp=True, dlp=True, sp=True)
 
-    got = distributed_eval(gh, evaluate, rank, world, dist.all_gather_object)
+    got = distributed_eval(gh, evaluate, rank, world)
     if rank == 0:
         ref = oracle.tsqbx_helmholtz(gh, 6, 5.0, muh, slp=True, dlp=True, sp=True)
         ok = all(np.array_equal(got[k], ref[k]) and got[k].dtype == np.complex128 for k in ref)
@@ -89,32 +89,61 @@ def test_shard_geometry_keeps_sources_and_lists():
     assert sub.tgt_normal is None or np.array_equal(sub.tgt_normal, g.tgt_normal[:, idx])
 
 
+def _fake_world(geometry, evaluate_for, world):
+    """distributed_eval for every rank of a world run in turn in this process:
+    a first pass records what each rank contributes to each all-gather call,
+    a second pass gives every rank's gather all the ranks' contributions."""
+    sent = {r: [] for r in range(world)}
+
+    def recorder(r):
+        def all_gather(tensor_list, tensor):
+            sent[r].append(tensor.clone())
+            for t in tensor_list:
+                t.zero_()
+        return all_gather
+
+    def replayer(r):
+        calls = iter(range(len(sent[r])))
+
+        def all_gather(tensor_list, tensor):
+            i = next(calls)
+            for q in range(world):
+                tensor_list[q].copy_(tensor if q == r else sent[q][i])
+        return all_gather
+
+    for r in range(world):
+        distributed_eval(geometry, evaluate_for(r), r, world, all_gather=recorder(r))
+    return [distributed_eval(geometry, evaluate_for(r), r, world, all_gather=replayer(r)) for r in range(world)]
+
+
 def test_distributed_eval_single_process_world3():
     """The driver with a fake all-gather over three ranks run in turn."""
     import oracle
     from tsqbx_inputs import configs
     g, mu, _ = configs.torus(20, 8)
-    world = 3
-    mine = {}
+    ref = oracle.tsqbx_laplace(g, 5, mu, slp=True, dlp=True)
+    got = _fake_world(g, lambda r: (lambda shard: oracle.tsqbx_laplace(shard, 5, mu, slp=True, dlp=True)), 3)
+    for res in got:
+        assert all(np.array_equal(res[k], ref[k]) for k in ("slp", "dlp"))
+
+
+def test_distributed_eval_complex_and_torch_outputs():
+    """Complex (Helmholtz) outputs travel as (re, im) pairs; torch outputs
+    come back as torch tensors."""
+    import torch
+    import oracle
+    from tsqbx_inputs import configs
+    g, muh, _ = configs.torus_helmholtz(12, 5, k=3.0)
+    ref = oracle.tsqbx_helmholtz(g, 4, 3.0, muh, slp=True, dlp=True)
 
     def evaluate_for(r):
-        return lambda shard: oracle.tsqbx_laplace(shard, 5, mu, slp=True, dlp=True)
+        return lambda sh: {k: torch.from_numpy(v) for k, v in
+                           oracle.tsqbx_helmholtz(sh, 4, 3.0, muh, slp=True, dlp=True).items()}
 
-    # collect every rank's part first, then let each rank's gather see them all
-    shards = shard_targets(g, world)
-    for r in range(world):
-        mine[r] = evaluate_for(r)(shard_geometry(g, shards[r]))
-
-    def gather_for(r):
-        def all_gather_object(parts, obj):
-            for q in range(world):
-                parts[q] = obj if q == r else mine[q]
-        return all_gather_object
-
-    ref = oracle.tsqbx_laplace(g, 5, mu, slp=True, dlp=True)
-    for r in range(world):
-        got = distributed_eval(g, evaluate_for(r), r, world, gather_for(r))
-        assert all(np.array_equal(got[k], ref[k]) for k in ("slp", "dlp"))
+    for res in _fake_world(g, evaluate_for, 2):
+        for k in ("slp", "dlp"):
+            assert isinstance(res[k], torch.Tensor) and res[k].dtype == torch.complex128
+            assert np.array_equal(res[k].numpy(), ref[k])
 
 
 def test_more_ranks_than_targets():
@@ -127,15 +156,7 @@ def test_more_ranks_than_targets():
     world = 5
     shards = shard_targets(g, world)
     assert sum(len(s) for s in shards) == g.n_tgt and sum(len(s) == 0 for s in shards) >= world - g.n_tgt
-    parts = {r: oracle.tsqbx_laplace(shard_geometry(g, shards[r]), 4, mu, slp=True) for r in range(world)}
-
-    def gather_for(r):
-        def all_gather_object(out, obj):
-            for q in range(world):
-                out[q] = obj if q == r else parts[q]
-        return all_gather_object
-
     ref = oracle.tsqbx_laplace(g, 4, mu, slp=True)["slp"]
-    for r in range(world):
-        got = distributed_eval(g, lambda sh: oracle.tsqbx_laplace(sh, 4, mu, slp=True), r, world, gather_for(r))
-        assert np.array_equal(got["slp"], ref)
+    got = _fake_world(g, lambda r: (lambda sh: oracle.tsqbx_laplace(sh, 4, mu, slp=True)), world)
+    for res in got:
+        assert np.array_equal(res["slp"], ref)
