@@ -1,7 +1,9 @@
 // batch.cu -- many plans in one persistent, load-balanced launch.
 //
 // The work items of every plan (each already cut by its own schedule) are
-// merged into one queue sorted by estimated cost, heaviest first.  A
+// merged into one queue, plan by plan (the plans with the most work first, so
+// the smallest surfaces' light items fill the end), each plan's items heaviest
+// first: a surface's sources then stay in L2 while its items run.  A
 // persistent grid (one wave: the occupancy limit times the SM count) of
 // independent warps pops items from the queue with an atomic counter, so a
 // warp that finishes a light item immediately takes the next one; each item
@@ -69,18 +71,18 @@ __global__ void batch_walk_kernel(const BatchPlan *plans, const Item *items, int
 
 template <bool DLP, int... Ps>
 __device__ __forceinline__ void run_item_fp64(int p, const DevGeom &g, const DevEval &ev, const Item &it,
-                                              const WalkStart &ws, double (*T)[kTile], int lane,
+                                              const WalkStart &ws, double *T, int lane,
                                               std::integer_sequence<int, Ps...>)
 {
-    ((p == Ps ? (laplace_fp64_item<Ps, DLP, false>(g, ev, it, ws, T, lane), 0) : 0), ...);
+    ((p == Ps ? (laplace_fp64_item<Ps, DLP, false>(g, ev, it, ws, T, kTile, lane), 0) : 0), ...);
 }
 
 template <bool DLP, int... Ps>
 __device__ __forceinline__ void run_item_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
-                                               const WalkStart &ws, float4 (*T)[kMixedPairs], int lane,
+                                               const WalkStart &ws, float4 *T, int lane,
                                                std::integer_sequence<int, Ps...>)
 {
-    ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, ws, T, lane), 0) : 0), ...);
+    ((p == Ps ? (laplace_mixed_item<Ps, DLP, false>(g, ev, it, ws, T, kTile, lane), 0) : 0), ...);
 }
 
 template <int W, int... Ps>
@@ -95,8 +97,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, DLP ? 1 : 8)
 batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, const WalkStart *walks,
                      int64_t n_items, unsigned long long *head)
 {
-    // per-warp tile: mixed, pair records (laplace_items.cuh); FP64, one row per field
-    constexpr int kWarpBytes = MIXED ? mixed_tile_rows(DLP) * kMixedPairs * 16 : (DLP ? 7 : 4) * kTile * 8;
+    // per-warp tile at the default depth kTile (a batch stages every plan's
+    // sources alike): mixed, pair records (laplace_items.cuh); FP64, one row per field
+    constexpr int kWarpBytes = MIXED ? mixed_tile_rows(DLP) * (kTile / 2) * 16 : (DLP ? 7 : 4) * kTile * 8;
     __shared__ __align__(16) unsigned char tile_raw[kWarpsPerBlock * kWarpBytes];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
@@ -139,10 +142,10 @@ batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *item
             }
             unsigned char *mine = tile_raw + warp * kWarpBytes;
             if constexpr (MIXED)
-                run_item_mixed<DLP>(bp.p, bp.g, ev, it, ws, reinterpret_cast<float4 (*)[kMixedPairs]>(mine), lane,
+                run_item_mixed<DLP>(bp.p, bp.g, ev, it, ws, reinterpret_cast<float4 *>(mine), lane,
                                     std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
             else
-                run_item_fp64<DLP>(bp.p, bp.g, ev, it, ws, reinterpret_cast<double (*)[kTile]>(mine), lane,
+                run_item_fp64<DLP>(bp.p, bp.g, ev, it, ws, reinterpret_cast<double *>(mine), lane,
                                    std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
             __syncwarp();
         }
@@ -324,11 +327,15 @@ int tsqbx_batch_create(const tsqbx_plan *plans, int n_plans, int use_graph, tsqb
         B->d_status = B->dalloc<int>(1);
         ck(cudaMemset(B->d_status, 0, sizeof(int)));
         for (auto &p : bp) p.ev.status = B->d_status;
-        std::stable_sort(items.begin(), items.end(), [](const Entry &a, const Entry &b) {
-            return cost_bucket(a.cost) > cost_bucket(b.cost);
-        });
+        std::vector<int32_t> plan_of(items.size());
+        std::vector<double> cost(items.size());
+        for (size_t k = 0; k < items.size(); ++k) {
+            plan_of[k] = items[k].it.pad;
+            cost[k] = items[k].cost;
+        }
+        const std::vector<int64_t> order = batch_queue_order(plan_of, cost);
         std::vector<Item> item_v(items.size());
-        for (size_t k = 0; k < items.size(); ++k) item_v[k] = items[k].it;
+        for (size_t k = 0; k < items.size(); ++k) item_v[k] = items[(size_t)order[k]].it;
         B->n_items = (int64_t)item_v.size();
         B->n_combine = (int64_t)comb.size();
         B->d_plans = B->dalloc<BatchPlan>(n_plans);

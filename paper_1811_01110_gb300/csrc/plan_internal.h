@@ -75,6 +75,12 @@ int size_priority(int64_t n_pairs, const tsqbx_options &o);
 // (numerically greatest <= least): the pairs times a per-pair cost relative to
 // Laplace FP64, one level per decade above 1e5, clamped to the range.
 int priority_for_work(int64_t n_pairs, int kernel, int precision, int least, int greatest);
+// Queue order of a persistent batch over several plans (item i of plan
+// plan_of[i] with estimated cost cost[i]): plan by plan, the plans with the
+// most work first, each plan's items heaviest first.  Running one surface's
+// items together keeps its sources in L2; interleaving all surfaces by cost
+// alone swept every surface's sources through L2 in each cost bucket.
+std::vector<int64_t> batch_queue_order(const std::vector<int32_t> &plan_of, const std::vector<double> &cost);
 // Build the schedule; max_iters <= 0 picks the automatic cap.
 int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
                    int n_sm, Schedule &out);

@@ -139,4 +139,29 @@ int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64
     return TSQBX_OK;
 }
 
+std::vector<int64_t> batch_queue_order(const std::vector<int32_t> &plan_of, const std::vector<double> &cost)
+{
+    // plans with more work first (ties: the lower index), then each plan's
+    // items in their own schedule order: heaviest half-octave bucket first
+    int32_t n_plans = 0;
+    for (int32_t q : plan_of) n_plans = std::max(n_plans, q + 1);
+    std::vector<double> work((size_t)n_plans, 0.0);
+    for (size_t i = 0; i < plan_of.size(); ++i) work[(size_t)plan_of[i]] += cost[i];
+    std::vector<int32_t> rank((size_t)n_plans);
+    {
+        std::vector<int32_t> byw((size_t)n_plans);
+        for (int32_t q = 0; q < n_plans; ++q) byw[(size_t)q] = q;
+        std::stable_sort(byw.begin(), byw.end(), [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
+        for (int32_t r = 0; r < n_plans; ++r) rank[(size_t)byw[(size_t)r]] = r;
+    }
+    std::vector<int64_t> order(plan_of.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const int32_t ra = rank[(size_t)plan_of[(size_t)a]], rb = rank[(size_t)plan_of[(size_t)b]];
+        if (ra != rb) return ra < rb;
+        return cost_bucket(cost[(size_t)a]) > cost_bucket(cost[(size_t)b]);
+    });
+    return order;
+}
+
 }  // namespace tsqbx

@@ -24,6 +24,15 @@ __attribute__((visibility("default"))) int shim_conventional_cheaper(int64_t nt,
     return tsqbx::conventional_cheaper(nt, ns, p, layers, helmholtz != 0) ? 1 : 0;
 }
 
+// The batch queue order: order[k] = index of the k-th item.
+__attribute__((visibility("default"))) void shim_batch_queue_order(int64_t n, const int32_t *plan_of,
+                                                                    const double *cost, int64_t *order)
+{
+    const std::vector<int64_t> o = tsqbx::batch_queue_order(std::vector<int32_t>(plan_of, plan_of + n),
+                                                            std::vector<double>(cost, cost + n));
+    for (int64_t i = 0; i < n; ++i) order[i] = o[(size_t)i];
+}
+
 // Items as 8 int32 each {group, slot_begin, n_tgt, L, src_lo, src_hi, part, pad}
 // plus their costs; combine records as 4 int32 each {slot_begin, n_tgt, part, n_slices}.  With
 // items == NULL only the counts are returned.

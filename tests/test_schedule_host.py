@@ -8,7 +8,7 @@ test shim and checked without a GPU:
 * sliced lists get one combine record each, whose partial blocks are disjoint
   and cover [0, n_parts);
 * the queue runs in half-octave cost buckets, heaviest first, keeping list
-  order within a bucket;
+  order within a bucket; a persistent batch's queue runs plan by plan;
 * the size-priority levels: one per decade of work above 1e5 Laplace-FP64
   pair equivalents, smallest plans highest, clamped to the device's range;
 * the cost model's choice between the target-specific and the conventional
@@ -193,3 +193,32 @@ def test_size_priority_levels(shim):
     assert f(4 * 10 ** 6, lap, df64) == f(10 ** 6)
     # a device with a single priority puts everything at it
     assert shim.shim_priority_for_work(10 ** 9, lap, fp64, 0, 0) == 0
+
+
+def test_batch_queue_runs_plan_by_plan(shim):
+    """A persistent batch's queue: every item exactly once, the items of one
+    plan contiguous, the plans in decreasing total work, and each plan's items
+    in decreasing half-octave cost bucket, keeping their own order within a
+    bucket (a surface's sources stay in L2 while its items run)."""
+    L = shim
+    L.shim_batch_queue_order.argtypes = [ctypes.c_int64, i32p, f64p, i64p]
+    rng = np.random.default_rng(3)
+    n = 5000
+    plan_of = rng.integers(0, 13, n).astype(np.int32)
+    cost = rng.lognormal(3.0, 1.2, n)
+    order = np.zeros(n, np.int64)
+    L.shim_batch_queue_order(n, plan_of.ctypes.data_as(i32p), cost.ctypes.data_as(f64p), order.ctypes.data_as(i64p))
+    assert np.array_equal(np.sort(order), np.arange(n))
+    plans = plan_of[order]
+    runs = [plans[0]] + [b for a, b in zip(plans[:-1], plans[1:]) if a != b]
+    assert len(runs) == len(set(runs))                       # contiguous per plan
+    work = {q: cost[plan_of == q].sum() for q in set(runs)}
+    assert all(work[a] >= work[b] for a, b in zip(runs[:-1], runs[1:]))
+    bucket = lambda c: int(np.floor(2.0 * np.log2(c)))
+    for q in runs:
+        mine = order[plans == q]
+        b = [bucket(c) for c in cost[mine]]
+        assert all(x >= y for x, y in zip(b[:-1], b[1:]))
+        for k in set(b):                                     # stable within a bucket
+            same = mine[np.array(b) == k]
+            assert np.all(np.diff(same) > 0)
