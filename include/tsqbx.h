@@ -136,6 +136,9 @@ typedef struct {
                                    longer lists are cut into source slices whose
                                    partial sums are added in slice order; 0 = automatic
                                    (32..512, scaled to the problem and the SM count) */
+    int tile_depth;             /* sources a warp stages per shared-memory tile: 32, 64
+                                   or 128; 0 = 64.  Results agree across depths to
+                                   rounding (the order of the lanes' sums changes)     */
 } tsqbx_options;
 
 /* ------------------------------------------------------------ geometry */
@@ -273,8 +276,9 @@ TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
  * batches up to four single-target items of one plan share a warp (8 or 16
  * lanes each), so their lane sums are reduced in another order than the plan
  * alone reduces them: the two agree to rounding (within the mixed error bar),
- * not bit for bit.  Otherwise a batch reproduces each plan's results bit for
- * bit. */
+ * not bit for bit.  A batch stages sources at the default depth (64 per
+ * tile) whatever a plan's own tile_depth; otherwise it reproduces the results
+ * of each plan at that depth bit for bit. */
 typedef struct tsqbx_batch_s *tsqbx_batch;
 
 typedef struct {
@@ -366,19 +370,29 @@ TSQBX_API int tsqbx_server_reset_stats(tsqbx_server server);
  * lower median latency for mixes of small and large requests, at the cost of
  * the largest requests' latency.  Errors: TSQBX_E_INVAL. */
 TSQBX_API int tsqbx_server_set_size_priority(tsqbx_server server, int on);
+/* How the server evaluates Laplace requests that ask for TSQBX_FP64, for the
+ * requests submitted (and plans prepared) from now on: TSQBX_FP64 (the
+ * default) on the FP64 kernels, or TSQBX_DF64 on the double-float kernels,
+ * which meet the same FP64 bound (1e-12 relative) on the FP32 pipes at
+ * several times the speed on GPUs whose FP64 rate is a small fraction of
+ * their FP32 rate.  Such requests then share the DF64 plans of their
+ * geometry.  Errors: TSQBX_E_INVAL. */
+TSQBX_API int tsqbx_server_set_laplace_fp64_path(tsqbx_server server, int precision);
 
 /* ------------------------------------------------------------- tuning
  * Work decomposition of a plan: lanes per target (0 = chosen per group from
- * its target and source counts) and the cap on per-lane pair iterations of one
- * warp item (longer lists are cut into slices). */
+ * its target and source counts), the cap on per-lane pair iterations of one
+ * warp item (longer lists are cut into slices) and the staging depth (sources
+ * per shared-memory tile, as tsqbx_options.tile_depth). */
 typedef struct {
     int lanes_per_target;
     int max_item_iters;
     float kernel_ms;            /* autotune: measured expansion time of this choice */
+    int tile_depth;             /* 32, 64 or 128 (0 in tsqbx_plan_set_tuning: 64)   */
 } tsqbx_tuning;
 
 /* Autotuner: times candidate decompositions of this plan (slice caps, then
- * lane policies) with CUDA events on the plan's stream, evaluating the DEVICE
+ * lane policies, then tile depths) with CUDA events on the plan's stream, evaluating the DEVICE
  * density d_density `repeats` times each (after one untimed run), keeps the
  * fastest, records it in the process-wide tuning cache (see
  * TSQBX_FLAG_USE_TUNED) and returns it in *chosen (may be NULL).  Uses the

@@ -77,13 +77,13 @@ def marshal_geometry(g, with_normals=True, with_tgt_normals=False):
 
 
 def make_options(kernel="laplace", layers=("slp",), p=5, k=0.0, precision="fp64", device=0, flags=0,
-                 lanes_per_target=0, n_slots=2, max_item_iters=0):
+                 lanes_per_target=0, n_slots=2, max_item_iters=0, tile_depth=0):
     mask = 0
     for name in layers:
         mask |= _LAYERS[name]
     return _lib.tsqbx_options(_KERNELS[kernel], mask, int(p), float(k), _PRECISIONS[precision],
                               int(device), int(flags), int(lanes_per_target), int(n_slots),
-                              int(max_item_iters))
+                              int(max_item_iters), int(tile_depth))
 
 
 class Plan:
@@ -92,11 +92,12 @@ class Plan:
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
                  lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False,
-                 conventional="off", size_priority=False):
+                 conventional="off", size_priority=False, tile_depth=0):
         """conventional: "off" (target-specific expansions only), "auto"
         (conventional QBX for the centers the cost model finds cheaper) or
         "all" (conventional QBX for every center).  size_priority: stream
-        priority from the plan's work (TSQBX_FLAG_SIZE_PRIORITY)."""
+        priority from the plan's work (TSQBX_FLAG_SIZE_PRIORITY).  tile_depth:
+        sources staged per warp tile (32, 64 or 128; 0 = 64)."""
         self.kernel = kernel
         self.layers = tuple(layers)
         self.p = int(p)
@@ -112,7 +113,7 @@ class Plan:
                  "all": _lib.TSQBX_FLAG_CONVENTIONAL_ALL}[conventional] | \
                 (_lib.TSQBX_FLAG_SIZE_PRIORITY if size_priority else 0)
         opt = make_options(kernel, self.layers, self.p, k, precision, device, flags,
-                           lanes_per_target, n_slots, max_item_iters)
+                           lanes_per_target, n_slots, max_item_iters, tile_depth)
         h = ctypes.c_void_p()
         check(lib().tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)),
               "tsqbx_plan_create")
@@ -161,15 +162,16 @@ class Plan:
         check(lib().tsqbx_plan_autotune(self._h, self._density_addr(density), int(repeats),
                                         ctypes.byref(t)), "tsqbx_plan_autotune")
         return {"lanes_per_target": t.lanes_per_target, "max_item_iters": t.max_item_iters,
-                "kernel_ms": t.kernel_ms}
+                "tile_depth": t.tile_depth, "kernel_ms": t.kernel_ms}
 
     def get_tuning(self):
         t = _lib.tsqbx_tuning()
         check(lib().tsqbx_plan_get_tuning(self._h, ctypes.byref(t)), "tsqbx_plan_get_tuning")
-        return {"lanes_per_target": t.lanes_per_target, "max_item_iters": t.max_item_iters}
+        return {"lanes_per_target": t.lanes_per_target, "max_item_iters": t.max_item_iters,
+                "tile_depth": t.tile_depth}
 
-    def set_tuning(self, lanes_per_target=0, max_item_iters=0):
-        t = _lib.tsqbx_tuning(int(lanes_per_target), int(max_item_iters), 0.0)
+    def set_tuning(self, lanes_per_target=0, max_item_iters=0, tile_depth=0):
+        t = _lib.tsqbx_tuning(int(lanes_per_target), int(max_item_iters), 0.0, int(tile_depth))
         check(lib().tsqbx_plan_set_tuning(self._h, ctypes.byref(t)), "tsqbx_plan_set_tuning")
 
     # -- evaluation
@@ -305,9 +307,12 @@ class Server:
     """Request-serving runtime (tsqbx_server_*): register geometries, submit
     evaluations as they arrive, poll for completion, read p50/p99 latency."""
 
-    def __init__(self, device=0, hbm_budget=16 << 30, max_inflight=64, size_priority=False):
+    def __init__(self, device=0, hbm_budget=16 << 30, max_inflight=64, size_priority=False,
+                 laplace_fp64_path="fp64"):
         """size_priority: build plans whose streams are prioritised by size
-        (tsqbx_server_set_size_priority): short evaluations overtake long ones."""
+        (tsqbx_server_set_size_priority): short evaluations overtake long ones.
+        laplace_fp64_path: "fp64" or "df64", the kernels that serve Laplace
+        requests asking for FP64 (tsqbx_server_set_laplace_fp64_path)."""
         h = ctypes.c_void_p()
         check(lib().tsqbx_server_create(int(device), int(hbm_budget), int(max_inflight), ctypes.byref(h)),
               "tsqbx_server_create")
@@ -316,6 +321,9 @@ class Server:
         self._pending = {}
         if size_priority:
             check(lib().tsqbx_server_set_size_priority(self._h, 1), "tsqbx_server_set_size_priority")
+        if laplace_fp64_path != "fp64":
+            check(lib().tsqbx_server_set_laplace_fp64_path(self._h, _PRECISIONS[laplace_fp64_path]),
+                  "tsqbx_server_set_laplace_fp64_path")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

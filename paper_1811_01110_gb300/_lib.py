@@ -45,7 +45,7 @@ class tsqbx_options(ctypes.Structure):
         ("kernel", ctypes.c_int), ("layers", ctypes.c_uint32), ("p", ctypes.c_int),
         ("k", ctypes.c_double), ("precision", ctypes.c_int), ("device", ctypes.c_int),
         ("flags", ctypes.c_uint32), ("lanes_per_target", ctypes.c_int), ("n_slots", ctypes.c_int),
-        ("max_item_iters", ctypes.c_int),
+        ("max_item_iters", ctypes.c_int), ("tile_depth", ctypes.c_int),
     ]
 
 
@@ -99,7 +99,7 @@ class tsqbx_pipe_peaks(ctypes.Structure):
 
 class tsqbx_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_target", ctypes.c_int), ("max_item_iters", ctypes.c_int),
-                ("kernel_ms", ctypes.c_float)]
+                ("kernel_ms", ctypes.c_float), ("tile_depth", ctypes.c_int)]
 
 
 # (name, restype, argtypes) for every entry point declared in include/tsqbx.h
@@ -152,6 +152,7 @@ _SIGNATURES = [
     ("tsqbx_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tsqbx_server_stats)]),
     ("tsqbx_server_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
     ("tsqbx_server_set_size_priority", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("tsqbx_server_set_laplace_fp64_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("tsqbx_eval_noalloc", ctypes.c_int,
      [ctypes.POINTER(tsqbx_geometry), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

@@ -10,6 +10,11 @@
 namespace tsqbx {
 namespace {
 
+// Rows of the warp's staging tile: x, y, z, Re and Im of w mu, and for the
+// double layer the normal's three components; each row holds DevGeom::tile
+// sources.
+__host__ __device__ constexpr int helmholtz_tile_rows(bool dlp) { return dlp ? 8 : 5; }
+
 // Per-target radial factors, orders 0..P (z = k rho):
 //   cj[n]  = (2n+1) kappa_n j_n(z)
 //   caj[n] = (2n+1) kappa_n k j_n'(z) (that.n_t)        (S' only)
@@ -81,8 +86,9 @@ template <int P, bool DLP, bool SP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 helmholtz_kernel(const DevGeom g, const DevEval ev)
 {
-    constexpr int kRows = DLP ? 8 : 5;
-    __shared__ double tile[kWarpsPerBlock][kRows][kTile];
+    constexpr int kRows = helmholtz_tile_rows(DLP);
+    extern __shared__ __align__(16) double smem_helm[];
+    const int tile = g.tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
@@ -116,28 +122,29 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
     }
     ListWalk walk(g, g.item_walk[item]);
     const int src_hi = it.src_hi;
-    double (*T)[kTile] = tile[warp];
+    double *const Tbase = smem_helm + (size_t)warp * kRows * tile;
+    auto T = [&](int row) { return Tbase + row * tile; };
     double acc_re = 0.0, acc_im = 0.0, dacc_re = 0.0, dacc_im = 0.0, pacc_re = 0.0, pacc_im = 0.0;
 
-    for (int base = it.src_lo; base < src_hi; base += kTile) {
-        const int cnt = min(kTile, src_hi - base);
+    for (int base = it.src_lo; base < src_hi; base += tile) {
+        const int cnt = min(tile, src_hi - base);
         for (int kk = lane; kk < cnt; kk += 32) {
             int s = walk.at(base + kk);
             double2 wm = make_double2(0.0, 0.0);
             if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
             else wm = ev.wmu_c[s];
             const double4_32a pw = g.src_pw[s];
-            T[0][kk] = pw.x; T[1][kk] = pw.y; T[2][kk] = pw.z;
-            T[3][kk] = wm.x; T[4][kk] = wm.y;
+            T(0)[kk] = pw.x; T(1)[kk] = pw.y; T(2)[kk] = pw.z;
+            T(3)[kk] = wm.x; T(4)[kk] = wm.y;
             if (DLP) {
                 const double4_32a n = g.src_n[s];
-                T[kRows - 3][kk] = n.x; T[kRows - 2][kk] = n.y; T[kRows - 1][kk] = n.z;
+                T(kRows - 3)[kk] = n.x; T(kRows - 2)[kk] = n.y; T(kRows - 1)[kk] = n.z;
             }
         }
         __syncwarp();
         if (active) {
             for (int kk = sub; kk < cnt; kk += L) {
-                const double dx = T[0][kk] - cx, dy = T[1][kk] - cy, dz = T[2][kk] - cz;
+                const double dx = T(0)[kk] - cx, dy = T(1)[kk] - cy, dz = T(2)[kk] - cz;
                 const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
                 const double rinv = rsqrt(R2);
                 const double x = fma(dx, ex, fma(dy, ey, dz * ez)) * rinv * rhoinv;
@@ -159,7 +166,7 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
                 double kah = 0.0, u = 0.0, Cr = 0.0, Cl = 0.0;
                 if (DLP) {
                     // n_s.grad_s: R' = a/R, x' = (1/R) ((e.n_s)/rho - (a/R) x), a = d.n_s
-                    const double nx = T[kRows - 3][kk], ny = T[kRows - 2][kk], nz = T[kRows - 1][kk];
+                    const double nx = T(kRows - 3)[kk], ny = T(kRows - 2)[kk], nz = T(kRows - 1)[kk];
                     const double ah = fma(dx, nx, fma(dy, ny, dz * nz)) * rinv;
                     u = (fma(ex, nx, fma(ey, ny, ez * nz)) * rhoinv - ah * x) * rinv;
                     kah = k * ah;
@@ -214,7 +221,7 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
                 close(cj[0], bA1, bA2, Ar, Ai);
                 double sn, cs;
                 sincos(z, &sn, &cs);
-                const double wr = T[3][kk], wi = T[4][kk];
+                const double wr = T(3)[kk], wi = T(4)[kk];
                 // out += ik e^{iz} (X) (w mu):  with v = e^{iz} X, ik v = (-k v_i, k v_r)
                 auto accumulate = [&](double Xr, double Xi, double &or_, double &oi) {
                     const double vr = fma(cs, Xr, -sn * Xi), vi = fma(sn, Xr, cs * Xi);
@@ -274,8 +281,10 @@ int launch_helm_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
-    if (dlp) helmholtz_kernel<P, true, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
-    else     helmholtz_kernel<P, false, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
+    const size_t smem = (size_t)kWarpsPerBlock * helmholtz_tile_rows(dlp) * g.tile * sizeof(double);
+    if (dlp) helmholtz_kernel<P, true, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
+    else     helmholtz_kernel<P, false, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
     return (int)cudaGetLastError();
 }
 

@@ -24,7 +24,14 @@ struct __align__(16) Combine {
 };
 
 constexpr int kWarpsPerBlock = 4;   // independent warps per CTA
-constexpr int kTile = 64;           // sources staged per warp per tile
+// Sources staged per warp per shared-memory tile: kTile by default; a plan's
+// tuning may choose any power of two in [kTileMin, kTileMax] (DevGeom::tile).
+constexpr int kTile = 64;
+constexpr int kTileMin = 32, kTileMax = 128;
+__host__ __device__ constexpr bool tile_depth_ok(int t)
+{
+    return t == 32 || t == 64 || t == 128;
+}
 constexpr double kInv4Pi = 0.0795774715459476678844418816862571810;  // 1/(4 pi)
 
 // Conventional-path records.  A center on the conventional path owns the
@@ -52,6 +59,7 @@ struct __align__(16) WalkStart {
 // Everything a kernel needs about a plan's geometry (device pointers).
 struct DevGeom {
     int64_t n_src = 0, n_tgt = 0, n_items = 0, n_combine = 0, n_parts = 0;
+    int32_t tile = kTile;               // staging depth of the one-plan kernels (tile_depth_ok)
     const Item *items = nullptr;
     const Combine *combine = nullptr;
     // Each group's source list as merged runs of consecutive sources: run r
@@ -70,16 +78,16 @@ struct DevGeom {
     // mixed-precision source records: coordinates as float-float pairs
     const float4 *src_hi = nullptr;     // {xh, yh, zh, 0}
     const float4 *src_lo = nullptr;     // {xl, yl, zl, 0}
-    const float4 *src_nf = nullptr;     // {nx, ny, nz, 0}
+    const float4 *src_nf = nullptr;     // {-nx, -ny, -nz, 0}: the negated normal
     // target slots, in item order
     const int32_t *slot_tgt = nullptr;  // output index of the slot's target
     const double4_32a *slot_c = nullptr;    // {cx, cy, cz, 0}
     const double4_32a *slot_e = nullptr;    // {ex, ey, ez, rho^2},  e = t - c
     const float4 *slot_chi = nullptr;   // float-float center
     const float4 *slot_clo = nullptr;
-    const float4 *slot_ef = nullptr;    // {ex, ey, ez, rho^2} rounded to FP32
+    const float4 *slot_ef = nullptr;    // {ex, ey, ez, -rho^2} rounded to FP32
     const double4_32a *slot_n = nullptr;    // target normal {nx, ny, nz, 0} (S')
-    const float4 *slot_nf = nullptr;    // target normal rounded to FP32 (mixed S')
+    const float4 *slot_nf = nullptr;    // {n_t, -e.n_t} rounded to FP32 (mixed S')
     // conventional path
     int64_t n_conv_centers = 0, n_conv_items = 0, n_conv_eval = 0;
     const ConvCenter *conv_centers = nullptr;

@@ -106,9 +106,12 @@ __device__ __forceinline__ void df_target_normal(const DevGeom &g, int slot, con
     en = df_from_double(fma(e4.x, n.x, fma(e4.y, n.y, e4.z * n.z)));
 }
 
+// T: the warp's staging tile, rows of `tile` records: {x, y, z, w mu} hi and
+// lo parts relative to the item's reference point and, for the double layer,
+// the normal's hi and lo parts.
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                const WalkStart &ws, float4 (*T)[kTile], const int lane)
+                                                const WalkStart &ws, float4 *T, const int tile, const int lane)
 {
     ListWalk walk(g, ws);
     const int src_hi = it.src_hi;
@@ -158,8 +161,9 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
         rho2 = df_from_double(e4.w);
         if (SP) df_target_normal(g, it.slot_begin + j, e4, tn, ent);
     }
-    for (int base = it.src_lo; base < src_hi; base += kTile) {
-        const int cnt = min(kTile, src_hi - base);
+    float4 *const T0 = T, *const T1 = T + tile, *const T2 = T + 2 * tile, *const T3 = T + 3 * tile;
+    for (int base = it.src_lo; base < src_hi; base += tile) {
+        const int cnt = min(tile, src_hi - base);
         for (int k = lane; k < cnt; k += 32) {
             int s = walk.at(base + k);
             double wmd = 0.0;
@@ -168,24 +172,24 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
             const double4_32a pw = g.src_pw[s];
             const df3 r = df3_from(pw.x - ref.x, pw.y - ref.y, pw.z - ref.z);
             const df w = df_from_double(wmd);
-            T[0][k] = make_float4(r.x.hi, r.y.hi, r.z.hi, w.hi);
-            T[1][k] = make_float4(r.x.lo, r.y.lo, r.z.lo, w.lo);
+            T0[k] = make_float4(r.x.hi, r.y.hi, r.z.hi, w.hi);
+            T1[k] = make_float4(r.x.lo, r.y.lo, r.z.lo, w.lo);
             if (DLP) {
                 const double4_32a nn = g.src_n[s];
                 const df3 n = df3_from(nn.x, nn.y, nn.z);
-                T[2][k] = make_float4(n.x.hi, n.y.hi, n.z.hi, 0.f);
-                T[3][k] = make_float4(n.x.lo, n.y.lo, n.z.lo, 0.f);
+                T2[k] = make_float4(n.x.hi, n.y.hi, n.z.hi, 0.f);
+                T3[k] = make_float4(n.x.lo, n.y.lo, n.z.lo, 0.f);
             }
         }
         __syncwarp();
         if (active) {
             for (int k = sub; k < cnt; k += L) {
-                const float4 a = T[0][k], b = T[1][k];
+                const float4 a = T0[k], b = T1[k];
                 const df3 d{df_sub(df{a.x, b.x}, crel.x), df_sub(df{a.y, b.y}, crel.y),
                             df_sub(df{a.z, b.z}, crel.z)};
                 df3 n = zero3;
                 if (DLP) {
-                    const float4 c = T[2][k], h = T[3][k];
+                    const float4 c = T2[k], h = T3[k];
                     n = df3{{c.x, h.x}, {c.y, h.y}, {c.z, h.z}};
                 }
                 pair_df<P, DLP, SP>(d, e, rho2, df{a.w, b.w}, n, tn, ent, acc_s, acc_d, acc_p);
@@ -207,11 +211,12 @@ template <int P, bool DLP, bool SP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 laplace_df_kernel(const DevGeom g, const DevEval ev)
 {
-    __shared__ float4 tile[kWarpsPerBlock][DLP ? 4 : 2][kTile];
+    extern __shared__ __align__(16) float4 smem_df[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
-    laplace_df_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], tile[warp], lane);
+    float4 *T = smem_df + (size_t)warp * (DLP ? 4 : 2) * g.tile;
+    laplace_df_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], T, g.tile, lane);
 }
 
 template <bool SP, int P>
@@ -219,8 +224,10 @@ int launch_df_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
-    if (dlp) laplace_df_kernel<P, true, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
-    else     laplace_df_kernel<P, false, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
+    const size_t smem = (size_t)kWarpsPerBlock * (dlp ? 4 : 2) * g.tile * sizeof(float4);
+    if (dlp) laplace_df_kernel<P, true, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
+    else     laplace_df_kernel<P, false, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
     return (int)cudaGetLastError();
 }
 

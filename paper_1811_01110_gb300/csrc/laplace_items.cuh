@@ -126,9 +126,12 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// T: the warp's staging tile, rows of `tile` doubles (x, y, z, w mu and, for
+// the double layer, the normal's three components); tile is the staging depth
+// (kTileMin..kTileMax sources per tile).
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                  const WalkStart &ws, double (*T)[kTile], const int lane)
+                                                  const WalkStart &ws, double *T, const int tile, const int lane)
 {
     ListWalk walk(g, ws);
     const int src_hi = it.src_hi;
@@ -175,25 +178,27 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
             ent = fma(ex, tx, fma(ey, ty, ez * tz));                      // e.n_t
         }
     }
-    for (int base = it.src_lo; base < src_hi; base += kTile) {
-        const int cnt = min(kTile, src_hi - base);
+    double *const Tx = T, *const Ty = T + tile, *const Tz = T + 2 * tile, *const Tw = T + 3 * tile;
+    double *const Nx = T + 4 * tile, *const Ny = T + 5 * tile, *const Nz = T + 6 * tile;   // DLP only
+    for (int base = it.src_lo; base < src_hi; base += tile) {
+        const int cnt = min(tile, src_hi - base);
         for (int k = lane; k < cnt; k += 32) {
             int s = walk.at(base + k);
             double wm = 0.0;
             if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
             else wm = ev.wmu[s];
             const double4_32a pw = g.src_pw[s];
-            T[0][k] = pw.x; T[1][k] = pw.y; T[2][k] = pw.z; T[3][k] = wm;
+            Tx[k] = pw.x; Ty[k] = pw.y; Tz[k] = pw.z; Tw[k] = wm;
             if (DLP) {
                 const double4_32a n = g.src_n[s];
-                T[4][k] = n.x; T[5][k] = n.y; T[6][k] = n.z;
+                Nx[k] = n.x; Ny[k] = n.y; Nz[k] = n.z;
             }
         }
         __syncwarp();
         if (active) {
             for (int k = sub; k < cnt; k += L)
-                pair_fp64<P, DLP, SP>(T[0][k] - cx, T[1][k] - cy, T[2][k] - cz, ex, ey, ez, rho2, T[3][k],
-                                      DLP ? T[4][k] : 0.0, DLP ? T[5][k] : 0.0, DLP ? T[6][k] : 0.0,
+                pair_fp64<P, DLP, SP>(Tx[k] - cx, Ty[k] - cy, Tz[k] - cz, ex, ey, ez, rho2, Tw[k],
+                                      DLP ? Nx[k] : 0.0, DLP ? Ny[k] : 0.0, DLP ? Nz[k] : 0.0,
                                       tx, ty, tz, ent, acc_s, acc_d, acc_p);
         }
         __syncwarp();
@@ -207,25 +212,36 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
 // Two (target, source) pairs at once in mixed precision, every FP32 operation
 // packed (f32x2.cuh): the recurrences and closing sums of pair_fp64 in FP32,
 // for the sources in the two halves, with s - c formed as (s_hi - c_hi) +
-// (s_lo - c_lo) from float-float coordinates.  hx.. = source hi coordinates, w = w mu, lx.. = lo parts,
-// nx.. = n_s; ch/cl = center hi/lo, e = {t - c, rho^2}, tn = {n_t, e.n_t}
-// (per target, both halves equal); one sum per layer, per half, added with
-// sum_add2 (KAHAN: compensated per pair; else plain, the caller compensating
-// per tile).
+// (s_lo - c_lo) from float-float coordinates.  hx.. = source hi coordinates,
+// w = w mu, lx.. = lo parts, mx.. = -n_s (the plan stores the source normals
+// negated); ch/cl = center hi/lo, e = {t - c, -rho^2}, tn = {n_t, -e.n_t}
+// (per target, both halves equal); one sum per layer, per half (KAHAN:
+// compensated per pair; else a plain fused multiply-add, the caller
+// compensating per tile).
+//
+// Operation count (p = 9, both layers, per pair): float-float difference 9,
+// R^2 3, 1/R (rsqrtf) and 1/R^2 with one Newton step 4, qx, -q2 and w/R 6,
+// the Q' recurrence 4 per order from n = 2 (its n = 1 step is U_2 = qx,
+// S2m = 1 exactly) and 3 at n = 2, its top 5, the closing sums 4, the double
+// layer 11 with its sum, the single layer's sum 1.  Negated operands (-q2,
+// -n_s, -e.n_t) are prepared outside the pair loop; only -R^2 costs an
+// operation.
 
-// Adds x to the packed sum s: Kahan-compensated (c the compensation) or plain.
+// Adds w * x to the packed sum s: Kahan-compensated (c the compensation) or
+// a plain fused multiply-add.
 template <bool KAHAN>
-__device__ __forceinline__ void sum_add2(f2 &s, f2 &c, f2 x)
+__device__ __forceinline__ void sum_fma2(f2 &s, f2 &c, f2 w, f2 x)
 {
-    if constexpr (KAHAN) kahan_add2(s, c, x);
-    else s = add2(s, x);
+    if constexpr (KAHAN) kahan_add2(s, c, mul2(w, x));
+    else s = fma2(w, x, s);
 }
 
 template <int P, bool DLP, bool SP, bool KAHAN = true>
-__device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2 ly, f2 lz, f2 nx, f2 ny, f2 nz,
+__device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2 ly, f2 lz, f2 mx, f2 my, f2 mz,
                                             const float4 &ch, const float4 &cl, const float4 &e,
                                             const float4 &tn, f2 &as, f2 &ac, f2 &ds, f2 &dc, f2 &ps, f2 &pc)
 {
+    const f2 one = f2_splat(1.f);
     const f2 dx = add2(sub2(hx, f2_splat(ch.x)), sub2(lx, f2_splat(cl.x)));
     const f2 dy = add2(sub2(hy, f2_splat(ch.y)), sub2(ly, f2_splat(cl.y)));
     const f2 dz = add2(sub2(hz, f2_splat(ch.z)), sub2(lz, f2_splat(cl.z)));
@@ -233,49 +249,68 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
     float r0, r1;
     f2_split(R2, r0, r1);
     const f2 rinv = f2_make(rsqrtf(r0), rsqrtf(r1));
-    const f2 r2inv = mul2(rinv, rinv);
+    f2 r2inv = mul2(rinv, rinv);
+    if constexpr (DLP || SP) {
+        // one Newton step for 1/R^2: x <- x + x (1 - R^2 x).  rsqrtf's error
+        // (up to ~2 ulp) doubles in rinv^2 and, through qx and q2, grows with
+        // the order in the Q' recurrence; the refined 1/R^2 is within about
+        // an ulp, which halves the worst double-layer and S' errors
+        const f2 ee = fma2(mul2(f2_splat(-1.f), R2), r2inv, f2_splat(1.f));
+        r2inv = fma2(r2inv, ee, r2inv);
+    }
     const f2 qx = mul2(fma2(dx, f2_splat(e.x), fma2(dy, f2_splat(e.y), mul2(dz, f2_splat(e.z)))), r2inv);
-    const f2 q2 = mul2(f2_splat(e.w), r2inv);
+    const f2 nq2 = mul2(f2_splat(e.w), r2inv);                       // -q2
     const f2 wr = mul2(w, rinv);
     if constexpr (!DLP && !SP) {
-        f2 b1 = P >= 1 ? fma2(qx, f2_splat((float)rec_kappa(P)), f2_splat((float)rec_kappa(P - 1))) : f2_splat(1.f);
+        // Clenshaw: b_k = kappa_k + qx b_{k+1} - beta_{k+1} q2 b_{k+2}
+        f2 b1 = P >= 1 ? fma2(qx, f2_splat((float)rec_kappa(P)), f2_splat((float)rec_kappa(P - 1))) : one;
         f2 b2 = f2_splat((float)rec_kappa(P));
 #pragma unroll
         for (int k = P - 2; k >= 0; --k) {
-            const f2 bq = mul2(f2_splat(-(float)rec_beta(k + 1)), q2);
+            const f2 bq = mul2(f2_splat((float)rec_beta(k + 1)), nq2);
             const f2 bk = fma2(bq, b2, fma2(qx, b1, f2_splat((float)rec_kappa(k))));
             b2 = b1; b1 = bk;
         }
-        sum_add2<KAHAN>(as, ac, mul2(wr, b1));
+        sum_fma2<KAHAN>(as, ac, wr, b1);
     } else {
-        f2 Um = f2_splat(0.f), Uc = f2_splat(1.f), S2m = f2_splat(0.f);
+        // U_{n-1}, U_n and S2m = sum_{m<n} Q'_m after the step of order n - 1:
+        // at n = 2 (P >= 2) U_1 = 1, U_2 = qx (gamma_1 = 0), S2m = lambda_1 U_1 = 1
+        f2 Um, Uc, S2m;
+        if (P >= 2) { Um = one; Uc = qx; S2m = one; }
+        else { Um = f2_splat(0.f); Uc = one; S2m = f2_splat(0.f); }
 #pragma unroll
-        for (int n = 1; n < P; ++n) {
+        for (int n = 2; n < P; ++n) {
             S2m = fma2(f2_splat((float)rec_lambda(n)), Uc, S2m);
-            const f2 gq = mul2(f2_splat(-(float)rec_gamma(n)), q2);
-            const f2 Un = fma2(gq, Um, mul2(qx, Uc));
+            const f2 gq = mul2(f2_splat((float)rec_gamma(n)), nq2);          // -gamma_n q2
+            const f2 Un = n == 2 ? fma2(qx, Uc, gq) : fma2(gq, Um, mul2(qx, Uc));   // U_1 = 1 at n = 2
             Um = Uc; Uc = Un;
         }
-        f2 Qp = f2_splat(0.f), Qp1 = f2_splat(1.f);
+        // Uc = U_P, Um = U_{P-1} (P >= 1);  P = 0: Q'_0 = 0, Q'_1 = 1
+        f2 Qp = f2_splat(0.f), Qp1 = one;
         if (P >= 1) {
             Qp = mul2(f2_splat((float)rec_lambda(P)), Uc);
-            const f2 gq = mul2(f2_splat(-(float)rec_gamma(P)), q2);
+            const f2 gq = mul2(f2_splat((float)rec_gamma(P)), nq2);
             Qp1 = mul2(f2_splat((float)rec_lambda(P + 1)), fma2(gq, Um, mul2(qx, Uc)));
         }
-        const f2 S2 = add2(S2m, Qp);
-        const f2 c1 = add2(fma2(f2_splat(-2.f), qx, f2_splat(1.f)), q2);
-        const f2 S = fma2(c1, S2, fma2(sub2(f2_splat(0.f), q2), Qp, Qp1));
-        sum_add2<KAHAN>(as, ac, mul2(wr, S));
+        // S = (1 - 2 qx + q2) S2 + Q'_{p+1} - q2 Q'_p with S2 = S2m + Q'_p:
+        //   = (1 - 2 qx + q2) S2m + (1 - 2 qx) Q'_p + Q'_{p+1}
+        const f2 u = fma2(f2_splat(-2.f), qx, one);
+        const f2 c1 = sub2(u, nq2);
+        const f2 S = fma2(c1, S2m, fma2(u, Qp, Qp1));
+        sum_fma2<KAHAN>(as, ac, wr, S);
         const f2 wr3 = mul2(wr, r2inv);
+        const f2 S2 = add2(S2m, Qp);
         if (DLP) {
-            const f2 a = fma2(dx, nx, fma2(dy, ny, mul2(dz, nz)));
-            const f2 b = fma2(f2_splat(e.x), nx, fma2(f2_splat(e.y), ny, mul2(f2_splat(e.z), nz)));
-            const f2 na = sub2(f2_splat(0.f), a);
-            sum_add2<KAHAN>(ds, dc, mul2(wr3, fma2(na, Qp1, mul2(sub2(b, a), S2))));
+            // (b - a) S2 - a Q'_{p+1} with a = d.n_s, b = e.n_s, from the
+            // negated normal: a' = -a, b' = -b give (a' - b') S2 + a' Q'_{p+1}
+            const f2 am = fma2(dx, mx, fma2(dy, my, mul2(dz, mz)));
+            const f2 bm = fma2(f2_splat(e.x), mx, fma2(f2_splat(e.y), my, mul2(f2_splat(e.z), mz)));
+            sum_fma2<KAHAN>(ds, dc, wr3, fma2(am, Qp1, mul2(sub2(am, bm), S2)));
         }
         if (SP) {
+            // (d.n_t) S2 - (e.n_t) S2m, tn.w = -e.n_t
             const f2 dn = fma2(dx, f2_splat(tn.x), fma2(dy, f2_splat(tn.y), mul2(dz, f2_splat(tn.z))));
-            sum_add2<KAHAN>(ps, pc, mul2(wr3, fma2(dn, S2, mul2(f2_splat(-tn.w), S2m))));
+            sum_fma2<KAHAN>(ps, pc, wr3, fma2(dn, S2, mul2(f2_splat(tn.w), S2m)));
         }
     }
 }
@@ -316,11 +351,15 @@ __device__ __forceinline__ df segment_sum_df(df v, int sub, int L)
 }
 
 // Shared-memory tile of the mixed item, two sources per record (pair j holds
-// sources 2j and 2j+1 of the tile): {hx0, hx1, hy0, hy1}, {hz0, hz1, w0, w1},
-// {lx0, lx1, ly0, ly1}, {lz0, lz1, nx0, nx1} and, for the double layer,
-// {ny0, ny1, nz0, nz1}.  One 16-byte load gives two packed operands.
-constexpr int kMixedPairs = kTile / 2;
+// sources 2j and 2j+1 of the tile): rows {hx0, hx1, hy0, hy1}, {hz0, hz1, w0,
+// w1}, {lx0, lx1, ly0, ly1}, {lz0, lz1, mx0, mx1} and, for the double layer,
+// {my0, my1, mz0, mz1} (m = -n_s), each row tile / 2 records long.  One
+// 16-byte load gives two packed operands.
 __host__ __device__ constexpr int mixed_tile_rows(bool dlp) { return dlp ? 5 : 4; }
+// Longest run of source pairs a lane sums in plain FP32 before adding the run
+// to its compensated sums: the rounding error of a plain run grows with its
+// length, so deeper tiles do not lengthen it.
+constexpr int kPlainRun = 16;
 
 // Load the list positions k0 and k1 (k1 < 0: a zero-weight copy of k0) of a
 // group's list as packed operands; k0 < k1, neither before the walk's last call.
@@ -376,7 +415,7 @@ __device__ __forceinline__ void laplace_mixed_part_item(const DevGeom &g, const 
 
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEval &ev, const Item &it,
-                                                   const WalkStart &ws, float4 (*T)[kMixedPairs], const int lane)
+                                                   const WalkStart &ws, float4 *T, const int tile, const int lane)
 {
     ListWalk walk(g, ws);
     const int src_hi = it.src_hi;
@@ -387,11 +426,7 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         const float4 ch = g.slot_chi[it.slot_begin];
         const float4 cl = g.slot_clo[it.slot_begin];
         const float4 e = g.slot_ef[it.slot_begin];
-        float4 tn = zero;
-        if (SP) {
-            tn = g.slot_nf[it.slot_begin];
-            tn.w = fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));    // e.n_t
-        }
+        const float4 tn = SP ? g.slot_nf[it.slot_begin] : zero;
         for (int k = it.src_lo + lane; k < src_hi; k += 64) {
             f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
             load_mixed_pair<DLP>(g, ev, walk, k, k + 32 < src_hi ? k + 32 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
@@ -412,41 +447,45 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         ch = g.slot_chi[it.slot_begin + j];
         cl = g.slot_clo[it.slot_begin + j];
         e = g.slot_ef[it.slot_begin + j];
-        if (SP) {
-            tn = g.slot_nf[it.slot_begin + j];
-            tn.w = fmaf(e.x, tn.x, fmaf(e.y, tn.y, e.z * tn.z));    // e.n_t
-        }
+        if (SP) tn = g.slot_nf[it.slot_begin + j];
     }
-    for (int base = it.src_lo; base < src_hi; base += kTile) {
-        const int cnt = min(kTile, src_hi - base);
+    const int tp = tile >> 1;                          // records (source pairs) per row
+    float4 *const T0 = T, *const T1 = T + tp, *const T2 = T + 2 * tp, *const T3 = T + 3 * tp;
+    float4 *const T4 = T + 4 * tp;                     // DLP only
+    for (int base = it.src_lo; base < src_hi; base += tile) {
+        const int cnt = min(tile, src_hi - base);
         const int npairs = (cnt + 1) >> 1;
-        if (lane < npairs) {                           // lane stages pair `lane`
-            const int k0 = base + 2 * lane;
+        for (int q = lane; q < npairs; q += 32) {      // lane stages pairs lane, lane + 32, ...
+            const int k0 = base + 2 * q;
             f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
-            load_mixed_pair<DLP>(g, ev, walk, k0, 2 * lane + 1 < cnt ? k0 + 1 : -1, hx, hy, hz, w, lx, ly, lz, nx,
+            load_mixed_pair<DLP>(g, ev, walk, k0, 2 * q + 1 < cnt ? k0 + 1 : -1, hx, hy, hz, w, lx, ly, lz, nx,
                                  ny, nz);
             float a0, a1, b0, b1;
-            f2_split(hx, a0, a1); f2_split(hy, b0, b1); T[0][lane] = make_float4(a0, a1, b0, b1);
-            f2_split(hz, a0, a1); f2_split(w, b0, b1);  T[1][lane] = make_float4(a0, a1, b0, b1);
-            f2_split(lx, a0, a1); f2_split(ly, b0, b1); T[2][lane] = make_float4(a0, a1, b0, b1);
-            f2_split(lz, a0, a1); f2_split(nx, b0, b1); T[3][lane] = make_float4(a0, a1, b0, b1);
-            if (DLP) { f2_split(ny, a0, a1); f2_split(nz, b0, b1); T[4][lane] = make_float4(a0, a1, b0, b1); }
+            f2_split(hx, a0, a1); f2_split(hy, b0, b1); T0[q] = make_float4(a0, a1, b0, b1);
+            f2_split(hz, a0, a1); f2_split(w, b0, b1);  T1[q] = make_float4(a0, a1, b0, b1);
+            f2_split(lx, a0, a1); f2_split(ly, b0, b1); T2[q] = make_float4(a0, a1, b0, b1);
+            f2_split(lz, a0, a1); f2_split(nx, b0, b1); T3[q] = make_float4(a0, a1, b0, b1);
+            if (DLP) { f2_split(ny, a0, a1); f2_split(nz, b0, b1); T4[q] = make_float4(a0, a1, b0, b1); }
         }
         __syncwarp();
         if (active) {
-            // plain FP32 sums over the tile (at most 32 source pairs per lane),
-            // added to the compensated sums once per tile
-            f2 ts = z2, td = z2, tp = z2, unused = z2;
-            for (int q = sub; q < npairs; q += L) {
-                const float4 A = T[0][q], B = T[1][q], C = T[2][q], D = T[3][q];
-                const float4 E = DLP ? T[4][q] : zero;
-                pair_mixed2<P, DLP, SP, false>(f2_xy(A), f2_zw(A), f2_xy(B), f2_zw(B), f2_xy(C), f2_zw(C),
-                                               f2_xy(D), f2_zw(D), f2_xy(E), f2_zw(E), ch, cl, e, tn, ts, unused,
-                                               td, unused, tp, unused);
+            // plain FP32 sums over runs of at most kPlainRun source pairs per
+            // lane, each run added to the compensated sums (at the default
+            // depth and L >= 2, one run per tile)
+            for (int q0 = sub; q0 < npairs; q0 += kPlainRun * L) {
+                const int q1 = min(npairs, q0 + kPlainRun * L);
+                f2 ts = z2, td = z2, tp2 = z2, unused = z2;
+                for (int q = q0; q < q1; q += L) {
+                    const float4 A = T0[q], B = T1[q], C = T2[q], D = T3[q];
+                    const float4 E = DLP ? T4[q] : zero;
+                    pair_mixed2<P, DLP, SP, false>(f2_xy(A), f2_zw(A), f2_xy(B), f2_zw(B), f2_xy(C), f2_zw(C),
+                                                   f2_xy(D), f2_zw(D), f2_xy(E), f2_zw(E), ch, cl, e, tn, ts,
+                                                   unused, td, unused, tp2, unused);
+                }
+                kahan_add2(as, ac, ts);
+                if (DLP) kahan_add2(ds, dc, td);
+                if (SP) kahan_add2(ps, pc, tp2);
             }
-            kahan_add2(as, ac, ts);
-            if (DLP) kahan_add2(ds, dc, td);
-            if (SP) kahan_add2(ps, pc, tp);
         }
         __syncwarp();
     }

@@ -13,33 +13,47 @@
 namespace tsqbx {
 namespace {
 
+// Rows of a warp's staging tile (elements of `tile` sources each) and the
+// dynamic shared memory of one CTA at staging depth `tile`.
+template <bool MIXED, bool DLP>
+__host__ __device__ constexpr int tile_rows() { return MIXED ? mixed_tile_rows(DLP) : (DLP ? 7 : 4); }
+template <bool MIXED, bool DLP>
+inline size_t tile_smem_bytes(int tile)
+{
+    // FP64: doubles per source; mixed: one 16-byte record per two sources
+    return (size_t)kWarpsPerBlock * tile_rows<MIXED, DLP>() * (size_t)(MIXED ? (tile / 2) * 16 : tile * 8);
+}
+
 template <int P, bool DLP, bool SP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 laplace_fp64_kernel(const DevGeom g, const DevEval ev)
 {
-    __shared__ double tile[kWarpsPerBlock][DLP ? 7 : 4][kTile];
+    extern __shared__ __align__(16) double smem_fp64[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;                       // whole warp leaves together
-    laplace_fp64_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], tile[warp], lane);
+    double *T = smem_fp64 + (size_t)warp * tile_rows<false, DLP>() * g.tile;
+    laplace_fp64_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], T, g.tile, lane);
 }
 
 template <int P, bool DLP, bool SP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 laplace_mixed_kernel(const DevGeom g, const DevEval ev)
 {
-    __shared__ float4 tile[kWarpsPerBlock][mixed_tile_rows(DLP)][kMixedPairs];
+    extern __shared__ __align__(16) float4 smem_mixed[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
-    laplace_mixed_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], tile[warp], lane);
+    float4 *T = smem_mixed + (size_t)warp * tile_rows<true, DLP>() * (g.tile / 2);
+    laplace_mixed_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], T, g.tile, lane);
 }
 
 template <bool MIXED, int P, bool DLP, bool SP>
 void launch_one(unsigned blocks, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
-    if constexpr (MIXED) laplace_mixed_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
-    else                 laplace_fp64_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(g, e);
+    const size_t smem = tile_smem_bytes<MIXED, DLP>(g.tile);
+    if constexpr (MIXED) laplace_mixed_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
+    else                 laplace_fp64_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
 }
 
 template <bool MIXED, bool SP, int P>
@@ -47,6 +61,7 @@ int launch_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
+    if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
     if (dlp) launch_one<MIXED, P, true, SP>((unsigned)blocks, g, e, s);
     else     launch_one<MIXED, P, false, SP>((unsigned)blocks, g, e, s);
     return (int)cudaGetLastError();

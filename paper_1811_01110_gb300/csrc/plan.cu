@@ -168,7 +168,7 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
     if (o->precision != TSQBX_FP64 && o->precision != TSQBX_MIXED && o->precision != TSQBX_DF64)
         return TSQBX_E_INVAL;
     if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64 ||
-        o->max_item_iters < 0)
+        o->max_item_iters < 0 || (o->tile_depth != 0 && !tsqbx::tile_depth_ok(o->tile_depth)))
         return TSQBX_E_INVAL;
     if (o->kernel == TSQBX_HELMHOLTZ) {
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
@@ -366,7 +366,7 @@ tsqbx_plan_s::~tsqbx_plan_s()
 
 extern "C" {
 
-int tsqbx_version(void) { return 10100; }
+int tsqbx_version(void) { return 10200; }
 
 const char *tsqbx_last_error(void) { return t_last_error; }
 
@@ -539,13 +539,17 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
                 for (int a = 0; a < 3; ++a) split_ff(cc[a], h[a], l[a]);
                 slot_chi[i] = make_float4(h[0], h[1], h[2], 0.f);
                 slot_clo[i] = make_float4(l[0], l[1], l[2], 0.f);
-                slot_ef[i] = make_float4((float)e[0], (float)e[1], (float)e[2], (float)rho2);
+                // -rho^2: the mixed kernels form -q2 directly (no sign operation per pair)
+                slot_ef[i] = make_float4((float)e[0], (float)e[1], (float)e[2], (float)-rho2);
             }
             if (sp) {
                 double nt[3];
                 for (int a = 0; a < 3; ++a) nt[a] = G->tgt_normal[a * n_tgt + t];
                 slot_n[i] = make_double4_32a(nt[0], nt[1], nt[2], 0.0);
-                if (mixed) slot_nf[i] = make_float4((float)nt[0], (float)nt[1], (float)nt[2], 0.f);
+                // the mixed S' kernels take -e.n_t, formed here in FP64
+                if (mixed)
+                    slot_nf[i] = make_float4((float)nt[0], (float)nt[1], (float)nt[2],
+                                             (float)-(e[0] * nt[0] + e[1] * nt[1] + e[2] * nt[2]));
             }
         }
         // source records
@@ -560,7 +564,8 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
                 const double nx = G->src_normal[s], ny = G->src_normal[n_src + s],
                              nz = G->src_normal[2 * n_src + s];
                 src_n[s] = make_double4_32a(nx, ny, nz, 0.0);
-                if (mixed) src_nf[s] = make_float4((float)nx, (float)ny, (float)nz, 0.f);
+                // negated: the mixed double layer is formed from a' = -d.n_s, b' = -e.n_s
+                if (mixed) src_nf[s] = make_float4((float)-nx, (float)-ny, (float)-nz, 0.f);
             }
             if (mixed) {
                 float h[3], l[3];
@@ -633,14 +638,17 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         // work schedule: options, else a cached tuning, else automatic
         int lanes = o->lanes_per_target;
         int64_t max_iters = o->max_item_iters;
-        if ((o->flags & TSQBX_FLAG_USE_TUNED) && !lanes && !max_iters) {
+        int tile = o->tile_depth ? o->tile_depth : kTile;
+        if ((o->flags & TSQBX_FLAG_USE_TUNED) && !lanes && !max_iters && !o->tile_depth) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(tune_key(P));
             if (it != g_tune_cache.end()) {
                 lanes = it->second.lanes_per_target;
                 max_iters = it->second.max_item_iters;
+                tile = it->second.tile_depth;
             }
         }
+        P->g.tile = tile;
         Schedule sched;
         if ((rc = build_schedule(P->groups, lanes, max_iters, P->n_sm, sched)) != TSQBX_OK) {
             delete P;
@@ -757,12 +765,14 @@ int tsqbx_plan_get_tuning(tsqbx_plan P, tsqbx_tuning *t)
     t->lanes_per_target = P->sched.lanes_policy;
     t->max_item_iters = (int)P->sched.max_iters;
     t->kernel_ms = 0.f;
+    t->tile_depth = P->g.tile;
     return TSQBX_OK;
 }
 
 int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
 {
-    if (!P || !t || t->lanes_per_target < 0 || t->lanes_per_target > 32 || t->max_item_iters < 0)
+    if (!P || !t || t->lanes_per_target < 0 || t->lanes_per_target > 32 || t->max_item_iters < 0 ||
+        (t->tile_depth != 0 && !tile_depth_ok(t->tile_depth)))
         return TSQBX_E_INVAL;
     try {
         DeviceGuard dg(P->opt.device);
@@ -772,6 +782,7 @@ int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
         int rc = build_schedule(P->groups, t->lanes_per_target, t->max_item_iters, P->n_sm, sched);
         if (rc) return rc;
         apply_schedule(P, std::move(sched));
+        P->g.tile = t->tile_depth ? t->tile_depth : kTile;
         return TSQBX_OK;
     } catch (const CudaFail &f) {
         cudaGetLastError();
@@ -805,31 +816,36 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
             median_ms = acc[reps / 2];
             return TSQBX_OK;
         };
-        struct Cand { int lanes; int64_t iters; float ms; };
-        Cand best{P->sched.lanes_policy, P->sched.max_iters, 0.f};
+        struct Cand { int lanes; int64_t iters; int tile; float ms; };
+        Cand best{P->sched.lanes_policy, P->sched.max_iters, P->g.tile, 0.f};
         int rc = time_current(best.ms);
         if (rc) return rc;
-        auto trial = [&](int lanes, int64_t iters) -> int {
+        auto trial = [&](int lanes, int64_t iters, int tile) -> int {
             Schedule sched;
             int r = build_schedule(P->groups, lanes, iters, P->n_sm, sched);
             if (r) return r;
             apply_schedule(P, std::move(sched));
+            P->g.tile = tile;
             float ms = 0.f;
             if ((r = time_current(ms)) != TSQBX_OK) return r;
-            if (ms < best.ms) best = {lanes, P->sched.max_iters, ms};
+            if (ms < best.ms) best = {lanes, P->sched.max_iters, tile, ms};
             return TSQBX_OK;
         };
-        // stage 1: slice caps with the current lane policy; stage 2: lane
-        // policies at the best cap
+        // stage 1: slice caps with the current lane policy and depth; stage 2:
+        // lane policies at the best cap; stage 3: tile depths at both
         for (int64_t iters : {64, 128, 256, 512, 1024, 2048})
-            if ((rc = trial(best.lanes, iters)) != TSQBX_OK) return rc;
+            if ((rc = trial(best.lanes, iters, best.tile)) != TSQBX_OK) return rc;
         const int64_t cap = best.iters;
         for (int lanes : {0, 1, 2, 4, 8, 16})
-            if ((rc = trial(lanes, cap)) != TSQBX_OK) return rc;
+            if ((rc = trial(lanes, cap, best.tile)) != TSQBX_OK) return rc;
+        const int lanes_best = best.lanes;
+        for (int tile : {kTileMin, kTile, kTileMax})
+            if ((rc = trial(lanes_best, cap, tile)) != TSQBX_OK) return rc;
         Schedule sched;
         if ((rc = build_schedule(P->groups, best.lanes, best.iters, P->n_sm, sched)) != TSQBX_OK) return rc;
         apply_schedule(P, std::move(sched));
-        tsqbx_tuning t{best.lanes, (int)best.iters, best.ms};
+        P->g.tile = best.tile;
+        tsqbx_tuning t{best.lanes, (int)best.iters, best.ms, best.tile};
         {
             std::lock_guard<std::mutex> tl(g_tune_mu);
             g_tune_cache[tune_key(P)] = t;

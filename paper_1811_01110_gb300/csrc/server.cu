@@ -91,6 +91,7 @@ struct tsqbx_server_s {
     int device = 0;
     size_t budget = 0;
     bool size_priority = false;              // plans built with TSQBX_FLAG_SIZE_PRIORITY
+    bool laplace_fp64_as_df64 = false;       // Laplace FP64 requests served by DF64 plans
     int max_inflight = 64;
     std::mutex mu;
     std::condition_variable cv;
@@ -325,8 +326,10 @@ int tsqbx_server_submit(tsqbx_server S, int geom_id, const tsqbx_options *opt, c
         r->geom = geom_id;
         r->opt = *opt;
         if (S->size_priority) r->opt.flags |= TSQBX_FLAG_SIZE_PRIORITY;
+        if (S->laplace_fp64_as_df64 && r->opt.kernel == TSQBX_LAPLACE && r->opt.precision == TSQBX_FP64)
+            r->opt.precision = TSQBX_DF64;
         r->opt.device = S->device;
-        r->key = PlanKey{geom_id, (int)opt->kernel, opt->layers, (int)opt->precision};
+        r->key = PlanKey{geom_id, (int)r->opt.kernel, r->opt.layers, (int)r->opt.precision};
         const double *d = static_cast<const double *>(density);
         if (d) r->density.assign(d, d + g.view.n_src * width);
         r->out_slp = out_slp;
@@ -412,6 +415,14 @@ int tsqbx_server_set_size_priority(tsqbx_server S, int on)
     return TSQBX_OK;
 }
 
+int tsqbx_server_set_laplace_fp64_path(tsqbx_server S, int precision)
+{
+    if (!S || (precision != TSQBX_FP64 && precision != TSQBX_DF64)) return TSQBX_E_INVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->laplace_fp64_as_df64 = precision == TSQBX_DF64;
+    return TSQBX_OK;
+}
+
 int tsqbx_server_prepare(tsqbx_server S, int geom_id, const tsqbx_options *opt)
 {
     if (!S || !opt) return TSQBX_E_INVAL;
@@ -419,6 +430,8 @@ int tsqbx_server_prepare(tsqbx_server S, int geom_id, const tsqbx_options *opt)
     if (geom_id < 0 || geom_id >= (int)S->geoms.size()) return TSQBX_E_INVAL;
     tsqbx_options o = *opt;
     if (S->size_priority) o.flags |= TSQBX_FLAG_SIZE_PRIORITY;
+    if (S->laplace_fp64_as_df64 && o.kernel == TSQBX_LAPLACE && o.precision == TSQBX_FP64)
+        o.precision = TSQBX_DF64;
     o.device = S->device;
     const PlanKey key{geom_id, (int)o.kernel, o.layers, (int)o.precision};
     auto it = S->plans.find(key);

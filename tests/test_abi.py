@@ -100,6 +100,8 @@ def test_more_invalid_options_rejected_on_host(L):
     assert _create(g, kernel="helmholtz", k=float("inf")) == -1
     assert _create(g, kernel="helmholtz", k=float("nan")) == -1
     assert _create(g, kernel="helmholtz", k=-1.0) == -1
+    for depth in (-64, 16, 48, 96, 256):                  # staging depth: 0, 32, 64 or 128
+        assert _create(g, tile_depth=depth) == -1
 
 
 def test_invalid_options_rejected_on_host(L):

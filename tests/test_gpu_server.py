@@ -169,3 +169,37 @@ def test_size_priority_server_matches_fifo_server(pkg):
     for a, b in zip(*results):
         for layer in ("slp", "dlp"):
             assert np.array_equal(a[layer], b[layer])
+
+
+def test_laplace_fp64_requests_on_the_double_float_path(pkg):
+    """With the server's Laplace FP64 path set to double-float, FP64 requests
+    run on DF64 plans: bit-identical to a DF64 plan evaluated alone, within
+    the FP64 bar (1e-12) of the oracle; mixed and Helmholtz requests are
+    unaffected."""
+    geoms = _geoms()
+    rng = np.random.default_rng(89)
+    reqs = []
+    with pkg.Server(hbm_budget=8 << 30, max_inflight=8, laplace_fp64_path="df64") as srv:
+        gids = [srv.add_geometry(g) for g in geoms]
+        for i in range(12):
+            gi = i % len(geoms)
+            kernel, layers, prec, k = KINDS[i % len(KINDS)]
+            g = geoms[gi]
+            mu = rng.standard_normal(g.n_src)
+            if kernel == "helmholtz":
+                mu = mu + 1j * rng.standard_normal(g.n_src)
+            rid, outs = srv.submit(gids[gi], mu, kernel, layers, 9, k, prec)
+            reqs.append((rid, outs, gi, kernel, layers, k, prec, mu))
+        for rid, *_ in reqs:
+            assert srv.poll(rid, timeout_us=-1)
+    for rid, outs, gi, kernel, layers, k, prec, mu in reqs:
+        g = geoms[gi]
+        run_as = "df64" if (kernel == "laplace" and prec == "fp64") else prec
+        with pkg.Plan(g, kernel, layers, p=9, k=k, precision=run_as) as alone:
+            ref = alone.eval(mu)
+        for l in layers:
+            assert np.array_equal(outs[l], ref[l]), (kernel, prec, l)
+        if kernel == "laplace" and prec == "fp64":
+            ora = oracle.tsqbx_laplace(g, 9, mu, slp=True, dlp="dlp" in layers)
+            for l in layers:
+                assert np.max(np.abs(outs[l] - ora[l])) / np.max(np.abs(ora[l])) <= 1e-12

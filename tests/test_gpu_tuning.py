@@ -33,15 +33,17 @@ def test_autotune_keeps_results_and_caches(env, precision, tol):
         t = plan.autotune(torch.from_numpy(mu).cuda(), repeats=3)
         assert t["max_item_iters"] in (64, 128, 256, 512, 1024, 2048) or t["max_item_iters"] > 0
         assert t["lanes_per_target"] in (0, 1, 2, 4, 8, 16)
+        assert t["tile_depth"] in (32, 64, 128)
         assert t["kernel_ms"] > 0
         assert plan.get_tuning()["max_item_iters"] == t["max_item_iters"]
+        assert plan.get_tuning()["tile_depth"] == t["tile_depth"]
         out = plan.eval(mu)
         for l in ("slp", "dlp"):
             assert relerr(out[l], ref[l]) <= tol
     # a new plan with the same shape starts from the cached choice
     with pkg.Plan(g, "laplace", ("slp", "dlp"), p=7, precision=precision, use_tuned=True) as plan2:
         assert plan2.get_tuning() == {"lanes_per_target": t["lanes_per_target"],
-                                      "max_item_iters": t["max_item_iters"]}
+                                      "max_item_iters": t["max_item_iters"], "tile_depth": t["tile_depth"]}
 
 
 def test_set_tuning_roundtrip(env):
@@ -51,9 +53,37 @@ def test_set_tuning_roundtrip(env):
     mu = rng.standard_normal(g.n_src)
     ref = oracle.tsqbx_laplace(g, 5, mu)["slp"]
     with pkg.Plan(g, "laplace", ("slp",), p=5) as plan:
-        for lanes, iters in ((1, 3), (4, 50), (0, 1), (32, 1000)):
-            plan.set_tuning(lanes, iters)
-            assert plan.get_tuning() == {"lanes_per_target": lanes, "max_item_iters": iters}
+        for lanes, iters, depth in ((1, 3, 32), (4, 50, 128), (0, 1, 0), (32, 1000, 64)):
+            plan.set_tuning(lanes, iters, depth)
+            assert plan.get_tuning() == {"lanes_per_target": lanes, "max_item_iters": iters,
+                                         "tile_depth": depth or 64}
             assert relerr(plan.eval(mu)["slp"], ref) <= 1e-12
         info = plan.info()
         assert info["launches_per_eval"] in (2, 3)
+
+
+@pytest.mark.parametrize("depth", [32, 64, 128])
+@pytest.mark.parametrize("kernel,precision,tol", [("laplace", "fp64", 1e-12), ("laplace", "mixed", 1e-6),
+                                                  ("laplace", "df64", 1e-12), ("helmholtz", "fp64", 1e-12)])
+def test_every_tile_depth_matches_the_oracle(env, depth, kernel, precision, tol):
+    """Each staging depth (sources per shared-memory tile) over lists that are
+    not multiples of it (ragged last tiles), several lane counts per target,
+    and every layer, against the oracle."""
+    torch, pkg = env
+    rng = np.random.default_rng(47 + depth)
+    g = cloud_geometry(rng, n_ctr=8, n_src=700, q_max=0.5, tgt_per_ctr=11, list_frac=0.43)
+    layers = ("slp", "dlp", "sp")
+    if kernel == "helmholtz":
+        mu = rng.standard_normal(g.n_src) + 1j * rng.standard_normal(g.n_src)
+        ref = oracle.tsqbx_helmholtz(g, 8, 3.0, mu, slp=True, dlp=True, sp=True)
+        kw = {"k": 3.0}
+    else:
+        mu = rng.standard_normal(g.n_src)
+        ref = oracle.tsqbx_laplace(g, 8, mu, slp=True, dlp=True, sp=True)
+        kw = {"precision": precision}
+    for lanes in (0, 3, 8):
+        with pkg.Plan(g, kernel, layers, p=8, tile_depth=depth, lanes_per_target=lanes, **kw) as plan:
+            assert plan.get_tuning()["tile_depth"] == depth
+            out = plan.eval(mu)
+        for l in layers:
+            assert relerr(out[l], ref[l]) <= tol, (l, lanes, relerr(out[l], ref[l]))

@@ -26,6 +26,14 @@ def test_server_argument_checks(pkg):
     assert L.tsqbx_server_create(-1, 1 << 20, 4, ctypes.byref(h)) == -1
     assert L.tsqbx_server_poll(None, ctypes.c_uint64(1), 0) == -1
     assert L.tsqbx_server_set_size_priority(None, 1) == -1
+    assert L.tsqbx_server_set_laplace_fp64_path(None, 2) == -1
+    assert L.tsqbx_server_create(0, 1 << 20, 4, ctypes.byref(h)) == 0   # worker thread only, no CUDA yet
+    try:
+        assert L.tsqbx_server_set_laplace_fp64_path(h, 1) == -1          # mixed is not an FP64 path
+        assert L.tsqbx_server_set_laplace_fp64_path(h, 2) == 0
+        assert L.tsqbx_server_set_laplace_fp64_path(h, 0) == 0
+    finally:
+        L.tsqbx_server_destroy(h)
 
 
 def test_request_failure_is_reported_without_gpu(pkg):
