@@ -790,6 +790,7 @@ def leg_serving(pkg, duration_s=10.0, rate=200.0, seed=20191114, size_priority=F
         return {"offered_req_per_s": rate_hz, "requests": n, "submit_s": t_submit,
                 "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
                 "completed": st["completed"], "failed": st["failed"], "rejected": st["rejected"],
+                "merged": st["merged"],
                 "peak_queued": int(peak_queued), "peak_running": int(peak_running),
                 "achieved_req_per_s": st["completed"] / max(st["span_s"], 1e-9),
                 "pair_terms_per_s": st["pair_terms_completed"] / max(st["span_s"], 1e-9),

@@ -139,6 +139,10 @@ typedef struct {
     int tile_depth;             /* sources a warp stages per shared-memory tile: 32, 64
                                    or 128; 0 = 64.  Results agree across depths to
                                    rounding (the order of the lanes' sums changes)     */
+    int max_rhs;                /* densities one tsqbx_submit_multi may carry, 1..4;
+                                   0 = 1.  Above 1 only for Helmholtz single-layer
+                                   plans (else TSQBX_E_UNSUPPORTED); each slot then
+                                   holds scratch for that many densities            */
 } tsqbx_options;
 
 /* ------------------------------------------------------------ geometry */
@@ -249,6 +253,22 @@ TSQBX_API int tsqbx_eval_async_pk(tsqbx_plan plan, int p, double k, const void *
 TSQBX_API int tsqbx_submit(tsqbx_plan plan, const void *density, void *out_slp, void *out_dlp,
                  uint64_t *ticket);
 
+/* Several densities in one evaluation: the single layer of a Helmholtz plan
+ * (layers == TSQBX_SLP, created with max_rhs >= n; no conventional centers)
+ * for the n densities density[0..n), with order p and wavenumber k as in
+ * tsqbx_submit_pk.  The per-pair work of Appendix A's expansion -- geometry,
+ * the Legendre and Hankel recurrences, e^{ikR}, the sums over the orders --
+ * depends on the geometry, p and k only, so the densities share it and each
+ * adds only its own complex weight: n densities cost little more than one.
+ * Result i (out_slp[i], layout as tsqbx_submit) is bit-identical to the
+ * evaluation of density[i] alone.  Pointers host or device as for
+ * tsqbx_submit; one ticket covers all n results (tsqbx_poll).  Errors:
+ * TSQBX_E_INVAL (n outside 1..max_rhs, NULL pointers, p or k),
+ * TSQBX_E_UNSUPPORTED (not a Helmholtz single-layer plan, or one with
+ * conventional centers), TSQBX_E_BUSY, TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_submit_multi(tsqbx_plan plan, int p, double k, int n, const void *const *density,
+                                 void *const *out_slp, uint64_t *ticket);
+
 /* Wait up to timeout_us microseconds (0: just test, < 0: wait indefinitely)
  * for a ticket.  Returns TSQBX_OK once (the ticket is then retired),
  * TSQBX_PENDING if timeout_us == 0 and work is in flight, TSQBX_E_TIMEOUT if
@@ -321,8 +341,11 @@ TSQBX_API int tsqbx_batch_info(tsqbx_batch batch, tsqbx_batch_stats *stats);
  * the resident plans fit the HBM budget (idle plans are evicted least recently
  * used).  Started requests run on their own plan slots and streams, so work
  * that arrives while other requests are on the GPU overlaps with them
- * (continuous batching).  A worker thread owned by the server does the
- * admission and completion bookkeeping. */
+ * (continuous batching).  Queued Helmholtz single-layer requests with the same
+ * geometry, order and wavenumber are started together, up to four, as one
+ * multi-density evaluation (tsqbx_submit_multi): each result is bit-identical
+ * to the request evaluated alone.  A worker thread owned by the server does
+ * the admission and completion bookkeeping. */
 typedef struct tsqbx_server_s *tsqbx_server;
 
 typedef struct {
@@ -333,6 +356,8 @@ typedef struct {
     size_t resident_bytes;
     int64_t pair_terms_completed;
     double span_s;                           /* first arrival to last completion */
+    int64_t merged;                          /* requests that ran inside another queued
+                                                request's multi-density evaluation  */
 } tsqbx_server_stats;
 
 /* hbm_budget_bytes: cap on the device memory of resident plans; max_inflight:

@@ -77,13 +77,13 @@ def marshal_geometry(g, with_normals=True, with_tgt_normals=False):
 
 
 def make_options(kernel="laplace", layers=("slp",), p=5, k=0.0, precision="fp64", device=0, flags=0,
-                 lanes_per_target=0, n_slots=2, max_item_iters=0, tile_depth=0):
+                 lanes_per_target=0, n_slots=2, max_item_iters=0, tile_depth=0, max_rhs=0):
     mask = 0
     for name in layers:
         mask |= _LAYERS[name]
     return _lib.tsqbx_options(_KERNELS[kernel], mask, int(p), float(k), _PRECISIONS[precision],
                               int(device), int(flags), int(lanes_per_target), int(n_slots),
-                              int(max_item_iters), int(tile_depth))
+                              int(max_item_iters), int(tile_depth), int(max_rhs))
 
 
 class Plan:
@@ -92,12 +92,13 @@ class Plan:
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
                  lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False,
-                 conventional="off", size_priority=False, tile_depth=0):
+                 conventional="off", size_priority=False, tile_depth=0, max_rhs=0):
         """conventional: "off" (target-specific expansions only), "auto"
         (conventional QBX for the centers the cost model finds cheaper) or
         "all" (conventional QBX for every center).  size_priority: stream
         priority from the plan's work (TSQBX_FLAG_SIZE_PRIORITY).  tile_depth:
-        sources staged per warp tile (32, 64 or 128; 0 = 64)."""
+        sources staged per warp tile (32, 64 or 128; 0 = 64).  max_rhs:
+        densities one submit_multi may carry (Helmholtz single layer)."""
         self.kernel = kernel
         self.layers = tuple(layers)
         self.p = int(p)
@@ -113,7 +114,7 @@ class Plan:
                  "all": _lib.TSQBX_FLAG_CONVENTIONAL_ALL}[conventional] | \
                 (_lib.TSQBX_FLAG_SIZE_PRIORITY if size_priority else 0)
         opt = make_options(kernel, self.layers, self.p, k, precision, device, flags,
-                           lanes_per_target, n_slots, max_item_iters, tile_depth)
+                           lanes_per_target, n_slots, max_item_iters, tile_depth, max_rhs)
         h = ctypes.c_void_p()
         check(lib().tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)),
               "tsqbx_plan_create")
@@ -248,6 +249,39 @@ class Plan:
                                         a_sp, ctypes.byref(t)), "tsqbx_submit_pk")
         self._inflight = getattr(self, "_inflight", {})
         self._inflight[t.value] = (outs, getattr(self, "_keep_density", None))
+        return t.value, outs
+
+
+    def submit_multi(self, densities, p=None, k=None, outs=None):
+        """tsqbx_submit_multi: the single layer for several densities in one
+        evaluation (Helmholtz single-layer plans created with max_rhs);
+        returns (ticket, [{"slp": out} per density]), valid once poll()
+        returns True."""
+        n = len(densities)
+        cw = np.complex128
+        keep = []
+        d_addr = (ctypes.c_void_p * n)()
+        o_addr = (ctypes.c_void_p * n)()
+        if outs is None:
+            outs = []
+            for d in densities:
+                if _is_torch(d) and d.is_cuda:
+                    import torch
+                    outs.append({"slp": torch.empty(self.n_tgt, dtype=torch.complex128, device=d.device)})
+                else:
+                    outs.append({"slp": np.empty(self.n_tgt, dtype=cw)})
+        for i, d in enumerate(densities):
+            if not _is_torch(d):
+                d = np.ascontiguousarray(d, dtype=cw)
+            keep.append(d)
+            d_addr[i] = _addr(d, self.n_src * 16, "density").value
+            o_addr[i] = _addr(outs[i]["slp"], self.n_tgt * 16, "out_slp").value
+        t = ctypes.c_uint64()
+        pp = self.p if p is None else int(p)
+        kk = self.k if k is None else float(k)
+        check(lib().tsqbx_submit_multi(self._h, pp, kk, n, d_addr, o_addr, ctypes.byref(t)), "tsqbx_submit_multi")
+        self._inflight = getattr(self, "_inflight", {})
+        self._inflight[t.value] = (outs, keep)
         return t.value, outs
 
 

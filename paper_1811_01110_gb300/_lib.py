@@ -45,7 +45,7 @@ class tsqbx_options(ctypes.Structure):
         ("kernel", ctypes.c_int), ("layers", ctypes.c_uint32), ("p", ctypes.c_int),
         ("k", ctypes.c_double), ("precision", ctypes.c_int), ("device", ctypes.c_int),
         ("flags", ctypes.c_uint32), ("lanes_per_target", ctypes.c_int), ("n_slots", ctypes.c_int),
-        ("max_item_iters", ctypes.c_int), ("tile_depth", ctypes.c_int),
+        ("max_item_iters", ctypes.c_int), ("tile_depth", ctypes.c_int), ("max_rhs", ctypes.c_int),
     ]
 
 
@@ -77,7 +77,7 @@ class tsqbx_server_stats(ctypes.Structure):
         ("rejected", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
         ("plans_resident", ctypes.c_int64), ("plans_created", ctypes.c_int64),
         ("plans_evicted", ctypes.c_int64), ("resident_bytes", ctypes.c_size_t),
-        ("pair_terms_completed", ctypes.c_int64), ("span_s", ctypes.c_double),
+        ("pair_terms_completed", ctypes.c_int64), ("span_s", ctypes.c_double), ("merged", ctypes.c_int64),
     ]
 
 
@@ -119,6 +119,9 @@ _SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
       ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_poll", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int]),
+    ("tsqbx_submit_multi", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint64)]),
     ("tsqbx_eval_pk", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
       ctypes.c_void_p]),

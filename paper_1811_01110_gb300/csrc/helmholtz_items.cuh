@@ -10,10 +10,13 @@
 namespace tsqbx {
 namespace {
 
-// Rows of the warp's staging tile: x, y, z, Re and Im of w mu, and for the
-// double layer the normal's three components; each row holds DevGeom::tile
-// sources.
-__host__ __device__ constexpr int helmholtz_tile_rows(bool dlp) { return dlp ? 8 : 5; }
+// Rows of the warp's staging tile: x, y, z, Re and Im of w mu (of each of the
+// nrhs densities), and for the double layer the normal's three components;
+// each row holds DevGeom::tile sources.
+__host__ __device__ constexpr int helmholtz_tile_rows(bool dlp, int nrhs = 1)
+{
+    return dlp ? 8 : 3 + 2 * nrhs;
+}
 
 // Per-target radial factors, orders 0..P (z = k rho):
 //   cj[n]  = (2n+1) kappa_n j_n(z)
@@ -82,11 +85,16 @@ __device__ __forceinline__ void cfma(double c, double gr, double gi, double &ar,
     ai = fma(c, gi, ai);
 }
 
-template <int P, bool DLP, bool SP>
+// NRHS > 1 (single layer only): the densities ev.n_rhs = NRHS share every
+// per-pair quantity -- geometry, recurrences, e^{ikR} and the Clenshaw sum --
+// and differ only in the final weight, applied with the same operations as
+// for one density, so each result is bit-identical to its own evaluation.
+template <int P, bool DLP, bool SP, int NRHS = 1>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 helmholtz_kernel(const DevGeom g, const DevEval ev)
 {
-    constexpr int kRows = helmholtz_tile_rows(DLP);
+    static_assert(NRHS == 1 || (!DLP && !SP), "several densities: single layer only");
+    constexpr int kRows = helmholtz_tile_rows(DLP, NRHS);
     extern __shared__ __align__(16) double smem_helm[];
     const int tile = g.tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -125,17 +133,26 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
     double *const Tbase = smem_helm + (size_t)warp * kRows * tile;
     auto T = [&](int row) { return Tbase + row * tile; };
     double acc_re = 0.0, acc_im = 0.0, dacc_re = 0.0, dacc_im = 0.0, pacc_re = 0.0, pacc_im = 0.0;
+    double xacc_re[NRHS > 1 ? NRHS - 1 : 1], xacc_im[NRHS > 1 ? NRHS - 1 : 1];   // densities 1..NRHS-1
+#pragma unroll
+    for (int r = 0; r < (NRHS > 1 ? NRHS - 1 : 1); ++r) xacc_re[r] = xacc_im[r] = 0.0;
 
     for (int base = it.src_lo; base < src_hi; base += tile) {
         const int cnt = min(tile, src_hi - base);
         for (int kk = lane; kk < cnt; kk += 32) {
             int s = walk.at(base + kk);
             double2 wm = make_double2(0.0, 0.0);
-            if ((unsigned)s >= (unsigned)g.n_src) { atomicOr(ev.status, 1); s = 0; }
+            const bool in_range = (unsigned)s < (unsigned)g.n_src;
+            if (!in_range) { atomicOr(ev.status, 1); s = 0; }
             else wm = ev.wmu_c[s];
             const double4_32a pw = g.src_pw[s];
             T(0)[kk] = pw.x; T(1)[kk] = pw.y; T(2)[kk] = pw.z;
             T(3)[kk] = wm.x; T(4)[kk] = wm.y;
+#pragma unroll
+            for (int r = 1; r < NRHS; ++r) {
+                const double2 wr = in_range ? ev.wmu_c[r * ev.rhs_src_stride + s] : make_double2(0.0, 0.0);
+                T(3 + 2 * r)[kk] = wr.x; T(4 + 2 * r)[kk] = wr.y;
+            }
             if (DLP) {
                 const double4_32a n = g.src_n[s];
                 T(kRows - 3)[kk] = n.x; T(kRows - 2)[kk] = n.y; T(kRows - 1)[kk] = n.z;
@@ -230,6 +247,17 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
                     oi = fma(ur, wi, fma(ui, wr, oi));
                 };
                 accumulate(Ar, Ai, acc_re, acc_im);
+                if constexpr (NRHS > 1) {
+                    // the other densities: the same operations with their own weights
+                    const double vr = fma(cs, Ar, -sn * Ai), vi = fma(sn, Ar, cs * Ai);
+                    const double ur = -k * vi, ui = k * vr;
+#pragma unroll
+                    for (int r = 1; r < NRHS; ++r) {
+                        const double w2r = T(3 + 2 * r)[kk], w2i = T(4 + 2 * r)[kk];
+                        xacc_re[r - 1] = fma(ur, w2r, fma(-ui, w2i, xacc_re[r - 1]));
+                        xacc_im[r - 1] = fma(ur, w2i, fma(ui, w2r, xacc_im[r - 1]));
+                    }
+                }
                 if (DLP) {
                     double Dr, Di;
                     close(kah * fma(-w, cj[0], a_next), bD1, bD2, Dr, Di);     // a_next = a_1 (0 if P = 0)
@@ -256,6 +284,12 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
             dacc_re += dr; dacc_im += di;
             pacc_re += pr; pacc_im += pi;
         }
+#pragma unroll
+        for (int r = 0; r < NRHS - 1; ++r) {
+            const double xr = __shfl_down_sync(0xffffffffu, xacc_re[r], off);
+            const double xi = __shfl_down_sync(0xffffffffu, xacc_im[r], off);
+            if (sub + off < L) { xacc_re[r] += xr; xacc_im[r] += xi; }
+        }
     }
     if (active && sub == 0) {
         auto put = [&](double *out, double *part, double re, double im) {
@@ -273,6 +307,10 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
         put(ev.out_slp, ev.part_slp, acc_re, acc_im);
         if (DLP) put(ev.out_dlp, ev.part_dlp, dacc_re, dacc_im);
         if (SP) put(ev.out_sp, ev.part_sp, pacc_re, pacc_im);
+#pragma unroll
+        for (int r = 1; r < NRHS; ++r)
+            put(ev.out_rhs[r], ev.part_slp ? ev.part_slp + r * ev.rhs_part_stride : nullptr, xacc_re[r - 1],
+                xacc_im[r - 1]);
     }
 }
 
@@ -294,6 +332,26 @@ int dispatch_helm(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStrea
 {
     int rc = (int)cudaErrorInvalidValue;
     ((p == Ps ? (rc = launch_helm_p<SP, Ps>(dlp, g, e, s), 0) : 0), ...);
+    return rc;
+}
+
+template <int NRHS, int P>
+int launch_helm_multi_p(const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks == 0) return 0;
+    if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
+    const size_t smem = (size_t)kWarpsPerBlock * helmholtz_tile_rows(false, NRHS) * g.tile * sizeof(double);
+    helmholtz_kernel<P, false, false, NRHS><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
+    return (int)cudaGetLastError();
+}
+
+template <int NRHS, int... Ps>
+int dispatch_helm_multi(int p, const DevGeom &g, const DevEval &e, cudaStream_t s,
+                        std::integer_sequence<int, Ps...>)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    ((p == Ps ? (rc = launch_helm_multi_p<NRHS, Ps>(g, e, s), 0) : 0), ...);
     return rc;
 }
 

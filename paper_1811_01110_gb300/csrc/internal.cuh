@@ -147,6 +147,9 @@ __device__ __forceinline__ WalkStart walk_start_of(const DevGeom &g, const Item 
     return WalkStart{r, p0, p1, g.run_src[r]};
 }
 
+// Most densities one evaluation may carry (tsqbx_submit_multi).
+constexpr int kMaxRhs = 4;
+
 // Per-evaluation buffers (device pointers).
 struct DevEval {
     const double *wmu = nullptr;        // Laplace FP64: w_s mu_s
@@ -161,6 +164,14 @@ struct DevEval {
     int *status = nullptr;              // bit 0: out-of-range source index seen
     double k = 0.0;                     // Helmholtz wavenumber
     double *conv_coef = nullptr;        // conventional partial coefficients (scratch)
+    // Several densities in one evaluation (Helmholtz single layer only): the
+    // w mu of density r starts at wmu_c + r * rhs_src_stride, its output at
+    // out_rhs[r] (out_rhs[0] == out_slp) and its partial sums at part_slp +
+    // r * rhs_part_stride (doubles).
+    int n_rhs = 1;
+    int64_t rhs_src_stride = 0;
+    int64_t rhs_part_stride = 0;
+    double *out_rhs[kMaxRhs] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // Launchers (one per translation unit).  Return a cudaError_t as int.
@@ -169,6 +180,8 @@ int launch_laplace_fp64(int p, unsigned layers, const DevGeom &g, const DevEval 
 int launch_laplace_mixed(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_laplace_df64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_helmholtz_fp64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
+// The Helmholtz single layer for e.n_rhs (2..kMaxRhs) densities at once.
+int launch_helmholtz_multi(int p, const DevGeom &g, const DevEval &e, cudaStream_t s);
 // Conventional path: coefficient formation, then evaluation (Laplace in
 // conventional.cu, Helmholtz in conventional_helm.cu).
 int launch_conventional(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);

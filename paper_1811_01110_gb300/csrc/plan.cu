@@ -168,7 +168,8 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
     if (o->precision != TSQBX_FP64 && o->precision != TSQBX_MIXED && o->precision != TSQBX_DF64)
         return TSQBX_E_INVAL;
     if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64 ||
-        o->max_item_iters < 0 || (o->tile_depth != 0 && !tsqbx::tile_depth_ok(o->tile_depth)))
+        o->max_item_iters < 0 || (o->tile_depth != 0 && !tsqbx::tile_depth_ok(o->tile_depth)) ||
+        o->max_rhs < 0 || o->max_rhs > tsqbx::kMaxRhs)
         return TSQBX_E_INVAL;
     if (o->kernel == TSQBX_HELMHOLTZ) {
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
@@ -178,6 +179,8 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         return TSQBX_E_UNSUPPORTED;
     if ((o->flags & TSQBX_FLAG_CONVENTIONAL_ALL) && o->kernel == TSQBX_HELMHOLTZ && o->p > kConvHelmMaxP)
         return TSQBX_E_UNSUPPORTED;
+    // several densities per evaluation: the Helmholtz single layer only
+    if (o->max_rhs > 1 && (o->kernel != TSQBX_HELMHOLTZ || o->layers != TSQBX_SLP)) return TSQBX_E_UNSUPPORTED;
     if (G->n_src < 0 || G->n_ctr < 0 || G->n_tgt < 0 || G->n_group < 0) return TSQBX_E_INVAL;
     if (G->n_src > INT32_MAX || G->n_ctr > INT32_MAX || G->n_tgt > INT32_MAX || G->n_group > INT32_MAX)
         return TSQBX_E_INVAL;
@@ -277,7 +280,8 @@ void apply_schedule(tsqbx_plan P, Schedule &&s)
     P->g.n_parts = s.n_parts;
     const size_t part_doubles = (size_t)s.n_parts * (helm ? 2 : 1);
     for (Slot &sl : P->slots) {
-        if (s.n_parts && (P->opt.layers & TSQBX_SLP)) sl.d_part[0] = P->dalloc<double>(part_doubles);
+        if (s.n_parts && (P->opt.layers & TSQBX_SLP))
+            sl.d_part[0] = P->dalloc<double>(part_doubles * (size_t)rhs_capacity(P->opt));
         if (s.n_parts && (P->opt.layers & TSQBX_DLP)) sl.d_part[1] = P->dalloc<double>(part_doubles);
         if (s.n_parts && (P->opt.layers & TSQBX_SP)) sl.d_part[2] = P->dalloc<double>(part_doubles);
     }
@@ -345,6 +349,49 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     if (timed) {
         ck(cudaEventRecord(P->k_end, s));
         P->k_timed = true;
+    }
+    return TSQBX_OK;
+}
+
+// Enqueue one evaluation of the Helmholtz single layer for n densities (the
+// first at d_density, the others at steps of density_bytes) into d_outs[r]:
+// w mu of each density, the multi-density expansion kernel, and the slice
+// combine per density.
+int enqueue_multi(tsqbx_plan P, Slot &slot, int n, const void *d_density, const void *const *d_densities,
+                  double *const *d_outs, cudaStream_t s, int p, double k)
+{
+    const int64_t ns = P->g.n_src;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((ns + threads - 1) / threads, (int64_t)P->n_sm * 16);
+    double2 *wmu = static_cast<double2 *>(slot.d_wmu);
+    for (int r = 0; r < n && ns > 0; ++r) {
+        const double2 *dens = d_densities ? static_cast<const double2 *>(d_densities[r])
+                                          : static_cast<const double2 *>(d_density) + (size_t)r * ns;
+        prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, dens, ns, wmu + (size_t)r * ns);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return status_of(e);
+    }
+    DevEval ev;
+    ev.status = slot.d_status;
+    ev.out_slp = d_outs[0];
+    ev.part_slp = slot.d_part[0];
+    ev.k = k;
+    ev.wmu_c = wmu;
+    ev.n_rhs = n;
+    ev.rhs_src_stride = ns;
+    ev.rhs_part_stride = 2 * P->g.n_parts;
+    for (int r = 0; r < n; ++r) ev.out_rhs[r] = d_outs[r];
+    int rc = n == 1 ? launch_helmholtz_fp64(p, TSQBX_SLP, P->g, ev, s) : launch_helmholtz_multi(p, P->g, ev, s);
+    if (rc != 0) return status_of((cudaError_t)rc);
+    if (P->g.n_combine > 0) {
+        const int64_t th = P->g.n_combine * 32;
+        const int cb = (int)std::min<int64_t>((th + 255) / 256, (int64_t)P->n_sm * 8);
+        for (int r = 0; r < n; ++r) {
+            combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp + r * ev.rhs_part_stride, nullptr, nullptr,
+                                              d_outs[r], nullptr, nullptr, 2);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return status_of(e);
+        }
     }
     return TSQBX_OK;
 }
@@ -619,15 +666,19 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         for (auto &s : P->slots) {
             ck(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio));
             ck(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
-            s.d_density = P->dalloc<char>(P->density_bytes);
-            s.d_wmu = P->dalloc<char>(P->wmu_bytes);
-            if (o->layers & TSQBX_SLP) s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            // density, w mu and single-layer buffers hold rhs_capacity densities
+            // (tsqbx_submit_multi), one after another
+            const size_t R = (size_t)rhs_capacity(*o);
+            s.d_density = P->dalloc<char>(R * P->density_bytes);
+            s.d_wmu = P->dalloc<char>(R * P->wmu_bytes);
+            if (o->layers & TSQBX_SLP)
+                s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(R * P->out_bytes));
             if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             if (o->layers & TSQBX_SP) s.d_out[2] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             s.d_status = P->dalloc<int>(1);
             if (P->conv_coef_doubles) s.d_conv = P->dalloc<double>(P->conv_coef_doubles);
-            s.h_density = P->halloc(P->density_bytes);
-            s.h_out[0] = P->halloc(P->out_bytes);
+            s.h_density = P->halloc(R * P->density_bytes);
+            s.h_out[0] = P->halloc(R * P->out_bytes);
             s.h_out[1] = P->halloc(P->out_bytes);
             if (o->layers & TSQBX_SP) s.h_out[2] = P->halloc(P->out_bytes);
             s.h_status = static_cast<int *>(P->halloc(sizeof(int)));
@@ -891,6 +942,8 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
     }
     void *outs[3] = {out_slp, out_dlp, out_sp};
     double *d_outs[3] = {nullptr, nullptr, nullptr};
+    slot.n_rhs = 1;
+    for (bool &c : slot.copy_out_rhs) c = false;
     for (int l = 0; l < 3; ++l) {
         slot.user_out[l] = outs[l];
         slot.copy_out[l] = false;
@@ -910,10 +963,56 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
     return TSQBX_OK;
 }
 
+// The same for n densities of a Helmholtz single-layer plan (tsqbx_submit_multi):
+// host densities are staged one after another in the slot's buffers, host
+// outputs come back through the slot's single-layer staging.
+int start_multi(tsqbx_plan P, Slot &slot, int n, const void *const *density, void *const *out_slp, int p, double k)
+{
+    const void *dens[kMaxRhs];
+    for (int r = 0; r < n; ++r) {
+        dens[r] = density[r];
+        if (P->g.n_src && !is_device_ptr(density[r])) {
+            char *h = static_cast<char *>(slot.h_density) + (size_t)r * P->density_bytes;
+            char *d = static_cast<char *>(slot.d_density) + (size_t)r * P->density_bytes;
+            std::memcpy(h, density[r], P->density_bytes);
+            ck(cudaMemcpyAsync(d, h, P->density_bytes, cudaMemcpyHostToDevice, slot.stream));
+            dens[r] = d;
+        }
+    }
+    double *d_outs[kMaxRhs];
+    slot.n_rhs = n;
+    for (int l = 0; l < 3; ++l) {
+        slot.user_out[l] = nullptr;
+        slot.copy_out[l] = false;
+    }
+    for (int r = 0; r < n; ++r) {
+        slot.user_out_rhs[r] = out_slp[r];
+        slot.copy_out_rhs[r] = !is_device_ptr(out_slp[r]);
+        d_outs[r] = slot.copy_out_rhs[r] ? slot.d_out[0] + (size_t)r * (P->out_bytes / sizeof(double))
+                                         : static_cast<double *>(out_slp[r]);
+    }
+    ck(cudaMemsetAsync(slot.d_status, 0, sizeof(int), slot.stream));
+    int rc = enqueue_multi(P, slot, n, nullptr, dens, d_outs, slot.stream, p, k);
+    if (rc) return rc;
+    for (int r = 0; r < n; ++r)
+        if (slot.copy_out_rhs[r] && P->out_bytes)
+            ck(cudaMemcpyAsync(static_cast<char *>(slot.h_out[0]) + (size_t)r * P->out_bytes, d_outs[r],
+                               P->out_bytes, cudaMemcpyDeviceToHost, slot.stream));
+    ck(cudaMemcpyAsync(slot.h_status, slot.d_status, sizeof(int), cudaMemcpyDeviceToHost, slot.stream));
+    ck(cudaEventRecord(slot.done, slot.stream));
+    return TSQBX_OK;
+}
+
 int finish(tsqbx_plan P, Slot &slot)
 {
     for (int l = 0; l < 3; ++l)
         if (slot.copy_out[l]) std::memcpy(slot.user_out[l], slot.h_out[l], P->out_bytes);
+    for (int r = 0; r < slot.n_rhs; ++r)          // outputs of a tsqbx_submit_multi call
+        if (slot.copy_out_rhs[r])
+            std::memcpy(slot.user_out_rhs[r], static_cast<char *>(slot.h_out[0]) + (size_t)r * P->out_bytes,
+                        P->out_bytes);
+    slot.n_rhs = 1;
+    for (bool &c : slot.copy_out_rhs) c = false;
     return *slot.h_status ? TSQBX_E_KERNEL : TSQBX_OK;
 }
 
@@ -988,6 +1087,45 @@ int tsqbx_submit_pk(tsqbx_plan P, int p, double k, const void *density, void *ou
         Slot &slot = P->slots[idx];
         int rc = start(P, slot, density, out_slp, out_dlp, out_sp, false, p, k);
         if (rc) return rc;
+        slot.busy = true;
+        slot.ticket = g_next_ticket.fetch_add(1);
+        {
+            std::lock_guard<std::mutex> tl(g_ticket_mu);
+            g_tickets[slot.ticket] = {P, idx};
+        }
+        *ticket = slot.ticket;
+        return TSQBX_OK;
+    } catch (const CudaFail &f) {
+        cudaGetLastError();
+        return status_of(f.err);
+    } catch (...) {
+        return TSQBX_E_CUDA;
+    }
+}
+
+int tsqbx_submit_multi(tsqbx_plan P, int p, double k, int n, const void *const *density, void *const *out_slp,
+                       uint64_t *ticket)
+{
+    if (!P || !ticket || !density || !out_slp || n < 1 || n > rhs_capacity(P->opt) || !pk_ok(P, p, k))
+        return TSQBX_E_INVAL;
+    if (P->opt.kernel != TSQBX_HELMHOLTZ || P->opt.layers != TSQBX_SLP || P->g.n_conv_centers > 0)
+        return TSQBX_E_UNSUPPORTED;
+    for (int r = 0; r < n; ++r)
+        if ((P->g.n_src && !density[r]) || (P->g.n_tgt && !out_slp[r])) return TSQBX_E_INVAL;
+    try {
+        DeviceGuard dg(P->opt.device);
+        std::lock_guard<std::mutex> lk(P->mu);
+        int idx = -1;
+        for (size_t i = 1; i < P->slots.size(); ++i)
+            if (!P->slots[i].busy) { idx = (int)i; break; }
+        if (idx < 0) return TSQBX_E_BUSY;
+        Slot &slot = P->slots[idx];
+        int rc = start_multi(P, slot, n, density, out_slp, p, k);
+        if (rc) {
+            slot.n_rhs = 1;
+            for (bool &c : slot.copy_out_rhs) c = false;
+            return rc;
+        }
         slot.busy = true;
         slot.ticket = g_next_ticket.fetch_add(1);
         {

@@ -101,6 +101,11 @@ struct Slot {
     uint64_t ticket = 0;
     void *user_out[3] = {nullptr, nullptr, nullptr};
     bool copy_out[3] = {false, false, false};
+    // densities 1..n_rhs-1 of a tsqbx_submit_multi call (their single-layer
+    // outputs; density 0 uses user_out[0] / copy_out[0])
+    int n_rhs = 1;
+    void *user_out_rhs[kMaxRhs] = {nullptr, nullptr, nullptr, nullptr};
+    bool copy_out_rhs[kMaxRhs] = {false, false, false, false};
 };
 
 }  // namespace tsqbx
@@ -164,6 +169,8 @@ namespace tsqbx {
 // Install a schedule on a plan: upload items and combine records, size the
 // partial-sum buffers of every slot (frees what the old schedule used).
 void apply_schedule(tsqbx_plan P, Schedule &&s);
+// Densities a slot's buffers hold: o.max_rhs (0 = 1).
+inline int rhs_capacity(const tsqbx_options &o) { return o.max_rhs > 1 ? o.max_rhs : 1; }
 // Enqueue prep + expansion (+ combine) for one evaluation on stream s, with
 // expansion order p and (Helmholtz) wavenumber k; S' is formed only when the
 // plan's mask has it and d_sp is given.

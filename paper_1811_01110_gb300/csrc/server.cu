@@ -9,7 +9,10 @@
 //    exceeded;
 //  * continuous batching: every started request runs on its own plan slot
 //    (own stream), so requests that arrive while others are on the GPU overlap
-//    with them; completions free slots for the next queued requests;
+//    with them; completions free slots for the next queued requests.  Queued
+//    Helmholtz single-layer requests that share a plan, an order and a
+//    wavenumber start together as one multi-density evaluation
+//    (tsqbx_submit_multi), which costs little more than one of them;
 //  * accounting: latency (arrival to completion) per request, p50/p99,
 //    pair-terms completed, plans created/evicted, resident bytes.
 #include <algorithm>
@@ -17,7 +20,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
-#include <deque>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -68,7 +71,19 @@ struct Request {
     int status = TSQBX_OK;
     uint64_t ticket = 0;
     int64_t pair_terms = 0;
+    std::vector<Request *> merged;   // queued requests that ride in this one's evaluation
 };
+
+// Densities a Helmholtz single-layer evaluation of the server may carry: queued
+// requests with the same plan, order and wavenumber are started together
+// (tsqbx_submit_multi) when a slot frees up.
+constexpr int kServerMaxRhs = 4;
+
+bool mergeable(const tsqbx_options &o)
+{
+    return o.kernel == TSQBX_HELMHOLTZ && o.layers == TSQBX_SLP &&
+           !(o.flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL));
+}
 
 size_t estimate_bytes(const GeomCopy &g, const tsqbx_options &o)
 {
@@ -81,7 +96,8 @@ size_t estimate_bytes(const GeomCopy &g, const tsqbx_options &o)
     if (o.layers & TSQBX_SP) b += nt * 32;
     if (mixed) b += ns * 48 + nt * 48;
     const int slots = (o.n_slots ? o.n_slots : 2) + 1;
-    b += (size_t)slots * (ns * (helm ? 32 : 16) + nt * 16 * (helm ? 2 : 1));
+    const size_t rhs = o.max_rhs > 1 ? (size_t)o.max_rhs : 1;
+    b += (size_t)slots * rhs * (ns * (helm ? 32 : 16) + nt * 16 * (helm ? 2 : 1));
     return b;
 }
 
@@ -100,13 +116,13 @@ struct tsqbx_server_s {
     std::vector<std::unique_ptr<GeomCopy>> geoms;
     std::map<PlanKey, PlanEntry> plans;
     std::map<PlanKey, size_t> known_bytes;   // exact footprints of plans built before
-    std::deque<Request *> queue;
+    std::list<Request *> queue;
     std::vector<Request *> running;
     std::unordered_map<uint64_t, std::unique_ptr<Request>> requests;
     uint64_t next_id = 1, use_clock = 0;
     size_t resident = 0;
     std::vector<double> lat;                 // seconds, completed requests
-    int64_t completed = 0, failed = 0, rejected = 0, created = 0, evicted = 0, pair_terms = 0;
+    int64_t completed = 0, failed = 0, rejected = 0, created = 0, evicted = 0, pair_terms = 0, merged = 0;
     Clock::time_point t_first{}, t_last{};
     bool any_done = false, span_started = false;
 
@@ -167,8 +183,28 @@ bool tsqbx_server_s::admit(Request *r)
         ++created;
     }
     PlanEntry &pe = it->second;
-    const int rc = tsqbx_submit_pk(pe.plan, r->opt.p, r->opt.k, r->density.data(), r->out_slp, r->out_dlp,
-                                   r->out_sp, &r->ticket);
+    // queued requests for the same plan, order and wavenumber ride along
+    std::vector<Request *> group{r};
+    if (r->opt.max_rhs > 1)
+        for (Request *q : queue) {
+            if ((int)group.size() >= r->opt.max_rhs) break;
+            if (q != r && q->state == RState::Queued && q->key == r->key && q->opt.p == r->opt.p &&
+                q->opt.k == r->opt.k)
+                group.push_back(q);
+        }
+    int rc;
+    if (group.size() > 1) {
+        const void *dens[kServerMaxRhs];
+        void *outs[kServerMaxRhs];
+        for (size_t i = 0; i < group.size(); ++i) {
+            dens[i] = group[i]->density.data();
+            outs[i] = group[i]->out_slp;
+        }
+        rc = tsqbx_submit_multi(pe.plan, r->opt.p, r->opt.k, (int)group.size(), dens, outs, &r->ticket);
+    } else {
+        rc = tsqbx_submit_pk(pe.plan, r->opt.p, r->opt.k, r->density.data(), r->out_slp, r->out_dlp, r->out_sp,
+                             &r->ticket);
+    }
     if (rc == TSQBX_E_BUSY) return false;                      // every slot of the plan busy
     if (rc != TSQBX_OK) {
         r->status = rc;
@@ -177,6 +213,13 @@ bool tsqbx_server_s::admit(Request *r)
     tsqbx_plan_stats st{};
     tsqbx_plan_info(pe.plan, &st);
     r->pair_terms = st.n_pairs * (int64_t)(r->opt.p + 1);
+    for (size_t i = 1; i < group.size(); ++i) {
+        Request *q = group[i];
+        q->state = RState::Running;
+        q->pair_terms = r->pair_terms;
+        r->merged.push_back(q);
+        queue.remove(q);
+    }
     ++pe.inflight;
     pe.last_use = ++use_clock;
     r->state = RState::Running;
@@ -195,17 +238,22 @@ void tsqbx_server_s::run()
             Request *r = running[i];
             const int rc = tsqbx_poll(r->ticket, 0);
             if (rc == TSQBX_PENDING) { ++i; continue; }
-            r->latency_s = seconds_since(r->arrive);
-            r->status = rc;
-            r->state = RState::Done;
             auto pit = plans.find(r->key);
             if (pit != plans.end()) --pit->second.inflight;
-            if (rc == TSQBX_OK) {
-                ++completed;
-                pair_terms += r->pair_terms;
-                lat.push_back(r->latency_s);
-            } else {
-                ++failed;
+            merged += (int64_t)r->merged.size();
+            std::vector<Request *> done{r};
+            done.insert(done.end(), r->merged.begin(), r->merged.end());
+            for (Request *d : done) {
+                d->latency_s = seconds_since(d->arrive);
+                d->status = rc;
+                d->state = RState::Done;
+                if (rc == TSQBX_OK) {
+                    ++completed;
+                    pair_terms += d->pair_terms;
+                    lat.push_back(d->latency_s);
+                } else {
+                    ++failed;
+                }
             }
             t_last = Clock::now();
             any_done = true;
@@ -328,6 +376,7 @@ int tsqbx_server_submit(tsqbx_server S, int geom_id, const tsqbx_options *opt, c
         if (S->size_priority) r->opt.flags |= TSQBX_FLAG_SIZE_PRIORITY;
         if (S->laplace_fp64_as_df64 && r->opt.kernel == TSQBX_LAPLACE && r->opt.precision == TSQBX_FP64)
             r->opt.precision = TSQBX_DF64;
+        if (mergeable(r->opt)) r->opt.max_rhs = kServerMaxRhs;
         r->opt.device = S->device;
         r->key = PlanKey{geom_id, (int)r->opt.kernel, r->opt.layers, (int)r->opt.precision};
         const double *d = static_cast<const double *>(density);
@@ -392,6 +441,7 @@ int tsqbx_server_get_stats(tsqbx_server S, tsqbx_server_stats *st)
     st->resident_bytes = S->resident;
     st->pair_terms_completed = S->pair_terms;
     st->span_s = S->any_done ? std::chrono::duration<double>(S->t_last - S->t_first).count() : 0.0;
+    st->merged = S->merged;
     return TSQBX_OK;
 }
 
@@ -402,6 +452,7 @@ int tsqbx_server_reset_stats(tsqbx_server S)
     S->lat.clear();
     S->completed = S->failed = S->rejected = 0;
     S->pair_terms = 0;
+    S->merged = 0;
     S->any_done = false;
     S->span_started = false;
     return TSQBX_OK;
@@ -432,6 +483,7 @@ int tsqbx_server_prepare(tsqbx_server S, int geom_id, const tsqbx_options *opt)
     if (S->size_priority) o.flags |= TSQBX_FLAG_SIZE_PRIORITY;
     if (S->laplace_fp64_as_df64 && o.kernel == TSQBX_LAPLACE && o.precision == TSQBX_FP64)
         o.precision = TSQBX_DF64;
+    if (mergeable(o)) o.max_rhs = kServerMaxRhs;
     o.device = S->device;
     const PlanKey key{geom_id, (int)o.kernel, o.layers, (int)o.precision};
     auto it = S->plans.find(key);

@@ -102,6 +102,10 @@ def test_more_invalid_options_rejected_on_host(L):
     assert _create(g, kernel="helmholtz", k=-1.0) == -1
     for depth in (-64, 16, 48, 96, 256):                  # staging depth: 0, 32, 64 or 128
         assert _create(g, tile_depth=depth) == -1
+    for rhs in (-1, 5):                                    # densities per evaluation: 0..4
+        assert _create(g, kernel="helmholtz", k=1.0, max_rhs=rhs) == -1
+    assert _create(g, max_rhs=2) == -9                     # several densities: Helmholtz single layer only
+    assert _create(g, kernel="helmholtz", k=1.0, layers=("slp", "dlp"), max_rhs=2) == -9
 
 
 def test_invalid_options_rejected_on_host(L):
@@ -214,6 +218,12 @@ def test_noalloc_arguments_rejected_on_host(L):
     assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == _lib.TSQBX_E_TOO_LARGE
     geo.n_src = -1
     assert L.tsqbx_eval_noalloc(ctypes.byref(geo), 3, 1, fake, fake, None, None) == inval
+
+
+def test_submit_multi_rejects_null_on_host(L):
+    from paper_1811_01110_gb300 import _lib
+    t = ctypes.c_uint64()
+    assert L.tsqbx_submit_multi(None, 3, 1.0, 2, None, None, ctypes.byref(t)) == _lib.TSQBX_E_INVAL
 
 
 def test_pipe_peak_probe_rejects_null_on_host(L):
