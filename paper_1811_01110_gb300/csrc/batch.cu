@@ -92,6 +92,14 @@ __device__ __forceinline__ void run_part_item_mixed(int p, const DevGeom &g, con
     ((p == Ps ? (laplace_mixed_part_item<Ps, W>(g, ev, it, ws, sl), 0) : 0), ...);
 }
 
+template <int... Ps>
+__device__ __forceinline__ void run_window4_mixed(int p, const DevGeom &g, const DevEval &ev, const Item &it,
+                                                  int32_t a, int32_t b, int32_t A, int32_t B, float4 *T, int lane,
+                                                  std::integer_sequence<int, Ps...>)
+{
+    ((p == Ps ? (laplace_mixed_window4<Ps>(g, ev, it, a, b, A, B, T, lane), 0) : 0), ...);
+}
+
 template <bool MIXED, bool DLP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, DLP ? 1 : 8)
 batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, const WalkStart *walks,
@@ -124,6 +132,30 @@ batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *item
                         const Item o = items[idx + m];
                         if (o.n_tgt != 1 || o.pad != it.pad) break;
                     }
+                if (m >= 4) {
+                    // four items whose lists are single runs with a short union:
+                    // stage the union once for all four
+                    const int q = lane >> 3;
+                    const Item mine_it = items[idx + q];
+                    int32_t a = 0, b = 0;
+                    const bool run = single_run_range(mine_it, walks[idx + q], a, b);
+                    const bool all_runs = __all_sync(0xffffffffu, run);
+                    int32_t A = a, B = b, len = b - a;
+#pragma unroll
+                    for (int off = 8; off < 32; off <<= 1) {
+                        A = min(A, __shfl_xor_sync(0xffffffffu, A, off));
+                        B = max(B, __shfl_xor_sync(0xffffffffu, B, off));
+                        len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
+                    }
+                    if (all_runs && B - A <= 2 * len) {
+                        run_window4_mixed(bp.p, bp.g, ev, mine_it, a, b, A, B,
+                                          reinterpret_cast<float4 *>(tile_raw + warp * kWarpBytes), lane,
+                                          std::make_integer_sequence<int, TSQBX_P_MAX + 1>{});
+                        __syncwarp();
+                        idx += 3;
+                        continue;
+                    }
+                }
                 if (m >= 2) {
                     const int W = m >= 4 ? 8 : 16;
                     const int q = lane / W;

@@ -413,6 +413,87 @@ __device__ __forceinline__ void laplace_mixed_part_item(const DevGeom &g, const 
     if (sl == 0) write_item_result<false, false>(g, ev, it, 0, df_to_double(v), 0.0, 0.0);
 }
 
+// The source range [a, b) of a single-target item whose slice lies in one run
+// of its group's list (the run's sources are consecutive); false otherwise.
+__device__ __forceinline__ bool single_run_range(const Item &it, const WalkStart &ws, int32_t &a, int32_t &b)
+{
+    if (it.n_tgt != 1 || it.src_hi > ws.p1 || it.src_lo < ws.p0) return false;
+    a = ws.s0 + (it.src_lo - ws.p0);
+    b = ws.s0 + (it.src_hi - ws.p0);
+    return true;
+}
+
+// Four single-target items of one single-layer mixed plan whose sources are
+// the consecutive ranges [a_q, b_q) (one run each), read through their union
+// [A, B): the warp stages the union in tiles of kTile sources (the pair
+// records of the mixed tile) and each item's 8 lanes (q = lane / 8, sl = lane
+// % 8) take, in step with the other items' lanes, the tile's source pairs that
+// meet its own range, with the weight of a pair's half outside the range set
+// to zero.  Neighbouring centers of a
+// surface list overlapping windows, so the union is little longer than each:
+// one load of a source record serves every item that lists it.  Plain FP32
+// sums per tile, Kahan across tiles, double-float across the 8 lanes.
+template <int P>
+__device__ __forceinline__ void laplace_mixed_window4(const DevGeom &g, const DevEval &ev, const Item &it,
+                                                      int32_t a, int32_t b, int32_t A, int32_t B, float4 *T,
+                                                      const int lane)
+{
+    constexpr int kPairs = kTile / 2;
+    constexpr float kFar = 1.0e4f;
+    float4 *const T0 = T, *const T1 = T + kPairs, *const T2 = T + 2 * kPairs, *const T3 = T + 3 * kPairs;
+    const int sl = lane & 7;
+    const f2 z2 = f2_splat(0.f);
+    f2 as = z2, ac = z2, unused = z2;
+    const float4 ch = g.slot_chi[it.slot_begin];
+    const float4 cl = g.slot_clo[it.slot_begin];
+    const float4 e = g.slot_ef[it.slot_begin];
+    const float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int32_t base = A; base < B; base += kTile) {
+        {   // record `lane` holds sources base + lane and base + lane + kPairs, so that
+            // the warp's loads of each array are contiguous
+            int32_t s0 = base + lane, s1 = s0 + kPairs;
+            float w0 = 0.f, w1 = 0.f;
+            if (s0 < B && (unsigned)s0 < (unsigned)g.n_src) w0 = ev.wmu_f[s0];
+            else s0 = 0;
+            if (s1 < B && (unsigned)s1 < (unsigned)g.n_src) w1 = ev.wmu_f[s1];
+            else s1 = s0;
+            const float4 h0 = g.src_hi[s0], h1 = g.src_hi[s1], l0 = g.src_lo[s0], l1 = g.src_lo[s1];
+            T0[lane] = make_float4(h0.x, h1.x, h0.y, h1.y);
+            T1[lane] = make_float4(h0.z, h1.z, w0, w1);
+            T2[lane] = make_float4(l0.x, l1.x, l0.y, l1.y);
+            T3[lane] = make_float4(l0.z, l1.z, 0.f, 0.f);
+        }
+        __syncwarp();
+        // the four items walk the tile's records in step (lane sl of every item
+        // reads the same record: one shared-memory broadcast serves four), each
+        // computing the halves that fall in its own sources max(a, base) ..
+        // min(b, base + kTile) - 1
+        const int32_t lo = max(a, base) - base, hi = min(b, base + kTile) - base;
+        f2 ts = z2;
+        for (int i = sl; i < kPairs; i += 8) {
+            const bool m0 = i < lo || i >= hi, m1 = i + kPairs < lo || i + kPairs >= hi;
+            if (m0 && m1) continue;                            // no source of this item in the record
+            float4 A4 = T0[i], B4 = T1[i], C4 = T2[i], D4 = T3[i];
+            if (m0 || m1) {
+                // a half outside this item's range (another item's source, which
+                // this center does not list and may even coincide with): weight 0
+                // at a point far from the center, so its term is an exact zero
+                if (m0) { A4.x = ch.x + kFar; A4.z = ch.y; B4.x = ch.z; C4.x = cl.x; C4.z = cl.y; D4.x = cl.z; B4.z = 0.f; }
+                if (m1) { A4.y = ch.x + kFar; A4.w = ch.y; B4.y = ch.z; C4.y = cl.x; C4.w = cl.y; D4.y = cl.z; B4.w = 0.f; }
+            }
+            pair_mixed2<P, false, false, false>(f2_xy(A4), f2_zw(A4), f2_xy(B4), f2_zw(B4), f2_xy(C4), f2_zw(C4),
+                                                f2_xy(D4), z2, z2, z2, ch, cl, e, tn, ts, unused, unused, unused,
+                                                unused, unused);
+        }
+        kahan_add2(as, ac, ts);
+        __syncwarp();
+    }
+    df v = kahan2_df(as, ac);
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
+    if (sl == 0) write_item_result<false, false>(g, ev, it, 0, df_to_double(v), 0.0, 0.0);
+}
+
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEval &ev, const Item &it,
                                                    const WalkStart &ws, float4 *T, const int tile, const int lane)

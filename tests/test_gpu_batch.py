@@ -111,3 +111,43 @@ def test_single_layer_mixed_batch_shared_warp_items(env):
     finally:
         for p_ in plans:
             p_.close()
+
+
+def test_window_items_with_a_source_on_a_neighbours_center(env):
+    """Four consecutive single-target items whose lists are overlapping windows
+    of consecutive sources share one staged union in a single-layer mixed
+    batch.  A source inside the union sits exactly on the first center but
+    outside that center's own window: it must contribute nothing there (no
+    inf/NaN), and every result must match the oracle within 1e-6."""
+    torch, pkg = env
+    from tsqbx_inputs.geometry import Geometry
+    rng = np.random.default_rng(71)
+    n_src, n_ctr, width, step = 130, 8, 50, 10
+    t = np.linspace(0.0, 2.0, n_src)
+    src = np.stack([t, 0.3 * np.sin(3 * t), 0.2 * np.cos(2 * t)])
+    ctr = np.stack([np.linspace(0.2, 1.2, n_ctr), np.full(n_ctr, 0.6), np.full(n_ctr, 0.5)])
+    src[:, 55] = ctr[:, 0]                                   # in centers 1-4's windows, not in center 0's
+    begin = np.arange(n_ctr, dtype=np.int32) * step
+    end = begin + width
+    d = rng.standard_normal((3, n_ctr))
+    d /= np.linalg.norm(d, axis=0)
+    rmin = np.array([np.linalg.norm(src[:, b:e] - ctr[:, [c]], axis=0).min()
+                     for c, (b, e) in enumerate(zip(begin, end))])
+    tgt = ctr + 0.3 * rmin * d
+    g = Geometry(np.ascontiguousarray(src), rng.uniform(0.5, 1.5, n_src), None, np.ascontiguousarray(ctr),
+                 np.full(n_ctr, 0.1), np.ascontiguousarray(tgt), np.arange(n_ctr, dtype=np.int32), None,
+                 np.arange(n_ctr, dtype=np.int32), np.arange(n_ctr + 1, dtype=np.int64), begin, end)
+    mu = rng.standard_normal(n_src)
+    plan = pkg.Plan(g, "laplace", ("slp",), p=7, precision="mixed")
+    try:
+        with pkg.Batch([plan]) as batch:
+            dmu = torch.from_numpy(mu).cuda()
+            out = {"slp": torch.full((n_ctr,), np.nan, dtype=torch.float64, device="cuda")}
+            batch.eval_async([dmu], [out], stream=torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            got = out["slp"].cpu().numpy()
+    finally:
+        plan.close()
+    ref = oracle.tsqbx_laplace(g, 7, mu, slp=True)["slp"]
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-6
