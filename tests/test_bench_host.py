@@ -55,7 +55,7 @@ def _full_result():
           "peak_source": "measured: register-only FMA probe", "flops_per_pair": 101,
           "hbm": {"achieved_gbs": x, "peak_gbs": 6802.4, "frac": x, "peak_source": "measured"},
           "a_priori_count": {"flops_per_pair": 134, "achieved": x, "frac": x}}
-    df_rf = dict(rf, pipe="fp32", fp64_equivalent={"flops_per_pair": 101, "achieved": x, "frac_of_fp64_peak": x})
+    df_rf = dict(rf, pipe="fp32", fp64_equivalent={"flops_per_pair": 101, "achieved": x, "times_fp64_peak": x})
     leg = {"value": 5.7e10 * x, "ms_per_step": 262.4 * x, "kernel_ms": x, "roofline": rf,
            "error_vs_oracle": {"slp": 1e-15 * x, "targets": 900}, "workload": "w" * 120}
     serving = {"workload": "w" * 150, "policy": "fifo",
