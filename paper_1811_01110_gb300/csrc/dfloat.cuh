@@ -11,11 +11,13 @@
 //   df_mul   -- DWTimesDW (FMA variant): relative error <= 5 * 2^-48;
 //   df_mul_f -- DWTimesFP: relative error <= 2 * 2^-48.
 // All steps use explicit round-to-nearest intrinsics so the compiler neither
-// contracts nor reassociates them.  1/sqrt is rsqrtf refined by two Newton
+// contracts nor reassociates them.  1/sqrt is rsqrt.approx refined by two Newton
 // steps y <- y + y (1 - a y^2) / 2 evaluated in double-float.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "f32x2.cuh"
 
 namespace tsqbx {
 
@@ -81,7 +83,7 @@ __device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (do
 // 1/sqrt(a), a > 0 (relative error ~2^-46)
 __device__ __forceinline__ df df_rsqrt(df a)
 {
-    const float r0 = rsqrtf(a.hi);
+    const float r0 = rsqrt_approx(a.hi);
     const df ar0 = df_mul(a, two_prod(r0, r0));
     const df h0 = df_add(df{1.f, 0.f}, df_neg(ar0));
     const df r1 = fast_two_sum(r0, __fmul_rn(__fmul_rn(0.5f, r0), h0.hi));

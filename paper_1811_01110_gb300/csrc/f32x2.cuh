@@ -49,6 +49,25 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
     return d;
 }
+// 1/sqrt(x) and 1/x as single special-function-unit instructions (PTX
+// rsqrt.approx.ftz.f32, rcp.approx.ftz.f32; rcp within 1 ulp).  Unlike
+// rsqrtf they carry no handling of subnormal arguments, which flush to zero
+// (so give +inf): the kernels take them of squared center-source distances,
+// which for any surface of size 1e-3 .. 1e3 lie far above FP32's subnormal
+// range (below 1.2e-38).
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Both halves of a float4's (x, y) or (z, w) as one packed value.
 __device__ __forceinline__ f2 f2_xy(const float4 &q) { return f2_make(q.x, q.y); }
 __device__ __forceinline__ f2 f2_zw(const float4 &q) { return f2_make(q.z, q.w); }

@@ -220,12 +220,11 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
 // compensating per tile).
 //
 // Operation count (p = 9, both layers, per pair): float-float difference 9,
-// R^2 3, 1/R (rsqrtf) and 1/R^2 with one Newton step 4, qx, -q2 and w/R 6,
+// R^2 3, 1/R and 1/R^2 on the special-function unit, qx, -q2 and w/R 6,
 // the Q' recurrence 4 per order from n = 2 (its n = 1 step is U_2 = qx,
 // S2m = 1 exactly) and 3 at n = 2, its top 5, the closing sums 4, the double
 // layer 11 with its sum, the single layer's sum 1.  Negated operands (-q2,
-// -n_s, -e.n_t) are prepared outside the pair loop; only -R^2 costs an
-// operation.
+// -n_s, -e.n_t) are prepared outside the pair loop.
 
 // Adds w * x to the packed sum s: Kahan-compensated (c the compensation) or
 // a plain fused multiply-add.
@@ -248,16 +247,12 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
     const f2 R2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     float r0, r1;
     f2_split(R2, r0, r1);
-    const f2 rinv = f2_make(rsqrtf(r0), rsqrtf(r1));
-    f2 r2inv = mul2(rinv, rinv);
-    if constexpr (DLP || SP) {
-        // one Newton step for 1/R^2: x <- x + x (1 - R^2 x).  rsqrtf's error
-        // (up to ~2 ulp) doubles in rinv^2 and, through qx and q2, grows with
-        // the order in the Q' recurrence; the refined 1/R^2 is within about
-        // an ulp, which halves the worst double-layer and S' errors
-        const f2 ee = fma2(mul2(f2_splat(-1.f), R2), r2inv, f2_splat(1.f));
-        r2inv = fma2(r2inv, ee, r2inv);
-    }
+    const f2 rinv = f2_make(rsqrt_approx(r0), rsqrt_approx(r1));
+    // 1/R^2: rinv^2 for the single layer; with the double layer or S' its own
+    // reciprocal (within 1 ulp): rinv's error (up to ~2 ulp) doubles in
+    // rinv^2 and, through qx and q2, grows with the order in the Q'
+    // recurrence
+    const f2 r2inv = (DLP || SP) ? f2_make(rcp_approx(r0), rcp_approx(r1)) : mul2(rinv, rinv);
     const f2 qx = mul2(fma2(dx, f2_splat(e.x), fma2(dy, f2_splat(e.y), mul2(dz, f2_splat(e.z)))), r2inv);
     const f2 nq2 = mul2(f2_splat(e.w), r2inv);                       // -q2
     const f2 wr = mul2(w, rinv);

@@ -8,9 +8,10 @@
 //    (s_lo - c_lo), accurate to FP32 rounding of the difference itself, so
 //    nearby sources lose no digits to cancellation;
 //  * e = t - c and rho^2 are formed in FP64 at plan time and rounded once;
-//  * the geometry ratios, 1/R (rsqrtf), 1/R^2 (refined by one Newton step
-//    when the double layer or S' is formed: the Q' recurrence amplifies the
-//    error of qx and q2 with the order) and the recurrence run in FP32;
+//  * the geometry ratios, 1/R and 1/R^2 (each one special-function
+//    instruction; 1/R^2 its own reciprocal, not (1/R)^2, when the double
+//    layer or S' is formed: the Q' recurrence amplifies the error of qx and
+//    q2 with the order) and the recurrence run in FP32;
 //  * each lane sums a shared-memory tile's pairs in plain FP32 and adds the
 //    tile sum to Kahan-compensated FP32 sums (single-target items compensate
 //    every pair); the L lanes of a target are combined in double-float on the
