@@ -235,10 +235,15 @@ __device__ __forceinline__ void sum_fma2(f2 &s, f2 &c, f2 w, f2 x)
     else s = fma2(w, x, s);
 }
 
-template <int P, bool DLP, bool SP, bool KAHAN = true>
+//
+// MASK: a half whose flag (m0, m1) is set contributes an exact zero: its 1/R
+// and 1/R^2 are taken as 0, so w/R, qx and q2 vanish and every term stays
+// finite whatever the source's position (it may even sit on the center).
+template <int P, bool DLP, bool SP, bool KAHAN = true, bool MASK = false>
 __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2 ly, f2 lz, f2 mx, f2 my, f2 mz,
                                             const float4 &ch, const float4 &cl, const float4 &e,
-                                            const float4 &tn, f2 &as, f2 &ac, f2 &ds, f2 &dc, f2 &ps, f2 &pc)
+                                            const float4 &tn, f2 &as, f2 &ac, f2 &ds, f2 &dc, f2 &ps, f2 &pc,
+                                            bool m0 = false, bool m1 = false)
 {
     const f2 one = f2_splat(1.f);
     const f2 dx = add2(sub2(hx, f2_splat(ch.x)), sub2(lx, f2_splat(cl.x)));
@@ -247,12 +252,21 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
     const f2 R2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     float r0, r1;
     f2_split(R2, r0, r1);
-    const f2 rinv = f2_make(rsqrt_approx(r0), rsqrt_approx(r1));
+    float i0 = rsqrt_approx(r0), i1 = rsqrt_approx(r1);
+    if constexpr (MASK) { i0 = m0 ? 0.f : i0; i1 = m1 ? 0.f : i1; }
+    const f2 rinv = f2_make(i0, i1);
     // 1/R^2: rinv^2 for the single layer; with the double layer or S' its own
     // reciprocal (within 1 ulp): rinv's error (up to ~2 ulp) doubles in
     // rinv^2 and, through qx and q2, grows with the order in the Q'
     // recurrence
-    const f2 r2inv = (DLP || SP) ? f2_make(rcp_approx(r0), rcp_approx(r1)) : mul2(rinv, rinv);
+    f2 r2inv;
+    if constexpr (DLP || SP) {
+        float j0 = rcp_approx(r0), j1 = rcp_approx(r1);
+        if constexpr (MASK) { j0 = m0 ? 0.f : j0; j1 = m1 ? 0.f : j1; }
+        r2inv = f2_make(j0, j1);
+    } else {
+        r2inv = mul2(rinv, rinv);
+    }
     const f2 qx = mul2(fma2(dx, f2_splat(e.x), fma2(dy, f2_splat(e.y), mul2(dz, f2_splat(e.z)))), r2inv);
     const f2 nq2 = mul2(f2_splat(e.w), r2inv);                       // -q2
     const f2 wr = mul2(w, rinv);
@@ -422,9 +436,9 @@ __device__ __forceinline__ bool single_run_range(const Item &it, const WalkStart
 // the consecutive ranges [a_q, b_q) (one run each), read through their union
 // [A, B): the warp stages the union in tiles of kTile sources (the pair
 // records of the mixed tile) and each item's 8 lanes (q = lane / 8, sl = lane
-// % 8) take, in step with the other items' lanes, the tile's source pairs that
-// meet its own range, with the weight of a pair's half outside the range set
-// to zero.  Neighbouring centers of a
+// % 8) take, in step with the other items' lanes, every record of the tile,
+// a record half outside the item's range masked to an exact zero (its 1/R
+// taken as 0).  Neighbouring centers of a
 // surface list overlapping windows, so the union is little longer than each:
 // one load of a source record serves every item that lists it.  Plain FP32
 // sums per tile, Kahan across tiles, double-float across the 8 lanes.
@@ -434,7 +448,6 @@ __device__ __forceinline__ void laplace_mixed_window4(const DevGeom &g, const De
                                                       const int lane)
 {
     constexpr int kPairs = kTile / 2;
-    constexpr float kFar = 1.0e4f;
     float4 *const T0 = T, *const T1 = T + kPairs, *const T2 = T + 2 * kPairs, *const T3 = T + 3 * kPairs;
     const int sl = lane & 7;
     const f2 z2 = f2_splat(0.f);
@@ -461,24 +474,20 @@ __device__ __forceinline__ void laplace_mixed_window4(const DevGeom &g, const De
         __syncwarp();
         // the four items walk the tile's records in step (lane sl of every item
         // reads the same record: one shared-memory broadcast serves four), each
-        // computing the halves that fall in its own sources max(a, base) ..
-        // min(b, base + kTile) - 1
-        const int32_t lo = max(a, base) - base, hi = min(b, base + kTile) - base;
+        // taking the halves that fall in its own sources max(a, base) ..
+        // min(b, base + kTile) - 1; a half outside them (another item's source,
+        // which this center does not list and may even coincide with) is
+        // masked to an exact zero, without a branch
+        const int32_t lo = max(a, base) - base, n_in = max(min(b, base + kTile) - base - lo, 0);
         f2 ts = z2;
-        for (int i = sl; i < kPairs; i += 8) {
-            const bool m0 = i < lo || i >= hi, m1 = i + kPairs < lo || i + kPairs >= hi;
-            if (m0 && m1) continue;                            // no source of this item in the record
-            float4 A4 = T0[i], B4 = T1[i], C4 = T2[i], D4 = T3[i];
-            if (m0 || m1) {
-                // a half outside this item's range (another item's source, which
-                // this center does not list and may even coincide with): weight 0
-                // at a point far from the center, so its term is an exact zero
-                if (m0) { A4.x = ch.x + kFar; A4.z = ch.y; B4.x = ch.z; C4.x = cl.x; C4.z = cl.y; D4.x = cl.z; B4.z = 0.f; }
-                if (m1) { A4.y = ch.x + kFar; A4.w = ch.y; B4.y = ch.z; C4.y = cl.x; C4.w = cl.y; D4.y = cl.z; B4.w = 0.f; }
-            }
-            pair_mixed2<P, false, false, false>(f2_xy(A4), f2_zw(A4), f2_xy(B4), f2_zw(B4), f2_xy(C4), f2_zw(C4),
-                                                f2_xy(D4), z2, z2, z2, ch, cl, e, tn, ts, unused, unused, unused,
-                                                unused, unused);
+#pragma unroll
+        for (int k = 0; k < kPairs / 8; ++k) {
+            const int i = sl + 8 * k;
+            const bool m0 = (unsigned)(i - lo) >= (unsigned)n_in, m1 = (unsigned)(i + kPairs - lo) >= (unsigned)n_in;
+            const float4 A4 = T0[i], B4 = T1[i], C4 = T2[i], D4 = T3[i];
+            pair_mixed2<P, false, false, false, true>(f2_xy(A4), f2_zw(A4), f2_xy(B4), f2_zw(B4), f2_xy(C4),
+                                                      f2_zw(C4), f2_xy(D4), z2, z2, z2, ch, cl, e, tn, ts, unused,
+                                                      unused, unused, unused, unused, m0, m1);
         }
         kahan_add2(as, ac, ts);
         __syncwarp();
