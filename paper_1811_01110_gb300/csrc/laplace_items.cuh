@@ -359,12 +359,15 @@ __device__ __forceinline__ df segment_sum_df(df v, int sub, int L)
     return v;
 }
 
-// Shared-memory tile of the mixed item, two sources per record (pair j holds
-// sources 2j and 2j+1 of the tile): rows {hx0, hx1, hy0, hy1}, {hz0, hz1, w0,
-// w1}, {lx0, lx1, ly0, ly1}, {lz0, lz1, mx0, mx1} and, for the double layer,
-// {my0, my1, mz0, mz1} (m = -n_s), each row tile / 2 records long.  One
-// 16-byte load gives two packed operands.
-__host__ __device__ constexpr int mixed_tile_rows(bool dlp) { return dlp ? 5 : 4; }
+// Shared-memory tile of the mixed item, two sources per record (record j
+// holds sources 2j and 2j+1 of the tile) of five 16-byte words: {hx0, hx1,
+// hy0, hy1}, {hz0, hz1, w0, w1}, {lx0, lx1, ly0, ly1}, {lz0, lz1, mx0, mx1}
+// and, for the double layer, {my0, my1, mz0, mz1} (m = -n_s; unused by the
+// single layer).  One 16-byte load gives two packed operands; the records of
+// a tile are consecutive, so one address and constant offsets reach a
+// record's words, and their odd length (80 bytes) puts the records that
+// eight lanes read at once on distinct banks.  tile / 2 records per tile.
+__host__ __device__ constexpr int mixed_tile_rows(bool) { return 5; }
 // Longest run of source pairs a lane sums in plain FP32 before adding the run
 // to its compensated sums: the rounding error of a plain run grows with its
 // length, so deeper tiles do not lengthen it.
@@ -534,9 +537,7 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         e = g.slot_ef[it.slot_begin + j];
         if (SP) tn = g.slot_nf[it.slot_begin + j];
     }
-    const int tp = tile >> 1;                          // records (source pairs) per row
-    float4 *const T0 = T, *const T1 = T + tp, *const T2 = T + 2 * tp, *const T3 = T + 3 * tp;
-    float4 *const T4 = T + 4 * tp;                     // DLP only
+    constexpr int kRec = mixed_tile_rows(DLP);         // 16-byte words per record
     for (int base = it.src_lo; base < src_hi; base += tile) {
         const int cnt = min(tile, src_hi - base);
         const int npairs = (cnt + 1) >> 1;
@@ -546,11 +547,12 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
             load_mixed_pair<DLP>(g, ev, walk, k0, 2 * q + 1 < cnt ? k0 + 1 : -1, hx, hy, hz, w, lx, ly, lz, nx,
                                  ny, nz);
             float a0, a1, b0, b1;
-            f2_split(hx, a0, a1); f2_split(hy, b0, b1); T0[q] = make_float4(a0, a1, b0, b1);
-            f2_split(hz, a0, a1); f2_split(w, b0, b1);  T1[q] = make_float4(a0, a1, b0, b1);
-            f2_split(lx, a0, a1); f2_split(ly, b0, b1); T2[q] = make_float4(a0, a1, b0, b1);
-            f2_split(lz, a0, a1); f2_split(nx, b0, b1); T3[q] = make_float4(a0, a1, b0, b1);
-            if (DLP) { f2_split(ny, a0, a1); f2_split(nz, b0, b1); T4[q] = make_float4(a0, a1, b0, b1); }
+            float4 *const r = T + q * kRec;
+            f2_split(hx, a0, a1); f2_split(hy, b0, b1); r[0] = make_float4(a0, a1, b0, b1);
+            f2_split(hz, a0, a1); f2_split(w, b0, b1);  r[1] = make_float4(a0, a1, b0, b1);
+            f2_split(lx, a0, a1); f2_split(ly, b0, b1); r[2] = make_float4(a0, a1, b0, b1);
+            f2_split(lz, a0, a1); f2_split(nx, b0, b1); r[3] = make_float4(a0, a1, b0, b1);
+            if (DLP) { f2_split(ny, a0, a1); f2_split(nz, b0, b1); r[4] = make_float4(a0, a1, b0, b1); }
         }
         __syncwarp();
         if (active) {
@@ -561,8 +563,9 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
                 const int q1 = min(npairs, q0 + kPlainRun * L);
                 f2 ts = z2, td = z2, tp2 = z2, unused = z2;
                 for (int q = q0; q < q1; q += L) {
-                    const float4 A = T0[q], B = T1[q], C = T2[q], D = T3[q];
-                    const float4 E = DLP ? T4[q] : zero;
+                    const float4 *const r = T + q * kRec;
+                    const float4 A = r[0], B = r[1], C = r[2], D = r[3];
+                    const float4 E = DLP ? r[4] : zero;
                     pair_mixed2<P, DLP, SP, false>(f2_xy(A), f2_zw(A), f2_xy(B), f2_zw(B), f2_xy(C), f2_zw(C),
                                                    f2_xy(D), f2_zw(D), f2_xy(E), f2_zw(E), ch, cl, e, tn, ts,
                                                    unused, td, unused, tp2, unused);
