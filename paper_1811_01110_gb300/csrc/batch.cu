@@ -134,15 +134,17 @@ batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *item
                     }
                 if (m >= 4) {
                     // four items whose lists are single runs with a short union:
-                    // stage the union once for all four
-                    const int q = lane >> 3;
+                    // stage the union once for all four (item q = lane % 4, so
+                    // that the lanes of the four items that read one staged
+                    // record sit in one quarter-warp)
+                    const int q = lane & 3;
                     const Item mine_it = items[idx + q];
                     int32_t a = 0, b = 0;
                     const bool run = single_run_range(mine_it, walks[idx + q], a, b);
                     const bool all_runs = __all_sync(0xffffffffu, run);
                     int32_t A = a, B = b, len = b - a;
 #pragma unroll
-                    for (int off = 8; off < 32; off <<= 1) {
+                    for (int off = 1; off < 4; off <<= 1) {
                         A = min(A, __shfl_xor_sync(0xffffffffu, A, off));
                         B = max(B, __shfl_xor_sync(0xffffffffu, B, off));
                         len = max(len, __shfl_xor_sync(0xffffffffu, len, off));

@@ -438,8 +438,8 @@ __device__ __forceinline__ bool single_run_range(const Item &it, const WalkStart
 // Four single-target items of one single-layer mixed plan whose sources are
 // the consecutive ranges [a_q, b_q) (one run each), read through their union
 // [A, B): the warp stages the union in tiles of kTile sources (the pair
-// records of the mixed tile) and each item's 8 lanes (q = lane / 8, sl = lane
-// % 8) take, in step with the other items' lanes, every record of the tile,
+// records of the mixed tile) and each item's 8 lanes (q = lane % 4, sl = lane
+// / 4) take, in step with the other items' lanes, every record of the tile,
 // a record half outside the item's range masked to an exact zero (its 1/R
 // taken as 0).  Neighbouring centers of a
 // surface list overlapping windows, so the union is little longer than each:
@@ -452,7 +452,7 @@ __device__ __forceinline__ void laplace_mixed_window4(const DevGeom &g, const De
 {
     constexpr int kPairs = kTile / 2;
     float4 *const T0 = T, *const T1 = T + kPairs, *const T2 = T + 2 * kPairs, *const T3 = T + 3 * kPairs;
-    const int sl = lane & 7;
+    const int sl = lane >> 2;
     const f2 z2 = f2_splat(0.f);
     f2 as = z2, ac = z2, unused = z2;
     const float4 ch = g.slot_chi[it.slot_begin];
@@ -476,7 +476,8 @@ __device__ __forceinline__ void laplace_mixed_window4(const DevGeom &g, const De
         }
         __syncwarp();
         // the four items walk the tile's records in step (lane sl of every item
-        // reads the same record: one shared-memory broadcast serves four), each
+        // reads the same record, and the four such lanes sit in one
+        // quarter-warp: one shared-memory broadcast serves four), each
         // taking the halves that fall in its own sources max(a, base) ..
         // min(b, base + kTile) - 1; a half outside them (another item's source,
         // which this center does not list and may even coincide with) is
@@ -497,7 +498,7 @@ __device__ __forceinline__ void laplace_mixed_window4(const DevGeom &g, const De
     }
     df v = kahan2_df(as, ac);
 #pragma unroll
-    for (int off = 4; off > 0; off >>= 1) v = df_add(v, df_shfl_xor(v, off));
+    for (int off = 16; off >= 4; off >>= 1) v = df_add(v, df_shfl_xor(v, off));   // sl ^ 4, ^ 2, ^ 1
     if (sl == 0) write_item_result<false, false>(g, ev, it, 0, df_to_double(v), 0.0, 0.0);
 }
 
