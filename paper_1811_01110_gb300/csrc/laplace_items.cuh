@@ -349,11 +349,13 @@ __device__ __forceinline__ df warp_sum_df(df v)
     return v;
 }
 
-// Sum over the L lanes of each target's segment (sub = 0 holds the total).
-__device__ __forceinline__ df segment_sum_df(df v, int sub, int L)
+// Sum over the L lanes of each target's segment (sub = 0 holds the total);
+// a target's lanes are `stride` apart (lane = sub * stride + target).
+__device__ __forceinline__ df segment_sum_df(df v, int sub, int L, int stride = 1)
 {
     for (int off = 1; off < L; off <<= 1) {
-        const df u{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+        const df u{__shfl_down_sync(0xffffffffu, v.hi, off * stride),
+                   __shfl_down_sync(0xffffffffu, v.lo, off * stride)};
         if (sub + off < L) v = df_add(v, u);
     }
     return v;
@@ -528,9 +530,12 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
             write_item_result<DLP, SP>(g, ev, it, 0, df_to_double(acc_s), df_to_double(acc_d), df_to_double(acc_p));
         return;
     }
-    const int L = it.L;
-    const int j = lane / L, sub = lane - j * L;
-    const bool active = j < it.n_tgt;
+    // target j = lane % n_tgt, its L lanes n_tgt apart: the lanes of the
+    // item's targets that read one staged record sit together, so that a
+    // shared-memory load serves them in fewer wavefronts
+    const int L = it.L, nt = it.n_tgt;
+    const int sub = lane / nt, j = lane - sub * nt;
+    const bool active = sub < L;
     float4 ch = zero, cl = zero, e = zero, tn = zero;
     if (active) {
         ch = g.slot_chi[it.slot_begin + j];
@@ -578,9 +583,9 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         }
         __syncwarp();
     }
-    const df acc_s = segment_sum_df(kahan2_df(as, ac), sub, L);
-    const df acc_d = DLP ? segment_sum_df(kahan2_df(ds, dc), sub, L) : df{0.f, 0.f};
-    const df acc_p = SP ? segment_sum_df(kahan2_df(ps, pc), sub, L) : df{0.f, 0.f};
+    const df acc_s = segment_sum_df(kahan2_df(as, ac), sub, L, nt);
+    const df acc_d = DLP ? segment_sum_df(kahan2_df(ds, dc), sub, L, nt) : df{0.f, 0.f};
+    const df acc_p = SP ? segment_sum_df(kahan2_df(ps, pc), sub, L, nt) : df{0.f, 0.f};
     if (active && sub == 0)
         write_item_result<DLP, SP>(g, ev, it, j, df_to_double(acc_s), df_to_double(acc_d), df_to_double(acc_p));
 }
