@@ -49,9 +49,11 @@ __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df 
         }
         acc_s = df_add(acc_s, df_mul(wr, b1));
     } else {
+        // the exact n = 1 step taken outside the loop, as in pair_fp64
         df Um{0.f, 0.f}, Uc = one, S2m{0.f, 0.f};
+        if constexpr (P >= 2) { Um = one; Uc = qx; S2m = df_of(df_const(rec_lambda(1))); }
 #pragma unroll
-        for (int n = 1; n < P; ++n) {
+        for (int n = 2; n < P; ++n) {
             S2m = df_add(S2m, df_mul(df_of(df_const(rec_lambda(n))), Uc));
             const df gq = df_mul(df_of(df_const(rec_gamma(n))), q2);
             const df Un = df_sub(df_mul(qx, Uc), df_mul(gq, Um));

@@ -64,10 +64,14 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
         }
         acc_s = fma(wr, b1, acc_s);
     } else {
-        // U_{n-1}, U_n starting at n = 1; S2m accumulates Q'_1..Q'_{P-1}
+        // U_{n-1}, U_n; S2m accumulates Q'_1..Q'_{P-1}.  The n = 1 step is
+        // exact (U_2 = qx since gamma_1 = 0, S2m = lambda_1 U_1 = 1), so for P
+        // >= 2 the loop starts at n = 2 (a product by U_0 = 0 would still cost
+        // two multiplies and an add: IEEE arithmetic does not fold x * 0)
         double Um = 0.0, Uc = 1.0, S2m = 0.0;
+        if constexpr (P >= 2) { Um = 1.0; Uc = qx; S2m = rec_lambda(1); }
 #pragma unroll
-        for (int n = 1; n < P; ++n) {
+        for (int n = 2; n < P; ++n) {
             S2m = fma(rec_lambda(n), Uc, S2m);
             const double Un = fma(qx, Uc, -(rec_gamma(n) * q2) * Um);
             Um = Uc; Uc = Un;
