@@ -64,15 +64,15 @@ def df64_fp32_flops_per_pair(p, dlp=True, sp=False):
     (laplace_df_items.cuh, multi-target items): geometry (s - c as three
     double-float differences, R^2, 1/R, 1/R^2, qx, q2, w/R) 258; the Clenshaw
     single layer 21 + 52 per order step + 21; with the double layer or S'
-    the Q' recurrence 62 per step, its top 61, the closing sums 83, the
-    single layer's accumulation 21 and w/R^3 10; the double layer 167 (two
-    dots, the combination, accumulation), S' 104.  1096 at p = 9 with both
-    layers."""
+    the Q' recurrence 62 per step n = 2..p-1 (the n = 1 step is exact), its
+    top 61, the closing sums 83, the single layer's accumulation 21 and w/R^3
+    10; the double layer 167 (two dots, the combination, accumulation), S'
+    104.  1034 at p = 9 with both layers."""
     geo = 3 * _DF_ADD + _DF_DOT + _DF_RSQRT + _DF_MUL + (_DF_DOT + _DF_MUL) + 2 * _DF_MUL
     q = max(p - 1, 0)
     if not dlp and not sp:
         return geo + (_DF_ADD + _DF_MUL) + (3 * _DF_MUL + 2 * _DF_ADD) * q + (_DF_ADD + _DF_MUL)
-    f = geo + (2 * _DF_ADD + 4 * _DF_MUL) * q
+    f = geo + (2 * _DF_ADD + 4 * _DF_MUL) * max(p - 2, 0)
     if p >= 1:
         f += 5 * _DF_MUL + _DF_ADD                                            # Q'_p, Q'_{p+1}
     f += _DF_ADD + (_DF_MULF + 2 * _DF_ADD) + (2 * _DF_MUL + 2 * _DF_ADD)     # S2, c1, S
@@ -88,7 +88,9 @@ def flops_per_pair(p, precision, dlp=True, sp=False):
     """Algorithmic flops per (target, source) pair (FMA = 2) of the Laplace
     kernels.  Single layer alone: geometry 19 (d, R^2, 1/R, qx, q2), 2 for
     b_{p-1}, 5 per Clenshaw step k = p-2..0, closing 3.  With the double layer or S' (one
-    recurrence for Q'_n): geometry 20, 6 per step n = 1..p-1, the top step
+    recurrence for Q'_n): geometry 20; the recurrence from n = 2 (its n = 1
+    step, U_2 = qx and the first closing sum, is exact), 5 at n = 2 (U_1 = 1)
+    and 6 per step n = 3..p-1; the top step
     and sums 7, sum Q_n from the closing identity 7, accumulation 2; the
     double layer adds 17 (two normal dots, (b - a) S2 - a Q'_{p+1} and its
     accumulation), S' 10 (one dot, the combination, accumulation; +1 for
@@ -98,7 +100,7 @@ def flops_per_pair(p, precision, dlp=True, sp=False):
     if not dlp and not sp:
         f = 19 + (2 + 5 * (p - 1) if p >= 1 else 0) + 3
     else:
-        f = 20 + 6 * max(p - 1, 0) + 16
+        f = 20 + (5 + 6 * (p - 3) if p >= 3 else 0) + 16
         if dlp:
             f += 17
         if sp:

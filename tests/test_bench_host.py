@@ -31,8 +31,9 @@ def test_flop_counts_per_pair():
     sys.path.insert(0, ROOT)
     import bench
     # mixed p = 9 SLP+DLP: the FP64 count plus the float-float geometry and
-    # compensated sums (109 flops per pair)
-    assert bench.flops_per_pair(9, "mixed") == 109
+    # compensated sums (102 flops per pair; FP64 94)
+    assert bench.flops_per_pair(9, "mixed") == 102
+    assert bench.flops_per_pair(9, "fp64") == 94
     assert bench.flops_per_pair(9, "fp64") < bench.flops_per_pair(9, "mixed")
     # more orders, more work; layers add work
     for prec in ("fp64", "mixed", "df64"):
@@ -123,10 +124,10 @@ def test_df64_and_a_priori_flop_counts():
     # the a priori estimate: 6p + 20 single layer, + 4 per pair-term + 20 double layer
     assert bench.survey_flops_per_pair(9) == 134
     assert bench.survey_flops_per_pair(9, dlp=False) == 74
-    # double-float FP32 flops per pair at p = 9: 1096 with both layers, 716 single layer, +104 for S'
-    assert bench.df64_fp32_flops_per_pair(9) == 1096
+    # double-float FP32 flops per pair at p = 9: 1034 with both layers, 716 single layer, +104 for S'
+    assert bench.df64_fp32_flops_per_pair(9) == 1034
     assert bench.df64_fp32_flops_per_pair(9, dlp=False) == 716
-    assert bench.df64_fp32_flops_per_pair(9, sp=True) == 1200
-    # each further order adds one Q' recurrence step (62 FP32 flops)
-    for p in range(2, 21):
+    assert bench.df64_fp32_flops_per_pair(9, sp=True) == 1138
+    # each further order from p = 3 adds one Q' recurrence step (62 FP32 flops)
+    for p in range(3, 21):
         assert bench.df64_fp32_flops_per_pair(p) - bench.df64_fp32_flops_per_pair(p - 1) == 62
