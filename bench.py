@@ -124,12 +124,18 @@ def helmholtz_flops_per_pair(p, dlp=False, sp=False):
       layer's coefficient and step).  Closing: normal dots 17, combination 11,
       e^{iz} and weight 16.
     * S': T'_n forward 4 per step (unless the double layer has it), 7 per
-      order backward, normal dot 10, combination 5, e^{iz} and weight 16."""
+      order backward, normal dot 10, combination 5, e^{iz} and weight 16.
+    * The backward step n = p starts from b_{p+1} = b_{p+2} = 0 and is taken
+      as b_p = c_p: it saves (2p+1)/z and the step's products by zero, 4
+      flops with the single layer alone, 8 with the double layer, 3 more
+      with S'."""
     q = max(p - 1, 0)
     f = 20 + 2 + 3 * q + p + 5 + 16
     f += 14 * p + 4 * q + 17 + 11 + 16 if dlp else 4 * p
     if sp:
         f += 7 * p + (0 if dlp else 4 * q) + 10 + 5 + 16
+    if p >= 1:
+        f -= (8 if dlp else 4) + (3 if sp else 0)
     return f
 
 

@@ -207,8 +207,27 @@ helmholtz_kernel(const DevGeom g, const DevEval ev)
                     if (DLP || SP) Uv[n + 1] = fma(-rec_beta(n), Uv[n - 1], fma(x, Uv[n], Tv[n]));
                 }
                 double bA1 = 0.0, bA2 = 0.0, bD1 = 0.0, bD2 = 0.0, bS1 = 0.0, bS2 = 0.0, a_next = 0.0;
+                if constexpr (P >= 1) {
+                    // n = P: b_{P+1} = b_{P+2} = 0, so b_P = c_P (a product by a
+                    // zero b would still cost an operation: IEEE x * 0 is not 0
+                    // for every x)
+                    constexpr int n = P;
+                    if (DLP) {
+                        const double an = cj[n] * Tv[n];
+                        bA1 = an;
+                        bD1 = fma(kah, (-(n + 1.0) * w) * an, u * (cj[n] * Uv[n]));
+                        a_next = an;
+                    } else {
+                        bA1 = cj[n] * Tv[n];
+                    }
+                    if (SP) {
+                        double hn = fma(Cr, cj[n] * Uv[(DLP || SP) ? n : 0], caj[SP ? n : 0] * Tv[n]);
+                        if (n == 1) hn += Cl;
+                        bS1 = hn;
+                    }
+                }
 #pragma unroll
-                for (int n = P; n >= 1; --n) {
+                for (int n = P - 1; n >= 1; --n) {
                     const double t = (2.0 * n + 1.0) * w;
                     if (DLP) {
                         const double an = cj[n] * Tv[n];
