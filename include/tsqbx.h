@@ -143,6 +143,15 @@ typedef struct {
                                    0 = 1.  Above 1 only for Helmholtz single-layer
                                    plans (else TSQBX_E_UNSUPPORTED); each slot then
                                    holds scratch for that many densities            */
+    int p_unroll;               /* how the order loop of the Laplace FP64 and mixed
+                                   kernels is compiled: 0 = one kernel per order p
+                                   with the recurrences fully unrolled (coefficients
+                                   as immediates); 1, 2 or 4 = one kernel for every
+                                   order, its loop over n unrolled by that factor
+                                   and the coefficients read from constant memory.
+                                   Other values: TSQBX_E_INVAL; nonzero for another
+                                   kernel or precision: TSQBX_E_UNSUPPORTED.  Results
+                                   are the same to rounding either way            */
 } tsqbx_options;
 
 /* ------------------------------------------------------------ geometry */
@@ -407,17 +416,21 @@ TSQBX_API int tsqbx_server_set_laplace_fp64_path(tsqbx_server server, int precis
 /* ------------------------------------------------------------- tuning
  * Work decomposition of a plan: lanes per target (0 = chosen per group from
  * its target and source counts), the cap on per-lane pair iterations of one
- * warp item (longer lists are cut into slices) and the staging depth (sources
- * per shared-memory tile, as tsqbx_options.tile_depth). */
+ * warp item (longer lists are cut into slices), the staging depth (sources
+ * per shared-memory tile, as tsqbx_options.tile_depth) and the order-loop
+ * form (as tsqbx_options.p_unroll). */
 typedef struct {
     int lanes_per_target;
     int max_item_iters;
     float kernel_ms;            /* autotune: measured expansion time of this choice */
     int tile_depth;             /* 32, 64 or 128 (0 in tsqbx_plan_set_tuning: 64)   */
+    int p_unroll;               /* 0, 1, 2 or 4; nonzero only for Laplace FP64 and
+                                   mixed plans (else TSQBX_E_UNSUPPORTED)            */
 } tsqbx_tuning;
 
 /* Autotuner: times candidate decompositions of this plan (slice caps, then
- * lane policies, then tile depths) with CUDA events on the plan's stream, evaluating the DEVICE
+ * lane policies, then tile depths, then, for Laplace FP64 and mixed plans, the
+ * order-loop forms p_unroll 0, 1, 2, 4) with CUDA events on the plan's stream, evaluating the DEVICE
  * density d_density `repeats` times each (after one untimed run), keeps the
  * fastest, records it in the process-wide tuning cache (see
  * TSQBX_FLAG_USE_TUNED) and returns it in *chosen (may be NULL).  Uses the
@@ -427,7 +440,9 @@ TSQBX_API int tsqbx_plan_autotune(tsqbx_plan plan, const void *d_density, int re
                                   tsqbx_tuning *chosen);
 
 /* Install a decomposition (e.g. one found by the autotuner) / read the current
- * one (kernel_ms = 0).  Errors: TSQBX_E_INVAL, TSQBX_E_NOMEM, TSQBX_E_CUDA. */
+ * one (kernel_ms = 0).  Errors: TSQBX_E_INVAL, TSQBX_E_UNSUPPORTED (p_unroll
+ * nonzero for a plan other than Laplace FP64 or mixed), TSQBX_E_NOMEM,
+ * TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_plan_set_tuning(tsqbx_plan plan, const tsqbx_tuning *tuning);
 TSQBX_API int tsqbx_plan_get_tuning(tsqbx_plan plan, tsqbx_tuning *tuning);
 

@@ -60,6 +60,8 @@ struct __align__(16) WalkStart {
 struct DevGeom {
     int64_t n_src = 0, n_tgt = 0, n_items = 0, n_combine = 0, n_parts = 0;
     int32_t tile = kTile;               // staging depth of the one-plan kernels (tile_depth_ok)
+    int32_t p_unroll = 0;               // Laplace FP64/mixed: 0 = per-order kernels, else the
+                                        // runtime-order kernel with its loop unrolled by this
     const Item *items = nullptr;
     const Combine *combine = nullptr;
     // Each group's source list as merged runs of consecutive sources: run r
@@ -147,6 +149,8 @@ __device__ __forceinline__ WalkStart walk_start_of(const DevGeom &g, const Item 
     return WalkStart{r, p0, p1, g.run_src[r]};
 }
 
+// Highest expansion order (TSQBX_P_MAX in tsqbx.h; plan.cu checks that they agree).
+constexpr int kPMax = 20;
 // Most densities one evaluation may carry (tsqbx_submit_multi).
 constexpr int kMaxRhs = 4;
 
@@ -163,6 +167,7 @@ struct DevEval {
     double *part_sp = nullptr;
     int *status = nullptr;              // bit 0: out-of-range source index seen
     double k = 0.0;                     // Helmholtz wavenumber
+    int p = 0;                          // the evaluation's order (read by the runtime-order kernels)
     double *conv_coef = nullptr;        // conventional partial coefficients (scratch)
     // Several densities in one evaluation (Helmholtz single layer only): the
     // w mu of density r starts at wmu_c + r * rhs_src_stride, its output at

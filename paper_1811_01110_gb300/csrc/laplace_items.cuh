@@ -19,6 +19,69 @@
 
 namespace tsqbx {
 
+// Order forms.  A template order P >= 0 compiles one kernel per order with
+// the recurrences fully unrolled and their coefficients as immediates.  P < 0
+// compiles one kernel for every order: the order is the runtime value the
+// pair functions receive (prt), the loops over n are unrolled by -P, and the
+// coefficients are read from the constant-memory table kRec (the same values,
+// so both forms compute the same quantities in the same order).
+struct RecTable {
+    double kappa[kPMax + 2], beta[kPMax + 2], lambda[kPMax + 2], gamma[kPMax + 2];
+    float kappa_f[kPMax + 2], beta_f[kPMax + 2], lambda_f[kPMax + 2],
+        gamma_f[kPMax + 2];
+};
+constexpr RecTable make_rec_table()
+{
+    RecTable t{};
+    for (int n = 0; n < kPMax + 2; ++n) {
+        t.kappa[n] = rec_kappa(n);
+        t.beta[n] = n > 0 ? rec_beta(n) : 0.0;
+        t.lambda[n] = rec_lambda(n);
+        t.gamma[n] = n > 0 ? rec_gamma(n) : 0.0;
+        t.kappa_f[n] = (float)t.kappa[n];
+        t.beta_f[n] = (float)t.beta[n];
+        t.lambda_f[n] = (float)t.lambda[n];
+        t.gamma_f[n] = (float)t.gamma[n];
+    }
+    return t;
+}
+static __constant__ RecTable kRec = make_rec_table();
+
+// for (n = lo; n < hi; ++n) step(n) and for (n = hi - 1; n >= lo; --n)
+// step(n), unrolled completely for a fixed order and by -P for the
+// runtime-order form.
+template <int P, class F>
+__device__ __forceinline__ void order_loop_up(int lo, int hi, F &&step)
+{
+    if constexpr (P >= 0) {
+#pragma unroll
+        for (int n = lo; n < hi; ++n) step(n);
+    } else {
+#pragma unroll (-P)
+        for (int n = lo; n < hi; ++n) step(n);
+    }
+}
+template <int P, class F>
+__device__ __forceinline__ void order_loop_down(int lo, int hi, F &&step)
+{
+    if constexpr (P >= 0) {
+#pragma unroll
+        for (int n = hi - 1; n >= lo; --n) step(n);
+    } else {
+#pragma unroll (-P)
+        for (int n = hi - 1; n >= lo; --n) step(n);
+    }
+}
+template <int P> __device__ __forceinline__ int order_of(int prt) { return P < 0 ? prt : P; }
+template <int P> __device__ __forceinline__ double c_kappa(int n) { if constexpr (P < 0) return kRec.kappa[n]; else return rec_kappa(n); }
+template <int P> __device__ __forceinline__ double c_beta(int n) { if constexpr (P < 0) return kRec.beta[n]; else return rec_beta(n); }
+template <int P> __device__ __forceinline__ double c_lambda(int n) { if constexpr (P < 0) return kRec.lambda[n]; else return rec_lambda(n); }
+template <int P> __device__ __forceinline__ double c_gamma(int n) { if constexpr (P < 0) return kRec.gamma[n]; else return rec_gamma(n); }
+template <int P> __device__ __forceinline__ float c_kappa_f(int n) { if constexpr (P < 0) return kRec.kappa_f[n]; else return (float)rec_kappa(n); }
+template <int P> __device__ __forceinline__ float c_beta_f(int n) { if constexpr (P < 0) return kRec.beta_f[n]; else return (float)rec_beta(n); }
+template <int P> __device__ __forceinline__ float c_lambda_f(int n) { if constexpr (P < 0) return kRec.lambda_f[n]; else return (float)rec_lambda(n); }
+template <int P> __device__ __forceinline__ float c_gamma_f(int n) { if constexpr (P < 0) return kRec.gamma_f[n]; else return (float)rec_gamma(n); }
+
 // One (target, source) pair in FP64: d = s - c, e = t - c, wm = w mu, n = n_s,
 // t = n_t and ent = e.n_t (S').
 //
@@ -46,8 +109,9 @@ template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, double ex, double ey, double ez,
                                           double rho2, double wm, double nx, double ny, double nz,
                                           double tx, double ty, double tz, double ent,
-                                          double &acc_s, double &acc_d, double &acc_p)
+                                          double &acc_s, double &acc_d, double &acc_p, int prt = 0)
 {
+    const int p = order_of<P>(prt);
     const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
     const double rinv = rsqrt(R2);
     const double r2inv = rinv * rinv;
@@ -55,30 +119,31 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
     const double q2 = rho2 * r2inv;
     const double wr = wm * rinv;
     if constexpr (!DLP && !SP) {
-        // b_{k+1}, b_{k+2} at k = P - 2 (b_{P+1} = 0 drops out of b_{P-1})
-        double b1 = P >= 1 ? fma(qx, rec_kappa(P), rec_kappa(P - 1)) : 1.0, b2 = rec_kappa(P);
-#pragma unroll
-        for (int k = P - 2; k >= 0; --k) {
-            const double bk = fma(-(rec_beta(k + 1) * q2), b2, fma(qx, b1, rec_kappa(k)));
+        // b_{k+1}, b_{k+2} at k = p - 2 (b_{p+1} = 0 drops out of b_{p-1})
+        double b1 = p >= 1 ? fma(qx, c_kappa<P>(p), c_kappa<P>(max(p - 1, 0))) : 1.0, b2 = c_kappa<P>(p);
+        order_loop_down<P>(0, p - 1, [&](int k) {
+            const double bk = fma(-(c_beta<P>(k + 1) * q2), b2, fma(qx, b1, c_kappa<P>(k)));
             b2 = b1; b1 = bk;
-        }
+        });
         acc_s = fma(wr, b1, acc_s);
     } else {
-        // U_{n-1}, U_n; S2m accumulates Q'_1..Q'_{P-1}.  The n = 1 step is
-        // exact (U_2 = qx since gamma_1 = 0, S2m = lambda_1 U_1 = 1), so for P
+        // U_{n-1}, U_n; S2m accumulates Q'_1..Q'_{p-1}.  The n = 1 step is
+        // exact (U_2 = qx since gamma_1 = 0, S2m = lambda_1 U_1 = 1), so for p
         // >= 2 the loop starts at n = 2 (a product by U_0 = 0 would still cost
         // two multiplies and an add: IEEE arithmetic does not fold x * 0)
         double Um = 0.0, Uc = 1.0, S2m = 0.0;
-        if constexpr (P >= 2) { Um = 1.0; Uc = qx; S2m = rec_lambda(1); }
-#pragma unroll
-        for (int n = 2; n < P; ++n) {
-            S2m = fma(rec_lambda(n), Uc, S2m);
-            const double Un = fma(qx, Uc, -(rec_gamma(n) * q2) * Um);
+        if (p >= 2) { Um = 1.0; Uc = qx; S2m = c_lambda<P>(1); }
+        order_loop_up<P>(2, p, [&](int n) {
+            S2m = fma(c_lambda<P>(n), Uc, S2m);
+            const double Un = fma(qx, Uc, -(c_gamma<P>(n) * q2) * Um);
             Um = Uc; Uc = Un;
+        });
+        // Uc = U_p, Um = U_{p-1} (p >= 1);  p = 0: Q'_0 = 0, Q'_1 = 1
+        double Qp = 0.0, Qp1 = 1.0;
+        if (p >= 1) {
+            Qp = c_lambda<P>(p) * Uc;
+            Qp1 = c_lambda<P>(p + 1) * fma(qx, Uc, -(c_gamma<P>(p) * q2) * Um);
         }
-        // Uc = U_P, Um = U_{P-1} (P >= 1);  P = 0: Q'_0 = 0, Q'_1 = 1
-        const double Qp = P >= 1 ? rec_lambda(P) * Uc : 0.0;
-        const double Qp1 = P >= 1 ? rec_lambda(P + 1) * fma(qx, Uc, -(rec_gamma(P) * q2) * Um) : 1.0;
         const double S2 = S2m + Qp;
         const double S = fma(fma(-2.0, qx, 1.0) + q2, S2, fma(-q2, Qp, Qp1));
         acc_s = fma(wr, S, acc_s);
@@ -159,7 +224,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
             double nx = 0, ny = 0, nz = 0;
             if (DLP) { const double4_32a n = g.src_n[s]; nx = n.x; ny = n.y; nz = n.z; }
             pair_fp64<P, DLP, SP>(pw.x - c.x, pw.y - c.y, pw.z - c.z, e.x, e.y, e.z, e.w, wm, nx, ny, nz,
-                                  tx, ty, tz, ent, acc_s, acc_d, acc_p);
+                                  tx, ty, tz, ent, acc_s, acc_d, acc_p, ev.p);
         }
         acc_s = warp_sum(acc_s);
         if (DLP) acc_d = warp_sum(acc_d);
@@ -203,7 +268,7 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
             for (int k = sub; k < cnt; k += L)
                 pair_fp64<P, DLP, SP>(Tx[k] - cx, Ty[k] - cy, Tz[k] - cz, ex, ey, ez, rho2, Tw[k],
                                       DLP ? Nx[k] : 0.0, DLP ? Ny[k] : 0.0, DLP ? Nz[k] : 0.0,
-                                      tx, ty, tz, ent, acc_s, acc_d, acc_p);
+                                      tx, ty, tz, ent, acc_s, acc_d, acc_p, ev.p);
         }
         __syncwarp();
     }
@@ -247,8 +312,9 @@ template <int P, bool DLP, bool SP, bool KAHAN = true, bool MASK = false>
 __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2 ly, f2 lz, f2 mx, f2 my, f2 mz,
                                             const float4 &ch, const float4 &cl, const float4 &e,
                                             const float4 &tn, f2 &as, f2 &ac, f2 &ds, f2 &dc, f2 &ps, f2 &pc,
-                                            bool m0 = false, bool m1 = false)
+                                            bool m0 = false, bool m1 = false, int prt = 0)
 {
+    const int p = order_of<P>(prt);
     const f2 one = f2_splat(1.f);
     const f2 dx = add2(sub2(hx, f2_splat(ch.x)), sub2(lx, f2_splat(cl.x)));
     const f2 dy = add2(sub2(hy, f2_splat(ch.y)), sub2(ly, f2_splat(cl.y)));
@@ -276,34 +342,38 @@ __device__ __forceinline__ void pair_mixed2(f2 hx, f2 hy, f2 hz, f2 w, f2 lx, f2
     const f2 wr = mul2(w, rinv);
     if constexpr (!DLP && !SP) {
         // Clenshaw: b_k = kappa_k + qx b_{k+1} - beta_{k+1} q2 b_{k+2}
-        f2 b1 = P >= 1 ? fma2(qx, f2_splat((float)rec_kappa(P)), f2_splat((float)rec_kappa(P - 1))) : one;
-        f2 b2 = f2_splat((float)rec_kappa(P));
-#pragma unroll
-        for (int k = P - 2; k >= 0; --k) {
-            const f2 bq = mul2(f2_splat((float)rec_beta(k + 1)), nq2);
-            const f2 bk = fma2(bq, b2, fma2(qx, b1, f2_splat((float)rec_kappa(k))));
+        f2 b1 = p >= 1 ? fma2(qx, f2_splat(c_kappa_f<P>(p)), f2_splat(c_kappa_f<P>(max(p - 1, 0)))) : one;
+        f2 b2 = f2_splat(c_kappa_f<P>(p));
+        order_loop_down<P>(0, p - 1, [&](int k) {
+            const f2 bq = mul2(f2_splat(c_beta_f<P>(k + 1)), nq2);
+            const f2 bk = fma2(bq, b2, fma2(qx, b1, f2_splat(c_kappa_f<P>(k))));
             b2 = b1; b1 = bk;
-        }
+        });
         sum_fma2<KAHAN>(as, ac, wr, b1);
     } else {
         // U_{n-1}, U_n and S2m = sum_{m<n} Q'_m after the step of order n - 1:
-        // at n = 2 (P >= 2) U_1 = 1, U_2 = qx (gamma_1 = 0), S2m = lambda_1 U_1 = 1
+        // at n = 2 (p >= 2) U_1 = 1, U_2 = qx (gamma_1 = 0), S2m = lambda_1 U_1 = 1
         f2 Um, Uc, S2m;
-        if (P >= 2) { Um = one; Uc = qx; S2m = one; }
+        if (p >= 2) { Um = one; Uc = qx; S2m = one; }
         else { Um = f2_splat(0.f); Uc = one; S2m = f2_splat(0.f); }
-#pragma unroll
-        for (int n = 2; n < P; ++n) {
-            S2m = fma2(f2_splat((float)rec_lambda(n)), Uc, S2m);
-            const f2 gq = mul2(f2_splat((float)rec_gamma(n)), nq2);          // -gamma_n q2
-            const f2 Un = n == 2 ? fma2(qx, Uc, gq) : fma2(gq, Um, mul2(qx, Uc));   // U_1 = 1 at n = 2
+        if (p > 2) {                                   // n = 2, with U_1 = 1
+            S2m = fma2(f2_splat(c_lambda_f<P>(2)), Uc, S2m);
+            const f2 gq = mul2(f2_splat(c_gamma_f<P>(2)), nq2);
+            const f2 Un = fma2(qx, Uc, gq);
             Um = Uc; Uc = Un;
         }
-        // Uc = U_P, Um = U_{P-1} (P >= 1);  P = 0: Q'_0 = 0, Q'_1 = 1
+        order_loop_up<P>(3, p, [&](int n) {
+            S2m = fma2(f2_splat(c_lambda_f<P>(n)), Uc, S2m);
+            const f2 gq = mul2(f2_splat(c_gamma_f<P>(n)), nq2);          // -gamma_n q2
+            const f2 Un = fma2(gq, Um, mul2(qx, Uc));
+            Um = Uc; Uc = Un;
+        });
+        // Uc = U_p, Um = U_{p-1} (p >= 1);  p = 0: Q'_0 = 0, Q'_1 = 1
         f2 Qp = f2_splat(0.f), Qp1 = one;
-        if (P >= 1) {
-            Qp = mul2(f2_splat((float)rec_lambda(P)), Uc);
-            const f2 gq = mul2(f2_splat((float)rec_gamma(P)), nq2);
-            Qp1 = mul2(f2_splat((float)rec_lambda(P + 1)), fma2(gq, Um, mul2(qx, Uc)));
+        if (p >= 1) {
+            Qp = mul2(f2_splat(c_lambda_f<P>(p)), Uc);
+            const f2 gq = mul2(f2_splat(c_gamma_f<P>(p)), nq2);
+            Qp1 = mul2(f2_splat(c_lambda_f<P>(p + 1)), fma2(gq, Um, mul2(qx, Uc)));
         }
         // S = (1 - 2 qx + q2) S2 + Q'_{p+1} - q2 Q'_p with S2 = S2m + Q'_p:
         //   = (1 - 2 qx + q2) S2m + (1 - 2 qx) Q'_p + Q'_{p+1}
@@ -525,7 +595,8 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
         for (int k = it.src_lo + lane; k < src_hi; k += 64) {
             f2 hx, hy, hz, w, lx, ly, lz, nx, ny, nz;
             load_mixed_pair<DLP>(g, ev, walk, k, k + 32 < src_hi ? k + 32 : -1, hx, hy, hz, w, lx, ly, lz, nx, ny, nz);
-            pair_mixed2<P, DLP, SP>(hx, hy, hz, w, lx, ly, lz, nx, ny, nz, ch, cl, e, tn, as, ac, ds, dc, ps, pc);
+            pair_mixed2<P, DLP, SP>(hx, hy, hz, w, lx, ly, lz, nx, ny, nz, ch, cl, e, tn, as, ac, ds, dc, ps, pc,
+                                    false, false, ev.p);
         }
         const df acc_s = warp_sum_df(kahan2_df(as, ac));
         const df acc_d = DLP ? warp_sum_df(kahan2_df(ds, dc)) : df{0.f, 0.f};
@@ -578,7 +649,7 @@ __device__ __forceinline__ void laplace_mixed_item(const DevGeom &g, const DevEv
                     const float4 E = DLP ? r[4] : zero;
                     pair_mixed2<P, DLP, SP, false>(f2_xy(A), f2_zw(A), f2_xy(B), f2_zw(B), f2_xy(C), f2_zw(C),
                                                    f2_xy(D), f2_zw(D), f2_xy(E), f2_zw(E), ch, cl, e, tn, ts,
-                                                   unused, td, unused, tp2, unused);
+                                                   unused, td, unused, tp2, unused, false, false, ev.p);
                 }
                 kahan_add2(as, ac, ts);
                 if (DLP) kahan_add2(ds, dc, td);

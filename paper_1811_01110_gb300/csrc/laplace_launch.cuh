@@ -67,6 +67,25 @@ int launch_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
     return (int)cudaGetLastError();
 }
 
+// The runtime-order kernels (DevGeom::p_unroll = 1, 2 or 4: one kernel for
+// every order, its loop over n unrolled by that factor); the order is e.p.
+template <bool MIXED, bool SP>
+int launch_runtime_order(int unroll, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    if (e.p < 0 || e.p > kPMax) return (int)cudaErrorInvalidValue;
+    const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks == 0) return 0;
+    if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
+    const unsigned b = (unsigned)blocks;
+    switch (unroll) {
+    case 1: dlp ? launch_one<MIXED, -1, true, SP>(b, g, e, s) : launch_one<MIXED, -1, false, SP>(b, g, e, s); break;
+    case 2: dlp ? launch_one<MIXED, -2, true, SP>(b, g, e, s) : launch_one<MIXED, -2, false, SP>(b, g, e, s); break;
+    case 4: dlp ? launch_one<MIXED, -4, true, SP>(b, g, e, s) : launch_one<MIXED, -4, false, SP>(b, g, e, s); break;
+    default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+}
+
 template <bool MIXED, bool SP, int... Ps>
 int dispatch_p(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s,
                std::integer_sequence<int, Ps...>)
@@ -76,11 +95,16 @@ int dispatch_p(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t
     return rc;
 }
 
-// p in [0, 20]; any other p returns cudaErrorInvalidValue.
+// p in [0, 20]; any other p returns cudaErrorInvalidValue.  With
+// g.p_unroll > 0 the runtime-order kernel runs (e.p must equal p).
 template <bool MIXED, bool SP>
 int laplace_dispatch(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
-    return dispatch_p<MIXED, SP>(p, dlp, g, e, s, std::make_integer_sequence<int, 21>{});
+    if (g.p_unroll > 0) {
+        if (e.p != p) return (int)cudaErrorInvalidValue;
+        return launch_runtime_order<MIXED, SP>(g.p_unroll, dlp, g, e, s);
+    }
+    return dispatch_p<MIXED, SP>(p, dlp, g, e, s, std::make_integer_sequence<int, kPMax + 1>{});
 }
 
 }  // namespace

@@ -21,6 +21,8 @@
 
 using namespace tsqbx;
 
+static_assert(kPMax == TSQBX_P_MAX, "the kernels' coefficient tables cover every order");
+
 namespace {
 
 // ------------------------------------------------------------- prep kernels
@@ -159,6 +161,15 @@ TuneKey tune_key(tsqbx_plan P)
     return TuneKey{(int)P->opt.kernel, (int)P->opt.precision, P->opt.p, P->opt.layers, bs, bt};
 }
 
+// The order-loop forms (tsqbx_options.p_unroll): 0 (per-order kernels) or the
+// runtime-order kernel's unroll factor 1, 2 or 4; the latter exist for the
+// Laplace FP64 and mixed kernels.
+bool p_unroll_ok(int u) { return u == 0 || u == 1 || u == 2 || u == 4; }
+bool has_runtime_order(int kernel, int precision)
+{
+    return kernel == TSQBX_LAPLACE && (precision == TSQBX_FP64 || precision == TSQBX_MIXED);
+}
+
 int validate(const tsqbx_geometry *G, const tsqbx_options *o)
 {
     if (!G || !o) return TSQBX_E_INVAL;
@@ -169,7 +180,7 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         return TSQBX_E_INVAL;
     if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64 ||
         o->max_item_iters < 0 || (o->tile_depth != 0 && !tsqbx::tile_depth_ok(o->tile_depth)) ||
-        o->max_rhs < 0 || o->max_rhs > tsqbx::kMaxRhs)
+        o->max_rhs < 0 || o->max_rhs > tsqbx::kMaxRhs || !p_unroll_ok(o->p_unroll))
         return TSQBX_E_INVAL;
     if (o->kernel == TSQBX_HELMHOLTZ) {
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
@@ -181,6 +192,8 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         return TSQBX_E_UNSUPPORTED;
     // several densities per evaluation: the Helmholtz single layer only
     if (o->max_rhs > 1 && (o->kernel != TSQBX_HELMHOLTZ || o->layers != TSQBX_SLP)) return TSQBX_E_UNSUPPORTED;
+    // runtime-order kernels: Laplace FP64 and mixed only
+    if (o->p_unroll != 0 && !has_runtime_order(o->kernel, o->precision)) return TSQBX_E_UNSUPPORTED;
     if (G->n_src < 0 || G->n_ctr < 0 || G->n_tgt < 0 || G->n_group < 0) return TSQBX_E_INVAL;
     if (G->n_src > INT32_MAX || G->n_ctr > INT32_MAX || G->n_tgt > INT32_MAX || G->n_group > INT32_MAX)
         return TSQBX_E_INVAL;
@@ -306,6 +319,7 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     ev.part_dlp = slot.d_part[1];
     ev.part_sp = ev.out_sp ? slot.d_part[2] : nullptr;
     ev.k = k;
+    ev.p = p;
     ev.conv_coef = slot.d_conv;
     if (n > 0) {
         if (o.kernel == TSQBX_HELMHOLTZ) {
@@ -690,16 +704,19 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         int lanes = o->lanes_per_target;
         int64_t max_iters = o->max_item_iters;
         int tile = o->tile_depth ? o->tile_depth : kTile;
-        if ((o->flags & TSQBX_FLAG_USE_TUNED) && !lanes && !max_iters && !o->tile_depth) {
+        int p_unroll = o->p_unroll;
+        if ((o->flags & TSQBX_FLAG_USE_TUNED) && !lanes && !max_iters && !o->tile_depth && !o->p_unroll) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(tune_key(P));
             if (it != g_tune_cache.end()) {
                 lanes = it->second.lanes_per_target;
                 max_iters = it->second.max_item_iters;
                 tile = it->second.tile_depth;
+                p_unroll = it->second.p_unroll;
             }
         }
         P->g.tile = tile;
+        P->g.p_unroll = p_unroll;
         Schedule sched;
         if ((rc = build_schedule(P->groups, lanes, max_iters, P->n_sm, sched)) != TSQBX_OK) {
             delete P;
@@ -817,14 +834,16 @@ int tsqbx_plan_get_tuning(tsqbx_plan P, tsqbx_tuning *t)
     t->max_item_iters = (int)P->sched.max_iters;
     t->kernel_ms = 0.f;
     t->tile_depth = P->g.tile;
+    t->p_unroll = P->g.p_unroll;
     return TSQBX_OK;
 }
 
 int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
 {
     if (!P || !t || t->lanes_per_target < 0 || t->lanes_per_target > 32 || t->max_item_iters < 0 ||
-        (t->tile_depth != 0 && !tile_depth_ok(t->tile_depth)))
+        (t->tile_depth != 0 && !tile_depth_ok(t->tile_depth)) || !p_unroll_ok(t->p_unroll))
         return TSQBX_E_INVAL;
+    if (t->p_unroll != 0 && !has_runtime_order(P->opt.kernel, P->opt.precision)) return TSQBX_E_UNSUPPORTED;
     try {
         DeviceGuard dg(P->opt.device);
         std::lock_guard<std::mutex> lk(P->mu);
@@ -834,6 +853,7 @@ int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
         if (rc) return rc;
         apply_schedule(P, std::move(sched));
         P->g.tile = t->tile_depth ? t->tile_depth : kTile;
+        P->g.p_unroll = t->p_unroll;
         return TSQBX_OK;
     } catch (const CudaFail &f) {
         cudaGetLastError();
@@ -867,36 +887,44 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
             median_ms = acc[reps / 2];
             return TSQBX_OK;
         };
-        struct Cand { int lanes; int64_t iters; int tile; float ms; };
-        Cand best{P->sched.lanes_policy, P->sched.max_iters, P->g.tile, 0.f};
+        struct Cand { int lanes; int64_t iters; int tile; int unroll; float ms; };
+        Cand best{P->sched.lanes_policy, P->sched.max_iters, P->g.tile, P->g.p_unroll, 0.f};
         int rc = time_current(best.ms);
         if (rc) return rc;
-        auto trial = [&](int lanes, int64_t iters, int tile) -> int {
+        auto trial = [&](int lanes, int64_t iters, int tile, int unroll) -> int {
             Schedule sched;
             int r = build_schedule(P->groups, lanes, iters, P->n_sm, sched);
             if (r) return r;
             apply_schedule(P, std::move(sched));
             P->g.tile = tile;
+            P->g.p_unroll = unroll;
             float ms = 0.f;
             if ((r = time_current(ms)) != TSQBX_OK) return r;
-            if (ms < best.ms) best = {lanes, P->sched.max_iters, tile, ms};
+            if (ms < best.ms) best = {lanes, P->sched.max_iters, tile, unroll, ms};
             return TSQBX_OK;
         };
-        // stage 1: slice caps with the current lane policy and depth; stage 2:
-        // lane policies at the best cap; stage 3: tile depths at both
+        // stage 1: slice caps with the current lane policy, depth and order
+        // form; stage 2: lane policies at the best cap; stage 3: tile depths at
+        // both; stage 4 (Laplace FP64 and mixed): the order-loop forms
         for (int64_t iters : {64, 128, 256, 512, 1024, 2048})
-            if ((rc = trial(best.lanes, iters, best.tile)) != TSQBX_OK) return rc;
+            if ((rc = trial(best.lanes, iters, best.tile, best.unroll)) != TSQBX_OK) return rc;
         const int64_t cap = best.iters;
         for (int lanes : {0, 1, 2, 4, 8, 16})
-            if ((rc = trial(lanes, cap, best.tile)) != TSQBX_OK) return rc;
+            if ((rc = trial(lanes, cap, best.tile, best.unroll)) != TSQBX_OK) return rc;
         const int lanes_best = best.lanes;
         for (int tile : {kTileMin, kTile, kTileMax})
-            if ((rc = trial(lanes_best, cap, tile)) != TSQBX_OK) return rc;
+            if ((rc = trial(lanes_best, cap, tile, best.unroll)) != TSQBX_OK) return rc;
+        if (has_runtime_order(P->opt.kernel, P->opt.precision)) {
+            const int tile_best = best.tile;
+            for (int unroll : {0, 1, 2, 4})
+                if ((rc = trial(lanes_best, cap, tile_best, unroll)) != TSQBX_OK) return rc;
+        }
         Schedule sched;
         if ((rc = build_schedule(P->groups, best.lanes, best.iters, P->n_sm, sched)) != TSQBX_OK) return rc;
         apply_schedule(P, std::move(sched));
         P->g.tile = best.tile;
-        tsqbx_tuning t{best.lanes, (int)best.iters, best.ms, best.tile};
+        P->g.p_unroll = best.unroll;
+        tsqbx_tuning t{best.lanes, (int)best.iters, best.ms, best.tile, best.unroll};
         {
             std::lock_guard<std::mutex> tl(g_tune_mu);
             g_tune_cache[tune_key(P)] = t;

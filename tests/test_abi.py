@@ -106,6 +106,11 @@ def test_more_invalid_options_rejected_on_host(L):
         assert _create(g, kernel="helmholtz", k=1.0, max_rhs=rhs) == -1
     assert _create(g, max_rhs=2) == -9                     # several densities: Helmholtz single layer only
     assert _create(g, kernel="helmholtz", k=1.0, layers=("slp", "dlp"), max_rhs=2) == -9
+    for unroll in (-1, 3, 8):                              # order-loop forms: 0, 1, 2 or 4
+        assert _create(g, p_unroll=unroll) == -1
+    # the runtime-order kernels exist for Laplace FP64 and mixed only
+    assert _create(g, kernel="helmholtz", k=1.0, p_unroll=2) == -9
+    assert _create(g, precision="df64", p_unroll=2) == -9
 
 
 def test_invalid_options_rejected_on_host(L):
