@@ -101,7 +101,7 @@ __device__ __forceinline__ void run_window4_mixed(int p, const DevGeom &g, const
 }
 
 template <bool MIXED, bool DLP>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, DLP ? 1 : 8)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, DLP ? 1 : 7)
 batch_laplace_kernel(const BatchPlan *plans, const BatchIO *io, const Item *items, const WalkStart *walks,
                      int64_t n_items, unsigned long long *head)
 {

@@ -535,22 +535,29 @@ __device__ __forceinline__ void laplace_mixed_window4(const DevGeom &g, const De
     const float4 cl = g.slot_clo[it.slot_begin];
     const float4 e = g.slot_ef[it.slot_begin];
     const float4 tn = make_float4(0.f, 0.f, 0.f, 0.f);
+    // record `lane` of a tile holds sources base + lane and base + lane +
+    // kPairs, so that the warp's loads of each array are contiguous.  The
+    // loads of the next tile are issued before the current tile's sums and
+    // stored after them, so their latency overlaps the arithmetic.
+    float4 h0, h1, l0, l1;
+    float w0, w1;
+    auto fetch = [&](int32_t base) {
+        int32_t s0 = base + lane, s1 = s0 + kPairs;
+        w0 = 0.f; w1 = 0.f;
+        if (s0 < B && (unsigned)s0 < (unsigned)g.n_src) w0 = ev.wmu_f[s0];
+        else s0 = 0;
+        if (s1 < B && (unsigned)s1 < (unsigned)g.n_src) w1 = ev.wmu_f[s1];
+        else s1 = s0;
+        h0 = g.src_hi[s0]; h1 = g.src_hi[s1]; l0 = g.src_lo[s0]; l1 = g.src_lo[s1];
+    };
+    fetch(A);
     for (int32_t base = A; base < B; base += kTile) {
-        {   // record `lane` holds sources base + lane and base + lane + kPairs, so that
-            // the warp's loads of each array are contiguous
-            int32_t s0 = base + lane, s1 = s0 + kPairs;
-            float w0 = 0.f, w1 = 0.f;
-            if (s0 < B && (unsigned)s0 < (unsigned)g.n_src) w0 = ev.wmu_f[s0];
-            else s0 = 0;
-            if (s1 < B && (unsigned)s1 < (unsigned)g.n_src) w1 = ev.wmu_f[s1];
-            else s1 = s0;
-            const float4 h0 = g.src_hi[s0], h1 = g.src_hi[s1], l0 = g.src_lo[s0], l1 = g.src_lo[s1];
-            T0[lane] = make_float4(h0.x, h1.x, h0.y, h1.y);
-            T1[lane] = make_float4(h0.z, h1.z, w0, w1);
-            T2[lane] = make_float4(l0.x, l1.x, l0.y, l1.y);
-            T3[lane] = make_float4(l0.z, l1.z, 0.f, 0.f);
-        }
+        T0[lane] = make_float4(h0.x, h1.x, h0.y, h1.y);
+        T1[lane] = make_float4(h0.z, h1.z, w0, w1);
+        T2[lane] = make_float4(l0.x, l1.x, l0.y, l1.y);
+        T3[lane] = make_float4(l0.z, l1.z, 0.f, 0.f);
         __syncwarp();
+        if (base + kTile < B) fetch(base + kTile);
         // the four items walk the tile's records in step (lane sl of every item
         // reads the same record, and the four such lanes sit in one
         // quarter-warp: one shared-memory broadcast serves four), each
