@@ -8,10 +8,12 @@
 // independent warps pops items from the queue with an atomic counter, so a
 // warp that finishes a light item immediately takes the next one; each item
 // carries its plan index, and the order p may differ between plans (the item
-// body is instantiated per p and selected per item).  In single-layer mixed
-// batches up to four consecutive single-target items of one plan run
-// together (8 or 16 lanes each), so that their dependent loads overlap.  The
-// whole sequence --
+// body is instantiated per p and selected per item; the batch always runs
+// the per-order item bodies, whatever a plan's p_unroll).  In single-layer
+// mixed batches up to four consecutive single-target items of one plan run
+// together (8 or 16 lanes each), so that their dependent loads overlap, and
+// four whose lists are single runs with a short union stage that union once
+// (laplace_mixed_window4).  The whole sequence --
 // copy of the per-evaluation pointer table, w mu preparation for every plan,
 // queue reset, persistent kernel, slice combine -- is captured once into a
 // CUDA graph and replayed per evaluation.

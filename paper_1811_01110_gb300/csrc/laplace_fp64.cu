@@ -12,8 +12,14 @@
 // the double layer or S', one recurrence for Q'_n alone (Gegenbauer C^(3/2))
 // gives every sum: sum Q_n and sum (n+1) Q_n follow from sum Q'_n, Q'_p and
 // Q'_{p+1} by two Legendre identities (pair_fp64 in laplace_items.cuh), so the
-// three layers cost one recurrence of three operations per order.
-// None of these forms divides by rho, so t = c needs no special case.
+// three layers cost one recurrence of three operations per order (from n = 2:
+// the n = 1 step is exact).  None of these forms divides by rho, so t = c
+// needs no special case.
+//
+// Order forms: one kernel per order p with the recurrences fully unrolled
+// (DevGeom::p_unroll = 0), or one kernel for every order whose loop over n
+// is unrolled by p_unroll = 1, 2 or 4, its coefficients read from a
+// constant-memory table (laplace_items.cuh); the autotuner picks.
 //
 // Mapping: one warp per work item (a group's target chunk, L lanes per
 // target); the group's sources are staged through shared memory in tiles of
