@@ -152,6 +152,15 @@ typedef struct {
                                    Other values: TSQBX_E_INVAL; nonzero for another
                                    kernel or precision: TSQBX_E_UNSUPPORTED.  Results
                                    are the same to rounding either way            */
+    int fp64_share;             /* double-float (TSQBX_DF64) Laplace plans: work items
+                                   whose index i has (i mod 20) < fp64_share run in
+                                   native FP64 on the FP64 pipe, in the same launch as
+                                   the double-float items on the FP32 pipes (GB300
+                                   runs both pipes at once).  0..20; 0 = all
+                                   double-float.  Each target's result comes from one
+                                   fixed form, FP64 or double-float, both within the
+                                   FP64 bar of 1e-12.  Out of range: TSQBX_E_INVAL;
+                                   nonzero for another plan: TSQBX_E_UNSUPPORTED    */
 } tsqbx_options;
 
 /* ------------------------------------------------------------ geometry */
@@ -426,11 +435,14 @@ typedef struct {
     int tile_depth;             /* 32, 64 or 128 (0 in tsqbx_plan_set_tuning: 64)   */
     int p_unroll;               /* 0, 1, 2 or 4; nonzero only for Laplace FP64 and
                                    mixed plans (else TSQBX_E_UNSUPPORTED)            */
+    int fp64_share;             /* 0..20 as tsqbx_options.fp64_share; nonzero only
+                                   for Laplace df64 plans (else TSQBX_E_UNSUPPORTED) */
 } tsqbx_tuning;
 
 /* Autotuner: times candidate decompositions of this plan (slice caps, then
  * lane policies, then tile depths, then, for Laplace FP64 and mixed plans, the
- * order-loop forms p_unroll 0, 1, 2, 4) with CUDA events on the plan's stream, evaluating the DEVICE
+ * order-loop forms p_unroll 0, 1, 2, 4, and for Laplace df64 plans the FP64
+ * shares 0, 1, 2, 3) with CUDA events on the plan's stream, evaluating the DEVICE
  * density d_density `repeats` times each (after one untimed run), keeps the
  * fastest, records it in the process-wide tuning cache (see
  * TSQBX_FLAG_USE_TUNED) and returns it in *chosen (may be NULL).  Uses the
@@ -441,8 +453,8 @@ TSQBX_API int tsqbx_plan_autotune(tsqbx_plan plan, const void *d_density, int re
 
 /* Install a decomposition (e.g. one found by the autotuner) / read the current
  * one (kernel_ms = 0).  Errors: TSQBX_E_INVAL, TSQBX_E_UNSUPPORTED (p_unroll
- * nonzero for a plan other than Laplace FP64 or mixed), TSQBX_E_NOMEM,
- * TSQBX_E_CUDA. */
+ * nonzero for a plan other than Laplace FP64 or mixed, fp64_share nonzero
+ * for a plan other than Laplace df64), TSQBX_E_NOMEM, TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_plan_set_tuning(tsqbx_plan plan, const tsqbx_tuning *tuning);
 TSQBX_API int tsqbx_plan_get_tuning(tsqbx_plan plan, tsqbx_tuning *tuning);
 

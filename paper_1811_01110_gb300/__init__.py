@@ -77,13 +77,15 @@ def marshal_geometry(g, with_normals=True, with_tgt_normals=False):
 
 
 def make_options(kernel="laplace", layers=("slp",), p=5, k=0.0, precision="fp64", device=0, flags=0,
-                 lanes_per_target=0, n_slots=2, max_item_iters=0, tile_depth=0, max_rhs=0, p_unroll=0):
+                 lanes_per_target=0, n_slots=2, max_item_iters=0, tile_depth=0, max_rhs=0, p_unroll=0,
+                 fp64_share=0):
     mask = 0
     for name in layers:
         mask |= _LAYERS[name]
     return _lib.tsqbx_options(_KERNELS[kernel], mask, int(p), float(k), _PRECISIONS[precision],
                               int(device), int(flags), int(lanes_per_target), int(n_slots),
-                              int(max_item_iters), int(tile_depth), int(max_rhs), int(p_unroll))
+                              int(max_item_iters), int(tile_depth), int(max_rhs), int(p_unroll),
+                              int(fp64_share))
 
 
 class Plan:
@@ -92,7 +94,8 @@ class Plan:
     def __init__(self, geometry, kernel="laplace", layers=("slp",), p=5, k=0.0,
                  precision="fp64", device=0, allow_divergent=False, skip_check=False,
                  lanes_per_target=0, n_slots=2, max_item_iters=0, use_tuned=False,
-                 conventional="off", size_priority=False, tile_depth=0, max_rhs=0, p_unroll=0):
+                 conventional="off", size_priority=False, tile_depth=0, max_rhs=0, p_unroll=0,
+                 fp64_share=0):
         """conventional: "off" (target-specific expansions only), "auto"
         (conventional QBX for the centers the cost model finds cheaper) or
         "all" (conventional QBX for every center).  size_priority: stream
@@ -101,7 +104,9 @@ class Plan:
         densities one submit_multi may carry (Helmholtz single layer).
         p_unroll: 0 = per-order kernels with the recurrences fully unrolled;
         1, 2 or 4 = the runtime-order kernel, its loop over n unrolled by that
-        factor (Laplace FP64 and mixed)."""
+        factor (Laplace FP64 and mixed).  fp64_share: df64 plans, the
+        twentieths of the work items that run in native FP64 on the FP64 pipe
+        beside the double-float items (0..20)."""
         self.kernel = kernel
         self.layers = tuple(layers)
         self.p = int(p)
@@ -117,7 +122,8 @@ class Plan:
                  "all": _lib.TSQBX_FLAG_CONVENTIONAL_ALL}[conventional] | \
                 (_lib.TSQBX_FLAG_SIZE_PRIORITY if size_priority else 0)
         opt = make_options(kernel, self.layers, self.p, k, precision, device, flags,
-                           lanes_per_target, n_slots, max_item_iters, tile_depth, max_rhs, p_unroll)
+                           lanes_per_target, n_slots, max_item_iters, tile_depth, max_rhs, p_unroll,
+                           fp64_share)
         h = ctypes.c_void_p()
         check(lib().tsqbx_plan_create(ctypes.byref(geo), ctypes.byref(opt), ctypes.byref(h)),
               "tsqbx_plan_create")
@@ -166,16 +172,18 @@ class Plan:
         check(lib().tsqbx_plan_autotune(self._h, self._density_addr(density), int(repeats),
                                         ctypes.byref(t)), "tsqbx_plan_autotune")
         return {"lanes_per_target": t.lanes_per_target, "max_item_iters": t.max_item_iters,
-                "tile_depth": t.tile_depth, "p_unroll": t.p_unroll, "kernel_ms": t.kernel_ms}
+                "tile_depth": t.tile_depth, "p_unroll": t.p_unroll, "fp64_share": t.fp64_share,
+                "kernel_ms": t.kernel_ms}
 
     def get_tuning(self):
         t = _lib.tsqbx_tuning()
         check(lib().tsqbx_plan_get_tuning(self._h, ctypes.byref(t)), "tsqbx_plan_get_tuning")
         return {"lanes_per_target": t.lanes_per_target, "max_item_iters": t.max_item_iters,
-                "tile_depth": t.tile_depth, "p_unroll": t.p_unroll}
+                "tile_depth": t.tile_depth, "p_unroll": t.p_unroll, "fp64_share": t.fp64_share}
 
-    def set_tuning(self, lanes_per_target=0, max_item_iters=0, tile_depth=0, p_unroll=0):
-        t = _lib.tsqbx_tuning(int(lanes_per_target), int(max_item_iters), 0.0, int(tile_depth), int(p_unroll))
+    def set_tuning(self, lanes_per_target=0, max_item_iters=0, tile_depth=0, p_unroll=0, fp64_share=0):
+        t = _lib.tsqbx_tuning(int(lanes_per_target), int(max_item_iters), 0.0, int(tile_depth), int(p_unroll),
+                              int(fp64_share))
         check(lib().tsqbx_plan_set_tuning(self._h, ctypes.byref(t)), "tsqbx_plan_set_tuning")
 
     # -- evaluation

@@ -46,7 +46,7 @@ class tsqbx_options(ctypes.Structure):
         ("k", ctypes.c_double), ("precision", ctypes.c_int), ("device", ctypes.c_int),
         ("flags", ctypes.c_uint32), ("lanes_per_target", ctypes.c_int), ("n_slots", ctypes.c_int),
         ("max_item_iters", ctypes.c_int), ("tile_depth", ctypes.c_int), ("max_rhs", ctypes.c_int),
-        ("p_unroll", ctypes.c_int),
+        ("p_unroll", ctypes.c_int), ("fp64_share", ctypes.c_int),
     ]
 
 
@@ -100,7 +100,8 @@ class tsqbx_pipe_peaks(ctypes.Structure):
 
 class tsqbx_tuning(ctypes.Structure):
     _fields_ = [("lanes_per_target", ctypes.c_int), ("max_item_iters", ctypes.c_int),
-                ("kernel_ms", ctypes.c_float), ("tile_depth", ctypes.c_int), ("p_unroll", ctypes.c_int)]
+                ("kernel_ms", ctypes.c_float), ("tile_depth", ctypes.c_int), ("p_unroll", ctypes.c_int),
+                ("fp64_share", ctypes.c_int)]
 
 
 # (name, restype, argtypes) for every entry point declared in include/tsqbx.h

@@ -62,6 +62,8 @@ struct DevGeom {
     int32_t tile = kTile;               // staging depth of the one-plan kernels (tile_depth_ok)
     int32_t p_unroll = 0;               // Laplace FP64/mixed: 0 = per-order kernels, else the
                                         // runtime-order kernel with its loop unrolled by this
+    int32_t fp64_share = 0;             // Laplace df64: items with (index mod 20) below this run
+                                        // in native FP64 on the FP64 pipe (0..20)
     const Item *items = nullptr;
     const Combine *combine = nullptr;
     // Each group's source list as merged runs of consecutive sources: run r

@@ -7,6 +7,7 @@
 
 #include "dfloat.cuh"
 #include "internal.cuh"
+#include "laplace_items.cuh"
 
 namespace tsqbx {
 namespace {
@@ -53,9 +54,9 @@ __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df 
         df Um{0.f, 0.f}, Uc = one, S2m{0.f, 0.f};
         if constexpr (P >= 2) { Um = one; Uc = qx; S2m = df_of(df_const(rec_lambda(1))); }
 #pragma unroll
-        for (int n = 2; n < P; ++n) {
-            S2m = df_add(S2m, df_mul(df_of(df_const(rec_lambda(n))), Uc));
-            const df gq = df_mul(df_of(df_const(rec_gamma(n))), q2);
+        for (int m = 2; m < P; ++m) {          // (n is the source normal here)
+            S2m = df_add(S2m, df_mul(df_of(df_const(rec_lambda(m))), Uc));
+            const df gq = df_mul(df_of(df_const(rec_gamma(m))), q2);
             const df Un = df_sub(df_mul(qx, Uc), df_mul(gq, Um));
             Um = Uc; Uc = Un;
         }
@@ -209,7 +210,15 @@ __device__ __forceinline__ void laplace_df_item(const DevGeom &g, const DevEval 
     if (active && sub == 0) write_df_result<DLP, SP>(g, ev, it, j, vs, vd, vp);
 }
 
-template <int P, bool DLP, bool SP>
+// BOTH_PIPES: items with (index mod 20) < g.fp64_share run the native FP64
+// item body (laplace_items.cuh) on the FP64 pipe, the others the
+// double-float body on the FP32 pipes.  The split is by item index, so the
+// two kinds are spread over the whole launch and share every SM, and each
+// target's result comes from the same body on every run.  The FP64 body
+// reads the same arrays (FP64 sources, w mu, target records) and its
+// staging tile fits in the double-float one (DLP: 7 doubles vs 4 float4 per
+// source; otherwise 4 doubles vs 2 float4).
+template <int P, bool DLP, bool SP, bool BOTH_PIPES = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 laplace_df_kernel(const DevGeom g, const DevEval ev)
 {
@@ -218,6 +227,14 @@ laplace_df_kernel(const DevGeom g, const DevEval ev)
     const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
     if (item >= g.n_items) return;
     float4 *T = smem_df + (size_t)warp * (DLP ? 4 : 2) * g.tile;
+    static_assert((DLP ? 7 : 4) * sizeof(double) <= (DLP ? 4 : 2) * sizeof(float4), "FP64 tile fits");
+    if constexpr (BOTH_PIPES) {
+        if ((int)(item % 20) < g.fp64_share) {
+            laplace_fp64_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], reinterpret_cast<double *>(T),
+                                          g.tile, lane);
+            return;
+        }
+    }
     laplace_df_item<P, DLP, SP>(g, ev, g.items[item], g.item_walk[item], T, g.tile, lane);
 }
 
@@ -226,10 +243,16 @@ int launch_df_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
-    if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
+    if (!tile_depth_ok(g.tile) || g.fp64_share < 0 || g.fp64_share > 20) return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)kWarpsPerBlock * (dlp ? 4 : 2) * g.tile * sizeof(float4);
-    if (dlp) laplace_df_kernel<P, true, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
-    else     laplace_df_kernel<P, false, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
+    const unsigned b = (unsigned)blocks, t = kWarpsPerBlock * 32;
+    if (g.fp64_share > 0) {
+        if (dlp) laplace_df_kernel<P, true, SP, true><<<b, t, smem, s>>>(g, e);
+        else     laplace_df_kernel<P, false, SP, true><<<b, t, smem, s>>>(g, e);
+    } else {
+        if (dlp) laplace_df_kernel<P, true, SP><<<b, t, smem, s>>>(g, e);
+        else     laplace_df_kernel<P, false, SP><<<b, t, smem, s>>>(g, e);
+    }
     return (int)cudaGetLastError();
 }
 

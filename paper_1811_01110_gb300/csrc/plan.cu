@@ -169,6 +169,8 @@ bool has_runtime_order(int kernel, int precision)
 {
     return kernel == TSQBX_LAPLACE && (precision == TSQBX_FP64 || precision == TSQBX_MIXED);
 }
+// FP64 items inside the double-float launch (tsqbx_options.fp64_share).
+bool has_both_pipes(int kernel, int precision) { return kernel == TSQBX_LAPLACE && precision == TSQBX_DF64; }
 
 int validate(const tsqbx_geometry *G, const tsqbx_options *o)
 {
@@ -180,7 +182,8 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         return TSQBX_E_INVAL;
     if (o->lanes_per_target < 0 || o->lanes_per_target > 32 || o->n_slots < 0 || o->n_slots > 64 ||
         o->max_item_iters < 0 || (o->tile_depth != 0 && !tsqbx::tile_depth_ok(o->tile_depth)) ||
-        o->max_rhs < 0 || o->max_rhs > tsqbx::kMaxRhs || !p_unroll_ok(o->p_unroll))
+        o->max_rhs < 0 || o->max_rhs > tsqbx::kMaxRhs || !p_unroll_ok(o->p_unroll) ||
+        o->fp64_share < 0 || o->fp64_share > 20)
         return TSQBX_E_INVAL;
     if (o->kernel == TSQBX_HELMHOLTZ) {
         if (!(o->k > 0.0) || !std::isfinite(o->k)) return TSQBX_E_INVAL;
@@ -194,6 +197,8 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
     if (o->max_rhs > 1 && (o->kernel != TSQBX_HELMHOLTZ || o->layers != TSQBX_SLP)) return TSQBX_E_UNSUPPORTED;
     // runtime-order kernels: Laplace FP64 and mixed only
     if (o->p_unroll != 0 && !has_runtime_order(o->kernel, o->precision)) return TSQBX_E_UNSUPPORTED;
+    // FP64 items inside the double-float launch: Laplace df64 only
+    if (o->fp64_share != 0 && !has_both_pipes(o->kernel, o->precision)) return TSQBX_E_UNSUPPORTED;
     if (G->n_src < 0 || G->n_ctr < 0 || G->n_tgt < 0 || G->n_group < 0) return TSQBX_E_INVAL;
     if (G->n_src > INT32_MAX || G->n_ctr > INT32_MAX || G->n_tgt > INT32_MAX || G->n_group > INT32_MAX)
         return TSQBX_E_INVAL;
@@ -704,8 +709,9 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         int lanes = o->lanes_per_target;
         int64_t max_iters = o->max_item_iters;
         int tile = o->tile_depth ? o->tile_depth : kTile;
-        int p_unroll = o->p_unroll;
-        if ((o->flags & TSQBX_FLAG_USE_TUNED) && !lanes && !max_iters && !o->tile_depth && !o->p_unroll) {
+        int p_unroll = o->p_unroll, fp64_share = o->fp64_share;
+        if ((o->flags & TSQBX_FLAG_USE_TUNED) && !lanes && !max_iters && !o->tile_depth && !o->p_unroll &&
+            !o->fp64_share) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(tune_key(P));
             if (it != g_tune_cache.end()) {
@@ -713,10 +719,12 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
                 max_iters = it->second.max_item_iters;
                 tile = it->second.tile_depth;
                 p_unroll = it->second.p_unroll;
+                fp64_share = it->second.fp64_share;
             }
         }
         P->g.tile = tile;
         P->g.p_unroll = p_unroll;
+        P->g.fp64_share = fp64_share;
         Schedule sched;
         if ((rc = build_schedule(P->groups, lanes, max_iters, P->n_sm, sched)) != TSQBX_OK) {
             delete P;
@@ -835,15 +843,18 @@ int tsqbx_plan_get_tuning(tsqbx_plan P, tsqbx_tuning *t)
     t->kernel_ms = 0.f;
     t->tile_depth = P->g.tile;
     t->p_unroll = P->g.p_unroll;
+    t->fp64_share = P->g.fp64_share;
     return TSQBX_OK;
 }
 
 int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
 {
     if (!P || !t || t->lanes_per_target < 0 || t->lanes_per_target > 32 || t->max_item_iters < 0 ||
-        (t->tile_depth != 0 && !tile_depth_ok(t->tile_depth)) || !p_unroll_ok(t->p_unroll))
+        (t->tile_depth != 0 && !tile_depth_ok(t->tile_depth)) || !p_unroll_ok(t->p_unroll) ||
+        t->fp64_share < 0 || t->fp64_share > 20)
         return TSQBX_E_INVAL;
     if (t->p_unroll != 0 && !has_runtime_order(P->opt.kernel, P->opt.precision)) return TSQBX_E_UNSUPPORTED;
+    if (t->fp64_share != 0 && !has_both_pipes(P->opt.kernel, P->opt.precision)) return TSQBX_E_UNSUPPORTED;
     try {
         DeviceGuard dg(P->opt.device);
         std::lock_guard<std::mutex> lk(P->mu);
@@ -854,6 +865,7 @@ int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
         apply_schedule(P, std::move(sched));
         P->g.tile = t->tile_depth ? t->tile_depth : kTile;
         P->g.p_unroll = t->p_unroll;
+        P->g.fp64_share = t->fp64_share;
         return TSQBX_OK;
     } catch (const CudaFail &f) {
         cudaGetLastError();
@@ -887,44 +899,48 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
             median_ms = acc[reps / 2];
             return TSQBX_OK;
         };
-        struct Cand { int lanes; int64_t iters; int tile; int unroll; float ms; };
-        Cand best{P->sched.lanes_policy, P->sched.max_iters, P->g.tile, P->g.p_unroll, 0.f};
+        struct Cand { int lanes; int64_t iters; int tile; int unroll; int share; float ms; };
+        Cand best{P->sched.lanes_policy, P->sched.max_iters, P->g.tile, P->g.p_unroll, P->g.fp64_share, 0.f};
         int rc = time_current(best.ms);
         if (rc) return rc;
-        auto trial = [&](int lanes, int64_t iters, int tile, int unroll) -> int {
+        auto trial = [&](int lanes, int64_t iters, int tile, int unroll, int share) -> int {
             Schedule sched;
             int r = build_schedule(P->groups, lanes, iters, P->n_sm, sched);
             if (r) return r;
             apply_schedule(P, std::move(sched));
             P->g.tile = tile;
             P->g.p_unroll = unroll;
+            P->g.fp64_share = share;
             float ms = 0.f;
             if ((r = time_current(ms)) != TSQBX_OK) return r;
-            if (ms < best.ms) best = {lanes, P->sched.max_iters, tile, unroll, ms};
+            if (ms < best.ms) best = {lanes, P->sched.max_iters, tile, unroll, share, ms};
             return TSQBX_OK;
         };
         // stage 1: slice caps with the current lane policy, depth and order
         // form; stage 2: lane policies at the best cap; stage 3: tile depths at
         // both; stage 4 (Laplace FP64 and mixed): the order-loop forms
         for (int64_t iters : {64, 128, 256, 512, 1024, 2048})
-            if ((rc = trial(best.lanes, iters, best.tile, best.unroll)) != TSQBX_OK) return rc;
+            if ((rc = trial(best.lanes, iters, best.tile, best.unroll, best.share)) != TSQBX_OK) return rc;
         const int64_t cap = best.iters;
         for (int lanes : {0, 1, 2, 4, 8, 16})
-            if ((rc = trial(lanes, cap, best.tile, best.unroll)) != TSQBX_OK) return rc;
+            if ((rc = trial(lanes, cap, best.tile, best.unroll, best.share)) != TSQBX_OK) return rc;
         const int lanes_best = best.lanes;
         for (int tile : {kTileMin, kTile, kTileMax})
-            if ((rc = trial(lanes_best, cap, tile, best.unroll)) != TSQBX_OK) return rc;
-        if (has_runtime_order(P->opt.kernel, P->opt.precision)) {
-            const int tile_best = best.tile;
+            if ((rc = trial(lanes_best, cap, tile, best.unroll, best.share)) != TSQBX_OK) return rc;
+        const int tile_best = best.tile;
+        if (has_runtime_order(P->opt.kernel, P->opt.precision))
             for (int unroll : {0, 1, 2, 4})
-                if ((rc = trial(lanes_best, cap, tile_best, unroll)) != TSQBX_OK) return rc;
-        }
+                if ((rc = trial(lanes_best, cap, tile_best, unroll, best.share)) != TSQBX_OK) return rc;
+        if (has_both_pipes(P->opt.kernel, P->opt.precision))
+            for (int share : {0, 1, 2, 3})
+                if ((rc = trial(lanes_best, cap, tile_best, best.unroll, share)) != TSQBX_OK) return rc;
         Schedule sched;
         if ((rc = build_schedule(P->groups, best.lanes, best.iters, P->n_sm, sched)) != TSQBX_OK) return rc;
         apply_schedule(P, std::move(sched));
         P->g.tile = best.tile;
         P->g.p_unroll = best.unroll;
-        tsqbx_tuning t{best.lanes, (int)best.iters, best.ms, best.tile, best.unroll};
+        P->g.fp64_share = best.share;
+        tsqbx_tuning t{best.lanes, (int)best.iters, best.ms, best.tile, best.unroll, best.share};
         {
             std::lock_guard<std::mutex> tl(g_tune_mu);
             g_tune_cache[tune_key(P)] = t;

@@ -111,6 +111,10 @@ def test_more_invalid_options_rejected_on_host(L):
     # the runtime-order kernels exist for Laplace FP64 and mixed only
     assert _create(g, kernel="helmholtz", k=1.0, p_unroll=2) == -9
     assert _create(g, precision="df64", p_unroll=2) == -9
+    for share in (-1, 21):                                 # FP64 share of a df64 launch: 0..20
+        assert _create(g, precision="df64", fp64_share=share) == -1
+    assert _create(g, fp64_share=2) == -9                  # FP64 items inside df64 plans only
+    assert _create(g, precision="mixed", fp64_share=2) == -9
 
 
 def test_invalid_options_rejected_on_host(L):

@@ -45,7 +45,7 @@ def test_autotune_keeps_results_and_caches(env, precision, tol):
     with pkg.Plan(g, "laplace", ("slp", "dlp"), p=7, precision=precision, use_tuned=True) as plan2:
         assert plan2.get_tuning() == {"lanes_per_target": t["lanes_per_target"],
                                       "max_item_iters": t["max_item_iters"], "tile_depth": t["tile_depth"],
-                                      "p_unroll": t["p_unroll"]}
+                                      "p_unroll": t["p_unroll"], "fp64_share": t["fp64_share"]}
 
 
 def test_set_tuning_roundtrip(env):
@@ -58,7 +58,7 @@ def test_set_tuning_roundtrip(env):
         for lanes, iters, depth, unroll in ((1, 3, 32, 0), (4, 50, 128, 2), (0, 1, 0, 1), (32, 1000, 64, 4)):
             plan.set_tuning(lanes, iters, depth, unroll)
             assert plan.get_tuning() == {"lanes_per_target": lanes, "max_item_iters": iters,
-                                         "tile_depth": depth or 64, "p_unroll": unroll}
+                                         "tile_depth": depth or 64, "p_unroll": unroll, "fp64_share": 0}
             assert relerr(plan.eval(mu)["slp"], ref) <= 1e-12
         info = plan.info()
         assert info["launches_per_eval"] in (2, 3)
@@ -137,4 +137,53 @@ def test_autotune_searches_the_order_loop_forms(env):
         assert plan.autotune(torch.from_numpy(mu + 0j).cuda(), repeats=1)["p_unroll"] == 0
         with pytest.raises(pkg.TsqbxError) as e:
             plan.set_tuning(0, 0, 0, 2)
+        assert e.value.code == -9
+
+
+@pytest.mark.parametrize("layers", [("slp",), ("slp", "dlp"), ("slp", "dlp", "sp")])
+@pytest.mark.parametrize("share", [1, 5, 10, 20])
+def test_double_float_plans_with_fp64_items(env, layers, share):
+    """Double-float plans whose items with (index mod 20) < fp64_share run
+    the native FP64 body in the same launch: every order 0..20 against the
+    oracle at the FP64 bar, sliced lists, several lane counts; each result
+    the same from run to run."""
+    torch, pkg = env
+    rng = np.random.default_rng(61 + share)
+    g = cloud_geometry(rng, n_ctr=16, n_src=300, q_max=0.6, tgt_per_ctr=4, list_frac=0.7)
+    mu = rng.standard_normal(g.n_src)
+    kw = dict(slp="slp" in layers, dlp="dlp" in layers, sp="sp" in layers)
+    with pkg.Plan(g, "laplace", layers, p=9, precision="df64", fp64_share=share, max_item_iters=3,
+                  lanes_per_target=3) as plan:
+        assert plan.get_tuning()["fp64_share"] == share
+        assert plan.info()["n_items"] >= 20
+        for p in range(0, 21):
+            ref = oracle.tsqbx_laplace(g, p, mu, **kw)
+            a = plan.eval(mu, p=p)
+            for l in layers:
+                if not np.any(ref[l]):
+                    assert not np.any(a[l]), (p, l)
+                    continue
+                assert relerr(a[l], ref[l]) <= 1e-12, (p, l)
+        b = plan.eval(mu, p=20)
+        for l in layers:
+            assert np.array_equal(a[l], b[l])
+
+
+def test_fp64_share_tuning_and_rejection(env):
+    torch, pkg = env
+    rng = np.random.default_rng(67)
+    g = cloud_geometry(rng, n_ctr=30, n_src=600, q_max=0.5, tgt_per_ctr=9, list_frac=0.6)
+    mu = rng.standard_normal(g.n_src)
+    ref = oracle.tsqbx_laplace(g, 9, mu, slp=True, dlp=True)
+    with pkg.Plan(g, "laplace", ("slp", "dlp"), p=9, precision="df64") as plan:
+        t = plan.autotune(torch.from_numpy(mu).cuda(), repeats=2)
+        assert t["fp64_share"] in (0, 1, 2, 3) and t["p_unroll"] == 0
+        out = plan.eval(mu)
+        for l in ("slp", "dlp"):
+            assert relerr(out[l], ref[l]) <= 1e-12
+        plan.set_tuning(0, 0, 0, 0, 7)
+        assert plan.get_tuning()["fp64_share"] == 7
+    with pkg.Plan(g, "laplace", ("slp",), p=9, precision="mixed") as plan:
+        with pytest.raises(pkg.TsqbxError) as e:
+            plan.set_tuning(0, 0, 0, 0, 2)
         assert e.value.code == -9
