@@ -305,8 +305,9 @@ TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
 /* -------------------------------------------------------------- batches
  * Many plans evaluated in ONE persistent, load-balanced launch (the plans'
  * work items merged into one queue sorted by cost; resident warps pop items
- * with an atomic counter).  All plans must be Laplace, on one device, with the
- * same precision and layer mask; their orders p may differ.  A batch
+ * with an atomic counter).  All plans must be Laplace FP64 or mixed (df64:
+ * TSQBX_E_UNSUPPORTED), on one device, with the same precision and layer mask;
+ * their orders p may differ.  A batch
  * snapshots the plans' schedules at creation and uses the plans' device
  * geometry, so the plans must outlive it; its scratch (w mu per plan, partial
  * sums, queue head) is its own, so batch and plan evaluations may interleave
@@ -315,8 +316,9 @@ TSQBX_API int tsqbx_plan_kernel_ms(tsqbx_plan plan, float *ms);
  * lanes each), so their lane sums are reduced in another order than the plan
  * alone reduces them: the two agree to rounding (within the mixed error bar),
  * not bit for bit.  A batch stages sources at the default depth (64 per
- * tile) whatever a plan's own tile_depth; otherwise it reproduces the results
- * of each plan at that depth bit for bit. */
+ * tile) whatever a plan's own tile_depth, and runs the per-order kernels
+ * whatever its p_unroll; otherwise it reproduces the results of each plan at
+ * that depth bit for bit. */
 typedef struct tsqbx_batch_s *tsqbx_batch;
 
 typedef struct {

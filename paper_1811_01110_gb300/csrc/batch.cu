@@ -318,7 +318,7 @@ int tsqbx_batch_create(const tsqbx_plan *plans, int n_plans, int use_graph, tsqb
     for (int i = 0; i < n_plans; ++i) {
         if (!plans[i]) return TSQBX_E_INVAL;
         const tsqbx_options &o = plans[i]->opt;
-        if (o.kernel != TSQBX_LAPLACE) return TSQBX_E_UNSUPPORTED;
+        if (o.kernel != TSQBX_LAPLACE || o.precision == TSQBX_DF64) return TSQBX_E_UNSUPPORTED;
         if (o.device != o0.device || o.precision != o0.precision || o.layers != o0.layers)
             return TSQBX_E_INVAL;
     }

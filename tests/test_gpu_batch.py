@@ -151,3 +151,37 @@ def test_window_items_with_a_source_on_a_neighbours_center(env):
     ref = oracle.tsqbx_laplace(g, 7, mu, slp=True)["slp"]
     assert np.all(np.isfinite(got))
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-6
+
+
+def test_batch_of_plans_with_tuned_order_forms(env):
+    """Plans whose own evaluations use the runtime-order kernel (p_unroll)
+    still batch: the persistent launch runs the per-order item bodies for
+    every plan, within the FP64 bar of the oracle and of each plan alone.
+    Double-float plans do not batch (the persistent kernel has no
+    double-float body)."""
+    torch, pkg = env
+    items = _geoms(57)
+    plans = [pkg.Plan(g, "laplace", ("slp", "dlp"), p=p, precision="fp64", p_unroll=(1, 2, 4, 0, 2)[i])
+             for i, (g, mu, p) in enumerate(items)]
+    try:
+        with pkg.Batch(plans) as batch:
+            dens = [torch.from_numpy(mu).cuda() for g, mu, p in items]
+            outs = [{l: torch.full((g.n_tgt,), np.nan, dtype=torch.float64, device="cuda") for l in ("slp", "dlp")}
+                    for g, mu, p in items]
+            batch.eval_async(dens, outs, stream=torch.cuda.current_stream())
+            torch.cuda.synchronize()
+        for (g, mu, p), plan, o in zip(items, plans, outs):
+            alone = plan.eval(mu)
+            ref = oracle.tsqbx_laplace(g, p, mu, slp=True, dlp=True)
+            for l in ("slp", "dlp"):
+                got = o[l].cpu().numpy()
+                assert np.max(np.abs(got - ref[l])) / np.max(np.abs(ref[l])) <= 1e-12
+                assert np.max(np.abs(got - alone[l])) / np.max(np.abs(alone[l])) <= 1e-13
+    finally:
+        for p_ in plans:
+            p_.close()
+    g, mu, p = items[0]
+    with pkg.Plan(g, "laplace", ("slp",), p=p, precision="df64") as dfp:
+        with pytest.raises(pkg.TsqbxError) as e:
+            pkg.Batch([dfp])
+        assert e.value.code == -9
