@@ -392,11 +392,11 @@ def gpu_selector(dev, local_rank):
 # the default staging depth (64); the timed plans are autotuned.
 # A kernel changed since its capture must map to None here.
 TRAFFIC_BYTES = {
-    ("laplace", "fp64", "slp+dlp"): 74.49e6,
-    ("laplace", "mixed", "slp+dlp"): 55.85e6,
-    ("laplace", "df64", "slp+dlp"): 72.48e6,
+    ("laplace", "fp64", "slp+dlp"): 87.96e6,
+    ("laplace", "mixed", "slp+dlp"): 56.30e6,
+    ("laplace", "df64", "slp+dlp"): 74.76e6,
     ("helmholtz", "fp64", "slp"): 321.79e6,
-    ("batched", "mixed", "slp"): 299.68e6,
+    ("batched", "mixed", "slp"): 299.55e6,
 }
 
 
