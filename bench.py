@@ -59,22 +59,36 @@ def survey_flops_per_pair(p, dlp=True):
 _DF_ADD, _DF_MUL, _DF_MULF, _DF_DOT, _DF_RSQRT = 11, 10, 8, 52, 81
 
 
+def _lambda_is_float(n):
+    """Whether the Q' coefficient lambda_n = prod_{m<n} (2m+1)/m is exactly a
+    float (a dyadic rational with a short enough numerator: n <= 12)."""
+    lam = 1.0
+    for m in range(1, n):
+        lam *= (2.0 * m + 1.0) / m
+    return float(np.float32(lam)) == lam
+
+
 def df64_fp32_flops_per_pair(p, dlp=True, sp=False):
     """FP32 flops per pair (FMA = 2) of the double-float Laplace kernel
     (laplace_df_items.cuh, multi-target items): geometry (s - c as three
     double-float differences, R^2, 1/R, 1/R^2, qx, q2, w/R) 258; the Clenshaw
     single layer 21 + 52 per order step + 21; with the double layer or S'
-    the Q' recurrence 62 per step n = 2..p-1 (the n = 1 step is exact), its
-    top 61, the closing sums 83, the single layer's accumulation 21 and w/R^3
-    10; the double layer 167 (two dots, the combination, accumulation), S'
-    104.  1034 at p = 9 with both layers."""
+    the Q' recurrence 62 per step n = 2..p-1 (the n = 1 step is exact; 60
+    where lambda_n is a float, n <= 12, and its product takes DWTimesFP), its
+    top 61 (57 when lambda_p and lambda_{p+1} are floats), the closing sums
+    83, the single layer's accumulation 21 and w/R^3 10; the double layer 167
+    (two dots, the combination, accumulation), S' 104.  1016 at p = 9 with
+    both layers."""
     geo = 3 * _DF_ADD + _DF_DOT + _DF_RSQRT + _DF_MUL + (_DF_DOT + _DF_MUL) + 2 * _DF_MUL
     q = max(p - 1, 0)
     if not dlp and not sp:
         return geo + (_DF_ADD + _DF_MUL) + (3 * _DF_MUL + 2 * _DF_ADD) * q + (_DF_ADD + _DF_MUL)
-    f = geo + (2 * _DF_ADD + 4 * _DF_MUL) * max(p - 2, 0)
+
+    def lam_mul(n):     # lambda_n times a double-float: DWTimesFP when lambda_n is a float
+        return _DF_MULF if _lambda_is_float(n) else _DF_MUL
+    f = geo + sum(2 * _DF_ADD + 3 * _DF_MUL + lam_mul(n) for n in range(2, p))
     if p >= 1:
-        f += 5 * _DF_MUL + _DF_ADD                                            # Q'_p, Q'_{p+1}
+        f += 3 * _DF_MUL + lam_mul(p) + lam_mul(p + 1) + _DF_ADD            # Q'_p, Q'_{p+1}
     f += _DF_ADD + (_DF_MULF + 2 * _DF_ADD) + (2 * _DF_MUL + 2 * _DF_ADD)     # S2, c1, S
     f += _DF_MUL + _DF_ADD + _DF_MUL                                          # acc_s, w/R^3
     if dlp:

@@ -102,4 +102,11 @@ __host__ __device__ constexpr dfc df_const(double v)
 }
 __device__ __forceinline__ df df_of(dfc c) { return df{c.hi, c.lo}; }
 
+// Product with a compile-time constant: a constant that is itself a float
+// (lo = 0, e.g. the dyadic lambda_n of low order) takes the double-word-
+// times-float algorithm, which skips the products by its zero lo part (IEEE
+// arithmetic does not fold x * 0).  The test folds away once the constant is
+// known.
+__device__ __forceinline__ df df_mul_c(dfc c, df x) { return c.lo == 0.f ? df_mul_f(x, c.hi) : df_mul(df_of(c), x); }
+
 }  // namespace tsqbx

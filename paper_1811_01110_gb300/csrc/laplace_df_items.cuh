@@ -55,16 +55,16 @@ __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df 
         if constexpr (P >= 2) { Um = one; Uc = qx; S2m = df_of(df_const(rec_lambda(1))); }
 #pragma unroll
         for (int m = 2; m < P; ++m) {          // (n is the source normal here)
-            S2m = df_add(S2m, df_mul(df_of(df_const(rec_lambda(m))), Uc));
-            const df gq = df_mul(df_of(df_const(rec_gamma(m))), q2);
+            S2m = df_add(S2m, df_mul_c(df_const(rec_lambda(m)), Uc));
+            const df gq = df_mul_c(df_const(rec_gamma(m)), q2);
             const df Un = df_sub(df_mul(qx, Uc), df_mul(gq, Um));
             Um = Uc; Uc = Un;
         }
         df Qp{0.f, 0.f}, Qp1 = one;
         if (P >= 1) {
-            Qp = df_mul(df_of(df_const(rec_lambda(P))), Uc);
-            const df gq = df_mul(df_of(df_const(rec_gamma(P))), q2);
-            Qp1 = df_mul(df_of(df_const(rec_lambda(P + 1))), df_sub(df_mul(qx, Uc), df_mul(gq, Um)));
+            Qp = df_mul_c(df_const(rec_lambda(P)), Uc);
+            const df gq = df_mul_c(df_const(rec_gamma(P)), q2);
+            Qp1 = df_mul_c(df_const(rec_lambda(P + 1)), df_sub(df_mul(qx, Uc), df_mul(gq, Um)));
         }
         const df S2 = df_add(S2m, Qp);
         // S = (1 - 2 qx + q2) S2 + Q'_{p+1} - q2 Q'_p
