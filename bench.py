@@ -408,7 +408,7 @@ def gpu_selector(dev, local_rank):
 TRAFFIC_BYTES = {
     ("laplace", "fp64", "slp+dlp"): 87.96e6,
     ("laplace", "mixed", "slp+dlp"): 56.30e6,
-    ("laplace", "df64", "slp+dlp"): 74.76e6,
+    ("laplace", "df64", "slp+dlp"): 74.24e6,
     ("helmholtz", "fp64", "slp"): 321.79e6,
     ("batched", "mixed", "slp"): 299.55e6,
 }
