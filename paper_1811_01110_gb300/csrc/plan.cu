@@ -169,6 +169,13 @@ bool has_runtime_order(int kernel, int precision)
 {
     return kernel == TSQBX_LAPLACE && (precision == TSQBX_FP64 || precision == TSQBX_MIXED);
 }
+// Weight of source staging in the per-group lane choice: the mixed kernels'
+// per-pair arithmetic is cheap, so their staging weighs more (measured on the
+// torus: mixed 1.008 -> 0.994 ms at 0.5; df64 best at 0.25).
+double staging_weight(const tsqbx_plan_s *P)
+{
+    return P->opt.precision == TSQBX_MIXED ? kStagingMixed : kStagingDefault;
+}
 // FP64 items inside the double-float launch (tsqbx_options.fp64_share).
 bool has_both_pipes(int kernel, int precision) { return kernel == TSQBX_LAPLACE && precision == TSQBX_DF64; }
 
@@ -726,7 +733,7 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         P->g.p_unroll = p_unroll;
         P->g.fp64_share = fp64_share;
         Schedule sched;
-        if ((rc = build_schedule(P->groups, lanes, max_iters, P->n_sm, sched)) != TSQBX_OK) {
+        if ((rc = build_schedule(P->groups, lanes, max_iters, P->n_sm, sched, staging_weight(P))) != TSQBX_OK) {
             delete P;
             return rc;
         }
@@ -860,7 +867,8 @@ int tsqbx_plan_set_tuning(tsqbx_plan P, const tsqbx_tuning *t)
         std::lock_guard<std::mutex> lk(P->mu);
         for (Slot &s : P->slots) ck(cudaStreamSynchronize(s.stream));
         Schedule sched;
-        int rc = build_schedule(P->groups, t->lanes_per_target, t->max_item_iters, P->n_sm, sched);
+        int rc = build_schedule(P->groups, t->lanes_per_target, t->max_item_iters, P->n_sm, sched,
+                                staging_weight(P));
         if (rc) return rc;
         apply_schedule(P, std::move(sched));
         P->g.tile = t->tile_depth ? t->tile_depth : kTile;
@@ -905,7 +913,7 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
         if (rc) return rc;
         auto trial = [&](int lanes, int64_t iters, int tile, int unroll, int share) -> int {
             Schedule sched;
-            int r = build_schedule(P->groups, lanes, iters, P->n_sm, sched);
+            int r = build_schedule(P->groups, lanes, iters, P->n_sm, sched, staging_weight(P));
             if (r) return r;
             apply_schedule(P, std::move(sched));
             P->g.tile = tile;
@@ -935,7 +943,9 @@ int tsqbx_plan_autotune(tsqbx_plan P, const void *d_density, int repeats, tsqbx_
             for (int share : {0, 1, 2, 3})
                 if ((rc = trial(lanes_best, cap, tile_best, best.unroll, share)) != TSQBX_OK) return rc;
         Schedule sched;
-        if ((rc = build_schedule(P->groups, best.lanes, best.iters, P->n_sm, sched)) != TSQBX_OK) return rc;
+        if ((rc = build_schedule(P->groups, best.lanes, best.iters, P->n_sm, sched, staging_weight(P))) !=
+            TSQBX_OK)
+            return rc;
         apply_schedule(P, std::move(sched));
         P->g.tile = best.tile;
         P->g.p_unroll = best.unroll;

@@ -62,8 +62,12 @@ struct Schedule {
 
 // Half-octave bucket of an item's estimated cost (queue order key).
 int cost_bucket(double cost);
-// Lanes per target chosen for a group (items * (lane iterations + staging)).
-int choose_lanes(int64_t nt, int64_t ns);
+// Lanes per target chosen for a group: the fewest items * (lane iterations +
+// staging + setup), with staging costing `staging` per listed source per 32
+// lanes.  Staging weighs more where the per-pair arithmetic is cheap (the
+// mixed kernels: kStagingMixed) than where it is heavy (FP64, df64).
+constexpr double kStagingDefault = 0.25, kStagingMixed = 0.5;
+int choose_lanes(int64_t nt, int64_t ns, double staging = kStagingDefault);
 // Sources per conventional coefficient-formation item.
 constexpr int64_t kConvSlice = 1024;
 // Cost model (the form of the paper's Table 2, with this GPU's constants):
@@ -81,9 +85,10 @@ int priority_for_work(int64_t n_pairs, int kernel, int precision, int least, int
 // items together keeps its sources in L2; interleaving all surfaces by cost
 // alone swept every surface's sources through L2 in each cost bucket.
 std::vector<int64_t> batch_queue_order(const std::vector<int32_t> &plan_of, const std::vector<double> &cost);
-// Build the schedule; max_iters <= 0 picks the automatic cap.
+// Build the schedule; max_iters <= 0 picks the automatic cap; `staging` as
+// in choose_lanes (used when lanes_policy is 0).
 int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
-                   int n_sm, Schedule &out);
+                   int n_sm, Schedule &out, double staging = kStagingDefault);
 
 struct Slot {
     cudaStream_t stream = nullptr;

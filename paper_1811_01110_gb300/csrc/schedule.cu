@@ -68,27 +68,27 @@ int priority_for_work(int64_t n_pairs, int kernel, int precision, int least, int
     return greatest + level;
 }
 
-int choose_lanes(int64_t nt, int64_t ns)
+int choose_lanes(int64_t nt, int64_t ns, double staging)
 {
     int best = 1;
     double best_cost = 1e300;
     for (int L = 1; L <= 32; ++L) {
         const int64_t tpw = 32 / L;
         const int64_t items = (nt + tpw - 1) / tpw;
-        const double cost = (double)items * ((double)((ns + L - 1) / L) + 0.25 * (double)ns / 32.0 + 4.0);
+        const double cost = (double)items * ((double)((ns + L - 1) / L) + staging * (double)ns / 32.0 + 4.0);
         if (cost < best_cost - 1e-9) { best_cost = cost; best = L; }
     }
     return best;
 }
 
 int build_schedule(const std::vector<GroupWork> &groups, int lanes_policy, int64_t max_iters,
-                   int n_sm, Schedule &out)
+                   int n_sm, Schedule &out, double staging)
 {
     struct Chunk { int64_t q, slot, m; int L; int64_t ns; };
     std::vector<Chunk> chunks;
     int64_t total_iters = 0;
     for (const GroupWork &w : groups) {
-        const int L = lanes_policy ? lanes_policy : choose_lanes(w.nt, w.ns);
+        const int L = lanes_policy ? lanes_policy : choose_lanes(w.nt, w.ns, staging);
         const int64_t tpw = 32 / L;
         for (int64_t b = 0; b < w.nt; b += tpw) {
             chunks.push_back({w.q, w.slot_begin + b, std::min(tpw, w.nt - b), L, w.ns});
