@@ -407,7 +407,7 @@ def gpu_selector(dev, local_rank):
 # A kernel changed since its capture must map to None here.
 TRAFFIC_BYTES = {
     ("laplace", "fp64", "slp+dlp"): 87.96e6,
-    ("laplace", "mixed", "slp+dlp"): 56.30e6,
+    ("laplace", "mixed", "slp+dlp"): 55.96e6,
     ("laplace", "df64", "slp+dlp"): 74.24e6,
     ("helmholtz", "fp64", "slp"): 321.79e6,
     ("batched", "mixed", "slp"): 299.55e6,
