@@ -10,6 +10,16 @@ __attribute__((visibility("default"))) int shim_choose_lanes(int64_t nt, int64_t
     return tsqbx::choose_lanes(nt, ns);
 }
 
+__attribute__((visibility("default"))) int shim_choose_lanes_weighted(int64_t nt, int64_t ns, double staging)
+{
+    return tsqbx::choose_lanes(nt, ns, staging);
+}
+
+__attribute__((visibility("default"))) double shim_staging_weight(int mixed)
+{
+    return mixed ? tsqbx::kStagingMixed : tsqbx::kStagingDefault;
+}
+
 __attribute__((visibility("default"))) int shim_priority_for_work(int64_t n_pairs, int kernel, int precision,
                                                                    int least, int greatest)
 {

@@ -39,6 +39,9 @@ def shim():
     L.shim_build_schedule.argtypes = [ctypes.c_int64, i64p, i64p, i64p, i64p, ctypes.c_int, ctypes.c_int64,
                                       ctypes.c_int, i64p, i32p, f64p, i64p, i32p, i64p, i64p, f64p]
     L.shim_choose_lanes.argtypes = [ctypes.c_int64, ctypes.c_int64]
+    L.shim_choose_lanes_weighted.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_double]
+    L.shim_staging_weight.argtypes = [ctypes.c_int]
+    L.shim_staging_weight.restype = ctypes.c_double
     L.shim_cost_bucket.argtypes = [ctypes.c_double]
     L.shim_priority_for_work.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.shim_conventional_cheaper.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint,
@@ -160,6 +163,21 @@ def test_lane_choice_extremes(shim):
     for nt, ns in ((4, 650), (16, 650), (1, 50), (100, 100000)):
         L = shim.shim_choose_lanes(nt, ns)
         assert 1 <= L <= 32
+
+
+def test_lane_choice_staging_weight(shim):
+    """Staging weighs more for the mixed plans (their per-pair arithmetic is
+    cheap) than for FP64 and df64; a heavier staging weight never picks more
+    lanes per target (fewer lanes: more targets share a staged tile), and the
+    default weight is the unweighted call's."""
+    assert shim.shim_staging_weight(1) > shim.shim_staging_weight(0) > 0
+    w0 = shim.shim_staging_weight(0)
+    for nt, ns in ((4, 650), (10, 456), (21, 547), (53, 318), (7, 29475), (1, 195)):
+        assert shim.shim_choose_lanes_weighted(nt, ns, w0) == shim.shim_choose_lanes(nt, ns)
+        Ls = [shim.shim_choose_lanes_weighted(nt, ns, w) for w in (0.0, 0.25, 0.5, 1.0, 4.0)]
+        assert all(a >= b for a, b in zip(Ls, Ls[1:])), (nt, ns, Ls)
+    # a single target keeps the whole warp whatever the weight
+    assert shim.shim_choose_lanes_weighted(1, 5000, 4.0) == 32
 
 
 @pytest.mark.parametrize("helmholtz,p", [(0, 9), (1, 12)])
