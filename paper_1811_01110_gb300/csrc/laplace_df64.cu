@@ -8,8 +8,13 @@
 // target's center) and forms s - ref and c - ref in FP64 before splitting
 // them into double-floats, so d = s - c keeps ~48 significant bits relative
 // to |d| itself.  The recurrence constants are exact double-float splits of
-// their double values.  Per-lane sums are double-floats; lanes of a target
-// are combined in FP64.
+// their double values (products by the ones that are floats take the cheaper
+// double-word-times-float algorithm).  Per-lane sums are double-floats; lanes
+// of a target are combined in FP64.
+//
+// Both pipes (DevGeom::fp64_share, tuned): items with index mod 20 below the
+// share run the native FP64 item body in the same launch, on the FP64 pipe
+// that the double-float items leave mostly idle.
 #include "laplace_df_items.cuh"
 
 namespace tsqbx {

@@ -3,7 +3,8 @@
 // instantiates the variants it owns: laplace_fp64.cu / laplace_mixed.cu the
 // single/double-layer ones, laplace_fp64_sp.cu / laplace_mixed_sp.cu the ones
 // that also form S' (the target-normal derivative), so the four compile in
-// parallel.
+// parallel.  Besides one kernel per order p, each owns the runtime-order
+// kernels (DevGeom::p_unroll 1, 2, 4; launch_runtime_order).
 #pragma once
 
 #include <utility>
