@@ -578,7 +578,10 @@ TSQBX_API const char *tsqbx_last_error(void);
 /* Static description of a status code. */
 TSQBX_API const char *tsqbx_strerror(int status);
 
-/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+/* Version of this ABI (major * 10000 + minor * 100 + patch).  1.3 added
+ * tsqbx_options.p_unroll / .fp64_share and tsqbx_tuning.p_unroll /
+ * .fp64_share (appended: callers built against 1.2 pass structs of the old
+ * size and must be rebuilt). */
 TSQBX_API int tsqbx_version(void);
 
 #ifdef __cplusplus

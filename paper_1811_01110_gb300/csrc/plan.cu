@@ -439,7 +439,7 @@ tsqbx_plan_s::~tsqbx_plan_s()
 
 extern "C" {
 
-int tsqbx_version(void) { return 10200; }
+int tsqbx_version(void) { return 10300; }
 
 const char *tsqbx_last_error(void) { return t_last_error; }
 

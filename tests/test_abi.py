@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_strerror_and_version(L):
     import paper_1811_01110_gb300 as pkg
-    assert L.tsqbx_version() >= 10000
+    assert L.tsqbx_version() >= 10300          # 1.3: p_unroll and fp64_share in options and tuning
     for code in range(-10, 2):
         assert pkg.strerror(code) != "unknown status"
     assert pkg.strerror(-100) == "unknown status"
