@@ -140,9 +140,11 @@ typedef struct {
                                    or 128; 0 = 64.  Results agree across depths to
                                    rounding (the order of the lanes' sums changes)     */
     int max_rhs;                /* densities one tsqbx_submit_multi may carry, 1..4;
-                                   0 = 1.  Above 1 only for Helmholtz single-layer
-                                   plans (else TSQBX_E_UNSUPPORTED); each slot then
-                                   holds scratch for that many densities            */
+                                   0 = 1.  Above 1 only for single-layer plans of
+                                   the Helmholtz kernel or of the Laplace kernel in
+                                   FP64 or double-float (else TSQBX_E_UNSUPPORTED);
+                                   each slot then holds scratch for that many
+                                   densities                                        */
     int p_unroll;               /* how the order loop of the Laplace FP64 and mixed
                                    kernels is compiled: 0 = one kernel per order p
                                    with the recurrences fully unrolled (coefficients
@@ -271,19 +273,20 @@ TSQBX_API int tsqbx_eval_async_pk(tsqbx_plan plan, int p, double k, const void *
 TSQBX_API int tsqbx_submit(tsqbx_plan plan, const void *density, void *out_slp, void *out_dlp,
                  uint64_t *ticket);
 
-/* Several densities in one evaluation: the single layer of a Helmholtz plan
- * (layers == TSQBX_SLP, created with max_rhs >= n; no conventional centers)
- * for the n densities density[0..n), with order p and wavenumber k as in
- * tsqbx_submit_pk.  The per-pair work of Appendix A's expansion -- geometry,
- * the Legendre and Hankel recurrences, e^{ikR}, the sums over the orders --
+/* Several densities in one evaluation: the single layer of a Helmholtz plan,
+ * or of a Laplace plan in TSQBX_FP64 or TSQBX_DF64 (layers == TSQBX_SLP,
+ * created with max_rhs >= n; no conventional centers), for the n densities
+ * density[0..n), with order p and wavenumber k as in tsqbx_submit_pk.  The
+ * per-pair work of Appendix A's expansion -- geometry, 1/R, the Legendre (and
+ * Helmholtz: Hankel) recurrences, e^{ikR}, the sums over the orders --
  * depends on the geometry, p and k only, so the densities share it and each
- * adds only its own complex weight: n densities cost little more than one.
- * Result i (out_slp[i], layout as tsqbx_submit) is bit-identical to the
- * evaluation of density[i] alone.  Pointers host or device as for
- * tsqbx_submit; one ticket covers all n results (tsqbx_poll).  Errors:
- * TSQBX_E_INVAL (n outside 1..max_rhs, NULL pointers, p or k),
- * TSQBX_E_UNSUPPORTED (not a Helmholtz single-layer plan, or one with
- * conventional centers), TSQBX_E_BUSY, TSQBX_E_CUDA. */
+ * adds only its own weight w_s mu_s (real for Laplace, complex for
+ * Helmholtz): n densities cost little more than one.  Result i (out_slp[i],
+ * layout as tsqbx_submit) is bit-identical to the evaluation of density[i]
+ * alone on the same plan.  Pointers host or device as for tsqbx_submit; one
+ * ticket covers all n results (tsqbx_poll).  Errors: TSQBX_E_INVAL (n
+ * outside 1..max_rhs, NULL pointers, p or k), TSQBX_E_UNSUPPORTED (not such
+ * a plan, or one with conventional centers), TSQBX_E_BUSY, TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_submit_multi(tsqbx_plan plan, int p, double k, int n, const void *const *density,
                                  void *const *out_slp, uint64_t *ticket);
 
@@ -361,8 +364,9 @@ TSQBX_API int tsqbx_batch_info(tsqbx_batch batch, tsqbx_batch_stats *stats);
  * the resident plans fit the HBM budget (idle plans are evicted least recently
  * used).  Started requests run on their own plan slots and streams, so work
  * that arrives while other requests are on the GPU overlaps with them
- * (continuous batching).  Queued Helmholtz single-layer requests with the same
- * geometry, order and wavenumber are started together, up to four, as one
+ * (continuous batching).  Queued single-layer requests (Helmholtz, or Laplace
+ * in FP64 or double-float) with the same geometry, precision, order and
+ * (Helmholtz) wavenumber are started together, up to four, as one
  * multi-density evaluation (tsqbx_submit_multi): each result is bit-identical
  * to the request evaluated alone.  A worker thread owned by the server does
  * the admission and completion bookkeeping. */
@@ -581,7 +585,9 @@ TSQBX_API const char *tsqbx_strerror(int status);
 /* Version of this ABI (major * 10000 + minor * 100 + patch).  1.3 added
  * tsqbx_options.p_unroll / .fp64_share and tsqbx_tuning.p_unroll /
  * .fp64_share (appended: callers built against 1.2 pass structs of the old
- * size and must be rebuilt). */
+ * size and must be rebuilt).  1.4 accepts max_rhs > 1, and so
+ * tsqbx_submit_multi, for Laplace single-layer plans in FP64 and
+ * double-float (no struct changed). */
 TSQBX_API int tsqbx_version(void);
 
 #ifdef __cplusplus

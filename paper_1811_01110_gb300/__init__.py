@@ -101,7 +101,8 @@ class Plan:
         "all" (conventional QBX for every center).  size_priority: stream
         priority from the plan's work (TSQBX_FLAG_SIZE_PRIORITY).  tile_depth:
         sources staged per warp tile (32, 64 or 128; 0 = 64).  max_rhs:
-        densities one submit_multi may carry (Helmholtz single layer).
+        densities one submit_multi may carry (single-layer plans: Helmholtz,
+        or Laplace in FP64 or df64).
         p_unroll: 0 = per-order kernels with the recurrences fully unrolled;
         1, 2 or 4 = the runtime-order kernel, its loop over n unrolled by that
         factor (Laplace FP64 and mixed).  fp64_share: df64 plans, the
@@ -265,11 +266,13 @@ class Plan:
 
     def submit_multi(self, densities, p=None, k=None, outs=None):
         """tsqbx_submit_multi: the single layer for several densities in one
-        evaluation (Helmholtz single-layer plans created with max_rhs);
-        returns (ticket, [{"slp": out} per density]), valid once poll()
-        returns True."""
+        evaluation (single-layer plans created with max_rhs: Helmholtz, or
+        Laplace in FP64 or df64); returns (ticket, [{"slp": out} per
+        density]), valid once poll() returns True."""
         n = len(densities)
-        cw = np.complex128
+        helm = self.kernel == "helmholtz"
+        cw = np.complex128 if helm else np.float64
+        esz = 16 if helm else 8
         keep = []
         d_addr = (ctypes.c_void_p * n)()
         o_addr = (ctypes.c_void_p * n)()
@@ -278,15 +281,16 @@ class Plan:
             for d in densities:
                 if _is_torch(d) and d.is_cuda:
                     import torch
-                    outs.append({"slp": torch.empty(self.n_tgt, dtype=torch.complex128, device=d.device)})
+                    outs.append({"slp": torch.empty(self.n_tgt, dtype=torch.complex128 if helm else torch.float64,
+                                                    device=d.device)})
                 else:
                     outs.append({"slp": np.empty(self.n_tgt, dtype=cw)})
         for i, d in enumerate(densities):
             if not _is_torch(d):
                 d = np.ascontiguousarray(d, dtype=cw)
             keep.append(d)
-            d_addr[i] = _addr(d, self.n_src * 16, "density").value
-            o_addr[i] = _addr(outs[i]["slp"], self.n_tgt * 16, "out_slp").value
+            d_addr[i] = _addr(d, self.n_src * esz, "density").value
+            o_addr[i] = _addr(outs[i]["slp"], self.n_tgt * esz, "out_slp").value
         t = ctypes.c_uint64()
         pp = self.p if p is None else int(p)
         kk = self.k if k is None else float(k)

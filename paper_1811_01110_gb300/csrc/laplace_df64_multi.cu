@@ -1,0 +1,177 @@
+// laplace_df64_multi.cu -- the double-float Laplace single layer (arithmetic
+// in laplace_df64.cu) for 2..kMaxRhs densities in one launch.  As in
+// laplace_multi.cu, the per-pair value S / R depends on the geometry and the
+// order alone; each density adds its own w mu (one double-float product by
+// 1/R, one by S, one double-float sum per pair).  Same items, lanes,
+// arithmetic and both-pipes split (DevGeom::fp64_share) as the single-density
+// double-float kernel, so each result is bit-identical to the evaluation of
+// its density alone.
+#include <utility>
+
+#include "laplace_df_items.cuh"
+
+namespace tsqbx {
+namespace {
+
+template <int P>
+__device__ __forceinline__ void pair_df_multi(const df3 &d, const df3 &e, df rho2, const df (&wm)[kMaxRhs],
+                                              df (&acc)[kMaxRhs], int nr)
+{
+    df rinv, r2inv, qx, q2;
+    pair_geom_df(d, e, rho2, rinv, r2inv, qx, q2);
+    const df S = slp_clenshaw_df<P>(qx, q2);
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r)
+        if (r < nr) acc[r] = df_add(acc[r], df_mul(df_mul(wm[r], rinv), S));
+}
+
+// laplace_df_item<P, false, false> with one double-float accumulator per
+// density.  T: rows of `tile` float4 records, {x, y, z, w mu_0} hi parts and
+// lo parts (relative to the item's reference point), then the hi, lo pairs of
+// {w mu_1, w mu_2} and {w mu_3, unused}.
+template <int P>
+__device__ __forceinline__ void laplace_df_multi_item(const DevGeom &g, const DevEval &ev, const Item &it,
+                                                      const WalkStart &ws, float4 *T, const int tile,
+                                                      const int lane)
+{
+    ListWalk walk(g, ws);
+    const int src_hi = it.src_hi;
+    const int nr = ev.n_rhs;
+    const int64_t stride = ev.rhs_src_stride;
+    const df zero{0.f, 0.f};
+    df acc[kMaxRhs] = {zero, zero, zero, zero};
+    if (it.n_tgt == 1) {                                   // direct loads, all 32 lanes
+        const double4_32a c = g.slot_c[it.slot_begin];
+        const double4_32a e4 = g.slot_e[it.slot_begin];
+        const df3 e = df3_from(e4.x, e4.y, e4.z);
+        const df rho2 = df_from_double(e4.w);
+#pragma unroll 1
+        for (int k = it.src_lo + lane; k < src_hi; k += 32) {
+            int s = walk.at(k);
+            const bool ok = (unsigned)s < (unsigned)g.n_src;
+            if (!ok) { atomicOr(ev.status, 1); s = 0; }
+            df wm[kMaxRhs];
+#pragma unroll
+            for (int r = 0; r < kMaxRhs; ++r) wm[r] = df_from_double(ok && r < nr ? ev.wmu[r * stride + s] : 0.0);
+            const double4_32a pw = g.src_pw[s];
+            const df3 d = df3_from(pw.x - c.x, pw.y - c.y, pw.z - c.z);
+            pair_df_multi<P>(d, e, rho2, wm, acc, nr);
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxRhs; ++r)
+            if (r < nr) {
+                double v = df_to_double(acc[r]);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0) write_multi_result(g, ev, it, 0, r, v);
+            }
+        return;
+    }
+    const int L = it.L;
+    const int j = lane / L, sub = lane - j * L;
+    const bool active = j < it.n_tgt;
+    const double4_32a ref = g.slot_c[it.slot_begin];      // item reference point
+    const df3 zero3{zero, zero, zero};
+    df3 crel = zero3, e = zero3;
+    df rho2 = zero;
+    if (active) {
+        const double4_32a c = g.slot_c[it.slot_begin + j];
+        const double4_32a e4 = g.slot_e[it.slot_begin + j];
+        crel = df3_from(c.x - ref.x, c.y - ref.y, c.z - ref.z);
+        e = df3_from(e4.x, e4.y, e4.z);
+        rho2 = df_from_double(e4.w);
+    }
+    float4 *const T0 = T, *const T1 = T + tile, *const T2 = T + 2 * tile, *const T3 = T + 3 * tile;
+    for (int base = it.src_lo; base < src_hi; base += tile) {
+        const int cnt = min(tile, src_hi - base);
+        for (int k = lane; k < cnt; k += 32) {
+            int s = walk.at(base + k);
+            const bool ok = (unsigned)s < (unsigned)g.n_src;
+            if (!ok) { atomicOr(ev.status, 1); s = 0; }
+            const double4_32a pw = g.src_pw[s];
+            const df3 r = df3_from(pw.x - ref.x, pw.y - ref.y, pw.z - ref.z);
+            const df w0 = df_from_double(ok ? ev.wmu[s] : 0.0);
+            const df w1 = df_from_double(ok ? ev.wmu[stride + s] : 0.0);
+            const df w2 = nr > 2 ? df_from_double(ok ? ev.wmu[2 * stride + s] : 0.0) : zero;
+            T0[k] = make_float4(r.x.hi, r.y.hi, r.z.hi, w0.hi);
+            T1[k] = make_float4(r.x.lo, r.y.lo, r.z.lo, w0.lo);
+            T2[k] = make_float4(w1.hi, w1.lo, w2.hi, w2.lo);
+            if (nr > 3) {
+                const df w3 = df_from_double(ok ? ev.wmu[3 * stride + s] : 0.0);
+                T3[k] = make_float4(w3.hi, w3.lo, 0.f, 0.f);
+            }
+        }
+        __syncwarp();
+        if (active) {
+            for (int k = sub; k < cnt; k += L) {
+                const float4 a = T0[k], b = T1[k], w12 = T2[k];
+                const float4 w3 = nr > 3 ? T3[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const df3 d{df_sub(df{a.x, b.x}, crel.x), df_sub(df{a.y, b.y}, crel.y),
+                            df_sub(df{a.z, b.z}, crel.z)};
+                const df wm[kMaxRhs] = {df{a.w, b.w}, df{w12.x, w12.y}, df{w12.z, w12.w}, df{w3.x, w3.y}};
+                pair_df_multi<P>(d, e, rho2, wm, acc, nr);
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r)
+        if (r < nr) {
+            double v = df_to_double(acc[r]);
+            for (int off = 1; off < L; off <<= 1) {
+                const double t = __shfl_down_sync(0xffffffffu, v, off);
+                if (sub + off < L) v += t;
+            }
+            if (active && sub == 0) write_multi_result(g, ev, it, j, r, v);
+        }
+}
+
+// Items with (index mod 20) < g.fp64_share run the native FP64 body, as in
+// laplace_df_kernel; its staging rows (3 + kMaxRhs doubles per source) fit in
+// the double-float ones (4 float4).
+template <int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+laplace_df_multi_kernel(const DevGeom g, const DevEval ev)
+{
+    extern __shared__ __align__(16) float4 smem_dfm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    if (item >= g.n_items) return;
+    float4 *T = smem_dfm + (size_t)warp * 4 * g.tile;
+    static_assert((3 + kMaxRhs) * sizeof(double) <= 4 * sizeof(float4), "FP64 multi tile fits");
+    if ((int)(item % 20) < g.fp64_share) {
+        laplace_fp64_multi_item<P>(g, ev, g.items[item], g.item_walk[item], reinterpret_cast<double *>(T), g.tile,
+                                   lane);
+        return;
+    }
+    laplace_df_multi_item<P>(g, ev, g.items[item], g.item_walk[item], T, g.tile, lane);
+}
+
+template <int P>
+int launch_df_multi_p(const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks == 0) return 0;
+    const size_t smem = (size_t)kWarpsPerBlock * 4 * g.tile * sizeof(float4);
+    laplace_df_multi_kernel<P><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
+    return (int)cudaGetLastError();
+}
+
+template <int... Ps>
+int dispatch_df_multi(int p, const DevGeom &g, const DevEval &e, cudaStream_t s, std::integer_sequence<int, Ps...>)
+{
+    int rc = (int)cudaErrorInvalidValue;
+    ((p == Ps ? (rc = launch_df_multi_p<Ps>(g, e, s), 0) : 0), ...);
+    return rc;
+}
+
+}  // namespace
+
+int launch_laplace_df64_multi(int p, const DevGeom &g, const DevEval &e, cudaStream_t s)
+{
+    if (e.n_rhs < 2 || e.n_rhs > kMaxRhs || !tile_depth_ok(g.tile) || g.fp64_share < 0 || g.fp64_share > 20)
+        return (int)cudaErrorInvalidValue;
+    return dispatch_df_multi(p, g, e, s, std::make_integer_sequence<int, kPMax + 1>{});
+}
+
+}  // namespace tsqbx

@@ -26,29 +26,44 @@ __device__ __forceinline__ df df_dot(const df3 &a, const df3 &b)
     return df_add(df_add(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_mul(a.z, b.z));
 }
 
+// The pair's geometry in double-float: 1/R, 1/R^2, qx and q2.
+__device__ __forceinline__ void pair_geom_df(const df3 &d, const df3 &e, df rho2, df &rinv, df &r2inv, df &qx,
+                                             df &q2)
+{
+    const df R2 = df_dot(d, d);
+    rinv = df_rsqrt(R2);
+    r2inv = df_mul(rinv, rinv);
+    qx = df_mul(df_dot(d, e), r2inv);
+    q2 = df_mul(rho2, r2inv);
+}
+
+// The single layer's sum S = b_0 by Clenshaw's recurrence, as in pair_fp64.
+template <int P>
+__device__ __forceinline__ df slp_clenshaw_df(df qx, df q2)
+{
+    df b2 = df_of(df_const(rec_kappa(P)));
+    df b1 = P >= 1 ? df_add(df_of(df_const(rec_kappa(P - 1))), df_mul(qx, b2)) : df{1.f, 0.f};
+#pragma unroll
+    for (int k = P - 2; k >= 0; --k) {
+        const df bq = df_mul(df_of(df_const(rec_beta(k + 1))), q2);
+        const df bk = df_sub(df_add(df_of(df_const(rec_kappa(k))), df_mul(qx, b1)), df_mul(bq, b2));
+        b2 = b1; b1 = bk;
+    }
+    return b1;
+}
+
 // One pair; tn = n_t and en = e.n_t (S' only).  Same two recurrences and
 // closing sums as pair_fp64 (laplace_items.cuh), in double-float.
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df wm, const df3 &n, const df3 &tn,
                                         df en, df &acc_s, df &acc_d, df &acc_p)
 {
-    const df R2 = df_dot(d, d);
-    const df rinv = df_rsqrt(R2);
-    const df r2inv = df_mul(rinv, rinv);
-    const df qx = df_mul(df_dot(d, e), r2inv);
-    const df q2 = df_mul(rho2, r2inv);
+    df rinv, r2inv, qx, q2;
+    pair_geom_df(d, e, rho2, rinv, r2inv, qx, q2);
     const df wr = df_mul(wm, rinv);
     const df one{1.f, 0.f};
     if constexpr (!DLP && !SP) {
-        df b2 = df_of(df_const(rec_kappa(P)));                 // Clenshaw, as in pair_fp64
-        df b1 = P >= 1 ? df_add(df_of(df_const(rec_kappa(P - 1))), df_mul(qx, b2)) : one;
-#pragma unroll
-        for (int k = P - 2; k >= 0; --k) {
-            const df bq = df_mul(df_of(df_const(rec_beta(k + 1))), q2);
-            const df bk = df_sub(df_add(df_of(df_const(rec_kappa(k))), df_mul(qx, b1)), df_mul(bq, b2));
-            b2 = b1; b1 = bk;
-        }
-        acc_s = df_add(acc_s, df_mul(wr, b1));
+        acc_s = df_add(acc_s, df_mul(wr, slp_clenshaw_df<P>(qx, q2)));
     } else {
         // the exact n = 1 step taken outside the loop, as in pair_fp64
         df Um{0.f, 0.f}, Uc = one, S2m{0.f, 0.f};

@@ -105,6 +105,30 @@ template <int P> __device__ __forceinline__ float c_gamma_f(int n) { if constexp
 //   S'            n_t.grad_t (S/R) = (1/R^3) [ (d.n_t) S2 - (e.n_t) S2m ],
 // a = d.n_s, b = e.n_s.  The closing sums cancel at most by a factor of a few
 // hundred over rho/R <= 0.9, orders 0..20, a cost of ~2e-14 in FP64.
+// The pair's geometry: 1/R, 1/R^2, qx = (d.e)/R^2 and q2 = rho^2/R^2.
+__device__ __forceinline__ void pair_geom_fp64(double dx, double dy, double dz, double ex, double ey, double ez,
+                                               double rho2, double &rinv, double &r2inv, double &qx, double &q2)
+{
+    const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    rinv = rsqrt(R2);
+    r2inv = rinv * rinv;
+    qx = fma(dx, ex, fma(dy, ey, dz * ez)) * r2inv;
+    q2 = rho2 * r2inv;
+}
+
+// The single layer's sum S = b_0 by Clenshaw's backward recurrence (order p).
+template <int P>
+__device__ __forceinline__ double slp_clenshaw_fp64(double qx, double q2, int p)
+{
+    // b_{k+1}, b_{k+2} at k = p - 2 (b_{p+1} = 0 drops out of b_{p-1})
+    double b1 = p >= 1 ? fma(qx, c_kappa<P>(p), c_kappa<P>(max(p - 1, 0))) : 1.0, b2 = c_kappa<P>(p);
+    order_loop_down<P>(0, p - 1, [&](int k) {
+        const double bk = fma(-(c_beta<P>(k + 1) * q2), b2, fma(qx, b1, c_kappa<P>(k)));
+        b2 = b1; b1 = bk;
+    });
+    return b1;
+}
+
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, double ex, double ey, double ez,
                                           double rho2, double wm, double nx, double ny, double nz,
@@ -112,20 +136,11 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
                                           double &acc_s, double &acc_d, double &acc_p, int prt = 0)
 {
     const int p = order_of<P>(prt);
-    const double R2 = fma(dx, dx, fma(dy, dy, dz * dz));
-    const double rinv = rsqrt(R2);
-    const double r2inv = rinv * rinv;
-    const double qx = fma(dx, ex, fma(dy, ey, dz * ez)) * r2inv;
-    const double q2 = rho2 * r2inv;
+    double rinv, r2inv, qx, q2;
+    pair_geom_fp64(dx, dy, dz, ex, ey, ez, rho2, rinv, r2inv, qx, q2);
     const double wr = wm * rinv;
     if constexpr (!DLP && !SP) {
-        // b_{k+1}, b_{k+2} at k = p - 2 (b_{p+1} = 0 drops out of b_{p-1})
-        double b1 = p >= 1 ? fma(qx, c_kappa<P>(p), c_kappa<P>(max(p - 1, 0))) : 1.0, b2 = c_kappa<P>(p);
-        order_loop_down<P>(0, p - 1, [&](int k) {
-            const double bk = fma(-(c_beta<P>(k + 1) * q2), b2, fma(qx, b1, c_kappa<P>(k)));
-            b2 = b1; b1 = bk;
-        });
-        acc_s = fma(wr, b1, acc_s);
+        acc_s = fma(wr, slp_clenshaw_fp64<P>(qx, q2, p), acc_s);
     } else {
         // U_{n-1}, U_n; S2m accumulates Q'_1..Q'_{p-1}.  The n = 1 step is
         // exact (U_2 = qx since gamma_1 = 0, S2m = lambda_1 U_1 = 1), so for p
@@ -276,6 +291,116 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
     if (DLP) acc_d = segment_sum(acc_d, sub, L);
     if (SP) acc_p = segment_sum(acc_p, sub, L);
     if (active && sub == 0) write_item_result<DLP, SP>(g, ev, it, j, acc_s, acc_d, acc_p);
+}
+
+// Several densities at once (DevEval::n_rhs = nr in 2..kMaxRhs): the single
+// layer's per-pair value S / R depends on the geometry and the order alone,
+// so the densities share it and each adds its own w mu with the same two
+// operations as pair_fp64 (wr = w mu / R, acc += wr S).
+template <int P>
+__device__ __forceinline__ void pair_fp64_multi(double dx, double dy, double dz, double ex, double ey, double ez,
+                                                double rho2, const double (&wm)[kMaxRhs], double (&acc)[kMaxRhs],
+                                                int nr, int prt)
+{
+    const int p = order_of<P>(prt);
+    double rinv, r2inv, qx, q2;
+    pair_geom_fp64(dx, dy, dz, ex, ey, ez, rho2, rinv, r2inv, qx, q2);
+    const double S = slp_clenshaw_fp64<P>(qx, q2, p);
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r)
+        if (r < nr) acc[r] = fma(wm[r] * rinv, S, acc[r]);
+}
+
+// Result of density r for target j of an item (the single-layer outputs of a
+// multi-density evaluation: out_rhs[r], partial sums at part_slp + r *
+// rhs_part_stride).
+__device__ __forceinline__ void write_multi_result(const DevGeom &g, const DevEval &ev, const Item &it, int j, int r,
+                                                   double acc)
+{
+    if (it.part < 0) {
+        ev.out_rhs[r][g.slot_tgt[it.slot_begin + j]] = acc * kInv4Pi;
+    } else if (ev.part_slp) {
+        ev.part_slp[r * ev.rhs_part_stride + it.part + j] = acc * kInv4Pi;
+    }
+}
+
+// The single layer for ev.n_rhs densities in one pass: the items, lanes,
+// staging and reductions of laplace_fp64_item<P, false, false>, each density
+// with its own accumulators, so that result r is bit-identical to the
+// evaluation of density r alone.  T: rows of `tile` doubles, x, y, z and
+// kMaxRhs rows of w mu (density r in row 3 + r).
+template <int P>
+__device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const DevEval &ev, const Item &it,
+                                                        const WalkStart &ws, double *T, const int tile,
+                                                        const int lane)
+{
+    ListWalk walk(g, ws);
+    const int src_hi = it.src_hi;
+    const int nr = ev.n_rhs;
+    const int64_t stride = ev.rhs_src_stride;
+    double acc[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
+    if (it.n_tgt == 1) {                                   // direct loads, all 32 lanes
+        const double4_32a c = g.slot_c[it.slot_begin];
+        const double4_32a e = g.slot_e[it.slot_begin];
+#pragma unroll 2
+        for (int k = it.src_lo + lane; k < src_hi; k += 32) {
+            int s = walk.at(k);
+            const bool ok = (unsigned)s < (unsigned)g.n_src;
+            if (!ok) { atomicOr(ev.status, 1); s = 0; }
+            double wm[kMaxRhs];
+#pragma unroll
+            for (int r = 0; r < kMaxRhs; ++r) wm[r] = ok && r < nr ? ev.wmu[r * stride + s] : 0.0;
+            const double4_32a pw = g.src_pw[s];
+            pair_fp64_multi<P>(pw.x - c.x, pw.y - c.y, pw.z - c.z, e.x, e.y, e.z, e.w, wm, acc, nr, ev.p);
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxRhs; ++r)
+            if (r < nr) {
+                const double v = warp_sum(acc[r]);
+                if (lane == 0) write_multi_result(g, ev, it, 0, r, v);
+            }
+        return;
+    }
+    const int L = it.L;
+    const int j = lane / L, sub = lane - j * L;
+    const bool active = j < it.n_tgt;
+    double cx = 0, cy = 0, cz = 0, ex = 0, ey = 0, ez = 0, rho2 = 0;
+    if (active) {
+        const double4_32a c = g.slot_c[it.slot_begin + j];
+        const double4_32a e = g.slot_e[it.slot_begin + j];
+        cx = c.x; cy = c.y; cz = c.z;
+        ex = e.x; ey = e.y; ez = e.z; rho2 = e.w;
+    }
+    double *const Tx = T, *const Ty = T + tile, *const Tz = T + 2 * tile, *const Tw = T + 3 * tile;
+    for (int base = it.src_lo; base < src_hi; base += tile) {
+        const int cnt = min(tile, src_hi - base);
+        for (int k = lane; k < cnt; k += 32) {
+            int s = walk.at(base + k);
+            const bool ok = (unsigned)s < (unsigned)g.n_src;
+            if (!ok) { atomicOr(ev.status, 1); s = 0; }
+            const double4_32a pw = g.src_pw[s];
+            Tx[k] = pw.x; Ty[k] = pw.y; Tz[k] = pw.z;
+#pragma unroll
+            for (int r = 0; r < kMaxRhs; ++r)
+                if (r < nr) Tw[r * tile + k] = ok ? ev.wmu[r * stride + s] : 0.0;
+        }
+        __syncwarp();
+        if (active) {
+            for (int k = sub; k < cnt; k += L) {
+                double wm[kMaxRhs];
+#pragma unroll
+                for (int r = 0; r < kMaxRhs; ++r) wm[r] = r < nr ? Tw[r * tile + k] : 0.0;
+                pair_fp64_multi<P>(Tx[k] - cx, Ty[k] - cy, Tz[k] - cz, ex, ey, ez, rho2, wm, acc, nr, ev.p);
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r)
+        if (r < nr) {
+            const double v = segment_sum(acc[r], sub, L);
+            if (active && sub == 0) write_multi_result(g, ev, it, j, r, v);
+        }
 }
 
 // Two (target, source) pairs at once in mixed precision, every FP32 operation

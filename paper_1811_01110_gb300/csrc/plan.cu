@@ -178,6 +178,14 @@ double staging_weight(const tsqbx_plan_s *P)
 }
 // FP64 items inside the double-float launch (tsqbx_options.fp64_share).
 bool has_both_pipes(int kernel, int precision) { return kernel == TSQBX_LAPLACE && precision == TSQBX_DF64; }
+// Several densities per evaluation (tsqbx_options.max_rhs > 1,
+// tsqbx_submit_multi): the single layer of Helmholtz plans and of Laplace
+// plans in FP64 or double-float.
+bool multi_ok(const tsqbx_options &o)
+{
+    return o.layers == TSQBX_SLP &&
+           (o.kernel == TSQBX_HELMHOLTZ || (o.kernel == TSQBX_LAPLACE && o.precision != TSQBX_MIXED));
+}
 
 int validate(const tsqbx_geometry *G, const tsqbx_options *o)
 {
@@ -200,8 +208,9 @@ int validate(const tsqbx_geometry *G, const tsqbx_options *o)
         return TSQBX_E_UNSUPPORTED;
     if ((o->flags & TSQBX_FLAG_CONVENTIONAL_ALL) && o->kernel == TSQBX_HELMHOLTZ && o->p > kConvHelmMaxP)
         return TSQBX_E_UNSUPPORTED;
-    // several densities per evaluation: the Helmholtz single layer only
-    if (o->max_rhs > 1 && (o->kernel != TSQBX_HELMHOLTZ || o->layers != TSQBX_SLP)) return TSQBX_E_UNSUPPORTED;
+    // several densities per evaluation: the single layer, Helmholtz or Laplace
+    // in FP64 or double-float
+    if (o->max_rhs > 1 && !multi_ok(*o)) return TSQBX_E_UNSUPPORTED;
     // runtime-order kernels: Laplace FP64 and mixed only
     if (o->p_unroll != 0 && !has_runtime_order(o->kernel, o->precision)) return TSQBX_E_UNSUPPORTED;
     // FP64 items inside the double-float launch: Laplace df64 only
@@ -379,21 +388,28 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     return TSQBX_OK;
 }
 
-// Enqueue one evaluation of the Helmholtz single layer for n densities (the
-// first at d_density, the others at steps of density_bytes) into d_outs[r]:
-// w mu of each density, the multi-density expansion kernel, and the slice
-// combine per density.
+// Enqueue one evaluation of the single layer for n densities (the first at
+// d_density, the others at steps of density_bytes, or the n pointers
+// d_densities) into d_outs[r]: w mu of each density, the multi-density
+// expansion kernel of the plan's kernel and precision, and the slice combine
+// per density.
 int enqueue_multi(tsqbx_plan P, Slot &slot, int n, const void *d_density, const void *const *d_densities,
                   double *const *d_outs, cudaStream_t s, int p, double k)
 {
+    const tsqbx_options &o = P->opt;
+    const bool helm = o.kernel == TSQBX_HELMHOLTZ;
     const int64_t ns = P->g.n_src;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((ns + threads - 1) / threads, (int64_t)P->n_sm * 16);
-    double2 *wmu = static_cast<double2 *>(slot.d_wmu);
     for (int r = 0; r < n && ns > 0; ++r) {
-        const double2 *dens = d_densities ? static_cast<const double2 *>(d_densities[r])
-                                          : static_cast<const double2 *>(d_density) + (size_t)r * ns;
-        prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, dens, ns, wmu + (size_t)r * ns);
+        const char *dens = d_densities ? static_cast<const char *>(d_densities[r])
+                                       : static_cast<const char *>(d_density) + (size_t)r * P->density_bytes;
+        if (helm)
+            prep_wmu_c128<<<blocks, threads, 0, s>>>(P->g.src_pw, reinterpret_cast<const double2 *>(dens), ns,
+                                                     static_cast<double2 *>(slot.d_wmu) + (size_t)r * ns);
+        else
+            prep_wmu_fp64<<<blocks, threads, 0, s>>>(P->g.src_pw, reinterpret_cast<const double *>(dens), ns,
+                                                     static_cast<double *>(slot.d_wmu) + (size_t)r * ns);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return status_of(e);
     }
@@ -402,19 +418,27 @@ int enqueue_multi(tsqbx_plan P, Slot &slot, int n, const void *d_density, const 
     ev.out_slp = d_outs[0];
     ev.part_slp = slot.d_part[0];
     ev.k = k;
-    ev.wmu_c = wmu;
+    ev.p = p;
+    ev.wmu = static_cast<const double *>(slot.d_wmu);
+    ev.wmu_c = static_cast<const double2 *>(slot.d_wmu);
     ev.n_rhs = n;
     ev.rhs_src_stride = ns;
-    ev.rhs_part_stride = 2 * P->g.n_parts;
+    ev.rhs_part_stride = (helm ? 2 : 1) * P->g.n_parts;
     for (int r = 0; r < n; ++r) ev.out_rhs[r] = d_outs[r];
-    int rc = n == 1 ? launch_helmholtz_fp64(p, TSQBX_SLP, P->g, ev, s) : launch_helmholtz_multi(p, P->g, ev, s);
+    int rc;
+    if (helm)
+        rc = n == 1 ? launch_helmholtz_fp64(p, TSQBX_SLP, P->g, ev, s) : launch_helmholtz_multi(p, P->g, ev, s);
+    else if (o.precision == TSQBX_DF64)
+        rc = n == 1 ? launch_laplace_df64(p, TSQBX_SLP, P->g, ev, s) : launch_laplace_df64_multi(p, P->g, ev, s);
+    else
+        rc = n == 1 ? launch_laplace_fp64(p, TSQBX_SLP, P->g, ev, s) : launch_laplace_fp64_multi(p, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
     if (P->g.n_combine > 0) {
         const int64_t th = P->g.n_combine * 32;
         const int cb = (int)std::min<int64_t>((th + 255) / 256, (int64_t)P->n_sm * 8);
         for (int r = 0; r < n; ++r) {
             combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp + r * ev.rhs_part_stride, nullptr, nullptr,
-                                              d_outs[r], nullptr, nullptr, 2);
+                                              d_outs[r], nullptr, nullptr, helm ? 2 : 1);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return status_of(e);
         }
@@ -439,7 +463,7 @@ tsqbx_plan_s::~tsqbx_plan_s()
 
 extern "C" {
 
-int tsqbx_version(void) { return 10300; }
+int tsqbx_version(void) { return 10400; }
 
 const char *tsqbx_last_error(void) { return t_last_error; }
 
@@ -1017,7 +1041,7 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
     return TSQBX_OK;
 }
 
-// The same for n densities of a Helmholtz single-layer plan (tsqbx_submit_multi):
+// The same for n densities of a single-layer plan (tsqbx_submit_multi):
 // host densities are staged one after another in the slot's buffers, host
 // outputs come back through the slot's single-layer staging.
 int start_multi(tsqbx_plan P, Slot &slot, int n, const void *const *density, void *const *out_slp, int p, double k)
@@ -1162,8 +1186,7 @@ int tsqbx_submit_multi(tsqbx_plan P, int p, double k, int n, const void *const *
 {
     if (!P || !ticket || !density || !out_slp || n < 1 || n > rhs_capacity(P->opt) || !pk_ok(P, p, k))
         return TSQBX_E_INVAL;
-    if (P->opt.kernel != TSQBX_HELMHOLTZ || P->opt.layers != TSQBX_SLP || P->g.n_conv_centers > 0)
-        return TSQBX_E_UNSUPPORTED;
+    if (!multi_ok(P->opt) || P->g.n_conv_centers > 0) return TSQBX_E_UNSUPPORTED;
     for (int r = 0; r < n; ++r)
         if ((P->g.n_src && !density[r]) || (P->g.n_tgt && !out_slp[r])) return TSQBX_E_INVAL;
     try {

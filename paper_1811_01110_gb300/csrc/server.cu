@@ -10,9 +10,10 @@
 //  * continuous batching: every started request runs on its own plan slot
 //    (own stream), so requests that arrive while others are on the GPU overlap
 //    with them; completions free slots for the next queued requests.  Queued
-//    Helmholtz single-layer requests that share a plan, an order and a
-//    wavenumber start together as one multi-density evaluation
-//    (tsqbx_submit_multi), which costs little more than one of them;
+//    single-layer requests (Helmholtz, or Laplace in FP64 or double-float)
+//    that share a plan, an order and (Helmholtz) a wavenumber start together
+//    as one multi-density evaluation (tsqbx_submit_multi), which costs little
+//    more than one of them;
 //  * accounting: latency (arrival to completion) per request, p50/p99,
 //    pair-terms completed, plans created/evicted, resident bytes.
 #include <algorithm>
@@ -74,14 +75,17 @@ struct Request {
     std::vector<Request *> merged;   // queued requests that ride in this one's evaluation
 };
 
-// Densities a Helmholtz single-layer evaluation of the server may carry: queued
-// requests with the same plan, order and wavenumber are started together
+// Densities a single-layer evaluation of the server may carry: queued requests
+// with the same plan, order and (Helmholtz) wavenumber are started together
 // (tsqbx_submit_multi) when a slot frees up.
 constexpr int kServerMaxRhs = 4;
 
+// Helmholtz single layer, or Laplace single layer in FP64 or double-float
+// (the plans tsqbx_submit_multi takes), without conventional centers.
 bool mergeable(const tsqbx_options &o)
 {
-    return o.kernel == TSQBX_HELMHOLTZ && o.layers == TSQBX_SLP &&
+    return o.layers == TSQBX_SLP &&
+           (o.kernel == TSQBX_HELMHOLTZ || (o.kernel == TSQBX_LAPLACE && o.precision != TSQBX_MIXED)) &&
            !(o.flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL));
 }
 
@@ -189,7 +193,7 @@ bool tsqbx_server_s::admit(Request *r)
         for (Request *q : queue) {
             if ((int)group.size() >= r->opt.max_rhs) break;
             if (q != r && q->state == RState::Queued && q->key == r->key && q->opt.p == r->opt.p &&
-                q->opt.k == r->opt.k)
+                (r->opt.kernel == TSQBX_LAPLACE || q->opt.k == r->opt.k))
                 group.push_back(q);
         }
     int rc;

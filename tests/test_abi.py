@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_strerror_and_version(L):
     import paper_1811_01110_gb300 as pkg
-    assert L.tsqbx_version() >= 10300          # 1.3: p_unroll and fp64_share in options and tuning
+    assert L.tsqbx_version() >= 10400          # 1.4: several densities for Laplace single-layer plans
     for code in range(-10, 2):
         assert pkg.strerror(code) != "unknown status"
     assert pkg.strerror(-100) == "unknown status"
@@ -104,7 +104,10 @@ def test_more_invalid_options_rejected_on_host(L):
         assert _create(g, tile_depth=depth) == -1
     for rhs in (-1, 5):                                    # densities per evaluation: 0..4
         assert _create(g, kernel="helmholtz", k=1.0, max_rhs=rhs) == -1
-    assert _create(g, max_rhs=2) == -9                     # several densities: Helmholtz single layer only
+    # several densities: the single layer only, Helmholtz or Laplace FP64 / df64
+    assert _create(g, layers=("slp", "dlp"), max_rhs=2) == -9
+    assert _create(g, precision="mixed", max_rhs=2) == -9
+    assert _create(g, precision="df64", layers=("slp", "sp"), max_rhs=2) == -9
     assert _create(g, kernel="helmholtz", k=1.0, layers=("slp", "dlp"), max_rhs=2) == -9
     for unroll in (-1, 3, 8):                              # order-loop forms: 0, 1, 2 or 4
         assert _create(g, p_unroll=unroll) == -1

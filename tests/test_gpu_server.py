@@ -97,10 +97,11 @@ def test_results_same_alone_and_in_the_mix(pkg):
 def test_admission_eviction_and_rejection(pkg):
     geoms = _geoms()
     rng = np.random.default_rng(83)
-    # a budget that holds the largest plan but never all three at once
+    # a budget that holds the largest plan but never all three at once (the
+    # server's Laplace single-layer plans hold scratch for four densities)
     fps = []
     for g in geoms[:3]:
-        with pkg.Plan(g, "laplace", ("slp",), p=5) as probe:
+        with pkg.Plan(g, "laplace", ("slp",), p=5, max_rhs=4) as probe:
             fps.append(probe.footprint())
     budget = max(fps) + min(fps) // 2
     assert budget < sum(fps)
