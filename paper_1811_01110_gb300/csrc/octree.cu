@@ -32,7 +32,8 @@
 // Mapping: the tree is built level by level (one pass per level: count, mark
 // the octants that receive points, prefix-sum the new boxes, move points);
 // subtree source counts bottom up, depth-first offsets top down, and one
-// stable radix sort of the sources by their leaf's offset.  The lists use one
+// stable radix sort of the sources by their leaf's offset (the prefix sums
+// and the sort are this library's own, radix.cuh).  The lists use one
 // thread per target box walking the tree with an explicit stack, in two
 // passes (count, fill), then a per-box sort and merge of the ranges.
 #include <algorithm>
@@ -40,13 +41,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <stdexcept>
 #include <vector>
-
-#include <cub/device/device_radix_sort.cuh>
-#include <cub/device/device_scan.cuh>
 
 #include "internal.cuh"
 #include "plan_internal.h"
+#include "radix.cuh"
 #include "tsqbx.h"
 
 namespace tsqbx {
@@ -761,7 +761,7 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     std::vector<int> lev_begin{0};
     int lb = 0, le = 1;
     DBuf<int> cnt, flag, off;
-    DBuf<unsigned char> tmp;
+    DBuf<int> tmp;                                      // scan and sort scratch
     while (lb < le) {
         if ((int)lev_begin.size() > kMaxLevel + 1) throw std::invalid_argument("octree too deep");
         const int nlev = le - lb;
@@ -774,10 +774,9 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
         octant_kernel<<<gp, 256>>>(ns, s.p, sbox.p, sact.p, soct.p, nc, c.p, r.p, cbox.p, cact.p, coct.p, B, lb, cnt.p,
                                    n_max, t_f, flag.p);
         ck(cudaGetLastError());
-        size_t tb = 0;
-        ck(cub::DeviceScan::ExclusiveSum(nullptr, tb, flag.p, off.p, 8 * nlev));
-        if (tb > tmp.n) tmp.alloc(tb);
-        ck(cub::DeviceScan::ExclusiveSum(tmp.p, tb, flag.p, off.p, 8 * nlev));
+        const int64_t n_flag = 8 * (int64_t)nlev;
+        if ((size_t)radix::scan_scratch(n_flag) > tmp.n) tmp.alloc(radix::scan_scratch(n_flag));
+        ck(radix::exclusive_scan(flag.p, off.p, n_flag, tmp.p, 0));
         int last[2] = {0, 0};
         ck(cudaMemcpy(&last[0], off.p + 8 * nlev - 1, sizeof(int), cudaMemcpyDeviceToHost));
         ck(cudaMemcpy(&last[1], flag.p + 8 * nlev - 1, sizeof(int), cudaMemcpyDeviceToHost));
@@ -818,15 +817,16 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     // depth-first source order: stable sort by the leaf's offset
     DBuf<int> key, val, key2, val2;
     key.alloc(ns); val.alloc(ns); key2.alloc(ns); val2.alloc(ns);
+    const int *perm = val.p;                            // the sorted source indices
     if (ns) {
         sort_keys_kernel<<<grid_for(ns, n_sm), 256>>>(ns, sbox.p, sbeg.p, key.p, val.p);
         ck(cudaGetLastError());
         int bits = 1;
         while ((int64_t)1 << bits <= ns) ++bits;
-        size_t tb = 0;
-        ck(cub::DeviceRadixSort::SortPairs(nullptr, tb, key.p, key2.p, val.p, val2.p, (int)ns, 0, bits));
-        if (tb > tmp.n) tmp.alloc(tb);
-        ck(cub::DeviceRadixSort::SortPairs(tmp.p, tb, key.p, key2.p, val.p, val2.p, (int)ns, 0, bits));
+        if ((size_t)radix::sort_scratch(ns) > tmp.n) tmp.alloc(radix::sort_scratch(ns));
+        bool in_b = false;
+        ck(radix::sort_pairs(key.p, val.p, key2.p, val2.p, ns, bits, tmp.p, &in_b, 0));
+        perm = in_b ? val2.p : val.p;
     }
 
     lap(O.stats.order_ms);
@@ -927,7 +927,7 @@ void build(tsqbx_octree_s &O, int64_t ns, const double *hs, int64_t nc, const do
     O.center.resize(3 * (size_t)nb);
     for (int b = 0; b < nb; ++b) { O.center[b] = x[b]; O.center[nb + b] = y[b]; O.center[2 * (size_t)nb + b] = z[b]; }
     to_host(O.halfwidth, hw.p, nb);
-    to_host(O.src_perm, val2.p, ns);
+    to_host(O.src_perm, perm, ns);
     to_host(O.ctr_box, cbox.p, nc);
     to_host(O.near_begin, near_b.p, (size_t)n_near);
     to_host(O.near_end, near_e.p, (size_t)n_near);
