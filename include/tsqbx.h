@@ -232,12 +232,16 @@ TSQBX_API int tsqbx_plan_info(tsqbx_plan plan, tsqbx_plan_stats *stats);
  * the admission unit of a serving loop.  Errors: TSQBX_E_INVAL. */
 TSQBX_API int tsqbx_plan_footprint(tsqbx_plan plan, size_t *bytes);
 
-/* Blocking evaluation.  density: n_src doubles (Laplace) or n_src complex
- * doubles as interleaved (re, im) pairs (Helmholtz).  out_slp / out_dlp:
- * n_tgt doubles (Laplace) or n_tgt interleaved complex values (Helmholtz),
- * indexed by target; NULL for a layer not in the plan's mask.  Each pointer
- * may be host (pageable or pinned) or device memory.  Returns after the
- * outputs are written.  Errors: TSQBX_E_INVAL, TSQBX_E_CUDA, TSQBX_E_KERNEL. */
+/* Blocking evaluation: the near-field TSQBX sums of Alg. 1 Stages 3, 5(a)
+ * and 6(a) (Sec. 2.6 eq. tsqbx, Appendix A; see the top of this file) for
+ * one density, every layer of the plan's mask.  density: n_src doubles
+ * (Laplace) or n_src complex doubles as interleaved (re, im) pairs
+ * (Helmholtz), the mu_s of the sums (the plan applies the weights w_s).
+ * out_slp / out_dlp: n_tgt doubles (Laplace) or n_tgt interleaved complex
+ * values (Helmholtz), indexed by target; NULL for a layer not in the plan's
+ * mask.  Each pointer may be host (pageable or pinned) or device memory.
+ * Returns after the outputs are written.  Errors: TSQBX_E_INVAL,
+ * TSQBX_E_CUDA, TSQBX_E_KERNEL. */
 TSQBX_API int tsqbx_eval(tsqbx_plan plan, const void *density, void *out_slp, void *out_dlp);
 
 /* tsqbx_eval / tsqbx_submit with the expansion order p (0..TSQBX_P_MAX) and,
@@ -265,8 +269,9 @@ TSQBX_API int tsqbx_eval_async(tsqbx_plan plan, const void *d_density, void *d_o
 TSQBX_API int tsqbx_eval_async_pk(tsqbx_plan plan, int p, double k, const void *d_density, void *d_out_slp,
                                   void *d_out_dlp, void *d_out_sp, void *stream);
 
-/* Submit an evaluation and return at once with a ticket.  Pointers as for
- * tsqbx_eval; host density is copied before return, host outputs are written
+/* Submit an evaluation (the sums of tsqbx_eval: Alg. 1 Stages 3, 5(a),
+ * 6(a)) and return at once with a ticket, so that a serving loop overlaps
+ * evaluations of many plans.  Pointers as for tsqbx_eval; host density is copied before return, host outputs are written
  * by the tsqbx_poll call that reports completion, so they must stay valid
  * until then.  Errors: TSQBX_E_INVAL, TSQBX_E_BUSY (every slot in flight:
  * poll first), TSQBX_E_CUDA. */
@@ -291,7 +296,8 @@ TSQBX_API int tsqbx_submit_multi(tsqbx_plan plan, int p, double k, int n, const 
                                  void *const *out_slp, uint64_t *ticket);
 
 /* Wait up to timeout_us microseconds (0: just test, < 0: wait indefinitely)
- * for a ticket.  Returns TSQBX_OK once (the ticket is then retired),
+ * for a ticket of tsqbx_submit / tsqbx_submit_pk / tsqbx_submit_multi (no
+ * counterpart in the paper: the completion side of the asynchronous calls).  Returns TSQBX_OK once (the ticket is then retired),
  * TSQBX_PENDING if timeout_us == 0 and work is in flight, TSQBX_E_TIMEOUT if
  * a positive timeout expired, TSQBX_E_NOTFOUND for an unknown ticket,
  * TSQBX_E_KERNEL / TSQBX_E_CUDA on failure (ticket retired). */
