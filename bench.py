@@ -168,7 +168,7 @@ def parse():
     ap.add_argument("--detail", default=os.path.join(ROOT, "bench_detail.json"),
                     help="file for the full result (every workload); stdout gets the headline line only")
     ap.add_argument("--only", choices=["batched", "helmholtz", "sphere", "serving", "target_derivative",
-                                       "conventional", "lists"],
+                                       "conventional", "lists", "multi_density"],
                     help="run one secondary workload alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -897,6 +897,9 @@ def main():
         elif args.only == "target_derivative":
             g, mu = workload()
             res = leg_target_derivative(pkg, torch, dev, g, mu, steps, args.warmup, flush)
+        elif args.only == "multi_density":
+            g, mu = workload()
+            res = leg_multi_density(pkg, torch, dev, g, steps, args.warmup, flush)
         else:
             fn = {"batched": leg_batched, "helmholtz": leg_helmholtz, "sphere": leg_sphere,
                   "conventional": leg_conventional, "lists": leg_lists}[args.only]
