@@ -725,41 +725,46 @@ def leg_target_derivative(pkg, torch, dev, g, mu, steps, warmup, flush, check_ta
 
 
 def leg_multi_density(pkg, torch, dev, g, steps, warmup, flush):
-    """The benchmark torus, Laplace single layer, p = 9, FP64 and df64: one
-    density per evaluation against four in one (tsqbx_submit_multi, device
-    buffers), each timed on the host around submit and poll with the L2
-    flushed before every step (both the same way, on one plan).  Throughput
-    counts the pair-terms of every density; the four results are checked bit
-    for bit against the single-density evaluations."""
+    """The benchmark torus, Laplace single layer and single + double layer,
+    p = 9, FP64 and df64: one density per evaluation against four in one
+    (tsqbx_submit_multi_layers, device buffers), each timed on the host
+    around submit and poll with the L2 flushed before every step (both the
+    same way, on one plan).  Throughput counts the pair-terms of every
+    density; the four results are checked bit for bit against the
+    single-density evaluations."""
     rng = np.random.default_rng(2718)
     dens = [torch.from_numpy(rng.standard_normal(g.n_src)).to(dev) for _ in range(4)]
-    res = {"workload": WORKLOAD.replace("SLP+DLP", "SLP") + ", 4 densities per evaluation", "unit": UNIT}
-    for prec in ("fp64", "df64"):
-        plan = pkg.Plan(g, "laplace", ("slp",), p=P, precision=prec, device=dev.index, max_rhs=4)
-        pt = plan.info()["n_pair_terms"]
-        outs = [{"slp": torch.empty(g.n_tgt, dtype=torch.float64, device=dev)} for _ in range(4)]
-        row = {}
-        for n in (1, 4):
-            dt = []
-            for i in range(warmup + steps):
-                flush.zero_()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                t, _ = plan.submit_multi(dens[:n], outs=outs[:n])
+    res = {"workload": WORKLOAD.replace(", Laplace SLP+DLP p=9", "") + ", 4 densities per evaluation",
+           "unit": UNIT}
+    for layers in (("slp",), ("slp", "dlp")):
+        key = "+".join(layers)
+        res[key] = {}
+        for prec in ("fp64", "df64"):
+            plan = pkg.Plan(g, "laplace", layers, p=P, precision=prec, device=dev.index, max_rhs=4)
+            pt = plan.info()["n_pair_terms"]
+            outs = [{l: torch.empty(g.n_tgt, dtype=torch.float64, device=dev) for l in layers} for _ in range(4)]
+            row = {}
+            for n in (1, 4):
+                dt = []
+                for i in range(warmup + steps):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    t, _ = plan.submit_multi(dens[:n], outs=outs[:n])
+                    pkg.poll(t, -1)
+                    if i >= warmup:
+                        dt.append(time.perf_counter() - t0)
+                row[f"ms_{n}"] = 1e3 * sum(dt) / len(dt)
+                row[f"value_{n}"] = n * pt * len(dt) / sum(dt)
+            same = True
+            for r in range(4):
+                t, alone = plan.submit_multi(dens[r:r + 1])
                 pkg.poll(t, -1)
-                if i >= warmup:
-                    dt.append(time.perf_counter() - t0)
-            row[f"ms_{n}"] = 1e3 * sum(dt) / len(dt)
-            row[f"value_{n}"] = n * pt * len(dt) / sum(dt)
-        same = True
-        for r in range(4):
-            t, alone = plan.submit_multi(dens[r:r + 1])
-            pkg.poll(t, -1)
-            same = same and bool(torch.equal(alone[0]["slp"], outs[r]["slp"]))
-        row["time_ratio_4_vs_1"] = row["ms_4"] / row["ms_1"]
-        row["bit_identical"] = same
-        res[prec] = row
-        plan.close()
+                same = same and all(bool(torch.equal(alone[0][l], outs[r][l])) for l in layers)
+            row["time_ratio_4_vs_1"] = row["ms_4"] / row["ms_1"]
+            row["bit_identical"] = same
+            res[key][prec] = row
+            plan.close()
     return res
 
 

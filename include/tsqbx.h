@@ -139,10 +139,11 @@ typedef struct {
     int tile_depth;             /* sources a warp stages per shared-memory tile: 32, 64
                                    or 128; 0 = 64.  Results agree across depths to
                                    rounding (the order of the lanes' sums changes)     */
-    int max_rhs;                /* densities one tsqbx_submit_multi may carry, 1..4;
-                                   0 = 1.  Above 1 only for single-layer plans of
-                                   the Helmholtz kernel or of the Laplace kernel in
-                                   FP64 or double-float (else TSQBX_E_UNSUPPORTED);
+    int max_rhs;                /* densities one tsqbx_submit_multi_layers may carry,
+                                   1..4; 0 = 1.  Above 1 only for Helmholtz
+                                   single-layer plans and for Laplace plans in
+                                   FP64 or double-float whose layers are the single
+                                   and/or double layer (else TSQBX_E_UNSUPPORTED);
                                    each slot then holds scratch for that many
                                    densities                                        */
     int p_unroll;               /* how the order loop of the Laplace FP64 and mixed
@@ -269,38 +270,48 @@ TSQBX_API int tsqbx_eval_async(tsqbx_plan plan, const void *d_density, void *d_o
 TSQBX_API int tsqbx_eval_async_pk(tsqbx_plan plan, int p, double k, const void *d_density, void *d_out_slp,
                                   void *d_out_dlp, void *d_out_sp, void *stream);
 
-/* Submit an evaluation (the sums of tsqbx_eval: Alg. 1 Stages 3, 5(a),
- * 6(a)) and return at once with a ticket, so that a serving loop overlaps
- * evaluations of many plans.  Pointers as for tsqbx_eval; host density is copied before return, host outputs are written
- * by the tsqbx_poll call that reports completion, so they must stay valid
- * until then.  Errors: TSQBX_E_INVAL, TSQBX_E_BUSY (every slot in flight:
- * poll first), TSQBX_E_CUDA. */
+/* Submit an evaluation (the sums of tsqbx_eval: Alg. 1 Stages 3, 5(a), 6(a))
+ * and return at once with a ticket, so that a serving loop overlaps
+ * evaluations of many plans.  Pointers as for tsqbx_eval; host density is
+ * copied before return, host outputs are written by the tsqbx_poll call that
+ * reports completion, so they must stay valid until then.  Errors:
+ * TSQBX_E_INVAL, TSQBX_E_BUSY (every slot in flight: poll first),
+ * TSQBX_E_CUDA. */
 TSQBX_API int tsqbx_submit(tsqbx_plan plan, const void *density, void *out_slp, void *out_dlp,
                  uint64_t *ticket);
 
-/* Several densities in one evaluation: the single layer of a Helmholtz plan,
- * or of a Laplace plan in TSQBX_FP64 or TSQBX_DF64 (layers == TSQBX_SLP,
- * created with max_rhs >= n; no conventional centers), for the n densities
- * density[0..n), with order p and wavenumber k as in tsqbx_submit_pk.  The
- * per-pair work of Appendix A's expansion -- geometry, 1/R, the Legendre (and
- * Helmholtz: Hankel) recurrences, e^{ikR}, the sums over the orders --
- * depends on the geometry, p and k only, so the densities share it and each
- * adds only its own weight w_s mu_s (real for Laplace, complex for
- * Helmholtz): n densities cost little more than one.  Result i (out_slp[i],
- * layout as tsqbx_submit) is bit-identical to the evaluation of density[i]
- * alone on the same plan.  Pointers host or device as for tsqbx_submit; one
- * ticket covers all n results (tsqbx_poll).  Errors: TSQBX_E_INVAL (n
- * outside 1..max_rhs, NULL pointers, p or k), TSQBX_E_UNSUPPORTED (not such
- * a plan, or one with conventional centers), TSQBX_E_BUSY, TSQBX_E_CUDA. */
+/* Several densities in one evaluation: for the n densities density[0..n),
+ * with order p and wavenumber k as in tsqbx_submit_pk, the single layer of a
+ * Helmholtz plan, or the single and/or double layer of a Laplace plan in
+ * TSQBX_FP64 or TSQBX_DF64 (no S'; created with max_rhs >= n; no
+ * conventional centers).  The per-pair work of Appendix A's expansion --
+ * geometry, 1/R, the Legendre (and Helmholtz: Hankel) recurrences, e^{ikR},
+ * the sums over the orders -- depends on the geometry, p and k only, so the
+ * densities share it and each adds only its own weight w_s mu_s (real for
+ * Laplace, complex for Helmholtz): n densities cost little more than one.
+ * out_slp[i] / out_dlp[i] (layout as tsqbx_submit) receive the layers of
+ * density i; an array is read only when its layer is in the plan's mask and
+ * may be NULL otherwise.  Each result is bit-identical to the evaluation of
+ * density[i] alone on the same plan.  Pointers host or device as for
+ * tsqbx_submit; one ticket covers all n results (tsqbx_poll).  Errors:
+ * TSQBX_E_INVAL (n outside 1..max_rhs, NULL pointers, p or k),
+ * TSQBX_E_UNSUPPORTED (not such a plan, or one with conventional centers),
+ * TSQBX_E_BUSY, TSQBX_E_CUDA. */
+TSQBX_API int tsqbx_submit_multi_layers(tsqbx_plan plan, int p, double k, int n, const void *const *density,
+                                        void *const *out_slp, void *const *out_dlp, uint64_t *ticket);
+
+/* tsqbx_submit_multi_layers without double-layer outputs: for plans whose
+ * mask holds the single layer alone. */
 TSQBX_API int tsqbx_submit_multi(tsqbx_plan plan, int p, double k, int n, const void *const *density,
                                  void *const *out_slp, uint64_t *ticket);
 
 /* Wait up to timeout_us microseconds (0: just test, < 0: wait indefinitely)
- * for a ticket of tsqbx_submit / tsqbx_submit_pk / tsqbx_submit_multi (no
- * counterpart in the paper: the completion side of the asynchronous calls).  Returns TSQBX_OK once (the ticket is then retired),
- * TSQBX_PENDING if timeout_us == 0 and work is in flight, TSQBX_E_TIMEOUT if
- * a positive timeout expired, TSQBX_E_NOTFOUND for an unknown ticket,
- * TSQBX_E_KERNEL / TSQBX_E_CUDA on failure (ticket retired). */
+ * for a ticket of tsqbx_submit / tsqbx_submit_pk / tsqbx_submit_multi(_layers)
+ * (no counterpart in the paper: the completion side of the asynchronous
+ * calls).  Returns TSQBX_OK once (the ticket is then retired), TSQBX_PENDING
+ * if timeout_us == 0 and work is in flight, TSQBX_E_TIMEOUT if a positive
+ * timeout expired, TSQBX_E_NOTFOUND for an unknown ticket, TSQBX_E_KERNEL /
+ * TSQBX_E_CUDA on failure (ticket retired). */
 TSQBX_API int tsqbx_poll(uint64_t ticket, int timeout_us);
 
 /* Duration in milliseconds of the expansion kernel of the most recent
@@ -370,10 +381,11 @@ TSQBX_API int tsqbx_batch_info(tsqbx_batch batch, tsqbx_batch_stats *stats);
  * the resident plans fit the HBM budget (idle plans are evicted least recently
  * used).  Started requests run on their own plan slots and streams, so work
  * that arrives while other requests are on the GPU overlaps with them
- * (continuous batching).  Queued single-layer requests (Helmholtz, or Laplace
- * in FP64 or double-float) with the same geometry, precision, order and
- * (Helmholtz) wavenumber are started together, up to four, as one
- * multi-density evaluation (tsqbx_submit_multi): each result is bit-identical
+ * (continuous batching).  Queued requests of the plans that
+ * tsqbx_submit_multi_layers takes (Helmholtz single layer; Laplace single
+ * and/or double layer in FP64 or double-float) with the same geometry,
+ * layers, precision, order and (Helmholtz) wavenumber are started together,
+ * up to four, as one multi-density evaluation: each result is bit-identical
  * to the request evaluated alone.  A worker thread owned by the server does
  * the admission and completion bookkeeping. */
 typedef struct tsqbx_server_s *tsqbx_server;
@@ -593,7 +605,8 @@ TSQBX_API const char *tsqbx_strerror(int status);
  * .fp64_share (appended: callers built against 1.2 pass structs of the old
  * size and must be rebuilt).  1.4 accepts max_rhs > 1, and so
  * tsqbx_submit_multi, for Laplace single-layer plans in FP64 and
- * double-float (no struct changed). */
+ * double-float (no struct changed).  1.5 adds tsqbx_submit_multi_layers
+ * (Laplace double layer with several densities). */
 TSQBX_API int tsqbx_version(void);
 
 #ifdef __cplusplus

@@ -101,8 +101,8 @@ class Plan:
         "all" (conventional QBX for every center).  size_priority: stream
         priority from the plan's work (TSQBX_FLAG_SIZE_PRIORITY).  tile_depth:
         sources staged per warp tile (32, 64 or 128; 0 = 64).  max_rhs:
-        densities one submit_multi may carry (single-layer plans: Helmholtz,
-        or Laplace in FP64 or df64).
+        densities one submit_multi may carry (the Helmholtz single layer; the
+        Laplace single and/or double layer in FP64 or df64).
         p_unroll: 0 = per-order kernels with the recurrences fully unrolled;
         1, 2 or 4 = the runtime-order kernel, its loop over n unrolled by that
         factor (Laplace FP64 and mixed).  fp64_share: df64 plans, the
@@ -265,36 +265,42 @@ class Plan:
 
 
     def submit_multi(self, densities, p=None, k=None, outs=None):
-        """tsqbx_submit_multi: the single layer for several densities in one
-        evaluation (single-layer plans created with max_rhs: Helmholtz, or
-        Laplace in FP64 or df64); returns (ticket, [{"slp": out} per
-        density]), valid once poll() returns True."""
+        """tsqbx_submit_multi_layers: every layer of the plan for several
+        densities in one evaluation (plans created with max_rhs: the
+        Helmholtz single layer, the Laplace single and/or double layer in
+        FP64 or df64); returns (ticket, [{layer: out} per density]), valid
+        once poll() returns True."""
         n = len(densities)
         helm = self.kernel == "helmholtz"
         cw = np.complex128 if helm else np.float64
         esz = 16 if helm else 8
+        layers = [l for l in ("slp", "dlp") if l in self.layers]
         keep = []
         d_addr = (ctypes.c_void_p * n)()
-        o_addr = (ctypes.c_void_p * n)()
+        o_addr = {l: (ctypes.c_void_p * n)() for l in ("slp", "dlp")}
         if outs is None:
             outs = []
             for d in densities:
                 if _is_torch(d) and d.is_cuda:
                     import torch
-                    outs.append({"slp": torch.empty(self.n_tgt, dtype=torch.complex128 if helm else torch.float64,
-                                                    device=d.device)})
+                    tdt = torch.complex128 if helm else torch.float64
+                    outs.append({l: torch.empty(self.n_tgt, dtype=tdt, device=d.device) for l in layers})
                 else:
-                    outs.append({"slp": np.empty(self.n_tgt, dtype=cw)})
+                    outs.append({l: np.empty(self.n_tgt, dtype=cw) for l in layers})
         for i, d in enumerate(densities):
             if not _is_torch(d):
                 d = np.ascontiguousarray(d, dtype=cw)
             keep.append(d)
             d_addr[i] = _addr(d, self.n_src * esz, "density").value
-            o_addr[i] = _addr(outs[i]["slp"], self.n_tgt * esz, "out_slp").value
+            for l in layers:
+                o_addr[l][i] = _addr(outs[i][l], self.n_tgt * esz, "out_" + l).value
         t = ctypes.c_uint64()
         pp = self.p if p is None else int(p)
         kk = self.k if k is None else float(k)
-        check(lib().tsqbx_submit_multi(self._h, pp, kk, n, d_addr, o_addr, ctypes.byref(t)), "tsqbx_submit_multi")
+        check(lib().tsqbx_submit_multi_layers(self._h, pp, kk, n, d_addr,
+                                              o_addr["slp"] if "slp" in layers else None,
+                                              o_addr["dlp"] if "dlp" in layers else None, ctypes.byref(t)),
+              "tsqbx_submit_multi_layers")
         self._inflight = getattr(self, "_inflight", {})
         self._inflight[t.value] = (outs, keep)
         return t.value, outs

@@ -171,15 +171,17 @@ struct DevEval {
     double k = 0.0;                     // Helmholtz wavenumber
     int p = 0;                          // the evaluation's order (read by the runtime-order kernels)
     double *conv_coef = nullptr;        // conventional partial coefficients (scratch)
-    // Several densities in one evaluation (the single layer of Helmholtz, and
-    // of Laplace in FP64 or double-float): the w mu of density r starts at
-    // wmu_c (Helmholtz) or wmu (Laplace) + r * rhs_src_stride, its output at
-    // out_rhs[r] (out_rhs[0] == out_slp) and its partial sums at part_slp +
-    // r * rhs_part_stride (doubles).
+    // Several densities in one evaluation (the single layer of Helmholtz; the
+    // single and double layers of Laplace in FP64 or double-float): the w mu
+    // of density r starts at wmu_c (Helmholtz) or wmu (Laplace) + r *
+    // rhs_src_stride, its outputs at out_rhs[r] / out_rhs_dlp[r] (NULL: layer
+    // not formed) and its partial sums at part_slp / part_dlp + r *
+    // rhs_part_stride (doubles).
     int n_rhs = 1;
     int64_t rhs_src_stride = 0;
     int64_t rhs_part_stride = 0;
     double *out_rhs[kMaxRhs] = {nullptr, nullptr, nullptr, nullptr};
+    double *out_rhs_dlp[kMaxRhs] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 // Launchers (one per translation unit).  Return a cudaError_t as int.
@@ -188,11 +190,12 @@ int launch_laplace_fp64(int p, unsigned layers, const DevGeom &g, const DevEval 
 int launch_laplace_mixed(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_laplace_df64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
 int launch_helmholtz_fp64(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);
-// The single layer for e.n_rhs (2..kMaxRhs) densities at once: Helmholtz,
-// Laplace FP64 (laplace_multi.cu), Laplace double-float (laplace_df64_multi.cu).
+// e.n_rhs (2..kMaxRhs) densities at once: the Helmholtz single layer; the
+// Laplace single layer, or single and double layer (dlp), in FP64
+// (laplace_multi.cu) and double-float (laplace_df64_multi.cu).
 int launch_helmholtz_multi(int p, const DevGeom &g, const DevEval &e, cudaStream_t s);
-int launch_laplace_fp64_multi(int p, const DevGeom &g, const DevEval &e, cudaStream_t s);
-int launch_laplace_df64_multi(int p, const DevGeom &g, const DevEval &e, cudaStream_t s);
+int launch_laplace_fp64_multi(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s);
+int launch_laplace_df64_multi(int p, bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s);
 // Conventional path: coefficient formation, then evaluation (Laplace in
 // conventional.cu, Helmholtz in conventional_helm.cu).
 int launch_conventional(int p, unsigned layers, const DevGeom &g, const DevEval &e, cudaStream_t s);

@@ -52,6 +52,36 @@ __device__ __forceinline__ df slp_clenshaw_df(df qx, df q2)
     return b1;
 }
 
+// The Q'-recurrence sums in double-float, as qprime_sums_fp64: S2m, S2 =
+// S2m + Q'_p, Q'_{p+1} and the single layer's S.
+template <int P>
+__device__ __forceinline__ void qprime_sums_df(df qx, df q2, df &S2m, df &S2, df &Qp1, df &S)
+{
+    const df one{1.f, 0.f};
+    // the exact n = 1 step taken outside the loop, as in pair_fp64
+    df Um{0.f, 0.f}, Uc = one;
+    S2m = df{0.f, 0.f};
+    if constexpr (P >= 2) { Um = one; Uc = qx; S2m = df_of(df_const(rec_lambda(1))); }
+#pragma unroll
+    for (int m = 2; m < P; ++m) {
+        S2m = df_add(S2m, df_mul_c(df_const(rec_lambda(m)), Uc));
+        const df gq = df_mul_c(df_const(rec_gamma(m)), q2);
+        const df Un = df_sub(df_mul(qx, Uc), df_mul(gq, Um));
+        Um = Uc; Uc = Un;
+    }
+    df Qp{0.f, 0.f};
+    Qp1 = one;
+    if (P >= 1) {
+        Qp = df_mul_c(df_const(rec_lambda(P)), Uc);
+        const df gq = df_mul_c(df_const(rec_gamma(P)), q2);
+        Qp1 = df_mul_c(df_const(rec_lambda(P + 1)), df_sub(df_mul(qx, Uc), df_mul(gq, Um)));
+    }
+    S2 = df_add(S2m, Qp);
+    // S = (1 - 2 qx + q2) S2 + Q'_{p+1} - q2 Q'_p
+    const df c1 = df_add(df_sub(one, df_mul_f(qx, 2.f)), q2);
+    S = df_add(df_mul(c1, S2), df_sub(Qp1, df_mul(q2, Qp)));
+}
+
 // One pair; tn = n_t and en = e.n_t (S' only).  Same two recurrences and
 // closing sums as pair_fp64 (laplace_items.cuh), in double-float.
 template <int P, bool DLP, bool SP>
@@ -61,30 +91,11 @@ __device__ __forceinline__ void pair_df(const df3 &d, const df3 &e, df rho2, df 
     df rinv, r2inv, qx, q2;
     pair_geom_df(d, e, rho2, rinv, r2inv, qx, q2);
     const df wr = df_mul(wm, rinv);
-    const df one{1.f, 0.f};
     if constexpr (!DLP && !SP) {
         acc_s = df_add(acc_s, df_mul(wr, slp_clenshaw_df<P>(qx, q2)));
     } else {
-        // the exact n = 1 step taken outside the loop, as in pair_fp64
-        df Um{0.f, 0.f}, Uc = one, S2m{0.f, 0.f};
-        if constexpr (P >= 2) { Um = one; Uc = qx; S2m = df_of(df_const(rec_lambda(1))); }
-#pragma unroll
-        for (int m = 2; m < P; ++m) {          // (n is the source normal here)
-            S2m = df_add(S2m, df_mul_c(df_const(rec_lambda(m)), Uc));
-            const df gq = df_mul_c(df_const(rec_gamma(m)), q2);
-            const df Un = df_sub(df_mul(qx, Uc), df_mul(gq, Um));
-            Um = Uc; Uc = Un;
-        }
-        df Qp{0.f, 0.f}, Qp1 = one;
-        if (P >= 1) {
-            Qp = df_mul_c(df_const(rec_lambda(P)), Uc);
-            const df gq = df_mul_c(df_const(rec_gamma(P)), q2);
-            Qp1 = df_mul_c(df_const(rec_lambda(P + 1)), df_sub(df_mul(qx, Uc), df_mul(gq, Um)));
-        }
-        const df S2 = df_add(S2m, Qp);
-        // S = (1 - 2 qx + q2) S2 + Q'_{p+1} - q2 Q'_p
-        const df c1 = df_add(df_sub(one, df_mul_f(qx, 2.f)), q2);
-        const df S = df_add(df_mul(c1, S2), df_sub(Qp1, df_mul(q2, Qp)));
+        df S2m, S2, Qp1, S;
+        qprime_sums_df<P>(qx, q2, S2m, S2, Qp1, S);
         acc_s = df_add(acc_s, df_mul(wr, S));
         const df wr3 = df_mul(wr, r2inv);
         if (DLP) {                     // (b - a) S2 - a Q'_{p+1}, as in pair_fp64

@@ -129,6 +129,35 @@ __device__ __forceinline__ double slp_clenshaw_fp64(double qx, double q2, int p)
     return b1;
 }
 
+// The Q'-recurrence sums of the double layer and S' (order p): S2m = sum_{n<p}
+// Q'_n, Q'_p, Q'_{p+1}, S2 = S2m + Q'_p and the single layer's S.
+template <int P>
+__device__ __forceinline__ void qprime_sums_fp64(double qx, double q2, int p, double &S2m, double &S2, double &Qp1,
+                                                 double &S)
+{
+    // U_{n-1}, U_n; S2m accumulates Q'_1..Q'_{p-1}.  The n = 1 step is
+    // exact (U_2 = qx since gamma_1 = 0, S2m = lambda_1 U_1 = 1), so for p
+    // >= 2 the loop starts at n = 2 (a product by U_0 = 0 would still cost
+    // two multiplies and an add: IEEE arithmetic does not fold x * 0)
+    double Um = 0.0, Uc = 1.0;
+    S2m = 0.0;
+    if (p >= 2) { Um = 1.0; Uc = qx; S2m = c_lambda<P>(1); }
+    order_loop_up<P>(2, p, [&](int n) {
+        S2m = fma(c_lambda<P>(n), Uc, S2m);
+        const double Un = fma(qx, Uc, -(c_gamma<P>(n) * q2) * Um);
+        Um = Uc; Uc = Un;
+    });
+    // Uc = U_p, Um = U_{p-1} (p >= 1);  p = 0: Q'_0 = 0, Q'_1 = 1
+    double Qp = 0.0;
+    Qp1 = 1.0;
+    if (p >= 1) {
+        Qp = c_lambda<P>(p) * Uc;
+        Qp1 = c_lambda<P>(p + 1) * fma(qx, Uc, -(c_gamma<P>(p) * q2) * Um);
+    }
+    S2 = S2m + Qp;
+    S = fma(fma(-2.0, qx, 1.0) + q2, S2, fma(-q2, Qp, Qp1));
+}
+
 template <int P, bool DLP, bool SP>
 __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, double ex, double ey, double ez,
                                           double rho2, double wm, double nx, double ny, double nz,
@@ -142,25 +171,8 @@ __device__ __forceinline__ void pair_fp64(double dx, double dy, double dz, doubl
     if constexpr (!DLP && !SP) {
         acc_s = fma(wr, slp_clenshaw_fp64<P>(qx, q2, p), acc_s);
     } else {
-        // U_{n-1}, U_n; S2m accumulates Q'_1..Q'_{p-1}.  The n = 1 step is
-        // exact (U_2 = qx since gamma_1 = 0, S2m = lambda_1 U_1 = 1), so for p
-        // >= 2 the loop starts at n = 2 (a product by U_0 = 0 would still cost
-        // two multiplies and an add: IEEE arithmetic does not fold x * 0)
-        double Um = 0.0, Uc = 1.0, S2m = 0.0;
-        if (p >= 2) { Um = 1.0; Uc = qx; S2m = c_lambda<P>(1); }
-        order_loop_up<P>(2, p, [&](int n) {
-            S2m = fma(c_lambda<P>(n), Uc, S2m);
-            const double Un = fma(qx, Uc, -(c_gamma<P>(n) * q2) * Um);
-            Um = Uc; Uc = Un;
-        });
-        // Uc = U_p, Um = U_{p-1} (p >= 1);  p = 0: Q'_0 = 0, Q'_1 = 1
-        double Qp = 0.0, Qp1 = 1.0;
-        if (p >= 1) {
-            Qp = c_lambda<P>(p) * Uc;
-            Qp1 = c_lambda<P>(p + 1) * fma(qx, Uc, -(c_gamma<P>(p) * q2) * Um);
-        }
-        const double S2 = S2m + Qp;
-        const double S = fma(fma(-2.0, qx, 1.0) + q2, S2, fma(-q2, Qp, Qp1));
+        double S2m, S2, Qp1, S;
+        qprime_sums_fp64<P>(qx, q2, p, S2m, S2, Qp1, S);
         acc_s = fma(wr, S, acc_s);
         const double wr3 = wr * r2inv;
         if (DLP) {
@@ -293,43 +305,69 @@ __device__ __forceinline__ void laplace_fp64_item(const DevGeom &g, const DevEva
     if (active && sub == 0) write_item_result<DLP, SP>(g, ev, it, j, acc_s, acc_d, acc_p);
 }
 
-// Several densities at once (DevEval::n_rhs = nr in 2..kMaxRhs): the single
-// layer's per-pair value S / R depends on the geometry and the order alone,
-// so the densities share it and each adds its own w mu with the same two
-// operations as pair_fp64 (wr = w mu / R, acc += wr S).
-template <int P>
+// Several densities at once (DevEval::n_rhs = nr in 2..kMaxRhs): the
+// per-pair kernel values -- S / R for the single layer, the double layer's
+// bracket over R^3 -- depend on the geometry and the order alone, so the
+// densities share them and each adds its own w mu with the same operations
+// as pair_fp64 (wr = w mu / R, acc += wr S; DLP: wr3 = wr / R^2, acc_d +=
+// wr3 val).  The double layer needs the normal n.
+template <int P, bool DLP>
 __device__ __forceinline__ void pair_fp64_multi(double dx, double dy, double dz, double ex, double ey, double ez,
-                                                double rho2, const double (&wm)[kMaxRhs], double (&acc)[kMaxRhs],
-                                                int nr, int prt)
+                                                double rho2, double nx, double ny, double nz,
+                                                const double (&wm)[kMaxRhs], double (&acc)[kMaxRhs],
+                                                double (&acc_d)[kMaxRhs], int nr, int prt)
 {
     const int p = order_of<P>(prt);
     double rinv, r2inv, qx, q2;
     pair_geom_fp64(dx, dy, dz, ex, ey, ez, rho2, rinv, r2inv, qx, q2);
-    const double S = slp_clenshaw_fp64<P>(qx, q2, p);
+    if constexpr (!DLP) {
+        const double S = slp_clenshaw_fp64<P>(qx, q2, p);
 #pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r)
-        if (r < nr) acc[r] = fma(wm[r] * rinv, S, acc[r]);
-}
-
-// Result of density r for target j of an item (the single-layer outputs of a
-// multi-density evaluation: out_rhs[r], partial sums at part_slp + r *
-// rhs_part_stride).
-__device__ __forceinline__ void write_multi_result(const DevGeom &g, const DevEval &ev, const Item &it, int j, int r,
-                                                   double acc)
-{
-    if (it.part < 0) {
-        ev.out_rhs[r][g.slot_tgt[it.slot_begin + j]] = acc * kInv4Pi;
-    } else if (ev.part_slp) {
-        ev.part_slp[r * ev.rhs_part_stride + it.part + j] = acc * kInv4Pi;
+        for (int r = 0; r < kMaxRhs; ++r)
+            if (r < nr) acc[r] = fma(wm[r] * rinv, S, acc[r]);
+    } else {
+        double S2m, S2, Qp1, S;
+        qprime_sums_fp64<P>(qx, q2, p, S2m, S2, Qp1, S);
+        const double a = fma(dx, nx, fma(dy, ny, dz * nz));
+        const double b = fma(ex, nx, fma(ey, ny, ez * nz));
+        const double val = fma(-a, Qp1, (b - a) * S2);
+#pragma unroll
+        for (int r = 0; r < kMaxRhs; ++r)
+            if (r < nr) {
+                const double wr = wm[r] * rinv;
+                acc[r] = fma(wr, S, acc[r]);
+                acc_d[r] = fma(wr * r2inv, val, acc_d[r]);
+            }
     }
 }
 
-// The single layer for ev.n_rhs densities in one pass: the items, lanes,
-// staging and reductions of laplace_fp64_item<P, false, false>, each density
-// with its own accumulators, so that result r is bit-identical to the
-// evaluation of density r alone.  T: rows of `tile` doubles, x, y, z and
-// kMaxRhs rows of w mu (density r in row 3 + r).
-template <int P>
+// Result of density r for target j of an item: the single layer (DLP false)
+// or the double layer of a multi-density evaluation, to its output or to its
+// partial sums (part + r * rhs_part_stride) when the item is one slice.
+template <bool DLP>
+__device__ __forceinline__ void write_multi_result(const DevGeom &g, const DevEval &ev, const Item &it, int j, int r,
+                                                   double acc)
+{
+    double *const out = DLP ? ev.out_rhs_dlp[r] : ev.out_rhs[r];
+    double *const part = DLP ? ev.part_dlp : ev.part_slp;
+    if (it.part < 0) {
+        if (out) out[g.slot_tgt[it.slot_begin + j]] = acc * kInv4Pi;
+    } else if (part) {
+        part[r * ev.rhs_part_stride + it.part + j] = acc * kInv4Pi;
+    }
+}
+
+// Staging rows of a multi-density item: x, y, z, (DLP) the normal's three
+// components, then kMaxRhs rows of w mu.
+__host__ __device__ constexpr int multi_tile_rows(bool dlp) { return (dlp ? 6 : 3) + kMaxRhs; }
+
+// The single layer, and with DLP the double layer, for ev.n_rhs densities in
+// one pass: the items, lanes, staging and reductions of laplace_fp64_item<P,
+// DLP, false>, each density with its own accumulators, so that result r is
+// bit-identical to the evaluation of density r alone.  T: multi_tile_rows(DLP)
+// rows of `tile` doubles (density r's w mu in the row after the geometry's
+// plus r).
+template <int P, bool DLP>
 __device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const DevEval &ev, const Item &it,
                                                         const WalkStart &ws, double *T, const int tile,
                                                         const int lane)
@@ -338,7 +376,7 @@ __device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const 
     const int src_hi = it.src_hi;
     const int nr = ev.n_rhs;
     const int64_t stride = ev.rhs_src_stride;
-    double acc[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
+    double acc[kMaxRhs] = {0.0, 0.0, 0.0, 0.0}, acc_d[kMaxRhs] = {0.0, 0.0, 0.0, 0.0};
     if (it.n_tgt == 1) {                                   // direct loads, all 32 lanes
         const double4_32a c = g.slot_c[it.slot_begin];
         const double4_32a e = g.slot_e[it.slot_begin];
@@ -351,13 +389,20 @@ __device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const 
 #pragma unroll
             for (int r = 0; r < kMaxRhs; ++r) wm[r] = ok && r < nr ? ev.wmu[r * stride + s] : 0.0;
             const double4_32a pw = g.src_pw[s];
-            pair_fp64_multi<P>(pw.x - c.x, pw.y - c.y, pw.z - c.z, e.x, e.y, e.z, e.w, wm, acc, nr, ev.p);
+            double nx = 0, ny = 0, nz = 0;
+            if (DLP) { const double4_32a n = g.src_n[s]; nx = n.x; ny = n.y; nz = n.z; }
+            pair_fp64_multi<P, DLP>(pw.x - c.x, pw.y - c.y, pw.z - c.z, e.x, e.y, e.z, e.w, nx, ny, nz, wm, acc,
+                                    acc_d, nr, ev.p);
         }
 #pragma unroll
         for (int r = 0; r < kMaxRhs; ++r)
             if (r < nr) {
                 const double v = warp_sum(acc[r]);
-                if (lane == 0) write_multi_result(g, ev, it, 0, r, v);
+                const double vd = DLP ? warp_sum(acc_d[r]) : 0.0;
+                if (lane == 0) {
+                    write_multi_result<false>(g, ev, it, 0, r, v);
+                    if (DLP) write_multi_result<true>(g, ev, it, 0, r, vd);
+                }
             }
         return;
     }
@@ -371,7 +416,10 @@ __device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const 
         cx = c.x; cy = c.y; cz = c.z;
         ex = e.x; ey = e.y; ez = e.z; rho2 = e.w;
     }
-    double *const Tx = T, *const Ty = T + tile, *const Tz = T + 2 * tile, *const Tw = T + 3 * tile;
+    constexpr int kGeomRows = DLP ? 6 : 3;
+    double *const Tx = T, *const Ty = T + tile, *const Tz = T + 2 * tile;
+    double *const Nx = T + 3 * tile, *const Ny = T + 4 * tile, *const Nz = T + 5 * tile;   // DLP only
+    double *const Tw = T + kGeomRows * tile;
     for (int base = it.src_lo; base < src_hi; base += tile) {
         const int cnt = min(tile, src_hi - base);
         for (int k = lane; k < cnt; k += 32) {
@@ -380,6 +428,10 @@ __device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const 
             if (!ok) { atomicOr(ev.status, 1); s = 0; }
             const double4_32a pw = g.src_pw[s];
             Tx[k] = pw.x; Ty[k] = pw.y; Tz[k] = pw.z;
+            if (DLP) {
+                const double4_32a n = g.src_n[s];
+                Nx[k] = n.x; Ny[k] = n.y; Nz[k] = n.z;
+            }
 #pragma unroll
             for (int r = 0; r < kMaxRhs; ++r)
                 if (r < nr) Tw[r * tile + k] = ok ? ev.wmu[r * stride + s] : 0.0;
@@ -390,7 +442,9 @@ __device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const 
                 double wm[kMaxRhs];
 #pragma unroll
                 for (int r = 0; r < kMaxRhs; ++r) wm[r] = r < nr ? Tw[r * tile + k] : 0.0;
-                pair_fp64_multi<P>(Tx[k] - cx, Ty[k] - cy, Tz[k] - cz, ex, ey, ez, rho2, wm, acc, nr, ev.p);
+                pair_fp64_multi<P, DLP>(Tx[k] - cx, Ty[k] - cy, Tz[k] - cz, ex, ey, ez, rho2,
+                                        DLP ? Nx[k] : 0.0, DLP ? Ny[k] : 0.0, DLP ? Nz[k] : 0.0, wm, acc, acc_d,
+                                        nr, ev.p);
             }
         }
         __syncwarp();
@@ -399,7 +453,11 @@ __device__ __forceinline__ void laplace_fp64_multi_item(const DevGeom &g, const 
     for (int r = 0; r < kMaxRhs; ++r)
         if (r < nr) {
             const double v = segment_sum(acc[r], sub, L);
-            if (active && sub == 0) write_multi_result(g, ev, it, j, r, v);
+            const double vd = DLP ? segment_sum(acc_d[r], sub, L) : 0.0;
+            if (active && sub == 0) {
+                write_multi_result<false>(g, ev, it, j, r, v);
+                if (DLP) write_multi_result<true>(g, ev, it, j, r, vd);
+            }
         }
 }
 

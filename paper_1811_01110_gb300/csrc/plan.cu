@@ -179,12 +179,21 @@ double staging_weight(const tsqbx_plan_s *P)
 // FP64 items inside the double-float launch (tsqbx_options.fp64_share).
 bool has_both_pipes(int kernel, int precision) { return kernel == TSQBX_LAPLACE && precision == TSQBX_DF64; }
 // Several densities per evaluation (tsqbx_options.max_rhs > 1,
-// tsqbx_submit_multi): the single layer of Helmholtz plans and of Laplace
-// plans in FP64 or double-float.
+// tsqbx_submit_multi_layers): the single layer of Helmholtz plans; the single
+// and/or double layer (no S') of Laplace plans in FP64 or double-float.
 bool multi_ok(const tsqbx_options &o)
 {
-    return o.layers == TSQBX_SLP &&
-           (o.kernel == TSQBX_HELMHOLTZ || (o.kernel == TSQBX_LAPLACE && o.precision != TSQBX_MIXED));
+    if (o.kernel == TSQBX_HELMHOLTZ) return o.layers == TSQBX_SLP;
+    return o.kernel == TSQBX_LAPLACE && o.precision != TSQBX_MIXED && o.layers != 0 &&
+           !(o.layers & ~(uint32_t)(TSQBX_SLP | TSQBX_DLP));
+}
+
+// Forget the per-density outputs of a multi-density call.
+void reset_multi(Slot &slot)
+{
+    slot.n_rhs = 1;
+    for (auto &l : slot.copy_out_rhs)
+        for (bool &c : l) c = false;
 }
 
 int validate(const tsqbx_geometry *G, const tsqbx_options *o)
@@ -316,7 +325,8 @@ void apply_schedule(tsqbx_plan P, Schedule &&s)
     for (Slot &sl : P->slots) {
         if (s.n_parts && (P->opt.layers & TSQBX_SLP))
             sl.d_part[0] = P->dalloc<double>(part_doubles * (size_t)rhs_capacity(P->opt));
-        if (s.n_parts && (P->opt.layers & TSQBX_DLP)) sl.d_part[1] = P->dalloc<double>(part_doubles);
+        if (s.n_parts && (P->opt.layers & TSQBX_DLP))
+            sl.d_part[1] = P->dalloc<double>(part_doubles * (size_t)rhs_capacity(P->opt));
         if (s.n_parts && (P->opt.layers & TSQBX_SP)) sl.d_part[2] = P->dalloc<double>(part_doubles);
     }
     P->sched = std::move(s);
@@ -388,16 +398,17 @@ int enqueue(tsqbx_plan P, Slot &slot, const void *d_density, double *d_slp, doub
     return TSQBX_OK;
 }
 
-// Enqueue one evaluation of the single layer for n densities (the first at
-// d_density, the others at steps of density_bytes, or the n pointers
-// d_densities) into d_outs[r]: w mu of each density, the multi-density
-// expansion kernel of the plan's kernel and precision, and the slice combine
-// per density.
+// Enqueue one evaluation for n densities (the first at d_density, the others
+// at steps of density_bytes, or the n pointers d_densities) of the plan's
+// single layer into d_outs[0][r] and, for Laplace, its double layer into
+// d_outs[1][r]: w mu of each density, the multi-density expansion kernel of
+// the plan's kernel and precision, and the slice combine per density.
 int enqueue_multi(tsqbx_plan P, Slot &slot, int n, const void *d_density, const void *const *d_densities,
-                  double *const *d_outs, cudaStream_t s, int p, double k)
+                  double *const (&d_outs)[2][kMaxRhs], cudaStream_t s, int p, double k)
 {
     const tsqbx_options &o = P->opt;
     const bool helm = o.kernel == TSQBX_HELMHOLTZ;
+    const bool slp = (o.layers & TSQBX_SLP) != 0, dlp = !helm && (o.layers & TSQBX_DLP) != 0;
     const int64_t ns = P->g.n_src;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((ns + threads - 1) / threads, (int64_t)P->n_sm * 16);
@@ -415,8 +426,10 @@ int enqueue_multi(tsqbx_plan P, Slot &slot, int n, const void *d_density, const 
     }
     DevEval ev;
     ev.status = slot.d_status;
-    ev.out_slp = d_outs[0];
-    ev.part_slp = slot.d_part[0];
+    ev.out_slp = slp ? d_outs[0][0] : nullptr;
+    ev.out_dlp = dlp ? d_outs[1][0] : nullptr;
+    ev.part_slp = slp ? slot.d_part[0] : nullptr;
+    ev.part_dlp = dlp ? slot.d_part[1] : nullptr;
     ev.k = k;
     ev.p = p;
     ev.wmu = static_cast<const double *>(slot.d_wmu);
@@ -424,21 +437,26 @@ int enqueue_multi(tsqbx_plan P, Slot &slot, int n, const void *d_density, const 
     ev.n_rhs = n;
     ev.rhs_src_stride = ns;
     ev.rhs_part_stride = (helm ? 2 : 1) * P->g.n_parts;
-    for (int r = 0; r < n; ++r) ev.out_rhs[r] = d_outs[r];
+    for (int r = 0; r < n; ++r) {
+        ev.out_rhs[r] = slp ? d_outs[0][r] : nullptr;
+        ev.out_rhs_dlp[r] = dlp ? d_outs[1][r] : nullptr;
+    }
+    const unsigned layers = (slp ? TSQBX_SLP : 0u) | (dlp ? TSQBX_DLP : 0u);
     int rc;
     if (helm)
         rc = n == 1 ? launch_helmholtz_fp64(p, TSQBX_SLP, P->g, ev, s) : launch_helmholtz_multi(p, P->g, ev, s);
     else if (o.precision == TSQBX_DF64)
-        rc = n == 1 ? launch_laplace_df64(p, TSQBX_SLP, P->g, ev, s) : launch_laplace_df64_multi(p, P->g, ev, s);
+        rc = n == 1 ? launch_laplace_df64(p, layers, P->g, ev, s) : launch_laplace_df64_multi(p, dlp, P->g, ev, s);
     else
-        rc = n == 1 ? launch_laplace_fp64(p, TSQBX_SLP, P->g, ev, s) : launch_laplace_fp64_multi(p, P->g, ev, s);
+        rc = n == 1 ? launch_laplace_fp64(p, layers, P->g, ev, s) : launch_laplace_fp64_multi(p, dlp, P->g, ev, s);
     if (rc != 0) return status_of((cudaError_t)rc);
     if (P->g.n_combine > 0) {
         const int64_t th = P->g.n_combine * 32;
         const int cb = (int)std::min<int64_t>((th + 255) / 256, (int64_t)P->n_sm * 8);
         for (int r = 0; r < n; ++r) {
-            combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp + r * ev.rhs_part_stride, nullptr, nullptr,
-                                              d_outs[r], nullptr, nullptr, helm ? 2 : 1);
+            combine_kernel<<<cb, 256, 0, s>>>(P->g, ev.part_slp ? ev.part_slp + r * ev.rhs_part_stride : nullptr,
+                                              ev.part_dlp ? ev.part_dlp + r * ev.rhs_part_stride : nullptr,
+                                              nullptr, ev.out_rhs[r], ev.out_rhs_dlp[r], nullptr, helm ? 2 : 1);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return status_of(e);
         }
@@ -463,7 +481,7 @@ tsqbx_plan_s::~tsqbx_plan_s()
 
 extern "C" {
 
-int tsqbx_version(void) { return 10400; }
+int tsqbx_version(void) { return 10500; }
 
 const char *tsqbx_last_error(void) { return t_last_error; }
 
@@ -716,20 +734,22 @@ int tsqbx_plan_create(const tsqbx_geometry *G, const tsqbx_options *o, tsqbx_pla
         for (auto &s : P->slots) {
             ck(cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, prio));
             ck(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
-            // density, w mu and single-layer buffers hold rhs_capacity densities
-            // (tsqbx_submit_multi), one after another
+            // density, w mu, single- and double-layer buffers hold
+            // rhs_capacity densities (tsqbx_submit_multi_layers), one after
+            // another
             const size_t R = (size_t)rhs_capacity(*o);
             s.d_density = P->dalloc<char>(R * P->density_bytes);
             s.d_wmu = P->dalloc<char>(R * P->wmu_bytes);
             if (o->layers & TSQBX_SLP)
                 s.d_out[0] = reinterpret_cast<double *>(P->dalloc<char>(R * P->out_bytes));
-            if (o->layers & TSQBX_DLP) s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
+            if (o->layers & TSQBX_DLP)
+                s.d_out[1] = reinterpret_cast<double *>(P->dalloc<char>(R * P->out_bytes));
             if (o->layers & TSQBX_SP) s.d_out[2] = reinterpret_cast<double *>(P->dalloc<char>(P->out_bytes));
             s.d_status = P->dalloc<int>(1);
             if (P->conv_coef_doubles) s.d_conv = P->dalloc<double>(P->conv_coef_doubles);
             s.h_density = P->halloc(R * P->density_bytes);
             s.h_out[0] = P->halloc(R * P->out_bytes);
-            s.h_out[1] = P->halloc(P->out_bytes);
+            s.h_out[1] = P->halloc(R * P->out_bytes);
             if (o->layers & TSQBX_SP) s.h_out[2] = P->halloc(P->out_bytes);
             s.h_status = static_cast<int *>(P->halloc(sizeof(int)));
         }
@@ -1020,8 +1040,7 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
     }
     void *outs[3] = {out_slp, out_dlp, out_sp};
     double *d_outs[3] = {nullptr, nullptr, nullptr};
-    slot.n_rhs = 1;
-    for (bool &c : slot.copy_out_rhs) c = false;
+    reset_multi(slot);
     for (int l = 0; l < 3; ++l) {
         slot.user_out[l] = outs[l];
         slot.copy_out[l] = false;
@@ -1041,10 +1060,13 @@ int start(tsqbx_plan P, Slot &slot, const void *density, void *out_slp, void *ou
     return TSQBX_OK;
 }
 
-// The same for n densities of a single-layer plan (tsqbx_submit_multi):
+// The same for n densities of a multi-density plan (tsqbx_submit_multi_layers):
 // host densities are staged one after another in the slot's buffers, host
-// outputs come back through the slot's single-layer staging.
-int start_multi(tsqbx_plan P, Slot &slot, int n, const void *const *density, void *const *out_slp, int p, double k)
+// outputs come back through the slot's single- and double-layer staging.
+// outs[0] / outs[1]: the single- / double-layer outputs (arrays of n
+// pointers; read only for the layers of the plan's mask).
+int start_multi(tsqbx_plan P, Slot &slot, int n, const void *const *density, void *const *const (&outs)[2], int p,
+                double k)
 {
     const void *dens[kMaxRhs];
     for (int r = 0; r < n; ++r) {
@@ -1057,25 +1079,30 @@ int start_multi(tsqbx_plan P, Slot &slot, int n, const void *const *density, voi
             dens[r] = d;
         }
     }
-    double *d_outs[kMaxRhs];
+    double *d_outs[2][kMaxRhs] = {};
+    const uint32_t mask[2] = {TSQBX_SLP, TSQBX_DLP};
     slot.n_rhs = n;
     for (int l = 0; l < 3; ++l) {
         slot.user_out[l] = nullptr;
         slot.copy_out[l] = false;
     }
-    for (int r = 0; r < n; ++r) {
-        slot.user_out_rhs[r] = out_slp[r];
-        slot.copy_out_rhs[r] = !is_device_ptr(out_slp[r]);
-        d_outs[r] = slot.copy_out_rhs[r] ? slot.d_out[0] + (size_t)r * (P->out_bytes / sizeof(double))
-                                         : static_cast<double *>(out_slp[r]);
+    for (int l = 0; l < 2; ++l) {
+        if (!(P->opt.layers & mask[l])) continue;
+        for (int r = 0; r < n; ++r) {
+            slot.user_out_rhs[l][r] = outs[l][r];
+            slot.copy_out_rhs[l][r] = !is_device_ptr(outs[l][r]);
+            d_outs[l][r] = slot.copy_out_rhs[l][r] ? slot.d_out[l] + (size_t)r * (P->out_bytes / sizeof(double))
+                                                   : static_cast<double *>(outs[l][r]);
+        }
     }
     ck(cudaMemsetAsync(slot.d_status, 0, sizeof(int), slot.stream));
     int rc = enqueue_multi(P, slot, n, nullptr, dens, d_outs, slot.stream, p, k);
     if (rc) return rc;
-    for (int r = 0; r < n; ++r)
-        if (slot.copy_out_rhs[r] && P->out_bytes)
-            ck(cudaMemcpyAsync(static_cast<char *>(slot.h_out[0]) + (size_t)r * P->out_bytes, d_outs[r],
-                               P->out_bytes, cudaMemcpyDeviceToHost, slot.stream));
+    for (int l = 0; l < 2; ++l)
+        for (int r = 0; r < n; ++r)
+            if (slot.copy_out_rhs[l][r] && P->out_bytes)
+                ck(cudaMemcpyAsync(static_cast<char *>(slot.h_out[l]) + (size_t)r * P->out_bytes, d_outs[l][r],
+                                   P->out_bytes, cudaMemcpyDeviceToHost, slot.stream));
     ck(cudaMemcpyAsync(slot.h_status, slot.d_status, sizeof(int), cudaMemcpyDeviceToHost, slot.stream));
     ck(cudaEventRecord(slot.done, slot.stream));
     return TSQBX_OK;
@@ -1085,12 +1112,12 @@ int finish(tsqbx_plan P, Slot &slot)
 {
     for (int l = 0; l < 3; ++l)
         if (slot.copy_out[l]) std::memcpy(slot.user_out[l], slot.h_out[l], P->out_bytes);
-    for (int r = 0; r < slot.n_rhs; ++r)          // outputs of a tsqbx_submit_multi call
-        if (slot.copy_out_rhs[r])
-            std::memcpy(slot.user_out_rhs[r], static_cast<char *>(slot.h_out[0]) + (size_t)r * P->out_bytes,
-                        P->out_bytes);
-    slot.n_rhs = 1;
-    for (bool &c : slot.copy_out_rhs) c = false;
+    for (int l = 0; l < 2; ++l)                   // outputs of a multi-density call
+        for (int r = 0; r < slot.n_rhs; ++r)
+            if (slot.copy_out_rhs[l][r])
+                std::memcpy(slot.user_out_rhs[l][r],
+                            static_cast<char *>(slot.h_out[l]) + (size_t)r * P->out_bytes, P->out_bytes);
+    reset_multi(slot);
     return *slot.h_status ? TSQBX_E_KERNEL : TSQBX_OK;
 }
 
@@ -1181,14 +1208,16 @@ int tsqbx_submit_pk(tsqbx_plan P, int p, double k, const void *density, void *ou
     }
 }
 
-int tsqbx_submit_multi(tsqbx_plan P, int p, double k, int n, const void *const *density, void *const *out_slp,
-                       uint64_t *ticket)
+int tsqbx_submit_multi_layers(tsqbx_plan P, int p, double k, int n, const void *const *density,
+                              void *const *out_slp, void *const *out_dlp, uint64_t *ticket)
 {
-    if (!P || !ticket || !density || !out_slp || n < 1 || n > rhs_capacity(P->opt) || !pk_ok(P, p, k))
-        return TSQBX_E_INVAL;
+    if (!P || !ticket || !density || n < 1 || n > rhs_capacity(P->opt) || !pk_ok(P, p, k)) return TSQBX_E_INVAL;
     if (!multi_ok(P->opt) || P->g.n_conv_centers > 0) return TSQBX_E_UNSUPPORTED;
+    const bool slp = (P->opt.layers & TSQBX_SLP) != 0, dlp = (P->opt.layers & TSQBX_DLP) != 0;
+    if ((slp && !out_slp) || (dlp && !out_dlp)) return TSQBX_E_INVAL;
     for (int r = 0; r < n; ++r)
-        if ((P->g.n_src && !density[r]) || (P->g.n_tgt && !out_slp[r])) return TSQBX_E_INVAL;
+        if ((P->g.n_src && !density[r]) || (P->g.n_tgt && ((slp && !out_slp[r]) || (dlp && !out_dlp[r]))))
+            return TSQBX_E_INVAL;
     try {
         DeviceGuard dg(P->opt.device);
         std::lock_guard<std::mutex> lk(P->mu);
@@ -1197,10 +1226,10 @@ int tsqbx_submit_multi(tsqbx_plan P, int p, double k, int n, const void *const *
             if (!P->slots[i].busy) { idx = (int)i; break; }
         if (idx < 0) return TSQBX_E_BUSY;
         Slot &slot = P->slots[idx];
-        int rc = start_multi(P, slot, n, density, out_slp, p, k);
+        void *const *const outs[2] = {out_slp, out_dlp};
+        int rc = start_multi(P, slot, n, density, outs, p, k);
         if (rc) {
-            slot.n_rhs = 1;
-            for (bool &c : slot.copy_out_rhs) c = false;
+            reset_multi(slot);
             return rc;
         }
         slot.busy = true;
@@ -1217,6 +1246,12 @@ int tsqbx_submit_multi(tsqbx_plan P, int p, double k, int n, const void *const *
     } catch (...) {
         return TSQBX_E_CUDA;
     }
+}
+
+int tsqbx_submit_multi(tsqbx_plan P, int p, double k, int n, const void *const *density, void *const *out_slp,
+                       uint64_t *ticket)
+{
+    return tsqbx_submit_multi_layers(P, p, k, n, density, out_slp, nullptr, ticket);
 }
 
 int tsqbx_submit(tsqbx_plan P, const void *density, void *out_slp, void *out_dlp, uint64_t *ticket)

@@ -106,11 +106,11 @@ struct Slot {
     uint64_t ticket = 0;
     void *user_out[3] = {nullptr, nullptr, nullptr};
     bool copy_out[3] = {false, false, false};
-    // densities 1..n_rhs-1 of a tsqbx_submit_multi call (their single-layer
-    // outputs; density 0 uses user_out[0] / copy_out[0])
+    // outputs of a tsqbx_submit_multi / tsqbx_submit_multi_layers call:
+    // layer l (0 single, 1 double) of density r
     int n_rhs = 1;
-    void *user_out_rhs[kMaxRhs] = {nullptr, nullptr, nullptr, nullptr};
-    bool copy_out_rhs[kMaxRhs] = {false, false, false, false};
+    void *user_out_rhs[2][kMaxRhs] = {};
+    bool copy_out_rhs[2][kMaxRhs] = {};
 };
 
 }  // namespace tsqbx

@@ -10,10 +10,10 @@
 //  * continuous batching: every started request runs on its own plan slot
 //    (own stream), so requests that arrive while others are on the GPU overlap
 //    with them; completions free slots for the next queued requests.  Queued
-//    single-layer requests (Helmholtz, or Laplace in FP64 or double-float)
-//    that share a plan, an order and (Helmholtz) a wavenumber start together
-//    as one multi-density evaluation (tsqbx_submit_multi), which costs little
-//    more than one of them;
+//    requests (Helmholtz single layer; Laplace single and/or double layer in
+//    FP64 or double-float) that share a plan, an order and (Helmholtz) a
+//    wavenumber start together as one multi-density evaluation
+//    (tsqbx_submit_multi_layers), which costs little more than one of them;
 //  * accounting: latency (arrival to completion) per request, p50/p99,
 //    pair-terms completed, plans created/evicted, resident bytes.
 #include <algorithm>
@@ -75,17 +75,19 @@ struct Request {
     std::vector<Request *> merged;   // queued requests that ride in this one's evaluation
 };
 
-// Densities a single-layer evaluation of the server may carry: queued requests
-// with the same plan, order and (Helmholtz) wavenumber are started together
-// (tsqbx_submit_multi) when a slot frees up.
+// Densities one evaluation of the server may carry: queued requests with the
+// same plan, order and (Helmholtz) wavenumber are started together
+// (tsqbx_submit_multi_layers) when a slot frees up.
 constexpr int kServerMaxRhs = 4;
 
-// Helmholtz single layer, or Laplace single layer in FP64 or double-float
-// (the plans tsqbx_submit_multi takes), without conventional centers.
+// The plans tsqbx_submit_multi_layers takes -- Helmholtz single layer;
+// Laplace single and/or double layer in FP64 or double-float -- without
+// conventional centers.
 bool mergeable(const tsqbx_options &o)
 {
-    return o.layers == TSQBX_SLP &&
-           (o.kernel == TSQBX_HELMHOLTZ || (o.kernel == TSQBX_LAPLACE && o.precision != TSQBX_MIXED)) &&
+    const bool laplace_ok = o.kernel == TSQBX_LAPLACE && o.precision != TSQBX_MIXED && o.layers != 0 &&
+                            !(o.layers & ~(uint32_t)(TSQBX_SLP | TSQBX_DLP));
+    return (laplace_ok || (o.kernel == TSQBX_HELMHOLTZ && o.layers == TSQBX_SLP)) &&
            !(o.flags & (TSQBX_FLAG_CONVENTIONAL_AUTO | TSQBX_FLAG_CONVENTIONAL_ALL));
 }
 
@@ -101,7 +103,8 @@ size_t estimate_bytes(const GeomCopy &g, const tsqbx_options &o)
     if (mixed) b += ns * 48 + nt * 48;
     const int slots = (o.n_slots ? o.n_slots : 2) + 1;
     const size_t rhs = o.max_rhs > 1 ? (size_t)o.max_rhs : 1;
-    b += (size_t)slots * rhs * (ns * (helm ? 32 : 16) + nt * 16 * (helm ? 2 : 1));
+    b += (size_t)slots * rhs *
+         (ns * (helm ? 32 : 16) + nt * 16 * (helm ? 2 : 1) + ((o.layers & TSQBX_DLP) ? nt * 16 : 0));
     return b;
 }
 
@@ -199,12 +202,14 @@ bool tsqbx_server_s::admit(Request *r)
     int rc;
     if (group.size() > 1) {
         const void *dens[kServerMaxRhs];
-        void *outs[kServerMaxRhs];
+        void *outs[kServerMaxRhs], *outs_dlp[kServerMaxRhs];
         for (size_t i = 0; i < group.size(); ++i) {
             dens[i] = group[i]->density.data();
             outs[i] = group[i]->out_slp;
+            outs_dlp[i] = group[i]->out_dlp;
         }
-        rc = tsqbx_submit_multi(pe.plan, r->opt.p, r->opt.k, (int)group.size(), dens, outs, &r->ticket);
+        rc = tsqbx_submit_multi_layers(pe.plan, r->opt.p, r->opt.k, (int)group.size(), dens, outs, outs_dlp,
+                                       &r->ticket);
     } else {
         rc = tsqbx_submit_pk(pe.plan, r->opt.p, r->opt.k, r->density.data(), r->out_slp, r->out_dlp, r->out_sp,
                              &r->ticket);

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_strerror_and_version(L):
     import paper_1811_01110_gb300 as pkg
-    assert L.tsqbx_version() >= 10400          # 1.4: several densities for Laplace single-layer plans
+    assert L.tsqbx_version() >= 10500          # 1.5: tsqbx_submit_multi_layers
     for code in range(-10, 2):
         assert pkg.strerror(code) != "unknown status"
     assert pkg.strerror(-100) == "unknown status"
@@ -104,10 +104,11 @@ def test_more_invalid_options_rejected_on_host(L):
         assert _create(g, tile_depth=depth) == -1
     for rhs in (-1, 5):                                    # densities per evaluation: 0..4
         assert _create(g, kernel="helmholtz", k=1.0, max_rhs=rhs) == -1
-    # several densities: the single layer only, Helmholtz or Laplace FP64 / df64
-    assert _create(g, layers=("slp", "dlp"), max_rhs=2) == -9
+    # several densities: the Helmholtz single layer, the Laplace single and/or
+    # double layer in FP64 or df64 (no S', no mixed)
     assert _create(g, precision="mixed", max_rhs=2) == -9
     assert _create(g, precision="df64", layers=("slp", "sp"), max_rhs=2) == -9
+    assert _create(g, layers=("slp", "dlp", "sp"), max_rhs=2) == -9
     assert _create(g, kernel="helmholtz", k=1.0, layers=("slp", "dlp"), max_rhs=2) == -9
     for unroll in (-1, 3, 8):                              # order-loop forms: 0, 1, 2 or 4
         assert _create(g, p_unroll=unroll) == -1
@@ -236,6 +237,7 @@ def test_submit_multi_rejects_null_on_host(L):
     from paper_1811_01110_gb300 import _lib
     t = ctypes.c_uint64()
     assert L.tsqbx_submit_multi(None, 3, 1.0, 2, None, None, ctypes.byref(t)) == _lib.TSQBX_E_INVAL
+    assert L.tsqbx_submit_multi_layers(None, 3, 1.0, 2, None, None, None, ctypes.byref(t)) == _lib.TSQBX_E_INVAL
 
 
 def test_pipe_peak_probe_rejects_null_on_host(L):
