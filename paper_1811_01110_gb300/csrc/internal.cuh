@@ -153,7 +153,7 @@ __device__ __forceinline__ WalkStart walk_start_of(const DevGeom &g, const Item 
 
 // Highest expansion order (TSQBX_P_MAX in tsqbx.h; plan.cu checks that they agree).
 constexpr int kPMax = 20;
-// Most densities one evaluation may carry (tsqbx_submit_multi).
+// Most densities one evaluation may carry (tsqbx_submit_multi_layers).
 constexpr int kMaxRhs = 4;
 
 // Per-evaluation buffers (device pointers).
