@@ -45,7 +45,7 @@ def derived_peaks(sm_count):
             "source": f"derived: {sm_count} SMs x (2 | 128) FMA/clk x 2 flop x {SM_MAX_MHZ:.0f} MHz"}
 
 
-def survey_flops_per_pair(p, dlp=True):
+def a_priori_flops_per_pair(p, dlp=True):
     """The a priori count of the Laplace kernel's work per pair (FMA = 2):
     6p + 20 for the single layer (geometry about 20, about 6 per order), plus
     4 per pair-term (p + 1 of them) and 20 per pair for the double layer.
@@ -971,7 +971,7 @@ def main():
             rf = roofline(fl * info["n_pairs"], kavg, "fp64" if prec == "fp64" else "fp32",
                           ("laplace", prec, "slp+dlp"))
             # the same launch counted with the a priori per-pair estimate
-            sf = survey_flops_per_pair(P) + (flops_per_pair(P, prec) - flops_per_pair(P, "fp64"))
+            sf = a_priori_flops_per_pair(P) + (flops_per_pair(P, prec) - flops_per_pair(P, "fp64"))
             sa = sf * info["n_pairs"] / kavg / 1e12
             rf["a_priori_count"] = {"flops_per_pair": sf, "achieved": sa, "frac": sa / rf["peak"]}
         rf["flops_per_pair"] = fl

@@ -122,8 +122,8 @@ def test_df64_and_a_priori_flop_counts():
     sys.path.insert(0, ROOT)
     import bench
     # the a priori estimate: 6p + 20 single layer, + 4 per pair-term + 20 double layer
-    assert bench.survey_flops_per_pair(9) == 134
-    assert bench.survey_flops_per_pair(9, dlp=False) == 74
+    assert bench.a_priori_flops_per_pair(9) == 134
+    assert bench.a_priori_flops_per_pair(9, dlp=False) == 74
     # double-float FP32 flops per pair at p = 9: 1016 with both layers, 716 single layer, +104 for S'
     assert bench.df64_fp32_flops_per_pair(9) == 1016
     assert bench.df64_fp32_flops_per_pair(9, dlp=False) == 716
