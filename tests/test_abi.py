@@ -105,7 +105,13 @@ def test_more_invalid_options_rejected_on_host(L):
     for rhs in (-1, 5):                                    # densities per evaluation: 0..4
         assert _create(g, kernel="helmholtz", k=1.0, max_rhs=rhs) == -1
     # several densities: the Helmholtz single layer, the Laplace single and/or
-    # double layer in FP64 or df64 (no S', no mixed)
+    # double layer in FP64 or df64 (no S', no mixed).  The accepted
+    # combinations pass validation and stop only at the missing device
+    # (TSQBX_E_CUDA, -4, on a machine without a GPU).
+    for kw in (dict(max_rhs=2), dict(layers=("slp", "dlp"), max_rhs=3), dict(layers=("dlp",), max_rhs=4),
+               dict(precision="df64", layers=("slp", "dlp"), max_rhs=4),
+               dict(kernel="helmholtz", k=1.0, max_rhs=4)):
+        assert _create(g, **kw) not in (-1, -9), kw
     assert _create(g, precision="mixed", max_rhs=2) == -9
     assert _create(g, precision="df64", layers=("slp", "sp"), max_rhs=2) == -9
     assert _create(g, layers=("slp", "dlp", "sp"), max_rhs=2) == -9
