@@ -203,6 +203,27 @@ def test_laplace_multi_sliced_lists_single_targets(pkg, precision, p_unroll, sha
                 assert _relerr(o[l], ref[l]) <= 1e-12, l
 
 
+@pytest.mark.parametrize("precision,p_unroll,share", LAPLACE_FORMS)
+@pytest.mark.parametrize("layers", LAPLACE_LAYERS)
+def test_laplace_multi_four_densities_deepest_tile(pkg, precision, p_unroll, share, layers):
+    """The largest staging footprint: four densities at staging depth 128
+    (the double-float double layer then fills 48 KB of shared memory per
+    block)."""
+    rng = np.random.default_rng(53 + p_unroll + share + len(layers))
+    g = cloud_geometry(rng, n_ctr=6, n_src=700, q_max=0.5, tgt_per_ctr=6, list_frac=0.9)
+    dens = _real_densities(rng, g.n_src, 4)
+    with pkg.Plan(g, "laplace", layers, p=9, precision=precision, max_rhs=4, tile_depth=128, p_unroll=p_unroll,
+                  fp64_share=share) as plan:
+        t, outs = plan.submit_multi(dens)
+        assert pkg.poll(t, -1)
+        for d, o in zip(dens, outs):
+            alone = plan.eval(d)
+            ref = _laplace_ref(g, 9, d, layers)
+            for l in layers:
+                assert np.array_equal(o[l], alone[l]), l
+                assert _relerr(o[l], ref[l]) <= 1e-12, l
+
+
 @pytest.mark.parametrize("precision", ["fp64", "df64"])
 @pytest.mark.parametrize("layers", [("slp",), ("slp", "dlp")])
 def test_laplace_multi_device_buffers_and_slot_reuse(pkg, precision, layers):
