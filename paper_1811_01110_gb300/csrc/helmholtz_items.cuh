@@ -339,6 +339,8 @@ int launch_helm_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
     if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
+    static_assert((size_t)kWarpsPerBlock * helmholtz_tile_rows(true) * kTileMax * sizeof(double) <= kSmemNoOptIn,
+                  "staging tiles fit the default shared memory");
     const size_t smem = (size_t)kWarpsPerBlock * helmholtz_tile_rows(dlp) * g.tile * sizeof(double);
     if (dlp) helmholtz_kernel<P, true, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
     else     helmholtz_kernel<P, false, SP><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
@@ -360,6 +362,9 @@ int launch_helm_multi_p(const DevGeom &g, const DevEval &e, cudaStream_t s)
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
     if (!tile_depth_ok(g.tile)) return (int)cudaErrorInvalidValue;
+    static_assert((size_t)kWarpsPerBlock * helmholtz_tile_rows(false, NRHS) * kTileMax * sizeof(double) <=
+                      kSmemNoOptIn,
+                  "staging tiles fit the default shared memory");
     const size_t smem = (size_t)kWarpsPerBlock * helmholtz_tile_rows(false, NRHS) * g.tile * sizeof(double);
     helmholtz_kernel<P, false, false, NRHS><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
     return (int)cudaGetLastError();

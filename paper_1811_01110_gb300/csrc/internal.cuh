@@ -28,6 +28,10 @@ constexpr int kWarpsPerBlock = 4;   // independent warps per CTA
 // tuning may choose any power of two in [kTileMin, kTileMax] (DevGeom::tile).
 constexpr int kTile = 64;
 constexpr int kTileMin = 32, kTileMax = 128;
+// Shared memory a block may take without opting in to more: every kernel's
+// staging tiles at the deepest depth stay within it (static_asserts beside
+// each launch), so no launch needs cudaFuncSetAttribute.
+constexpr size_t kSmemNoOptIn = 48 * 1024;
 __host__ __device__ constexpr bool tile_depth_ok(int t)
 {
     return t == 32 || t == 64 || t == 128;

@@ -197,6 +197,8 @@ int launch_df_multi_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t
 {
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
+    static_assert((size_t)kWarpsPerBlock * df_multi_rows(true) * kTileMax * sizeof(float4) <= kSmemNoOptIn,
+                  "staging tiles fit the default shared memory");
     const size_t smem = (size_t)kWarpsPerBlock * df_multi_rows(dlp) * g.tile * sizeof(float4);
     const unsigned b = (unsigned)blocks, t = kWarpsPerBlock * 32;
     if (dlp) laplace_df_multi_kernel<P, true><<<b, t, smem, s>>>(g, e);

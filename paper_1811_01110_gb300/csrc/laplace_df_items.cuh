@@ -270,6 +270,8 @@ int launch_df_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
     if (!tile_depth_ok(g.tile) || g.fp64_share < 0 || g.fp64_share > 20) return (int)cudaErrorInvalidValue;
+    static_assert((size_t)kWarpsPerBlock * 4 * kTileMax * sizeof(float4) <= kSmemNoOptIn,
+                  "staging tiles fit the default shared memory");
     const size_t smem = (size_t)kWarpsPerBlock * (dlp ? 4 : 2) * g.tile * sizeof(float4);
     const unsigned b = (unsigned)blocks, t = kWarpsPerBlock * 32;
     if (g.fp64_share > 0) {

@@ -52,6 +52,9 @@ laplace_mixed_kernel(const DevGeom g, const DevEval ev)
 template <bool MIXED, int P, bool DLP, bool SP>
 void launch_one(unsigned blocks, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
+    static_assert((size_t)kWarpsPerBlock * tile_rows<MIXED, DLP>() * (MIXED ? (kTileMax / 2) * 16 : kTileMax * 8) <=
+                      kSmemNoOptIn,
+                  "staging tiles fit the default shared memory");
     const size_t smem = tile_smem_bytes<MIXED, DLP>(g.tile);
     if constexpr (MIXED) laplace_mixed_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
     else                 laplace_fp64_kernel<P, DLP, SP><<<blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);

@@ -32,6 +32,8 @@ int launch_multi_p(bool dlp, const DevGeom &g, const DevEval &e, cudaStream_t s)
 {
     const int64_t blocks = (g.n_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks == 0) return 0;
+    static_assert((size_t)kWarpsPerBlock * multi_tile_rows(true) * kTileMax * sizeof(double) <= kSmemNoOptIn,
+                  "staging tiles fit the default shared memory");
     const size_t smem = (size_t)kWarpsPerBlock * multi_tile_rows(dlp) * g.tile * sizeof(double);
     if (dlp) laplace_fp64_multi_kernel<P, true><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
     else     laplace_fp64_multi_kernel<P, false><<<(unsigned)blocks, kWarpsPerBlock * 32, smem, s>>>(g, e);
